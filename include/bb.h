@@ -1,0 +1,138 @@
+/*
+ * bb.h - balanced butterfly counting on one GB300 GPU (sm_103a), C ABI.
+ *
+ * Problem (paper Section "Problem Definition", Defs. 1-2): a signed
+ * bipartite graph G = (U, V, E) labels every edge + or -. A butterfly is a
+ * 4-cycle u1 - v1 - u2 - v2; it is balanced when it has an even number of
+ * negative edges. The library returns the number of balanced butterflies,
+ * the number of all butterflies, and optionally, per vertex, the number of
+ * balanced butterflies that contain it (Algorithm 3, Section "Extensions").
+ *
+ * Method (Section "Bucket Approach", Lemma 2 and Algorithm 2, made data
+ * parallel as in Algorithm 4): vertices are ranked by degree priority
+ * (Def. 4); the wedges u - v - w whose highest-priority vertex is an
+ * endpoint are bucketed by endpoint pair and by wedge type (symmetric: both
+ * edge signs equal, Def. 5; asymmetric: Def. 6); a pair with l symmetric and
+ * m asymmetric wedges holds C(l,2) + C(m,2) balanced butterflies out of
+ * C(l+m,2). All arithmetic is integer; results are exact.
+ *
+ * Input layout (every call that takes a graph):
+ *   U-side CSR. rowptr: int64[nU+1], rowptr[0] = 0, non-decreasing,
+ *   rowptr[nU] = nE. col: int32[nE], V ids in [0, nV); a row may be in any
+ *   order but must not repeat a V id (E is a set). signs: int8[nE], each +1
+ *   or -1, aligned with col.
+ * Limits: nU + nV < 2^31, every vertex degree <= 65535 (counts per vertex
+ *   pair are held in 16-bit fields), nE < 2^32.
+ *
+ * Errors: every call returns a bb_status. On error no output is written and
+ * bb_last_error() (thread-local) describes the failure. Device-side input
+ * checks report BB_ERR_INVALID_ARG like host-side ones.
+ *
+ * Ownership: pointers passed in are borrowed for the duration of the call
+ * unless stated otherwise. Objects created by the library (contexts, graphs)
+ * are released by the matching destroy/free call.
+ *
+ * Threading: a context may be used from one thread at a time, except that
+ * bb_poll may run concurrently with bb_submit.
+ */
+#ifndef BB_H
+#define BB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BB_OK = 0,
+    BB_ERR_INVALID_ARG = 1, /* NULL pointer, bad CSR, sign not +-1, duplicate edge */
+    BB_ERR_TOO_LARGE = 2,   /* beyond the limits above */
+    BB_ERR_BUDGET = 3,      /* the call would exceed the context's device memory budget */
+    BB_ERR_OOM = 4,         /* the device (or pinned host) allocation failed */
+    BB_ERR_TIMEOUT = 5,     /* a bounded wait gave up */
+    BB_ERR_OVERFLOW = 6,    /* a count does not fit in int64 */
+    BB_ERR_CUDA = 7,        /* a CUDA runtime call failed */
+    BB_ERR_NO_DEVICE = 8,   /* no usable CUDA device of compute capability 10.3 */
+    BB_ERR_BUSY = 9         /* no free request slot (bb_submit) */
+} bb_status;
+
+typedef struct bb_ctx bb_ctx;
+typedef struct bb_graph bb_graph;
+typedef uint64_t bb_ticket;
+
+/* U-side CSR of a signed bipartite graph (layout above). */
+typedef struct {
+    int64_t nU, nV, nE;
+    const int64_t *rowptr;
+    const int32_t *col;
+} bb_csr;
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *bb_last_error(void);
+
+/* Library version string. */
+const char *bb_version(void);
+
+/* ---------------------------------------------------------------- context
+ * A context binds one device, one CUDA stream and a device memory budget.
+ * device: CUDA ordinal. hbm_budget_bytes: upper bound on device memory the
+ * context may hold (0 = 90% of the device's free memory at creation). */
+bb_status bb_ctx_create(int device, uint64_t hbm_budget_bytes, bb_ctx **out);
+void bb_ctx_destroy(bb_ctx *ctx);
+
+/* Run the context's work on `stream` (a cudaStream_t of the context's
+ * device; NULL restores the context's own stream). */
+bb_status bb_ctx_set_stream(bb_ctx *ctx, void *stream);
+
+/* Device bytes the context holds now (graphs, workspaces). */
+uint64_t bb_ctx_device_bytes(const bb_ctx *ctx);
+
+/* ---------------------------------------------------------- one-shot count
+ * The whole path on one graph: validate, degree-priority relabel,
+ * sign-packed CSR build, work classification, wedge aggregation and the
+ * C(.,2) reduction (Algorithm 2 and Lemma 2 over every wedge). Blocking.
+ *
+ * bb_count_csr: csr/signs in HOST memory (pinned memory makes the copies
+ *   asynchronous); per_vertex_opt: NULL or host int64[nU+nV] (U ids, then V
+ *   ids) receiving the balanced count of each vertex.
+ * bb_count_csr_device: csr arrays, signs and per_vertex_opt in DEVICE
+ *   memory of the context's device; the buffers are only read (written for
+ *   per_vertex_opt) on the context's stream, during the call.
+ * wedges_opt: NULL or receives the number of wedges aggregated.
+ * The workspace grows to the largest graph seen and is reused. */
+bb_status bb_count_csr(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int64_t *balanced,
+                       int64_t *total, int64_t *per_vertex_opt, int64_t *wedges_opt);
+bb_status bb_count_csr_device(bb_ctx *ctx, const bb_csr *csr_dev, const int8_t *signs_dev,
+                              int64_t *balanced, int64_t *total, int64_t *per_vertex_dev_opt,
+                              int64_t *wedges_opt);
+
+/* ------------------------------------------------------- resident graphs
+ * bb_graph_upload: copies a host graph to the device, builds the ranked
+ * sign-packed CSR and keeps it resident (counted against the budget).
+ * bb_graph_upload_device: the same from device buffers (borrowed for the
+ * call). */
+bb_status bb_graph_upload(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, bb_graph **out);
+bb_status bb_graph_upload_device(bb_ctx *ctx, const bb_csr *csr_dev, const int8_t *signs_dev,
+                                 bb_graph **out);
+
+/* Counts of a resident graph (wedge aggregation + reduction only). Blocking.
+ * per_vertex_opt: NULL or host int64[nU+nV] as above. */
+bb_status bb_count(bb_graph *g, int64_t *balanced, int64_t *total, int64_t *per_vertex_opt);
+
+/* Negate the sign of the listed input edges (indices into the CSR's col
+ * array, host int64[n]) in the resident graph, both directions. Repeated
+ * indices flip repeatedly. Later counts see the new signs. */
+bb_status bb_graph_flip_signs(bb_graph *g, const int64_t *edge_idx, int64_t n);
+
+/* Graph facts: vertex and edge counts, wedges the count aggregates. */
+bb_status bb_graph_info(const bb_graph *g, int64_t *nU, int64_t *nV, int64_t *nE,
+                        int64_t *wedges);
+
+void bb_graph_free(bb_graph *g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BB_H */
