@@ -40,6 +40,12 @@
 
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define BB_API __attribute__((visibility("default")))
+#else
+#define BB_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -69,24 +75,24 @@ typedef struct {
 } bb_csr;
 
 /* Message for the last failing call on this thread ("" if none). */
-const char *bb_last_error(void);
+BB_API const char *bb_last_error(void);
 
 /* Library version string. */
-const char *bb_version(void);
+BB_API const char *bb_version(void);
 
 /* ---------------------------------------------------------------- context
  * A context binds one device, one CUDA stream and a device memory budget.
  * device: CUDA ordinal. hbm_budget_bytes: upper bound on device memory the
  * context may hold (0 = 90% of the device's free memory at creation). */
-bb_status bb_ctx_create(int device, uint64_t hbm_budget_bytes, bb_ctx **out);
-void bb_ctx_destroy(bb_ctx *ctx);
+BB_API bb_status bb_ctx_create(int device, uint64_t hbm_budget_bytes, bb_ctx **out);
+BB_API void bb_ctx_destroy(bb_ctx *ctx);
 
 /* Run the context's work on `stream` (a cudaStream_t of the context's
  * device; NULL restores the context's own stream). */
-bb_status bb_ctx_set_stream(bb_ctx *ctx, void *stream);
+BB_API bb_status bb_ctx_set_stream(bb_ctx *ctx, void *stream);
 
 /* Device bytes the context holds now (graphs, workspaces). */
-uint64_t bb_ctx_device_bytes(const bb_ctx *ctx);
+BB_API uint64_t bb_ctx_device_bytes(const bb_ctx *ctx);
 
 /* ---------------------------------------------------------- one-shot count
  * The whole path on one graph: validate, degree-priority relabel,
@@ -101,9 +107,9 @@ uint64_t bb_ctx_device_bytes(const bb_ctx *ctx);
  *   per_vertex_opt) on the context's stream, during the call.
  * wedges_opt: NULL or receives the number of wedges aggregated.
  * The workspace grows to the largest graph seen and is reused. */
-bb_status bb_count_csr(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int64_t *balanced,
+BB_API bb_status bb_count_csr(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int64_t *balanced,
                        int64_t *total, int64_t *per_vertex_opt, int64_t *wedges_opt);
-bb_status bb_count_csr_device(bb_ctx *ctx, const bb_csr *csr_dev, const int8_t *signs_dev,
+BB_API bb_status bb_count_csr_device(bb_ctx *ctx, const bb_csr *csr_dev, const int8_t *signs_dev,
                               int64_t *balanced, int64_t *total, int64_t *per_vertex_dev_opt,
                               int64_t *wedges_opt);
 
@@ -112,24 +118,24 @@ bb_status bb_count_csr_device(bb_ctx *ctx, const bb_csr *csr_dev, const int8_t *
  * sign-packed CSR and keeps it resident (counted against the budget).
  * bb_graph_upload_device: the same from device buffers (borrowed for the
  * call). */
-bb_status bb_graph_upload(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, bb_graph **out);
-bb_status bb_graph_upload_device(bb_ctx *ctx, const bb_csr *csr_dev, const int8_t *signs_dev,
+BB_API bb_status bb_graph_upload(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, bb_graph **out);
+BB_API bb_status bb_graph_upload_device(bb_ctx *ctx, const bb_csr *csr_dev, const int8_t *signs_dev,
                                  bb_graph **out);
 
 /* Counts of a resident graph (wedge aggregation + reduction only). Blocking.
  * per_vertex_opt: NULL or host int64[nU+nV] as above. */
-bb_status bb_count(bb_graph *g, int64_t *balanced, int64_t *total, int64_t *per_vertex_opt);
+BB_API bb_status bb_count(bb_graph *g, int64_t *balanced, int64_t *total, int64_t *per_vertex_opt);
 
 /* Negate the sign of the listed input edges (indices into the CSR's col
  * array, host int64[n]) in the resident graph, both directions. Repeated
  * indices flip repeatedly. Later counts see the new signs. */
-bb_status bb_graph_flip_signs(bb_graph *g, const int64_t *edge_idx, int64_t n);
+BB_API bb_status bb_graph_flip_signs(bb_graph *g, const int64_t *edge_idx, int64_t n);
 
 /* Graph facts: vertex and edge counts, wedges the count aggregates. */
-bb_status bb_graph_info(const bb_graph *g, int64_t *nU, int64_t *nV, int64_t *nE,
+BB_API bb_status bb_graph_info(const bb_graph *g, int64_t *nU, int64_t *nV, int64_t *nE,
                         int64_t *wedges);
 
-void bb_graph_free(bb_graph *g);
+BB_API void bb_graph_free(bb_graph *g);
 
 #ifdef __cplusplus
 }

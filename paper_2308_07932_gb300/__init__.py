@@ -1,1 +1,229 @@
-"""Balanced butterfly counting on GB300 (placeholder; binding added below)."""
+"""Balanced butterfly counting on one GB300 GPU.
+
+A thin ctypes binding over the C ABI of ``libbb.so`` (declared in
+``include/bb.h``). Every step of the count runs in the library's CUDA
+kernels; this module only marshals arguments. There is no CPU fallback: if
+the library is not built or no sm_103 device is present, calls raise.
+
+    from paper_2308_07932_gb300 import Context, synth
+    g = synth.uniform_2k_1k()
+    with Context() as ctx:
+        balanced, total, wedges = ctx.count(g)
+
+``synth`` (seeded input graphs) has no dependency on the library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbb.so")
+
+BB_OK = 0
+STATUS = {
+    0: "BB_OK", 1: "BB_ERR_INVALID_ARG", 2: "BB_ERR_TOO_LARGE", 3: "BB_ERR_BUDGET",
+    4: "BB_ERR_OOM", 5: "BB_ERR_TIMEOUT", 6: "BB_ERR_OVERFLOW", 7: "BB_ERR_CUDA",
+    8: "BB_ERR_NO_DEVICE", 9: "BB_ERR_BUSY",
+}
+
+
+class BBError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("nU", ctypes.c_int64), ("nV", ctypes.c_int64), ("nE", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library. Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        S = ctypes.c_int
+        sig = {
+            "bb_last_error": (ctypes.c_char_p, []),
+            "bb_version": (ctypes.c_char_p, []),
+            "bb_ctx_create": (S, [ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(_VP)]),
+            "bb_ctx_destroy": (None, [_VP]),
+            "bb_ctx_set_stream": (S, [_VP, _VP]),
+            "bb_ctx_device_bytes": (ctypes.c_uint64, [_VP]),
+            "bb_count_csr": (S, [_VP, ctypes.POINTER(_Csr), _VP, _I64P, _I64P, _VP, _I64P]),
+            "bb_count_csr_device": (S, [_VP, ctypes.POINTER(_Csr), _VP, _I64P, _I64P, _VP, _I64P]),
+            "bb_graph_upload": (S, [_VP, ctypes.POINTER(_Csr), _VP, ctypes.POINTER(_VP)]),
+            "bb_graph_upload_device": (S, [_VP, ctypes.POINTER(_Csr), _VP, ctypes.POINTER(_VP)]),
+            "bb_count": (S, [_VP, _I64P, _I64P, _VP]),
+            "bb_graph_flip_signs": (S, [_VP, _VP, ctypes.c_int64]),
+            "bb_graph_info": (S, [_VP, _I64P, _I64P, _I64P, _I64P]),
+            "bb_graph_free": (None, [_VP]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != BB_OK:
+        raise BBError(status, lib().bb_last_error().decode(errors="replace"))
+
+
+def _host_arrays(g):
+    rowptr = np.ascontiguousarray(g.rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(g.col, dtype=np.int32)
+    sign = np.ascontiguousarray(g.sign, dtype=np.int8)
+    csr = _Csr(g.nU, g.nV, int(col.shape[0]), rowptr.ctypes.data, col.ctypes.data)
+    return csr, sign, (rowptr, col, sign)
+
+
+@dataclass
+class Counts:
+    balanced: int
+    total: int
+    wedges: int
+    per_vertex: np.ndarray | None = None
+
+    def __iter__(self):
+        yield self.balanced
+        yield self.total
+        yield self.wedges
+
+
+class Context:
+    """A device, a CUDA stream and a device memory budget (``bb_ctx``)."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0):
+        h = _VP()
+        _check(lib().bb_ctx_create(device, budget_bytes, ctypes.byref(h)))
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().bb_ctx_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def device_bytes(self) -> int:
+        return int(lib().bb_ctx_device_bytes(self._h))
+
+    def set_stream(self, stream_ptr: int | None):
+        """Run on a cudaStream_t given as an integer handle (e.g.
+        ``torch.cuda.current_stream().cuda_stream``); None = own stream."""
+        _check(lib().bb_ctx_set_stream(self._h, stream_ptr or None))
+
+    def count(self, g, per_vertex: bool = False) -> Counts:
+        """Whole path on a host graph (``bb_count_csr``)."""
+        csr, sign, keep = _host_arrays(g)
+        b, t, w = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        pv = np.zeros(g.nU + g.nV, np.int64) if per_vertex else None
+        _check(lib().bb_count_csr(self._h, ctypes.byref(csr), sign.ctypes.data, ctypes.byref(b),
+                                  ctypes.byref(t), pv.ctypes.data if pv is not None else None,
+                                  ctypes.byref(w)))
+        del keep
+        return Counts(b.value, t.value, w.value, pv)
+
+    def count_host_ptrs(self, nU: int, nV: int, nE: int, rowptr_ptr: int, col_ptr: int,
+                        sign_ptr: int) -> Counts:
+        """``bb_count_csr`` on raw host pointers (e.g. pinned tensors)."""
+        csr = _Csr(nU, nV, nE, rowptr_ptr, col_ptr)
+        b, t, w = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().bb_count_csr(self._h, ctypes.byref(csr), sign_ptr, ctypes.byref(b),
+                                  ctypes.byref(t), None, ctypes.byref(w)))
+        return Counts(b.value, t.value, w.value)
+
+    def count_device(self, nU: int, nV: int, nE: int, rowptr_ptr: int, col_ptr: int,
+                     sign_ptr: int, per_vertex_ptr: int | None = None) -> Counts:
+        """Whole path on device buffers (``bb_count_csr_device``); pointers
+        are device addresses, e.g. ``tensor.data_ptr()`` of CUDA tensors."""
+        csr = _Csr(nU, nV, nE, rowptr_ptr, col_ptr)
+        b, t, w = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().bb_count_csr_device(self._h, ctypes.byref(csr), sign_ptr, ctypes.byref(b),
+                                         ctypes.byref(t), per_vertex_ptr, ctypes.byref(w)))
+        return Counts(b.value, t.value, w.value)
+
+    def count_tensors(self, nV: int, rowptr, col, sign, per_vertex=None) -> Counts:
+        """``count_device`` on torch CUDA tensors (int64 rowptr, int32 col,
+        int8 sign; per_vertex: optional int64 CUDA tensor of nU+nV)."""
+        nU = rowptr.numel() - 1
+        return self.count_device(nU, nV, col.numel(), rowptr.data_ptr(), col.data_ptr(),
+                                 sign.data_ptr(),
+                                 per_vertex.data_ptr() if per_vertex is not None else None)
+
+    def upload(self, g) -> "Graph":
+        """Resident graph from a host graph (``bb_graph_upload``)."""
+        csr, sign, keep = _host_arrays(g)
+        h = _VP()
+        _check(lib().bb_graph_upload(self._h, ctypes.byref(csr), sign.ctypes.data, ctypes.byref(h)))
+        del keep
+        return Graph(self, h)
+
+
+class Graph:
+    """A graph kept resident on the device (``bb_graph``)."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self._h = handle
+
+    def count(self, per_vertex: bool = False) -> Counts:
+        b, t = ctypes.c_int64(), ctypes.c_int64()
+        nU, nV, nE, w = self.info()
+        pv = np.zeros(nU + nV, np.int64) if per_vertex else None
+        _check(lib().bb_count(self._h, ctypes.byref(b), ctypes.byref(t),
+                              pv.ctypes.data if pv is not None else None))
+        return Counts(b.value, t.value, w, pv)
+
+    def flip(self, edge_idx):
+        e = np.ascontiguousarray(edge_idx, dtype=np.int64)
+        _check(lib().bb_graph_flip_signs(self._h, e.ctypes.data, e.size))
+
+    def info(self):
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(lib().bb_graph_info(self._h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().bb_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def version() -> str:
+    return lib().bb_version().decode()

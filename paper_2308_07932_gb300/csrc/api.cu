@@ -1,0 +1,490 @@
+// api.cu - the C ABI declared in include/bb.h: contexts, device memory
+// budget, one-shot counts, resident graphs, errors.
+#include <algorithm>
+#include <cstdarg>
+#include <chrono>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+
+#include "../../include/bb.h"
+#include "graph.cuh"
+
+using namespace bb;
+
+namespace {
+
+thread_local std::string t_err;
+
+bb_status fail(bb_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+bb_status fail(bb_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return st;
+}
+
+bb_status cuda_fail(cudaError_t e, const char *what) {
+    cudaGetLastError();  // clear sticky-free errors
+    return fail(BB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define BB_CUDA(call, what)                                  \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);   \
+    } while (0)
+
+// Waits for all work queued so far on `s`, polling an event so that a stuck
+// device turns into BB_ERR_TIMEOUT instead of a hang of the caller.
+double g_timeout_s = 600.0;
+
+bb_status wait_bounded(cudaStream_t s, const char *what) {
+    cudaEvent_t ev;
+    BB_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event create");
+    cudaError_t e = cudaEventRecord(ev, s);
+    if (e != cudaSuccess) { cudaEventDestroy(ev); return cuda_fail(e, what); }
+    auto t0 = std::chrono::steady_clock::now();
+    int spins = 0;
+    for (;;) {
+        e = cudaEventQuery(ev);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) { cudaEventDestroy(ev); return cuda_fail(e, what); }
+        double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (dt > g_timeout_s) {
+            cudaEventDestroy(ev);
+            return fail(BB_ERR_TIMEOUT, "%s: device work did not finish within %.0f s", what,
+                        g_timeout_s);
+        }
+        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    cudaEventDestroy(ev);
+    return BB_OK;
+}
+
+bb_status check_csr(const bb_csr *csr, const int8_t *signs) {
+    if (!csr) return fail(BB_ERR_INVALID_ARG, "csr is NULL");
+    if (csr->nU < 0 || csr->nV < 0 || csr->nE < 0)
+        return fail(BB_ERR_INVALID_ARG, "negative size (nU=%lld nV=%lld nE=%lld)",
+                    (long long)csr->nU, (long long)csr->nV, (long long)csr->nE);
+    if (csr->nU + csr->nV >= ((int64_t)1 << 31))
+        return fail(BB_ERR_TOO_LARGE, "nU + nV = %lld must be below 2^31",
+                    (long long)(csr->nU + csr->nV));
+    if (csr->nE >= ((int64_t)1 << 32) - 1)
+        return fail(BB_ERR_TOO_LARGE, "nE = %lld must be below 2^32", (long long)csr->nE);
+    if (csr->nU == 0 && csr->nE != 0)
+        return fail(BB_ERR_INVALID_ARG, "nE must be 0 when nU is 0");
+    if (!csr->rowptr) return fail(BB_ERR_INVALID_ARG, "rowptr is NULL");
+    if (csr->nE > 0 && (!csr->col || !signs))
+        return fail(BB_ERR_INVALID_ARG, "col or signs is NULL");
+    return BB_OK;
+}
+
+bb_status map_build_error(uint32_t e) {
+    if (e & E_ROWPTR) return fail(BB_ERR_INVALID_ARG, "rowptr is not a valid CSR row pointer");
+    if (e & E_COL) return fail(BB_ERR_INVALID_ARG, "a column id is outside [0, nV)");
+    if (e & E_SIGN) return fail(BB_ERR_INVALID_ARG, "a sign is not +1 or -1");
+    if (e & E_DUP) return fail(BB_ERR_INVALID_ARG, "an edge is listed twice");
+    if (e & E_DEGREE) return fail(BB_ERR_TOO_LARGE, "a vertex degree exceeds %u", MAX_DEGREE);
+    if (e) return fail(BB_ERR_CUDA, "internal device check failed (0x%x)", e);
+    return BB_OK;
+}
+
+// results copied back after a count
+struct HostResult {
+    unsigned long long acc[4];
+    uint32_t count_err;
+    uint32_t build_err;
+    unsigned long long wedges;
+};
+
+}  // namespace
+
+struct bb_ctx {
+    int device = 0;
+    uint64_t budget = 0;
+    uint64_t used = 0;
+    cudaStream_t own = nullptr, stream = nullptr;
+    // one-shot workspace
+    void *ws_graph = nullptr;
+    size_t ws_graph_cap = 0;
+    void *ws_temp = nullptr;
+    size_t ws_temp_cap = 0;
+    void *ws_in = nullptr;  // device copies of host inputs (bb_count_csr)
+    size_t ws_in_cap = 0;
+    int64_t *ws_pv = nullptr;  // device per-vertex output for host requests
+    size_t ws_pv_cap = 0;
+    DevGraph oneshot;
+    int64_t layout_key[3] = {-1, -1, -1};
+    HostResult *h_res = nullptr;  // pinned
+    std::mutex mu;
+};
+
+struct bb_graph {
+    bb_ctx *ctx = nullptr;
+    DevGraph g;
+    void *mem = nullptr;
+    size_t bytes = 0;
+    void *raw = nullptr;
+    size_t raw_bytes = 0;
+};
+
+namespace {
+
+bb_status dev_alloc(bb_ctx *ctx, void **p, size_t bytes, const char *what) {
+    if (bytes == 0) bytes = 256;
+    if (ctx->used + bytes > ctx->budget)
+        return fail(BB_ERR_BUDGET, "%s: %zu bytes would exceed the budget (%llu of %llu used)",
+                    what, bytes, (unsigned long long)ctx->used, (unsigned long long)ctx->budget);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(BB_ERR_OOM, "%s: cudaMalloc(%zu) failed: %s", what, bytes,
+                    cudaGetErrorString(e));
+    }
+    ctx->used += bytes;
+    return BB_OK;
+}
+
+void dev_free(bb_ctx *ctx, void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    if (bytes == 0) bytes = 256;
+    ctx->used -= bytes;
+}
+
+// grow-only workspace buffer
+bb_status ensure(bb_ctx *ctx, void **buf, size_t *cap, size_t need, const char *what) {
+    if (*cap >= need && *buf) return BB_OK;
+    BB_CUDA(cudaStreamSynchronize(ctx->stream), "workspace sync");
+    dev_free(ctx, *buf, *cap);
+    *buf = nullptr;
+    *cap = 0;
+    size_t want = need + need / 8;  // headroom so slightly larger graphs reuse it
+    bb_status st = dev_alloc(ctx, buf, want, what);
+    if (st != BB_OK) {
+        st = dev_alloc(ctx, buf, need, what);
+        if (st != BB_OK) return st;
+        want = need;
+    }
+    *cap = want;
+    return BB_OK;
+}
+
+bb_status set_device(bb_ctx *ctx) {
+    BB_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    return BB_OK;
+}
+
+// reads back results and maps device-side errors
+bb_status finish_count(bb_ctx *ctx, const DevGraph &g, cudaStream_t s, int64_t *balanced,
+                       int64_t *total, int64_t *wedges_opt) {
+    HostResult *h = ctx->h_res;
+    BB_CUDA(cudaMemcpyAsync(h->acc, g.scratch->acc, sizeof(h->acc), cudaMemcpyDeviceToHost, s),
+            "copy counts");
+    BB_CUDA(cudaMemcpyAsync(&h->count_err, &g.scratch->err, 4, cudaMemcpyDeviceToHost, s),
+            "copy count status");
+    BB_CUDA(cudaMemcpyAsync(&h->build_err, g.err, 4, cudaMemcpyDeviceToHost, s),
+            "copy build status");
+    BB_CUDA(cudaMemcpyAsync(&h->wedges, g.wedges, 8, cudaMemcpyDeviceToHost, s), "copy wedges");
+    bb_status st = wait_bounded(s, "count");
+    if (st != BB_OK) return st;
+    BB_CUDA(cudaGetLastError(), "count kernels");
+    if (h->build_err) return map_build_error(h->build_err);
+    if (h->count_err) return fail(BB_ERR_CUDA, "internal count check failed (0x%x)", h->count_err);
+    if (h->acc[1] || h->acc[3] || h->acc[0] > (unsigned long long)LLONG_MAX ||
+        h->acc[2] > (unsigned long long)LLONG_MAX)
+        return fail(BB_ERR_OVERFLOW, "butterfly count exceeds int64");
+    *balanced = (int64_t)h->acc[0];
+    *total = (int64_t)h->acc[2];
+    if (wedges_opt) *wedges_opt = (int64_t)h->wedges;
+    return BB_OK;
+}
+
+// one-shot path on device-resident inputs
+bb_status count_device(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int64_t *balanced,
+                       int64_t *total, int64_t *pv_dev, int64_t *wedges_opt) {
+    const int64_t nU = csr->nU, nV = csr->nV, nE = csr->nE;
+    BuildSizes bs = build_sizes(nU, nV, nE);
+    bb_status st = ensure(ctx, &ctx->ws_graph, &ctx->ws_graph_cap, bs.graph_bytes, "graph workspace");
+    if (st != BB_OK) return st;
+    st = ensure(ctx, &ctx->ws_temp, &ctx->ws_temp_cap, bs.temp_bytes, "build workspace");
+    if (st != BB_OK) return st;
+    cudaStream_t s = ctx->stream;
+    DevGraph &g = ctx->oneshot;
+    bool relayout = ctx->layout_key[0] != nU || ctx->layout_key[1] != nV ||
+                    ctx->layout_key[2] != nE;
+    layout_graph(g, nU, nV, nE, ctx->ws_graph);
+    if (relayout) {
+        // split-merge counters must start at zero; counts leave them zeroed
+        BB_CUDA(cudaMemsetAsync(g.gpart, 0, (size_t)g.gpart_cap * 4, s), "zero merge buffer");
+        BB_CUDA(cudaMemsetAsync(g.gdone, 0, MAX_SPLIT_JOBS * 4, s), "zero merge counters");
+        ctx->layout_key[0] = nU; ctx->layout_key[1] = nV; ctx->layout_key[2] = nE;
+    }
+    uint32_t verr = build_graph(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s);
+    BB_CUDA(cudaGetLastError(), "build kernels");
+    if (verr) {
+        ctx->layout_key[0] = -1;  // leave the merge buffers to be re-zeroed
+        return map_build_error(verr);
+    }
+    if (pv_dev) return fail(BB_ERR_INVALID_ARG, "per-vertex counts are not available in this build");
+    launch_count(g, s, pv_dev);
+    BB_CUDA(cudaGetLastError(), "count launch");
+    return finish_count(ctx, g, s, balanced, total, wedges_opt);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bb_last_error(void) { return t_err.c_str(); }
+
+const char *bb_version(void) { return "bb 0.1 (sm_103a)"; }
+
+bb_status bb_ctx_create(int device, uint64_t hbm_budget_bytes, bb_ctx **out) {
+    if (!out) return fail(BB_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return fail(BB_ERR_NO_DEVICE, "no CUDA device (%s)", cudaGetErrorString(e));
+    }
+    if (device < 0 || device >= n) return fail(BB_ERR_INVALID_ARG, "device %d of %d", device, n);
+    cudaDeviceProp prop;
+    BB_CUDA(cudaGetDeviceProperties(&prop, device), "cudaGetDeviceProperties");
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(BB_ERR_NO_DEVICE, "device %d is sm_%d%d; this library is built for sm_103a",
+                    device, prop.major, prop.minor);
+    BB_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    bb_ctx *ctx = new (std::nothrow) bb_ctx();
+    if (!ctx) return fail(BB_ERR_OOM, "host allocation failed");
+    ctx->device = device;
+    size_t free_b = 0, total_b = 0;
+    e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "cudaMemGetInfo"); }
+    ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (uint64_t)(free_b * 0.9);
+    e = cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "cudaStreamCreate"); }
+    ctx->stream = ctx->own;
+    e = cudaMallocHost((void **)&ctx->h_res, sizeof(HostResult));
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(ctx->own);
+        delete ctx;
+        return cuda_fail(e, "cudaMallocHost");
+    }
+    count_init();
+    *out = ctx;
+    return BB_OK;
+}
+
+void bb_ctx_destroy(bb_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, ctx->ws_graph, ctx->ws_graph_cap);
+    dev_free(ctx, ctx->ws_temp, ctx->ws_temp_cap);
+    dev_free(ctx, ctx->ws_in, ctx->ws_in_cap);
+    dev_free(ctx, ctx->ws_pv, ctx->ws_pv_cap);
+    if (ctx->h_res) cudaFreeHost(ctx->h_res);
+    if (ctx->own) cudaStreamDestroy(ctx->own);
+    delete ctx;
+}
+
+bb_status bb_ctx_set_stream(bb_ctx *ctx, void *stream) {
+    if (!ctx) return fail(BB_ERR_INVALID_ARG, "ctx is NULL");
+    ctx->stream = stream ? (cudaStream_t)stream : ctx->own;
+    return BB_OK;
+}
+
+uint64_t bb_ctx_device_bytes(const bb_ctx *ctx) { return ctx ? ctx->used : 0; }
+
+bb_status bb_count_csr_device(bb_ctx *ctx, const bb_csr *csr_dev, const int8_t *signs_dev,
+                              int64_t *balanced, int64_t *total, int64_t *per_vertex_dev_opt,
+                              int64_t *wedges_opt) {
+    if (!ctx || !balanced || !total) return fail(BB_ERR_INVALID_ARG, "NULL argument");
+    bb_status st = check_csr(csr_dev, signs_dev);
+    if (st != BB_OK) return st;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if ((st = set_device(ctx)) != BB_OK) return st;
+    return count_device(ctx, csr_dev, signs_dev, balanced, total, per_vertex_dev_opt, wedges_opt);
+}
+
+bb_status bb_count_csr(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int64_t *balanced,
+                       int64_t *total, int64_t *per_vertex_opt, int64_t *wedges_opt) {
+    if (!ctx || !balanced || !total) return fail(BB_ERR_INVALID_ARG, "NULL argument");
+    bb_status st = check_csr(csr, signs);
+    if (st != BB_OK) return st;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if ((st = set_device(ctx)) != BB_OK) return st;
+    const int64_t nU = csr->nU, nE = csr->nE;
+    size_t b_row = ((size_t)(nU + 1) * 8 + 255) & ~(size_t)255;
+    size_t b_col = ((size_t)nE * 4 + 255) & ~(size_t)255;
+    size_t b_sg = ((size_t)nE + 255) & ~(size_t)255;
+    st = ensure(ctx, &ctx->ws_in, &ctx->ws_in_cap, b_row + b_col + b_sg + 256, "input workspace");
+    if (st != BB_OK) return st;
+    char *p = (char *)ctx->ws_in;
+    bb_csr d = *csr;
+    d.rowptr = (const int64_t *)p;
+    d.col = (const int32_t *)(p + b_row);
+    const int8_t *dsg = (const int8_t *)(p + b_row + b_col);
+    cudaStream_t s = ctx->stream;
+    BB_CUDA(cudaMemcpyAsync((void *)d.rowptr, csr->rowptr, (size_t)(nU + 1) * 8,
+                            cudaMemcpyHostToDevice, s), "copy rowptr");
+    if (nE > 0) {
+        BB_CUDA(cudaMemcpyAsync((void *)d.col, csr->col, (size_t)nE * 4, cudaMemcpyHostToDevice, s),
+                "copy col");
+        BB_CUDA(cudaMemcpyAsync((void *)dsg, signs, (size_t)nE, cudaMemcpyHostToDevice, s),
+                "copy signs");
+    }
+    int64_t *pv_dev = nullptr;
+    if (per_vertex_opt) {
+        size_t need = (size_t)(csr->nU + csr->nV) * 8;
+        st = ensure(ctx, (void **)&ctx->ws_pv, &ctx->ws_pv_cap, need, "per-vertex workspace");
+        if (st != BB_OK) return st;
+        pv_dev = ctx->ws_pv;
+    }
+    st = count_device(ctx, &d, dsg, balanced, total, pv_dev, wedges_opt);
+    if (st != BB_OK) return st;
+    if (per_vertex_opt) {
+        BB_CUDA(cudaMemcpyAsync(per_vertex_opt, pv_dev, (size_t)(csr->nU + csr->nV) * 8,
+                                cudaMemcpyDeviceToHost, s), "copy per-vertex");
+        st = wait_bounded(s, "per-vertex copy");
+    }
+    return st;
+}
+
+// ------------------------------------------------------- resident graphs
+static bb_status upload_impl(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, bool on_device,
+                             bb_graph **out) {
+    if (!ctx || !out) return fail(BB_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    bb_status st = check_csr(csr, signs);
+    if (st != BB_OK) return st;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if ((st = set_device(ctx)) != BB_OK) return st;
+    const int64_t nU = csr->nU, nV = csr->nV, nE = csr->nE;
+    BuildSizes bs = build_sizes(nU, nV, nE);
+    bb_graph *G = new (std::nothrow) bb_graph();
+    if (!G) return fail(BB_ERR_OOM, "host allocation failed");
+    G->ctx = ctx;
+    size_t b_row = ((size_t)(nU + 1) * 8 + 255) & ~(size_t)255;
+    size_t b_col = ((size_t)nE * 4 + 255) & ~(size_t)255;
+    size_t b_sg = ((size_t)nE + 255) & ~(size_t)255;
+    G->raw_bytes = b_row + b_col + b_sg + 256;
+    st = dev_alloc(ctx, &G->raw, G->raw_bytes, "graph input copy");
+    if (st != BB_OK) { delete G; return st; }
+    st = dev_alloc(ctx, &G->mem, bs.graph_bytes, "graph");
+    if (st != BB_OK) { dev_free(ctx, G->raw, G->raw_bytes); delete G; return st; }
+    G->bytes = bs.graph_bytes;
+    st = ensure(ctx, &ctx->ws_temp, &ctx->ws_temp_cap, bs.temp_bytes, "build workspace");
+    if (st != BB_OK) { bb_graph_free(G); return st; }
+    cudaStream_t s = ctx->stream;
+    char *p = (char *)G->raw;
+    G->g.rowptr = (int64_t *)p;
+    G->g.col = (int32_t *)(p + b_row);
+    G->g.sign = (int8_t *)(p + b_row + b_col);
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(G->g.rowptr, csr->rowptr, (size_t)(nU + 1) * 8, kind, s);
+    if (e == cudaSuccess && nE > 0) e = cudaMemcpyAsync(G->g.col, csr->col, (size_t)nE * 4, kind, s);
+    if (e == cudaSuccess && nE > 0) e = cudaMemcpyAsync(G->g.sign, signs, (size_t)nE, kind, s);
+    if (e != cudaSuccess) { bb_graph_free(G); return cuda_fail(e, "copy graph"); }
+    int64_t *rp = G->g.rowptr;
+    int32_t *cl = G->g.col;
+    int8_t *sg = G->g.sign;
+    layout_graph(G->g, nU, nV, nE, G->mem);
+    G->g.rowptr = rp; G->g.col = cl; G->g.sign = sg;
+    cudaMemsetAsync(G->g.gpart, 0, (size_t)G->g.gpart_cap * 4, s);
+    cudaMemsetAsync(G->g.gdone, 0, MAX_SPLIT_JOBS * 4, s);
+    uint32_t verr = build_graph(G->g, rp, cl, sg, ctx->ws_temp, s);
+    if (verr) { bb_graph_free(G); return map_build_error(verr); }
+    e = cudaMemcpyAsync(&ctx->h_res->build_err, G->g.err, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctx->h_res->wedges, G->g.wedges, 8, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) { bb_graph_free(G); return cuda_fail(e, "copy build status"); }
+    st = wait_bounded(s, "graph build");
+    if (st != BB_OK) { bb_graph_free(G); return st; }
+    if (ctx->h_res->build_err) {
+        uint32_t be = ctx->h_res->build_err;
+        bb_graph_free(G);
+        return map_build_error(be);
+    }
+    G->g.h_wedges = ctx->h_res->wedges;
+    *out = G;
+    return BB_OK;
+}
+
+bb_status bb_graph_upload(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, bb_graph **out) {
+    return upload_impl(ctx, csr, signs, false, out);
+}
+
+bb_status bb_graph_upload_device(bb_ctx *ctx, const bb_csr *csr_dev, const int8_t *signs_dev,
+                                 bb_graph **out) {
+    return upload_impl(ctx, csr_dev, signs_dev, true, out);
+}
+
+bb_status bb_count(bb_graph *G, int64_t *balanced, int64_t *total, int64_t *per_vertex_opt) {
+    if (!G || !balanced || !total) return fail(BB_ERR_INVALID_ARG, "NULL argument");
+    bb_ctx *ctx = G->ctx;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    bb_status st = set_device(ctx);
+    if (st != BB_OK) return st;
+    if (per_vertex_opt) return fail(BB_ERR_INVALID_ARG, "per-vertex counts are not available in this build");
+    launch_count(G->g, ctx->stream, nullptr);
+    BB_CUDA(cudaGetLastError(), "count launch");
+    return finish_count(ctx, G->g, ctx->stream, balanced, total, nullptr);
+}
+
+bb_status bb_graph_flip_signs(bb_graph *G, const int64_t *edge_idx, int64_t n) {
+    if (!G || (n > 0 && !edge_idx) || n < 0) return fail(BB_ERR_INVALID_ARG, "bad argument");
+    if (n == 0) return BB_OK;
+    for (int64_t i = 0; i < n; i++)
+        if (edge_idx[i] < 0 || edge_idx[i] >= G->g.nE)
+            return fail(BB_ERR_INVALID_ARG, "edge index %lld outside [0, %lld)",
+                        (long long)edge_idx[i], (long long)G->g.nE);
+    bb_ctx *ctx = G->ctx;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    bb_status st = set_device(ctx);
+    if (st != BB_OK) return st;
+    void *d = nullptr;
+    st = dev_alloc(ctx, &d, (size_t)n * 8, "flip list");
+    if (st != BB_OK) return st;
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaMemcpyAsync(d, edge_idx, (size_t)n * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        launch_flip(G->g, (const int64_t *)d, n, s);
+        e = cudaGetLastError();
+    }
+    st = e == cudaSuccess ? wait_bounded(s, "sign flip") : cuda_fail(e, "sign flip");
+    dev_free(ctx, d, (size_t)n * 8);
+    return st;
+}
+
+bb_status bb_graph_info(const bb_graph *G, int64_t *nU, int64_t *nV, int64_t *nE,
+                        int64_t *wedges) {
+    if (!G) return fail(BB_ERR_INVALID_ARG, "graph is NULL");
+    if (nU) *nU = G->g.nU;
+    if (nV) *nV = G->g.nV;
+    if (nE) *nE = G->g.nE;
+    if (wedges) *wedges = (int64_t)G->g.h_wedges;
+    return BB_OK;
+}
+
+void bb_graph_free(bb_graph *G) {
+    if (!G) return;
+    bb_ctx *ctx = G->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, G->mem, G->bytes);
+    dev_free(ctx, G->raw, G->raw_bytes);
+    delete G;
+}
+
+}  // extern "C"

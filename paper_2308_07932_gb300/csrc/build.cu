@@ -1,0 +1,640 @@
+// build.cu - from the input U-side CSR to the ranked, sign-packed CSR of
+// both sides, the wedge-suffix starts, per-anchor work and work classes.
+//
+// Steps (paper: Algorithm 2 lines 2-3 "calculate p(u)" and "rearrange
+// Gamma(u) in ascending order"; Def. 4 for the priority; the binning sort of
+// the complexity analysis for ordering by degree):
+//   1. validate the CSR and count degrees;
+//   2. rank each side by (degree, id) and derive the global priority rank;
+//   3. place every edge in the rows of both endpoints, keyed by the
+//      neighbour's side rank with the sign in bit 0, and sort each row;
+//   4. for every entry w -> v, the start of the suffix of v's row ranked
+//      above both v and w, and the wedges anchored at each vertex;
+//   5. split anchors into work classes ordered by decreasing work.
+#include <algorithm>
+#include "graph.cuh"
+#include "prims.cuh"
+
+namespace bb {
+
+namespace {
+
+constexpr int BT = 256;  // default threads per block for simple kernels
+
+inline unsigned grid_for(int64_t n, int threads, int64_t cap = 1 << 20) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (unsigned)b;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ------------------------------------------------------------ 1. validate
+__global__ void k_validate_rows(const int64_t *rowptr, int64_t nU, int64_t nE, uint32_t *degU,
+                                uint32_t *err) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nU;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a = rowptr[u], b = rowptr[u + 1];
+        uint32_t d = 0;
+        if (a < 0 || b < a || b > nE) set_error(err, E_ROWPTR);
+        else if (b - a > (int64_t)MAX_DEGREE) { set_error(err, E_DEGREE); d = 0; }
+        else d = (uint32_t)(b - a);
+        degU[u] = d;
+        if (u == 0 && a != 0) set_error(err, E_ROWPTR);
+        if (u == nU - 1 && b != nE) set_error(err, E_ROWPTR);
+    }
+}
+
+__global__ void k_validate_edges(const int32_t *col, const int8_t *sign, int64_t nE, int64_t nV,
+                                 uint32_t *degV, uint32_t *err) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nE;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t c = col[e];
+        int8_t sg = sign[e];
+        if (c < 0 || (int64_t)c >= nV) set_error(err, E_COL);
+        else atomicAdd(&degV[c], 1u);
+        if (sg != 1 && sg != -1) set_error(err, E_SIGN);
+    }
+}
+
+__global__ void k_check_degree(const uint32_t *deg, int64_t n, uint32_t *err) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (deg[i] > MAX_DEGREE) set_error(err, E_DEGREE);
+}
+
+__global__ void k_iota(uint32_t *a, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = (uint32_t)i;
+}
+
+// ------------------------------------------------------------- 2. ranking
+// sorted_deg/sorted_id: a side's vertices in ascending (degree, id) order.
+__global__ void k_side_rank(const uint32_t *sorted_id, const uint32_t *sorted_deg, int64_t n,
+                            SideCSR S) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t id = sorted_id[r];
+        S.id_of_sr[r] = id;
+        S.sr_of_id[id] = (uint32_t)r;
+        S.deg[r] = sorted_deg[r];
+    }
+}
+
+// Global priority (Def. 4) over U and V with ids compared as gid = u for U
+// and |U| + v for V: a U vertex of degree d outranks every V vertex of
+// degree < d; a V vertex of degree d outranks every U vertex of degree <= d.
+__global__ void k_global_rank(SideCSR S, const uint32_t *other_deg, int64_t n_other, int is_u) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < S.n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t d = S.deg[r];
+        int64_t lo = 0, hi = n_other;
+        if (is_u) {  // first other index with deg >= d
+            while (lo < hi) { int64_t m = (lo + hi) >> 1; if (other_deg[m] < d) lo = m + 1; else hi = m; }
+        } else {     // first other index with deg > d
+            while (lo < hi) { int64_t m = (lo + hi) >> 1; if (other_deg[m] <= d) lo = m + 1; else hi = m; }
+        }
+        S.grank[r] = (uint32_t)(r + lo);
+    }
+}
+
+// --------------------------------------------------------------- 3. rows
+// warp per input row u: the U-side entry keeps the input position within the
+// row; the V-side entry takes the next free slot of v's row.
+__global__ void k_fill(const int64_t *rowptr, const int32_t *col, const int8_t *sign, int64_t nU,
+                       SideCSR U, SideCSR V, uint32_t *cursorV, uint32_t *eidU, uint32_t *eidV) {
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned lane = lane_id();
+    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < nU; u += warps) {
+        uint32_t r = U.sr_of_id[u];
+        int64_t base = U.off[r];
+        int64_t a = rowptr[u], d = rowptr[u + 1] - a;
+        for (int64_t i = lane; i < d; i += 32) {
+            int64_t e = a + i;
+            uint32_t v = (uint32_t)col[e];
+            uint32_t neg = sign[e] < 0 ? 1u : 0u;
+            uint32_t rv = V.sr_of_id[v];
+            U.adj[base + i] = (rv << 1) | neg;
+            eidU[base + i] = (uint32_t)e;
+            int64_t p = V.off[rv] + atomicAdd(&cursorV[rv], 1u);
+            V.adj[p] = (r << 1) | neg;
+            eidV[p] = (uint32_t)e;
+        }
+    }
+}
+
+// Row length classes of a side (rows are in ascending degree, so each class
+// is a contiguous range of side ranks): bounds[k] = first side rank whose
+// degree exceeds ROW_LIMS[k]; bounds[4] = n.
+__constant__ uint32_t ROW_LIMS[4] = {1u, 32u, 2048u, 16384u};
+
+__global__ void k_row_bounds(const uint32_t *deg, int64_t n, int64_t *bounds) {
+    int k = threadIdx.x;
+    if (k == 4) bounds[4] = n;
+    if (k >= 4) return;
+    uint32_t lim = ROW_LIMS[k];
+    int64_t lo = 0, hi = n;
+    while (lo < hi) { int64_t m = (lo + hi) >> 1; if (deg[m] <= lim) lo = m + 1; else hi = m; }
+    bounds[k] = lo;
+}
+
+__device__ __forceinline__ uint64_t pack_entry(uint32_t entry, uint32_t eid) {
+    return ((uint64_t)entry << 32) | eid;
+}
+
+// rows of 2..32 entries: one warp per row, bitonic sort in registers
+__global__ void k_sort_rows_warp(SideCSR S, uint32_t *eid, const int64_t *bounds, uint32_t *err) {
+    const int64_t r0 = bounds[0], r1 = bounds[1];
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned lane = lane_id();
+    for (int64_t r = r0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); r < r1;
+         r += warps) {
+        int64_t b = S.off[r];
+        uint32_t d = (uint32_t)(S.off[r + 1] - b);
+        uint64_t x = lane < d ? pack_entry(S.adj[b + lane], eid[b + lane]) : ~0ull;
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                uint64_t y = __shfl_xor_sync(FULL, x, j);
+                bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+                x = keep_min ? (x < y ? x : y) : (x < y ? y : x);
+            }
+        }
+        uint64_t prev = __shfl_up_sync(FULL, x, 1);
+        if (lane < d) {
+            S.adj[b + lane] = (uint32_t)(x >> 32);
+            eid[b + lane] = (uint32_t)x;
+            if (lane > 0 && (prev >> 33) == (x >> 33)) set_error(err, E_DUP);
+        }
+    }
+}
+
+// rows of (32, CAP] entries: one CTA per row, bitonic sort in shared memory
+template <int CAP, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_sort_rows_smem(SideCSR S, uint32_t *eid,
+                                                            const int64_t *bounds, int lo_k,
+                                                            uint32_t *err) {
+    extern __shared__ uint64_t sbuf[];
+    const int64_t r0 = bounds[lo_k], r1 = bounds[lo_k + 1];
+    for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
+        int64_t b = S.off[r];
+        uint32_t d = (uint32_t)(S.off[r + 1] - b);
+        uint32_t P = 1;
+        while (P < d) P <<= 1;
+        for (uint32_t i = threadIdx.x; i < P; i += THREADS)
+            sbuf[i] = i < d ? pack_entry(S.adj[b + i], eid[b + i]) : ~0ull;
+        __syncthreads();
+        for (uint32_t k = 2; k <= P; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t i = threadIdx.x; i < P; i += THREADS) {
+                    uint32_t ixj = i ^ j;
+                    if (ixj > i) {
+                        uint64_t a = sbuf[i], c = sbuf[ixj];
+                        bool asc = (i & k) == 0;
+                        if ((a > c) == asc) { sbuf[i] = c; sbuf[ixj] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (uint32_t i = threadIdx.x; i < d; i += THREADS) {
+            uint64_t x = sbuf[i];
+            S.adj[b + i] = (uint32_t)(x >> 32);
+            eid[b + i] = (uint32_t)x;
+            if (i > 0 && (sbuf[i - 1] >> 33) == (x >> 33)) set_error(err, E_DUP);
+        }
+        __syncthreads();
+    }
+}
+
+// rows longer than the shared-memory sort: one CTA per row, stable LSD
+// radix sort (8-bit digits) through two global buffers
+constexpr int RR_THREADS = 1024;
+constexpr int RR_WARPS = RR_THREADS / 32;
+
+__global__ void __launch_bounds__(RR_THREADS) k_sort_rows_radix(SideCSR S, uint32_t *eid,
+                                                                const int64_t *bounds, int lo_k,
+                                                                uint64_t *bufA, uint64_t *bufB,
+                                                                int key_bits, uint32_t *err) {
+    __shared__ uint32_t wcnt[RR_WARPS][256];
+    __shared__ uint32_t run[256];
+    const int64_t r0 = bounds[lo_k], r1 = bounds[lo_k + 1];
+    const int t = threadIdx.x, warp = t >> 5;
+    const unsigned lane = lane_id();
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int passes = (key_bits + 7) / 8;
+    for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
+        int64_t b = S.off[r];
+        int64_t d = S.off[r + 1] - b;
+        uint64_t *A = bufA + b, *B = bufB + b;
+        for (int64_t i = t; i < d; i += RR_THREADS) A[i] = pack_entry(S.adj[b + i], eid[b + i]);
+        for (int k = t; k < RR_WARPS * 256; k += RR_THREADS) (&wcnt[0][0])[k] = 0;
+        __syncthreads();
+        uint64_t *src = A, *dst = B;
+        for (int p = 0; p < passes; p++) {
+            const int shift = 32 + 8 * p;
+            if (t < 256) run[t] = 0;
+            __syncthreads();
+            for (int64_t i = t; i < d; i += RR_THREADS) atomicAdd(&run[(src[i] >> shift) & 255u], 1u);
+            __syncthreads();
+            if (t < 32) {  // exclusive scan of 256 bins by one warp (8 per lane)
+                uint32_t v[8], s = 0;
+#pragma unroll
+                for (int k = 0; k < 8; k++) { v[k] = run[t * 8 + k]; s += v[k]; }
+                uint32_t incl = warp_incl_scan(s);
+                uint32_t acc = incl - s;
+#pragma unroll
+                for (int k = 0; k < 8; k++) { run[t * 8 + k] = acc; acc += v[k]; }
+            }
+            __syncthreads();
+            for (int64_t base = 0; base < d; base += RR_THREADS) {
+                int64_t i = base + t;
+                bool valid = i < d;
+                uint64_t x = valid ? src[i] : 0;
+                uint32_t dg = valid ? (uint32_t)((x >> shift) & 255u) : 256u + lane;
+                unsigned peers = __match_any_sync(FULL, dg);
+                uint32_t rank = __popc(peers & lt_mask);
+                if (valid && rank == 0) wcnt[warp][dg] = __popc(peers);
+                __syncthreads();
+                if (t < 256) {
+                    uint32_t s = run[t];
+                    for (int w = 0; w < RR_WARPS; w++) { uint32_t c = wcnt[w][t]; wcnt[w][t] = s; s += c; }
+                    run[t] = s;
+                }
+                __syncthreads();
+                if (valid) dst[wcnt[warp][dg] + rank] = x;
+                __syncthreads();
+                if (t < 256)
+                    for (int w = 0; w < RR_WARPS; w++) wcnt[w][t] = 0;
+                __syncthreads();
+            }
+            uint64_t *tmp = src; src = dst; dst = tmp;
+        }
+        for (int64_t i = t; i < d; i += RR_THREADS) {
+            uint64_t x = src[i];
+            S.adj[b + i] = (uint32_t)(x >> 32);
+            eid[b + i] = (uint32_t)x;
+            if (i > 0 && (src[i - 1] >> 33) == (x >> 33)) set_error(err, E_DUP);
+        }
+        __syncthreads();
+    }
+}
+
+// lo(x): neighbours of x with lower global priority (a prefix of its row)
+__global__ void k_lo(SideCSR S, SideCSR O) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < S.n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = S.off[r], hi = S.off[r + 1], b = lo;
+        uint32_t g = S.grank[r];
+        while (lo < hi) {
+            int64_t m = (lo + hi) >> 1;
+            if (O.grank[S.adj[m] >> 1] < g) lo = m + 1; else hi = m;
+        }
+        S.lo[r] = (uint32_t)(lo - b);
+    }
+}
+
+__global__ void k_epos(const uint32_t *eid, int64_t nE, uint32_t *epos) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nE;
+         p += (int64_t)gridDim.x * blockDim.x)
+        epos[eid[p]] = (uint32_t)p;
+}
+
+// ------------------------------------------------- 4. suffixes and work
+// For the entry w -> v at position p of anchor w's row: the wedge suffix of
+// v's row holds the neighbours ranked above max(v, w). If v outranks w that
+// is v's own upper part (from lo(v)); otherwise it starts right after w's
+// position in v's row (w and the suffix are on the same side).
+__global__ void k_sfx_work(SideCSR S, SideCSR O, const uint32_t *eid_s, const uint32_t *epos_o,
+                           unsigned long long *wedges) {
+    __shared__ unsigned long long block_sum;
+    if (threadIdx.x == 0) block_sum = 0;
+    __syncthreads();
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned lane = lane_id();
+    unsigned long long mine = 0;
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < S.n; r += warps) {
+        int64_t b = S.off[r], e = S.off[r + 1];
+        uint32_t g = S.grank[r];
+        uint64_t sum = 0;
+        for (int64_t p = b + lane; p < e; p += 32) {
+            uint32_t v = S.adj[p] >> 1;
+            int64_t vb = O.off[v];
+            uint32_t st;
+            if (O.grank[v] > g) st = O.lo[v];
+            else st = (uint32_t)(epos_o[eid_s[p]] - vb) + 1u;
+            S.sfx[p] = st;
+            sum += (uint64_t)(O.deg[v] - st);
+        }
+        sum = warp_sum_u64(sum);
+        if (lane == 0) S.work[r] = sum;
+        mine += sum;
+    }
+    if (lane == 0 && mine) atomicAdd(&block_sum, mine);
+    __syncthreads();
+    if (threadIdx.x == 0 && block_sum) atomicAdd(wedges, block_sum);
+}
+
+// ------------------------------------------------------ 5. classification
+constexpr int NB = 64;  // log2 work buckets
+
+struct ClassifyTemp {
+    uint32_t *meta;         // per anchor: cls | bucket << 2 | parts << 8 (0 = no work)
+    uint32_t *grp;          // per anchor: split group id
+    uint32_t *bucket_cnt;   // [NCLS][NB]
+    uint32_t *bucket_base;  // [NCLS][NB]
+};
+
+__device__ __forceinline__ uint32_t bucket_of(uint64_t w) { return 63u - (uint32_t)__clzll((long long)w); }
+
+// decides each anchor's class (and split) and counts entries per bucket
+__global__ void k_classify(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
+    __shared__ uint32_t cnt[NCLS * NB];
+    for (int k = threadIdx.x; k < NCLS * NB; k += blockDim.x) cnt[k] = 0;
+    __syncthreads();
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < S.n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t W = S.work[r];
+        uint32_t meta = 0;
+        if (W > 0) {
+            uint64_t above = (uint64_t)(S.n - r - 1);
+            uint64_t dh = W < above ? W : above;
+            uint32_t cls;
+            if (above <= DENSE_CAP && (above <= DENSE_RATIO * dh || dh > CTA_D_MAX)) cls = CLS_DENSE;
+            else if (dh <= WARP_D_MAX) cls = CLS_WARP;
+            else if (dh <= CTA_D_MAX) cls = CLS_CTAH;
+            else cls = CLS_DENSE;  // endpoint range walked in DENSE_CAP windows
+            uint32_t parts = 1;
+            if (cls == CLS_DENSE && above <= DENSE_CAP && above > 0) {
+                uint64_t unit = SPLIT_WEDGES > 4 * above ? SPLIT_WEDGES : 4 * above;
+                uint64_t k = W / unit;
+                uint32_t deg = (uint32_t)(S.off[r + 1] - S.off[r]);
+                if (k > MAX_PARTS) k = MAX_PARTS;
+                if (k > deg) k = deg;
+                if (k >= 2) {
+                    uint32_t jobs = atomicAdd(&G.ctr[CTR_SPLITJOBS], (uint32_t)k);
+                    uint32_t goff = atomicAdd(&G.ctr[CTR_GPART], (uint32_t)above);
+                    if (jobs + k <= MAX_SPLIT_JOBS && (uint64_t)goff + above <= G.gpart_cap) {
+                        uint32_t gid = atomicAdd(&G.ctr[CTR_GROUPS], 1u);
+                        G.groups[gid] = SplitGroup{(uint32_t)k, goff, (uint32_t)above, 0u};
+                        T.grp[r] = gid;
+                        parts = (uint32_t)k;
+                    }
+                }
+            }
+            uint32_t b = bucket_of(parts > 1 ? W / parts : W);
+            meta = 1u | cls << 1 | b << 3 | parts << 9;
+            atomicAdd(&cnt[cls * NB + b], parts);
+        }
+        T.meta[r] = meta;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < NCLS * NB; k += blockDim.x)
+        if (cnt[k]) atomicAdd(&T.bucket_cnt[k], cnt[k]);
+}
+
+// bucket bases in decreasing bucket order; class totals to the counters
+__global__ void k_bucket_base(ClassifyTemp T, DevGraph G) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int c = 0; c < NCLS; c++) {
+        uint32_t acc = 0;
+        for (int b = NB - 1; b >= 0; b--) {
+            T.bucket_base[c * NB + b] = acc;
+            acc += T.bucket_cnt[c * NB + b];
+        }
+        G.ctr[c] = acc;  // CTR_WARP, CTR_CTAH, CTR_DENSE
+    }
+}
+
+__global__ void k_emit(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
+    __shared__ uint32_t cnt[NCLS * NB];
+    __shared__ uint32_t base[NCLS * NB];
+    for (int k = threadIdx.x; k < NCLS * NB; k += blockDim.x) cnt[k] = 0;
+    __syncthreads();
+    // one pass per block-chunk so each block reserves its ranges once
+    const int64_t chunk = blockDim.x;
+    for (int64_t r0 = blockIdx.x * chunk; r0 < S.n; r0 += (int64_t)gridDim.x * chunk) {
+        int64_t r = r0 + threadIdx.x;
+        uint32_t meta = r < S.n ? T.meta[r] : 0u;
+        uint32_t local = 0, key = 0, parts = 0;
+        if (meta) {
+            uint32_t cls = (meta >> 1) & 3u, b = (meta >> 3) & 63u;
+            parts = meta >> 9;
+            key = cls * NB + b;
+            local = atomicAdd(&cnt[key], parts);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < NCLS * NB; k += blockDim.x) {
+            if (cnt[k]) base[k] = T.bucket_base[k] + atomicAdd(&T.bucket_cnt[k], cnt[k]);
+        }
+        __syncthreads();
+        if (meta) {
+            uint32_t cls = key / NB;
+            uint32_t pos = base[key] + local;
+            uint32_t anchor = (uint32_t)r << 1 | (uint32_t)side;
+            if (cls == CLS_WARP) G.warp_list[pos] = anchor;
+            else if (cls == CLS_CTAH) G.ctah_list[pos] = anchor;
+            else {
+                uint32_t deg = (uint32_t)(S.off[r + 1] - S.off[r]);
+                uint32_t grp = parts > 1 ? T.grp[r] : NO_GROUP;
+                for (uint32_t i = 0; i < parts; i++) {
+                    uint32_t m0 = (uint32_t)((uint64_t)deg * i / parts);
+                    uint32_t m1 = (uint32_t)((uint64_t)deg * (i + 1) / parts);
+                    G.dense_jobs[pos + i] = DenseJob{anchor, m0, m1, grp};
+                }
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < NCLS * NB; k += blockDim.x) cnt[k] = 0;
+        __syncthreads();
+    }
+}
+
+struct Carver {
+    char *p;
+    template <typename T>
+    T *take(size_t count) {
+        T *r = (T *)p;
+        p += align256(count * sizeof(T));
+        return r;
+    }
+};
+
+size_t side_bytes(int64_t n, int64_t nE) {
+    return align256((size_t)(n + 1) * 8) + 2 * align256((size_t)nE * 4) +
+           5 * align256((size_t)(n > 0 ? n : 1) * 4) + align256((size_t)(n > 0 ? n : 1) * 8);
+}
+
+}  // namespace
+
+void build_init() {
+    cudaFuncSetAttribute(k_sort_rows_smem<16384, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         16384 * 8);
+}
+
+BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE) {
+    int64_t n = nU + nV;
+    int64_t nmax = std::max<int64_t>(std::max(nU, nV), 1);
+    size_t g = side_bytes(nU, nE) + side_bytes(nV, nE);
+    g += 2 * align256((size_t)(n + 1) * 4);                                  // warp/ctah lists
+    g += align256((size_t)(n + MAX_SPLIT_JOBS) * sizeof(DenseJob));          // dense jobs
+    g += align256((size_t)MAX_SPLIT_JOBS * sizeof(SplitGroup));              // groups
+    g += align256((size_t)MAX_SPLIT_JOBS * 4);                               // gdone
+    g += align256(gpart_entries(nE) * 4);
+    g += align256(NCTR * 4) + 256 + 256 + align256(sizeof(CountScratch));
+    size_t t = 0;
+    t += align256((size_t)nU * 4 + 4) + align256((size_t)nV * 4 + 4);      // deg by id
+    t += 2 * align256((size_t)nE * 4 + 4);                                   // eid
+    t += align256((size_t)nV * 4 + 4);                                       // cursor
+    t += 2 * align256((size_t)nE * 8 + 8);                                   // row sort buffers / epos
+    t += 2 * align256((size_t)nmax * 4 + 4);                                 // rank sort alt
+    t += align256(std::max(radix_temp_bytes(nmax), scan_temp_bytes(nmax + 1)));
+    t += 2 * align256((size_t)nmax * 4 + 4) * 2;                             // classify meta/grp
+    t += 2 * align256(NCLS * NB * 4) + align256(64 * 8);                     // buckets, bounds
+    return {g, t};
+}
+
+void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_mem) {
+    Carver c{(char *)graph_mem};
+    g.nU = nU; g.nV = nV; g.nE = nE;
+    int64_t ns[2] = {nU, nV};
+    for (int s = 0; s < 2; s++) {
+        SideCSR &S = g.side[s];
+        int64_t n = ns[s], n1 = n > 0 ? n : 1;
+        S.n = n;
+        S.off = c.take<int64_t>(n + 1);
+        S.adj = c.take<uint32_t>(nE);
+        S.sfx = c.take<uint32_t>(nE);
+        S.id_of_sr = c.take<uint32_t>(n1);
+        S.sr_of_id = c.take<uint32_t>(n1);
+        S.grank = c.take<uint32_t>(n1);
+        S.deg = c.take<uint32_t>(n1);
+        S.lo = c.take<uint32_t>(n1);
+        S.work = c.take<uint64_t>(n1);
+    }
+    int64_t n = nU + nV;
+    g.warp_list = c.take<uint32_t>(n + 1);
+    g.ctah_list = c.take<uint32_t>(n + 1);
+    g.dense_jobs = c.take<DenseJob>(n + MAX_SPLIT_JOBS);
+    g.groups = c.take<SplitGroup>(MAX_SPLIT_JOBS);
+    g.gdone = c.take<uint32_t>(MAX_SPLIT_JOBS);
+    g.gpart_cap = (uint32_t)gpart_entries(nE);
+    g.gpart = c.take<uint32_t>(g.gpart_cap);
+    g.ctr = c.take<uint32_t>(NCTR);
+    g.wedges = c.take<unsigned long long>(1);
+    g.err = c.take<uint32_t>(1);
+    g.scratch = c.take<CountScratch>(1);
+}
+
+uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
+                     void *temp_mem, cudaStream_t s) {
+    const int64_t nU = g.nU, nV = g.nV, nE = g.nE;
+    const int64_t nmax = std::max<int64_t>(std::max(nU, nV), 1);
+    Carver c{(char *)temp_mem};
+    uint32_t *deg_in[2] = {c.take<uint32_t>(nU + 1), c.take<uint32_t>(nV + 1)};
+    uint32_t *eid[2] = {c.take<uint32_t>(nE + 1), c.take<uint32_t>(nE + 1)};
+    uint32_t *cursorV = c.take<uint32_t>(nV + 1);
+    uint64_t *bufA = c.take<uint64_t>(nE + 1);
+    uint64_t *bufB = c.take<uint64_t>(nE + 1);
+    uint32_t *ralt_k = c.take<uint32_t>(nmax + 1);
+    uint32_t *ralt_v = c.take<uint32_t>(nmax + 1);
+    void *ptemp = c.take<char>(std::max(radix_temp_bytes(nmax), scan_temp_bytes(nmax + 1)));
+    ClassifyTemp T;
+    uint32_t *meta[2] = {c.take<uint32_t>(nmax + 1), c.take<uint32_t>(nmax + 1)};
+    uint32_t *grp[2] = {c.take<uint32_t>(nmax + 1), c.take<uint32_t>(nmax + 1)};
+    T.bucket_cnt = c.take<uint32_t>(NCLS * NB);
+    T.bucket_base = c.take<uint32_t>(NCLS * NB);
+    int64_t *bounds = c.take<int64_t>(64);
+
+    cudaMemsetAsync(g.err, 0, 4, s);
+    cudaMemsetAsync(g.ctr, 0, NCTR * 4, s);
+    cudaMemsetAsync(g.wedges, 0, 8, s);
+    cudaMemsetAsync(deg_in[1], 0, (size_t)nV * 4, s);
+    cudaMemsetAsync(cursorV, 0, (size_t)nV * 4, s);
+    cudaMemsetAsync(T.bucket_cnt, 0, NCLS * NB * 4, s);
+
+    // 1. validate + degrees
+    if (nU > 0) k_validate_rows<<<grid_for(nU, BT, 8192), BT, 0, s>>>(rowptr, nU, nE, deg_in[0], g.err);
+    if (nE > 0) k_validate_edges<<<grid_for(nE, BT, 16384), BT, 0, s>>>(col, sign, nE, nV, deg_in[1], g.err);
+    if (nV > 0) k_check_degree<<<grid_for(nV, BT, 8192), BT, 0, s>>>(deg_in[1], nV, g.err);
+    uint32_t herr = 0;
+    cudaMemcpyAsync(&herr, g.err, 4, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    if (herr) return herr;
+
+    // 2. side ranks by (degree, id), then the global priority rank
+    int64_t ns[2] = {nU, nV};
+    for (int sd = 0; sd < 2; sd++) {
+        int64_t n = ns[sd];
+        if (n == 0) continue;
+        SideCSR &S = g.side[sd];
+        // sort ids by degree (stable => ties by id): reuse id_of_sr / deg as buffers
+        k_iota<<<grid_for(n, BT, 8192), BT, 0, s>>>(S.sr_of_id, n);
+        cudaMemcpyAsync(S.lo, deg_in[sd], (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+        radix_sort_pairs_u32(S.lo, S.sr_of_id, ralt_k, ralt_v, n, 16, ptemp, s);
+        cudaMemcpyAsync(ralt_v, S.sr_of_id, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+        k_side_rank<<<grid_for(n, BT, 8192), BT, 0, s>>>(ralt_v, S.lo, n, S);
+    }
+    if (nU > 0) k_global_rank<<<grid_for(nU, BT, 8192), BT, 0, s>>>(g.side[0], g.side[1].deg, nV, 1);
+    if (nV > 0) k_global_rank<<<grid_for(nV, BT, 8192), BT, 0, s>>>(g.side[1], g.side[0].deg, nU, 0);
+
+    // 3. offsets, row fill, row sorts, lo
+    for (int sd = 0; sd < 2; sd++)
+        scan_exclusive_u32_to_i64(g.side[sd].deg, g.side[sd].off, ns[sd], ptemp, s);
+    if (nU > 0 && nE > 0)
+        k_fill<<<grid_for(nU * 32, BT, 16384), BT, 0, s>>>(rowptr, col, sign, nU, g.side[0],
+                                                          g.side[1], cursorV, eid[0], eid[1]);
+    for (int sd = 0; sd < 2; sd++) {
+        int64_t n = ns[sd];
+        if (n == 0 || nE == 0) continue;
+        SideCSR &S = g.side[sd];
+        int64_t *bd = bounds + sd * 8;
+        // bd[0..3]: first rank with degree > 1, > 32, > 2048, > 16384; bd[4] = n
+        k_row_bounds<<<1, 32, 0, s>>>(S.deg, n, bd);
+        k_sort_rows_warp<<<grid_for(n * 32, BT, 16384), BT, 0, s>>>(S, eid[sd], bd, g.err);
+        k_sort_rows_smem<2048, 256><<<4096, 256, 2048 * 8, s>>>(S, eid[sd], bd, 1, g.err);
+        k_sort_rows_smem<16384, 1024><<<1024, 1024, 16384 * 8, s>>>(S, eid[sd], bd, 2, g.err);
+        int64_t n_other = ns[1 - sd];
+        int key_bits = 1;
+        while (key_bits < 32 && ((uint64_t)1 << key_bits) < (uint64_t)(2 * n_other + 2)) key_bits++;
+        k_sort_rows_radix<<<512, RR_THREADS, 0, s>>>(S, eid[sd], bd, 3, bufA, bufB, key_bits, g.err);
+    }
+    for (int sd = 0; sd < 2; sd++)
+        if (ns[sd] > 0) k_lo<<<grid_for(ns[sd], BT, 8192), BT, 0, s>>>(g.side[sd], g.side[1 - sd]);
+
+    // 4. twin positions, suffix starts, work per anchor
+    uint32_t *epos[2] = {(uint32_t *)bufA, (uint32_t *)bufA + (nE + 1)};
+    if (nE > 0) {
+        for (int sd = 0; sd < 2; sd++)
+            k_epos<<<grid_for(nE, BT, 16384), BT, 0, s>>>(eid[sd], nE, epos[sd]);
+        for (int sd = 0; sd < 2; sd++)
+            if (ns[sd] > 0)
+                k_sfx_work<<<grid_for(ns[sd] * 32, BT, 4096), BT, 0, s>>>(
+                    g.side[sd], g.side[1 - sd], eid[sd], epos[1 - sd], g.wedges);
+    } else {
+        for (int sd = 0; sd < 2; sd++)
+            if (ns[sd] > 0) cudaMemsetAsync(g.side[sd].work, 0, (size_t)ns[sd] * 8, s);
+    }
+
+    // 5. classes
+    for (int sd = 0; sd < 2; sd++) {
+        if (ns[sd] == 0) continue;
+        T.meta = meta[sd];
+        T.grp = grp[sd];
+        k_classify<<<grid_for(ns[sd], BT, 4096), BT, 0, s>>>(g.side[sd], sd, T, g);
+    }
+    k_bucket_base<<<1, 32, 0, s>>>(T, g);
+    cudaMemsetAsync(T.bucket_cnt, 0, NCLS * NB * 4, s);
+    for (int sd = 0; sd < 2; sd++) {
+        if (ns[sd] == 0) continue;
+        T.meta = meta[sd];
+        T.grp = grp[sd];
+        k_emit<<<grid_for(ns[sd], BT, 2048), BT, 0, s>>>(g.side[sd], sd, T, g);
+    }
+    return 0;
+}
+
+}  // namespace bb

@@ -1,0 +1,127 @@
+// graph.cuh - device-resident graph built for counting, and the work
+// classes of its anchors.
+//
+// Wedges and anchors. Algorithm 2 counts, for every wedge u - v - w in which
+// u has the highest priority of the three (Def. 4), one symmetric or
+// asymmetric tally for the pair (u, w). Those tallies are kept here at the
+// LOWER-priority endpoint w (the "anchor") keyed by the higher one u: the
+// wedge set and every pair's (symmetric, asymmetric) counts are exactly
+// Algorithm 2's, only the place where a pair's counters live differs. For an
+// anchor w the wedges are w - v - u for every neighbour v of w and every u in
+// the suffix of v's row ranked above both v and w; their endpoints u are the
+// same-side vertices ranked above w, so an anchor never needs more counters
+// than there are vertices above it on its side.
+#pragma once
+#include <cstdint>
+#include "common.cuh"
+
+namespace bb {
+
+// dense counters per job: 48Ki u32 (192 KiB of shared memory)
+constexpr uint32_t DENSE_CAP = 49152;
+// hash classes: per-warp table of at most 1024 slots, per-CTA table of at
+// most 16384 slots (u64 each), sized at 2x the distinct-endpoint bound
+constexpr uint32_t WARP_D_MAX = 512;
+constexpr uint32_t CTA_D_MAX = 8192;
+// prefer dense counters when the endpoint range is at most this many times
+// the distinct-endpoint bound
+constexpr uint32_t DENSE_RATIO = 4;
+// split one dense anchor over several CTAs when its wedges exceed both this
+// and 4x its endpoint range; parts are merged before the C(.,2) step
+constexpr uint64_t SPLIT_WEDGES = 65536;
+constexpr uint32_t MAX_PARTS = 64;
+constexpr uint32_t MAX_SPLIT_JOBS = 1u << 16;
+constexpr uint32_t MAX_GPART = 1u << 24;
+
+enum Cls : uint32_t { CLS_WARP = 0, CLS_CTAH = 1, CLS_DENSE = 2, NCLS = 3 };
+
+// One CTA job over dense counters: anchor (side rank << 1 | side), its
+// middle slice [m0, m1) of the anchor's row, and the split group (or
+// NO_GROUP). A job whose anchor has more than DENSE_CAP vertices above it
+// walks the endpoint range in DENSE_CAP windows.
+constexpr uint32_t NO_GROUP = 0xffffffffu;
+struct DenseJob {
+    uint32_t anchor;
+    uint32_t m0, m1;
+    uint32_t group;
+};
+
+struct SplitGroup {
+    uint32_t parts;   // CTAs contributing partial counters
+    uint32_t goff;    // offset of the merged counters in the partial buffer
+    uint32_t len;     // counters (endpoint range length)
+    uint32_t pad;
+};
+
+// counters written by the classifier
+enum Ctr : uint32_t {
+    CTR_WARP = 0, CTR_CTAH = 1, CTR_DENSE = 2, CTR_GROUPS = 3, CTR_GPART = 4, CTR_SPLITJOBS = 5,
+    NCTR = 8
+};
+
+// per-count scratch (zeroed before each count)
+struct CountScratch {
+    unsigned long long acc[4];   // balanced lo/hi, total lo/hi (128-bit sums)
+    uint32_t job_next[4];        // dynamic job cursors
+    uint32_t err;
+    uint32_t pad[3];
+};
+
+struct DevGraph {
+    int64_t nU = 0, nV = 0, nE = 0;
+    SideCSR side[2];
+    // raw input kept for flips (device; may be null for one-shot builds)
+    int64_t *rowptr = nullptr;
+    int32_t *col = nullptr;
+    int8_t *sign = nullptr;
+    // classification
+    uint32_t *warp_list = nullptr;   // anchors
+    uint32_t *ctah_list = nullptr;   // anchors
+    DenseJob *dense_jobs = nullptr;
+    SplitGroup *groups = nullptr;
+    uint32_t *gpart = nullptr;       // merged partial counters of split anchors
+    uint32_t gpart_cap = 0;          // entries in gpart
+    uint32_t *gdone = nullptr;       // per group arrival counters
+    uint32_t *ctr = nullptr;         // [NCTR]
+    unsigned long long *wedges = nullptr;  // [1]
+    uint32_t *err = nullptr;         // build error word
+    CountScratch *scratch = nullptr;
+    // host copies after the build
+    uint32_t h_ctr[NCTR] = {};
+    uint64_t h_wedges = 0;
+};
+
+// Bytes of device memory a graph of this size needs (graph + build temps).
+struct BuildSizes {
+    size_t graph_bytes;   // kept while the graph lives
+    size_t temp_bytes;    // needed only during the build
+};
+BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE);
+
+// Carve the graph's arrays out of `graph_mem` (graph_bytes long).
+void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_mem);
+
+// Build from device CSR (rowptr/col/sign on the device). Returns 0 or the
+// error bits; on success g.h_ctr / g.h_wedges are filled. Blocking only on
+// the validation check and at the end.
+uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
+                     void *temp_mem, cudaStream_t s);
+
+// Count balanced/total butterflies of a built graph on stream s. Writes the
+// 128-bit sums to g.scratch->acc (device); per_vertex may be null.
+void launch_count(const DevGraph &g, cudaStream_t s, int64_t *per_vertex_dev);
+
+// Flip the signs of listed input edges (device list of n indices).
+void launch_flip(DevGraph &g, const int64_t *edge_idx_dev, int64_t n, cudaStream_t s);
+
+// One-time per-device kernel attributes (shared-memory opt-ins).
+void build_init();
+void count_init();
+
+// entries of the split-merge buffer for a graph with nE edges
+inline size_t gpart_entries(int64_t nE) {
+    size_t want = (size_t)4 * (size_t)nE + 4096;
+    return want < MAX_GPART ? want : MAX_GPART;
+}
+
+}  // namespace bb

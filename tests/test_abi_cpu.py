@@ -1,0 +1,66 @@
+"""Host-only checks of the C ABI: the library loads, exports every function
+include/bb.h declares, and rejects bad arguments before touching a device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2308_07932_gb300 as pkg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bb.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bb_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2308_07932_gb300 import _build
+    _build.build()
+    return pkg.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ["bb_ctx_create", "bb_graph_upload", "bb_count", "bb_count_csr",
+                 "bb_count_csr_device", "bb_graph_flip_signs", "bb_last_error"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    out = subprocess.run(["nm", "-D", "--defined-only", pkg.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\s[TW]\s+(bb_\w+)$", out, flags=re.M))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert hasattr(built, n)
+
+
+def test_version_and_null_arguments(built):
+    assert "sm_103a" in pkg.version()
+    b, t = ctypes.c_int64(), ctypes.c_int64()
+    st = built.bb_count_csr(None, None, None, ctypes.byref(b), ctypes.byref(t), None, None)
+    assert st == 1  # BB_ERR_INVALID_ARG
+    assert b"NULL" in built.bb_last_error()
+    st = built.bb_ctx_create(0, 0, None)
+    assert st == 1
+
+
+def test_context_without_device_fails_loudly(built):
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if has_gpu:
+        pytest.skip("a GPU is present; covered by the gpu tests")
+    with pytest.raises(pkg.BBError) as ei:
+        pkg.Context(0)
+    assert ei.value.name in ("BB_ERR_NO_DEVICE", "BB_ERR_CUDA")
