@@ -1,0 +1,365 @@
+#!/usr/bin/env python3
+"""Throughput of balanced butterfly counting on GB300 (wedges/s).
+
+One step = the whole path on one graph already resident in HBM: validation,
+degree-priority ranking, sign-packed CSR build, work classification, wedge
+aggregation and the C(.,2) reduction (bb_count_csr_device). The metric unit
+is priority wedges (wedges u - v - w whose highest-priority vertex is an
+endpoint; Algorithm 2 buckets exactly these) per second.
+
+    python bench.py                       # 1 GPU, 2M x 500k Chung-Lu graph
+    python bench.py --impl reference      # the CPU oracle, bounded samples
+    torchrun --nproc-per-node N bench.py --gpus N   # N independent replicas
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "wedges/s"
+UNIT = "wedges/s"
+L2_FLUSH_BYTES = 512 << 20
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+WORKLOADS = {
+    "chunglu_2Mx500k_e20M_a2.1_p0.8": "chung_lu_2m",
+    "vote_500x50000_p0.4_b2": "vote_500_50k",
+    "uniform_2000x1000_e20000_p0.7": "uniform_2k_1k",
+}
+DEFAULT_WORKLOAD = "chunglu_2Mx500k_e20M_a2.1_p0.8"
+
+
+def make_graph(name):
+    from paper_2308_07932_gb300 import synth
+    return getattr(synth, WORKLOADS[name])()
+
+
+def priority_wedges(g) -> int:
+    """Number of wedges u - v - w with u the highest-priority vertex of the
+    three (Def. 4, ids u and |U|+v): per middle v and neighbour u ranked
+    above v, the neighbours of v ranked below u. Sizes the reference arm's
+    work in the metric's unit; computed on the host with NumPy sorts."""
+    u, v, _ = g.edges()
+    n = g.nU + g.nV
+    deg = np.concatenate([np.diff(g.rowptr), np.bincount(g.col, minlength=g.nV)])
+    order = np.lexsort((np.arange(n), deg))
+    rank = np.empty(n, np.int64)
+    rank[order] = np.arange(n)
+    rs = np.concatenate([rank[u], rank[g.nU + v]])
+    rd = np.concatenate([rank[g.nU + v], rank[u]])
+    o = np.lexsort((rd, rs))
+    rs, rd = rs[o], rd[o]
+    pos = np.arange(rs.size) - np.searchsorted(rs, rs, side="left")
+    return int(pos[rd > rs].sum())
+
+
+# ------------------------------------------------------------ clock samples
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int, period_ms: int = 100):
+        self.index, self.period_ms, self.proc = index, period_ms, None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={','.join(self.FIELDS)}",
+                 "--format=csv,noheader,nounits", f"-lms={self.period_ms}"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) == len(self.FIELDS):
+                self.rows.append(p)
+
+    def summary(self):
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------- CPU oracle
+def oracle_rate(g, wedges: int, stride: int, offset: int, threads: int):
+    """Times the oracle on every `stride`-th endpoint vertex (from `offset`)
+    of its cheaper side and extrapolates to the full graph: the graph-view
+    build is timed once (empty start list) and kept, the enumeration is
+    scaled by full steps / sampled steps. Returns (wedges/s, seconds of the
+    sampled call, description)."""
+    import oracle
+    from paper_2308_07932_gb300 import synth  # noqa: F401  (graph already built)
+    degU = np.diff(g.rowptr)
+    degV = np.bincount(g.col, minlength=g.nV)
+    c2 = lambda d: (d.astype(np.float64) * (d - 1) / 2).sum()  # noqa: E731
+    side = 1 if c2(degU) <= c2(degV) else 0     # endpoints on V when U-middles are cheaper
+    n_side = g.nV if side == 1 else g.nU
+    t0 = time.perf_counter()
+    oracle.sample_count(g, np.zeros(0, np.int64), side, threads)
+    t_view = time.perf_counter() - t0
+    starts = np.arange(offset % stride, n_side, stride, dtype=np.int64)
+    t0 = time.perf_counter()
+    _, _, steps, full = oracle.sample_count(g, starts, side, threads)
+    t_call = time.perf_counter() - t0
+    t_enum = max(t_call - t_view, 1e-9)
+    t_full = t_view + t_enum * (full / max(steps, 1))
+    desc = (f"every {stride}th endpoint vertex of side {'UV'[side]} ({starts.size} of {n_side}), "
+            f"{steps} of {full} two-hop steps; full-graph time extrapolated "
+            f"{t_full:.1f} s (view build {t_view:.2f} s kept once)")
+    return wedges / t_full, t_call, desc
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    g = make_graph(args.workload)
+    wedges = priority_wedges(g)
+    threads = os.cpu_count() or 1
+    # size each step at roughly 2-4 s of all-core work on this host
+    stride = args.ref_stride
+    for w in range(args.warmup):
+        oracle_rate(g, wedges, stride, w, threads)
+    rates, secs, desc = [], [], ""
+    for k in range(args.steps):
+        r, t, desc = oracle_rate(g, wedges, stride, args.warmup + k, threads)
+        rates.append(r)
+        secs.append(t)
+    value = statistics.median(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "nU": g.nU, "nV": g.nV, "nE": g.nE,
+                   "wedges": wedges},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"per step: {desc}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our path
+def count_sha() -> str:
+    h = hashlib.sha256()
+    for f in ["count.cu", "graph.cuh", "common.cuh"]:
+        with open(os.path.join(ROOT, "paper_2308_07932_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str, workload: str):
+    """ncu DRAM bytes per launch for `kernel` from profiles/traffic.json,
+    or None when missing or taken on other kernel sources."""
+    try:
+        rec = json.load(open(PROFILE_TRAFFIC))
+    except (OSError, ValueError):
+        return None
+    e = rec.get(workload, {}).get(kernel)
+    if not e or e.get("source_sha") != count_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def algorithmic_bytes(k: dict) -> int:
+    """Bytes the wedge kernel must read by its definition: 4 per wedge (the
+    packed entry of the suffix), 16 per middle (the anchor's entry, its
+    suffix start, and the middle's two row offsets), 16 per anchor (row
+    offsets and its work count); counters stay on chip."""
+    return 4 * k["wedges"] + 16 * k["middles"] + 16 * k["anchors"]
+
+
+def load_peaks():
+    try:
+        p = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def run_ours(args, world, rank, local_rank):
+    import torch
+    import paper_2308_07932_gb300 as pkg
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    g = make_graph(args.workload)
+    dev = torch.device("cuda", local_rank)
+    rowptr = torch.from_numpy(g.rowptr).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    sign = torch.from_numpy(g.sign).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = pkg.Context(local_rank)
+    ctx.set_stream(stream.cuda_stream)
+    ctx.set_timing(True)
+    torch.cuda.synchronize()
+
+    def step():
+        return ctx.count_device(g.nU, g.nV, g.nE, rowptr.data_ptr(), col.data_ptr(),
+                                sign.data_ptr())
+
+    for _ in range(args.warmup):
+        c = step()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    timings = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = pkg.launch_count()
+    with ClockSampler(local_rank) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)          # L2 flush, outside the timed events
+            ev[k][0].record(stream)
+            c = step()
+            ev[k][1].record(stream)
+            timings.append(ctx.last_timing())
+        torch.cuda.synchronize()
+    launches = pkg.launch_count() - launches0
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * c.wedges / (ms_per_step / 1e3)
+
+    # end to end through the public host-pointer call, pinned host inputs
+    h_rowptr = torch.from_numpy(g.rowptr).pin_memory()
+    h_col = torch.from_numpy(g.col).pin_memory()
+    h_sign = torch.from_numpy(g.sign).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+    ctx.set_timing(False)
+    for _ in range(2):
+        ctx.count_host_ptrs(g.nU, g.nV, g.nE, h_rowptr.data_ptr(), h_col.data_ptr(),
+                            h_sign.data_ptr())
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ce = ctx.count_host_ptrs(g.nU, g.nV, g.nE, h_rowptr.data_ptr(), h_col.data_ptr(),
+                                 h_sign.data_ptr())
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    assert (ce.balanced, ce.total) == (c.balanced, c.total)
+
+    # dominant wedge kernel and its roofline
+    kern = {k: {"ms": statistics.mean(t["kernels"][k]["ms"] for t in timings),
+                **{f: timings[-1]["kernels"][k][f] for f in ("wedges", "middles", "anchors")}}
+            for k in pkg.KERNELS}
+    build_ms = statistics.mean(t["build_ms"] for t in timings)
+    count_ms = statistics.mean(t["count_ms"] for t in timings)
+    top = max(kern, key=lambda k: kern[k]["ms"])
+    peak, peak_kind = load_peaks()
+    ach = algorithmic_bytes(kern[top]) / (kern[top]["ms"] / 1e3) / 1e9
+    clocks = clk.summary()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic",
+        "config": {
+            "workload": args.workload, "nU": g.nU, "nV": g.nV, "nE": g.nE, "wedges": c.wedges,
+            "balanced": c.balanced, "total": c.total, "inputs": "device-resident CSR",
+            "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        },
+        "phases_ms": {"build": build_ms, "count": count_ms,
+                      **{k: v["ms"] for k, v in kern.items()}},
+        "roofline": {"bound": "hbm", "kernel": top, "achieved": ach, "peak": peak, "unit": "GB/s",
+                     "frac": ach / peak, "peak_kind": peak_kind,
+                     "algorithmic_bytes": algorithmic_bytes(kern[top]),
+                     "traffic": traffic_for(top, args.workload)},
+        "e2e": {"value": world * c.wedges / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": g.rowptr.nbytes + g.col.nbytes + g.sign.nbytes,
+                "d2h_bytes_per_step": 52},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, secs, desc = oracle_rate(g, c.wedges, args.cpu_stride, 0, os.cpu_count() or 1)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count() or 1,
+                                "kind": "oracle", "sample": desc, "seconds": secs}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-stride", type=int, default=8,
+                    help="oracle sample: every k-th endpoint vertex")
+    ap.add_argument("--ref-stride", type=int, default=64,
+                    help="reference arm: every k-th endpoint vertex per step")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local_rank)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

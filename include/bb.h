@@ -137,6 +137,30 @@ BB_API bb_status bb_graph_info(const bb_graph *g, int64_t *nU, int64_t *nV, int6
 
 BB_API void bb_graph_free(bb_graph *g);
 
+/* ------------------------------------------------------------- tracing
+ * Phase timings of the last count on a context, from CUDA events recorded
+ * on the context's stream while timing is enabled (bb_ctx_set_timing).
+ * Index 0/1/2/3 of the per-kernel arrays is the dense-counter, CTA-hash,
+ * team and warp wedge kernel, in launch order; wedges/middles/anchors are
+ * the work each kernel was given (middle = one neighbour v of an anchor w,
+ * whose wedge suffix the kernel walks). build_ms covers validation through
+ * classification (0 for resident-graph counts). */
+#define BB_NKERNELS 4
+typedef struct {
+    double build_ms;
+    double count_ms;
+    double kernel_ms[BB_NKERNELS];
+    int64_t wedges[BB_NKERNELS];
+    int64_t middles[BB_NKERNELS];
+    int64_t anchors[BB_NKERNELS];
+} bb_timing;
+
+BB_API bb_status bb_ctx_set_timing(bb_ctx *ctx, int enable);
+BB_API bb_status bb_ctx_last_timing(const bb_ctx *ctx, bb_timing *out);
+
+/* Kernel launches the library has issued in this process. */
+BB_API uint64_t bb_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,6 +43,16 @@ class _Csr(ctypes.Structure):
                 ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p)]
 
 
+KERNELS = ("k_dense", "k_ctah", "k_team", "k_warp")
+
+
+class _Timing(ctypes.Structure):
+    _fields_ = [("build_ms", ctypes.c_double), ("count_ms", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double * len(KERNELS)),
+                ("wedges", ctypes.c_int64 * len(KERNELS)),
+                ("middles", ctypes.c_int64 * len(KERNELS)),
+                ("anchors", ctypes.c_int64 * len(KERNELS))]
+
 _lib = None
 _VP = ctypes.c_void_p
 _I64P = ctypes.POINTER(ctypes.c_int64)
@@ -72,6 +82,9 @@ def lib() -> ctypes.CDLL:
             "bb_graph_flip_signs": (S, [_VP, _VP, ctypes.c_int64]),
             "bb_graph_info": (S, [_VP, _I64P, _I64P, _I64P, _I64P]),
             "bb_graph_free": (None, [_VP]),
+            "bb_ctx_set_timing": (S, [_VP, ctypes.c_int]),
+            "bb_ctx_last_timing": (S, [_VP, ctypes.POINTER(_Timing)]),
+            "bb_launch_count": (ctypes.c_uint64, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -136,6 +149,19 @@ class Context:
     @property
     def device_bytes(self) -> int:
         return int(lib().bb_ctx_device_bytes(self._h))
+
+    def set_timing(self, on: bool = True):
+        """Record CUDA events around the build and each wedge kernel."""
+        _check(lib().bb_ctx_set_timing(self._h, 1 if on else 0))
+
+    def last_timing(self) -> dict:
+        """Phase timings (ms) and per-kernel work of the last count."""
+        t = _Timing()
+        _check(lib().bb_ctx_last_timing(self._h, ctypes.byref(t)))
+        return {"build_ms": t.build_ms, "count_ms": t.count_ms,
+                "kernels": {k: {"ms": t.kernel_ms[i], "wedges": t.wedges[i],
+                                "middles": t.middles[i], "anchors": t.anchors[i]}
+                            for i, k in enumerate(KERNELS)}}
 
     def set_stream(self, stream_ptr: int | None):
         """Run on a cudaStream_t given as an integer handle (e.g.
@@ -227,3 +253,8 @@ class Graph:
 
 def version() -> str:
     return lib().bb_version().decode()
+
+
+def launch_count() -> int:
+    """Kernel launches the library has issued in this process."""
+    return int(lib().bb_launch_count())

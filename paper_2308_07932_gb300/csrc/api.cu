@@ -1,6 +1,7 @@
 // api.cu - the C ABI declared in include/bb.h: contexts, device memory
 // budget, one-shot counts, resident graphs, errors.
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <chrono>
 #include <climits>
@@ -15,6 +16,12 @@
 #include "graph.cuh"
 
 using namespace bb;
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+}
+
+void bb::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 namespace {
 
@@ -103,7 +110,10 @@ struct HostResult {
     uint32_t count_err;
     uint32_t build_err;
     unsigned long long wedges;
+    unsigned long long cls_stats[3 * NCLS];
 };
+
+constexpr int NEV = 7;  // build begin/end, count kernel boundaries (5)
 
 }  // namespace
 
@@ -125,6 +135,10 @@ struct bb_ctx {
     int64_t layout_key[3] = {-1, -1, -1};
     HostResult *h_res = nullptr;  // pinned
     std::mutex mu;
+    bool timing = false;
+    cudaEvent_t ev[NEV] = {};
+    bool have_build_ev = false;
+    bb_timing last = {};
 };
 
 struct bb_graph {
@@ -195,9 +209,31 @@ bb_status finish_count(bb_ctx *ctx, const DevGraph &g, cudaStream_t s, int64_t *
     BB_CUDA(cudaMemcpyAsync(&h->build_err, g.err, 4, cudaMemcpyDeviceToHost, s),
             "copy build status");
     BB_CUDA(cudaMemcpyAsync(&h->wedges, g.wedges, 8, cudaMemcpyDeviceToHost, s), "copy wedges");
+    if (ctx->timing)
+        BB_CUDA(cudaMemcpyAsync(h->cls_stats, g.cls_stats, sizeof(h->cls_stats),
+                                cudaMemcpyDeviceToHost, s), "copy class stats");
     bb_status st = wait_bounded(s, "count");
     if (st != BB_OK) return st;
     BB_CUDA(cudaGetLastError(), "count kernels");
+    if (ctx->timing) {
+        bb_timing &T = ctx->last;
+        T = bb_timing{};
+        float ms = 0;
+        if (ctx->have_build_ev && cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess)
+            T.build_ms = ms;
+        for (int k = 0; k < BB_NKERNELS; k++)
+            if (cudaEventElapsedTime(&ms, ctx->ev[2 + k], ctx->ev[3 + k]) == cudaSuccess)
+                T.kernel_ms[k] = ms;
+        if (cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[2 + BB_NKERNELS]) == cudaSuccess)
+            T.count_ms = ms;
+        const int order[BB_NKERNELS] = {CLS_DENSE, CLS_CTAH, CLS_TEAM, CLS_WARP};
+        for (int k = 0; k < BB_NKERNELS; k++) {
+            T.wedges[k] = (int64_t)h->cls_stats[order[k]];
+            T.middles[k] = (int64_t)h->cls_stats[NCLS + order[k]];
+            T.anchors[k] = (int64_t)h->cls_stats[2 * NCLS + order[k]];
+        }
+        cudaGetLastError();
+    }
     if (h->build_err) return map_build_error(h->build_err);
     if (h->count_err) return fail(BB_ERR_CUDA, "internal count check failed (0x%x)", h->count_err);
     if (h->acc[1] || h->acc[3] || h->acc[0] > (unsigned long long)LLONG_MAX ||
@@ -229,14 +265,17 @@ bb_status count_device(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int6
         BB_CUDA(cudaMemsetAsync(g.gdone, 0, MAX_SPLIT_JOBS * 4, s), "zero merge counters");
         ctx->layout_key[0] = nU; ctx->layout_key[1] = nV; ctx->layout_key[2] = nE;
     }
+    if (ctx->timing) BB_CUDA(cudaEventRecord(ctx->ev[0], s), "event");
     uint32_t verr = build_graph(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s);
     BB_CUDA(cudaGetLastError(), "build kernels");
+    if (ctx->timing) BB_CUDA(cudaEventRecord(ctx->ev[1], s), "event");
+    ctx->have_build_ev = ctx->timing;
     if (verr) {
         ctx->layout_key[0] = -1;  // leave the merge buffers to be re-zeroed
         return map_build_error(verr);
     }
     if (pv_dev) return fail(BB_ERR_INVALID_ARG, "per-vertex counts are not available in this build");
-    launch_count(g, s, pv_dev);
+    launch_count(g, s, pv_dev, ctx->timing ? ctx->ev + 2 : nullptr);
     BB_CUDA(cudaGetLastError(), "count launch");
     return finish_count(ctx, g, s, balanced, total, wedges_opt);
 }
@@ -281,6 +320,10 @@ bb_status bb_ctx_create(int device, uint64_t hbm_budget_bytes, bb_ctx **out) {
         delete ctx;
         return cuda_fail(e, "cudaMallocHost");
     }
+    for (int k = 0; k < NEV; k++) {
+        e = cudaEventCreate(&ctx->ev[k]);
+        if (e != cudaSuccess) { bb_ctx_destroy(ctx); return cuda_fail(e, "cudaEventCreate"); }
+    }
     count_init();
     *out = ctx;
     return BB_OK;
@@ -295,9 +338,25 @@ void bb_ctx_destroy(bb_ctx *ctx) {
     dev_free(ctx, ctx->ws_in, ctx->ws_in_cap);
     dev_free(ctx, ctx->ws_pv, ctx->ws_pv_cap);
     if (ctx->h_res) cudaFreeHost(ctx->h_res);
+    for (int k = 0; k < NEV; k++)
+        if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
     if (ctx->own) cudaStreamDestroy(ctx->own);
     delete ctx;
 }
+
+bb_status bb_ctx_set_timing(bb_ctx *ctx, int enable) {
+    if (!ctx) return fail(BB_ERR_INVALID_ARG, "ctx is NULL");
+    ctx->timing = enable != 0;
+    return BB_OK;
+}
+
+bb_status bb_ctx_last_timing(const bb_ctx *ctx, bb_timing *out) {
+    if (!ctx || !out) return fail(BB_ERR_INVALID_ARG, "NULL argument");
+    *out = ctx->last;
+    return BB_OK;
+}
+
+uint64_t bb_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 bb_status bb_ctx_set_stream(bb_ctx *ctx, void *stream) {
     if (!ctx) return fail(BB_ERR_INVALID_ARG, "ctx is NULL");
@@ -437,7 +496,8 @@ bb_status bb_count(bb_graph *G, int64_t *balanced, int64_t *total, int64_t *per_
     bb_status st = set_device(ctx);
     if (st != BB_OK) return st;
     if (per_vertex_opt) return fail(BB_ERR_INVALID_ARG, "per-vertex counts are not available in this build");
-    launch_count(G->g, ctx->stream, nullptr);
+    ctx->have_build_ev = false;
+    launch_count(G->g, ctx->stream, nullptr, ctx->timing ? ctx->ev + 2 : nullptr);
     BB_CUDA(cudaGetLastError(), "count launch");
     return finish_count(ctx, G->g, ctx->stream, balanced, total, nullptr);
 }

@@ -297,6 +297,16 @@ __global__ void k_lo(SideCSR S, SideCSR O) {
     }
 }
 
+// hstart(v): first index in v's row of a neighbour inside the hub window of
+// the neighbours' side (side ranks >= window_base)
+__global__ void k_hstart(SideCSR S, uint32_t window_base) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < S.n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t b = S.off[r];
+        S.hstart[r] = (uint32_t)(lower_bound_u32(S.adj, b, S.off[r + 1], window_base << 1) - b);
+    }
+}
+
 __global__ void k_epos(const uint32_t *eid, int64_t nE, uint32_t *epos) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nE;
          p += (int64_t)gridDim.x * blockDim.x)
@@ -319,7 +329,7 @@ __global__ void k_sfx_work(SideCSR S, SideCSR O, const uint32_t *eid_s, const ui
     for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < S.n; r += warps) {
         int64_t b = S.off[r], e = S.off[r + 1];
         uint32_t g = S.grank[r];
-        uint64_t sum = 0;
+        uint64_t sum = 0, nh = 0;
         for (int64_t p = b + lane; p < e; p += 32) {
             uint32_t v = S.adj[p] >> 1;
             int64_t vb = O.off[v];
@@ -328,9 +338,12 @@ __global__ void k_sfx_work(SideCSR S, SideCSR O, const uint32_t *eid_s, const ui
             else st = (uint32_t)(epos_o[eid_s[p]] - vb) + 1u;
             S.sfx[p] = st;
             sum += (uint64_t)(O.deg[v] - st);
+            uint32_t hs = O.hstart[v];
+            nh += hs > st ? (uint64_t)(hs - st) : 0ull;
         }
         sum = warp_sum_u64(sum);
-        if (lane == 0) S.work[r] = sum;
+        nh = warp_sum_u64(nh);
+        if (lane == 0) { S.work[r] = sum; S.work_nh[r] = nh; }
         mine += sum;
     }
     if (lane == 0 && mine) atomicAdd(&block_sum, mine);
@@ -353,19 +366,25 @@ __device__ __forceinline__ uint32_t bucket_of(uint64_t w) { return 63u - (uint32
 // decides each anchor's class (and split) and counts entries per bucket
 __global__ void k_classify(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
     __shared__ uint32_t cnt[NCLS * NB];
+    __shared__ unsigned long long stats[3 * NCLS];
     for (int k = threadIdx.x; k < NCLS * NB; k += blockDim.x) cnt[k] = 0;
+    if (threadIdx.x < 3 * NCLS) stats[threadIdx.x] = 0;
     __syncthreads();
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < S.n;
          r += (int64_t)gridDim.x * blockDim.x) {
         uint64_t W = S.work[r];
         uint32_t meta = 0;
         if (W > 0) {
-            uint64_t above = (uint64_t)(S.n - r - 1);
-            uint64_t dh = W < above ? W : above;
+            const uint64_t above = (uint64_t)(S.n - r - 1);
+            const uint64_t wb = S.n > (int64_t)HUB_WINDOW ? (uint64_t)S.n - HUB_WINDOW : 0;
+            const uint64_t above_nh = wb > (uint64_t)r + 1 ? wb - (uint64_t)r - 1 : 0;
+            const uint64_t wnh = S.work_nh[r];
+            const uint64_t dnh = wnh < above_nh ? wnh : above_nh;
             uint32_t cls;
-            if (above <= DENSE_CAP && (above <= DENSE_RATIO * dh || dh > CTA_D_MAX)) cls = CLS_DENSE;
-            else if (dh <= WARP_D_MAX) cls = CLS_WARP;
-            else if (dh <= CTA_D_MAX) cls = CLS_CTAH;
+            if (W <= WARP_W_MAX) cls = CLS_WARP;
+            else if (W <= TEAM_W_MAX && dnh * 5 / 4 < TEAM_CAP) cls = CLS_TEAM;
+            else if (above <= DENSE_CAP) cls = CLS_DENSE;
+            else if (dnh * 2 < CTAH_CAP) cls = CLS_CTAH;
             else cls = CLS_DENSE;  // endpoint range walked in DENSE_CAP windows
             uint32_t parts = 1;
             if (cls == CLS_DENSE && above <= DENSE_CAP && above > 0) {
@@ -388,12 +407,17 @@ __global__ void k_classify(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
             uint32_t b = bucket_of(parts > 1 ? W / parts : W);
             meta = 1u | cls << 1 | b << 3 | parts << 9;
             atomicAdd(&cnt[cls * NB + b], parts);
+            atomicAdd(&stats[cls], (unsigned long long)W);
+            atomicAdd(&stats[NCLS + cls], (unsigned long long)(S.off[r + 1] - S.off[r]));
+            atomicAdd(&stats[2 * NCLS + cls], 1ull);
         }
         T.meta[r] = meta;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < NCLS * NB; k += blockDim.x)
         if (cnt[k]) atomicAdd(&T.bucket_cnt[k], cnt[k]);
+    if (threadIdx.x < 3 * NCLS && stats[threadIdx.x])
+        atomicAdd(&G.cls_stats[threadIdx.x], stats[threadIdx.x]);
 }
 
 // bucket bases in decreasing bucket order; class totals to the counters
@@ -405,7 +429,7 @@ __global__ void k_bucket_base(ClassifyTemp T, DevGraph G) {
             T.bucket_base[c * NB + b] = acc;
             acc += T.bucket_cnt[c * NB + b];
         }
-        G.ctr[c] = acc;  // CTR_WARP, CTR_CTAH, CTR_DENSE
+        G.ctr[c] = acc;  // CTR_WARP, CTR_TEAM, CTR_CTAH, CTR_DENSE
     }
 }
 
@@ -436,6 +460,7 @@ __global__ void k_emit(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
             uint32_t pos = base[key] + local;
             uint32_t anchor = (uint32_t)r << 1 | (uint32_t)side;
             if (cls == CLS_WARP) G.warp_list[pos] = anchor;
+            else if (cls == CLS_TEAM) G.team_list[pos] = anchor;
             else if (cls == CLS_CTAH) G.ctah_list[pos] = anchor;
             else {
                 uint32_t deg = (uint32_t)(S.off[r + 1] - S.off[r]);
@@ -465,7 +490,7 @@ struct Carver {
 
 size_t side_bytes(int64_t n, int64_t nE) {
     return align256((size_t)(n + 1) * 8) + 2 * align256((size_t)nE * 4) +
-           5 * align256((size_t)(n > 0 ? n : 1) * 4) + align256((size_t)(n > 0 ? n : 1) * 8);
+           6 * align256((size_t)(n > 0 ? n : 1) * 4) + 2 * align256((size_t)(n > 0 ? n : 1) * 8);
 }
 
 }  // namespace
@@ -479,12 +504,12 @@ BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE) {
     int64_t n = nU + nV;
     int64_t nmax = std::max<int64_t>(std::max(nU, nV), 1);
     size_t g = side_bytes(nU, nE) + side_bytes(nV, nE);
-    g += 2 * align256((size_t)(n + 1) * 4);                                  // warp/ctah lists
+    g += 3 * align256((size_t)(n + 1) * 4);                                  // warp/team/ctah lists
     g += align256((size_t)(n + MAX_SPLIT_JOBS) * sizeof(DenseJob));          // dense jobs
     g += align256((size_t)MAX_SPLIT_JOBS * sizeof(SplitGroup));              // groups
     g += align256((size_t)MAX_SPLIT_JOBS * 4);                               // gdone
     g += align256(gpart_entries(nE) * 4);
-    g += align256(NCTR * 4) + 256 + 256 + align256(sizeof(CountScratch));
+    g += align256(NCTR * 4) + 256 + 256 + 256 + align256(sizeof(CountScratch));
     size_t t = 0;
     t += align256((size_t)nU * 4 + 4) + align256((size_t)nV * 4 + 4);      // deg by id
     t += 2 * align256((size_t)nE * 4 + 4);                                   // eid
@@ -513,10 +538,13 @@ void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_m
         S.grank = c.take<uint32_t>(n1);
         S.deg = c.take<uint32_t>(n1);
         S.lo = c.take<uint32_t>(n1);
+        S.hstart = c.take<uint32_t>(n1);
         S.work = c.take<uint64_t>(n1);
+        S.work_nh = c.take<uint64_t>(n1);
     }
     int64_t n = nU + nV;
     g.warp_list = c.take<uint32_t>(n + 1);
+    g.team_list = c.take<uint32_t>(n + 1);
     g.ctah_list = c.take<uint32_t>(n + 1);
     g.dense_jobs = c.take<DenseJob>(n + MAX_SPLIT_JOBS);
     g.groups = c.take<SplitGroup>(MAX_SPLIT_JOBS);
@@ -525,6 +553,7 @@ void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_m
     g.gpart = c.take<uint32_t>(g.gpart_cap);
     g.ctr = c.take<uint32_t>(NCTR);
     g.wedges = c.take<unsigned long long>(1);
+    g.cls_stats = c.take<unsigned long long>(3 * NCLS);
     g.err = c.take<uint32_t>(1);
     g.scratch = c.take<CountScratch>(1);
 }
@@ -552,14 +581,15 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
     cudaMemsetAsync(g.err, 0, 4, s);
     cudaMemsetAsync(g.ctr, 0, NCTR * 4, s);
     cudaMemsetAsync(g.wedges, 0, 8, s);
+    cudaMemsetAsync(g.cls_stats, 0, 3 * NCLS * 8, s);
     cudaMemsetAsync(deg_in[1], 0, (size_t)nV * 4, s);
     cudaMemsetAsync(cursorV, 0, (size_t)nV * 4, s);
     cudaMemsetAsync(T.bucket_cnt, 0, NCLS * NB * 4, s);
 
     // 1. validate + degrees
-    if (nU > 0) k_validate_rows<<<grid_for(nU, BT, 8192), BT, 0, s>>>(rowptr, nU, nE, deg_in[0], g.err);
-    if (nE > 0) k_validate_edges<<<grid_for(nE, BT, 16384), BT, 0, s>>>(col, sign, nE, nV, deg_in[1], g.err);
-    if (nV > 0) k_check_degree<<<grid_for(nV, BT, 8192), BT, 0, s>>>(deg_in[1], nV, g.err);
+    if (nU > 0) k_validate_rows<<<grid_for(nU, BT, 8192), BT, 0, s>>>(rowptr, nU, nE, deg_in[0], g.err); note_launch();
+    if (nE > 0) k_validate_edges<<<grid_for(nE, BT, 16384), BT, 0, s>>>(col, sign, nE, nV, deg_in[1], g.err); note_launch();
+    if (nV > 0) k_check_degree<<<grid_for(nV, BT, 8192), BT, 0, s>>>(deg_in[1], nV, g.err); note_launch();
     uint32_t herr = 0;
     cudaMemcpyAsync(&herr, g.err, 4, cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
@@ -572,51 +602,59 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
         if (n == 0) continue;
         SideCSR &S = g.side[sd];
         // sort ids by degree (stable => ties by id): reuse id_of_sr / deg as buffers
-        k_iota<<<grid_for(n, BT, 8192), BT, 0, s>>>(S.sr_of_id, n);
+        k_iota<<<grid_for(n, BT, 8192), BT, 0, s>>>(S.sr_of_id, n); note_launch();
         cudaMemcpyAsync(S.lo, deg_in[sd], (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
         radix_sort_pairs_u32(S.lo, S.sr_of_id, ralt_k, ralt_v, n, 16, ptemp, s);
         cudaMemcpyAsync(ralt_v, S.sr_of_id, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
-        k_side_rank<<<grid_for(n, BT, 8192), BT, 0, s>>>(ralt_v, S.lo, n, S);
+        k_side_rank<<<grid_for(n, BT, 8192), BT, 0, s>>>(ralt_v, S.lo, n, S); note_launch();
     }
-    if (nU > 0) k_global_rank<<<grid_for(nU, BT, 8192), BT, 0, s>>>(g.side[0], g.side[1].deg, nV, 1);
-    if (nV > 0) k_global_rank<<<grid_for(nV, BT, 8192), BT, 0, s>>>(g.side[1], g.side[0].deg, nU, 0);
+    if (nU > 0) k_global_rank<<<grid_for(nU, BT, 8192), BT, 0, s>>>(g.side[0], g.side[1].deg, nV, 1); note_launch();
+    if (nV > 0) k_global_rank<<<grid_for(nV, BT, 8192), BT, 0, s>>>(g.side[1], g.side[0].deg, nU, 0); note_launch();
 
     // 3. offsets, row fill, row sorts, lo
     for (int sd = 0; sd < 2; sd++)
         scan_exclusive_u32_to_i64(g.side[sd].deg, g.side[sd].off, ns[sd], ptemp, s);
     if (nU > 0 && nE > 0)
         k_fill<<<grid_for(nU * 32, BT, 16384), BT, 0, s>>>(rowptr, col, sign, nU, g.side[0],
-                                                          g.side[1], cursorV, eid[0], eid[1]);
+                                                          g.side[1], cursorV, eid[0], eid[1]); note_launch();
     for (int sd = 0; sd < 2; sd++) {
         int64_t n = ns[sd];
         if (n == 0 || nE == 0) continue;
         SideCSR &S = g.side[sd];
         int64_t *bd = bounds + sd * 8;
         // bd[0..3]: first rank with degree > 1, > 32, > 2048, > 16384; bd[4] = n
-        k_row_bounds<<<1, 32, 0, s>>>(S.deg, n, bd);
-        k_sort_rows_warp<<<grid_for(n * 32, BT, 16384), BT, 0, s>>>(S, eid[sd], bd, g.err);
-        k_sort_rows_smem<2048, 256><<<4096, 256, 2048 * 8, s>>>(S, eid[sd], bd, 1, g.err);
-        k_sort_rows_smem<16384, 1024><<<1024, 1024, 16384 * 8, s>>>(S, eid[sd], bd, 2, g.err);
+        k_row_bounds<<<1, 32, 0, s>>>(S.deg, n, bd); note_launch();
+        k_sort_rows_warp<<<grid_for(n * 32, BT, 16384), BT, 0, s>>>(S, eid[sd], bd, g.err); note_launch();
+        k_sort_rows_smem<2048, 256><<<4096, 256, 2048 * 8, s>>>(S, eid[sd], bd, 1, g.err); note_launch();
+        k_sort_rows_smem<16384, 1024><<<1024, 1024, 16384 * 8, s>>>(S, eid[sd], bd, 2, g.err); note_launch();
         int64_t n_other = ns[1 - sd];
         int key_bits = 1;
         while (key_bits < 32 && ((uint64_t)1 << key_bits) < (uint64_t)(2 * n_other + 2)) key_bits++;
-        k_sort_rows_radix<<<512, RR_THREADS, 0, s>>>(S, eid[sd], bd, 3, bufA, bufB, key_bits, g.err);
+        k_sort_rows_radix<<<512, RR_THREADS, 0, s>>>(S, eid[sd], bd, 3, bufA, bufB, key_bits, g.err); note_launch();
     }
-    for (int sd = 0; sd < 2; sd++)
-        if (ns[sd] > 0) k_lo<<<grid_for(ns[sd], BT, 8192), BT, 0, s>>>(g.side[sd], g.side[1 - sd]);
+    for (int sd = 0; sd < 2; sd++) {
+        if (ns[sd] == 0) continue;
+        k_lo<<<grid_for(ns[sd], BT, 8192), BT, 0, s>>>(g.side[sd], g.side[1 - sd]); note_launch();
+        int64_t n_other = ns[1 - sd];
+        uint32_t wb = n_other > (int64_t)HUB_WINDOW ? (uint32_t)(n_other - HUB_WINDOW) : 0u;
+        k_hstart<<<grid_for(ns[sd], BT, 8192), BT, 0, s>>>(g.side[sd], wb); note_launch();
+    }
 
     // 4. twin positions, suffix starts, work per anchor
     uint32_t *epos[2] = {(uint32_t *)bufA, (uint32_t *)bufA + (nE + 1)};
     if (nE > 0) {
         for (int sd = 0; sd < 2; sd++)
-            k_epos<<<grid_for(nE, BT, 16384), BT, 0, s>>>(eid[sd], nE, epos[sd]);
+            k_epos<<<grid_for(nE, BT, 16384), BT, 0, s>>>(eid[sd], nE, epos[sd]); note_launch();
         for (int sd = 0; sd < 2; sd++)
             if (ns[sd] > 0)
                 k_sfx_work<<<grid_for(ns[sd] * 32, BT, 4096), BT, 0, s>>>(
-                    g.side[sd], g.side[1 - sd], eid[sd], epos[1 - sd], g.wedges);
+                    g.side[sd], g.side[1 - sd], eid[sd], epos[1 - sd], g.wedges); note_launch();
     } else {
         for (int sd = 0; sd < 2; sd++)
-            if (ns[sd] > 0) cudaMemsetAsync(g.side[sd].work, 0, (size_t)ns[sd] * 8, s);
+            if (ns[sd] > 0) {
+                cudaMemsetAsync(g.side[sd].work, 0, (size_t)ns[sd] * 8, s);
+                cudaMemsetAsync(g.side[sd].work_nh, 0, (size_t)ns[sd] * 8, s);
+            }
     }
 
     // 5. classes
@@ -624,15 +662,15 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
         if (ns[sd] == 0) continue;
         T.meta = meta[sd];
         T.grp = grp[sd];
-        k_classify<<<grid_for(ns[sd], BT, 4096), BT, 0, s>>>(g.side[sd], sd, T, g);
+        k_classify<<<grid_for(ns[sd], BT, 4096), BT, 0, s>>>(g.side[sd], sd, T, g); note_launch();
     }
-    k_bucket_base<<<1, 32, 0, s>>>(T, g);
+    k_bucket_base<<<1, 32, 0, s>>>(T, g); note_launch();
     cudaMemsetAsync(T.bucket_cnt, 0, NCLS * NB * 4, s);
     for (int sd = 0; sd < 2; sd++) {
         if (ns[sd] == 0) continue;
         T.meta = meta[sd];
         T.grp = grp[sd];
-        k_emit<<<grid_for(ns[sd], BT, 2048), BT, 0, s>>>(g.side[sd], sd, T, g);
+        k_emit<<<grid_for(ns[sd], BT, 2048), BT, 0, s>>>(g.side[sd], sd, T, g); note_launch();
     }
     return 0;
 }

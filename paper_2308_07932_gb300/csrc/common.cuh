@@ -6,6 +6,9 @@
 
 namespace bb {
 
+// counts kernel launches issued by the library (reported by bb_launch_count)
+void note_launch();
+
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int WARP = 32;
 
@@ -42,7 +45,10 @@ struct SideCSR {
     uint32_t *grank;      // [n]   side rank -> global priority rank
     uint32_t *deg;        // [n]   side rank -> degree
     uint32_t *lo;         // [n]   side rank -> neighbours of lower priority
+    uint32_t *hstart;     // [n]   side rank -> first index in its row of a neighbour in
+                          //       the other side's hub window (top HUB_WINDOW ranks)
     uint64_t *work;       // [n]   side rank -> wedges anchored at this vertex
+    uint64_t *work_nh;    // [n]   of those, wedges whose endpoint lies below the hub window
 };
 
 __host__ __device__ __forceinline__ uint64_t c2(uint64_t n) {

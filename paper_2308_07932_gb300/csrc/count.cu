@@ -9,16 +9,24 @@
 // symmetric and A asymmetric wedges adds C(S,2) + C(A,2) balanced and
 // C(S+A,2) total butterflies (Lemma 2).
 //
-// Counter storage per work class:
-//   dense  - one u32 per endpoint side rank in shared memory (S in the low
-//            16 bits, A in the high 16 bits), for anchors with a small
-//            endpoint range; long ranges are walked in windows; very heavy
-//            anchors are split over several CTAs whose counters are merged
-//            in global memory before the C(.,2) step (C is not additive);
-//   hash   - open addressing in shared memory, one u64 per slot
-//            (endpoint + 1 in the high half, S | A << 16 in the low half),
-//            sized at twice the anchor's distinct-endpoint bound; one table
-//            per warp (small anchors) or per CTA.
+// Work is spread by a team walker: a team (a warp, or a whole CTA) loads a
+// chunk of the anchor's middles, scans their suffix lengths, and splits the
+// chunk's wedges evenly across its warps; each warp finds the middle of each
+// of its wedges with a shuffle search over a 32-middle window.
+//
+// Counters, per class (all in shared memory; S in bits 0..15, A in bits
+// 16..31 of a u32, both bounded by the anchor's degree):
+//   warp  - small anchors, one per warp, open-addressing hash (u64 slots:
+//           endpoint + 1 in the high half);
+//   team  - medium anchors, one per 128-thread CTA: dense counters for the
+//           hub window (top HUB_WINDOW ranks of the side, where most
+//           endpoints fall) with a list of touched counters, and a hash for
+//           the endpoints below the window;
+//   ctah  - like team with a 512-thread CTA and a 16Ki-slot hash;
+//   dense - heavy anchors with a short endpoint range: dense counters over
+//           the whole range (walked in windows when longer than DENSE_CAP);
+//           the heaviest are split over CTAs and merged in global memory
+//           before the C(.,2) step (C is not additive).
 #include <algorithm>
 #include "graph.cuh"
 
@@ -26,11 +34,11 @@ namespace bb {
 
 namespace {
 
-constexpr int DENSE_THREADS = 512;
+constexpr int WARP_THREADS = 256;    // 8 independent warps per CTA
+constexpr int TEAM_THREADS = 128;    // one team per CTA
 constexpr int CTAH_THREADS = 512;
-constexpr uint32_t CTAH_CAP = 2 * CTA_D_MAX;        // 16384 slots, 128 KiB
-constexpr int WARPH_THREADS = 256;                   // 8 warps per CTA
-constexpr uint32_t WARPH_CAP = 2 * WARP_D_MAX;      // 1024 slots per warp
+constexpr int DENSE_THREADS = 512;
+constexpr int UNROLL = 4;            // wedge loads in flight per lane
 
 __device__ __forceinline__ void acc_add(CountScratch *sc, unsigned long long bal,
                                         unsigned long long tot) {
@@ -69,55 +77,115 @@ __device__ __forceinline__ void block_sum2(unsigned long long &a, unsigned long 
     __syncthreads();
 }
 
-// Walk the wedges of the anchor whose row starts at rb in side S, over its
-// middles [m0, m1), batches of 32 middles taken by this warp starting at
-// batch `first` with stride `stride`. With CLIP, only endpoints whose side
-// rank lies in [e0, e1) are visited. add(u_side_rank, asymmetric) per wedge.
-//
-// Each batch is flattened: lane j holds middle j's suffix (start, length),
-// a warp scan gives every wedge of the batch an index, and each lane finds
-// the middle of its wedge by binary search over the 32 running sums.
-template <bool CLIP, typename F>
-__device__ __forceinline__ void walk(const SideCSR &S, const SideCSR &O, int64_t rb, uint32_t m0,
-                                     uint32_t m1, uint32_t e0, uint32_t e1, uint32_t first,
-                                     uint32_t stride, F &&add) {
-    const unsigned lane = lane_id();
-    for (uint32_t mb = m0 + first * 32u; mb < m1; mb += stride * 32u) {
-        uint32_t j = mb + lane;
-        uint32_t len = 0, sw = 0;
+template <int TS>
+__device__ __forceinline__ void team_sync() {
+    if constexpr (TS == 32) __syncwarp();
+    else __syncthreads();   // teams of more than one warp are whole CTAs
+}
+
+// A chunk of middles, compacted to those with a non-empty segment.
+struct Desc {
+    long long st;     // first entry of the segment in the middle's row (absolute)
+    uint32_t excl;    // wedges of the chunk before this middle
+    uint32_t sw;      // sign bit of the anchor's edge to the middle
+};
+
+template <int TS>
+struct WalkSmem {
+    Desc desc[TS];
+    uint32_t incl[TS];
+    unsigned long long warp_part[TS / 32];
+    uint32_t tot[2];
+};
+
+// Walk the wedges of one anchor's middles [m0, m1) (row starting at rb in
+// side S) as a team of TS threads (t = thread index in the team). seg(v,
+// sfx, st, len) gives middle v's segment [st, st+len) of its row;
+// add(u_side_rank, asymmetric) is called once per wedge.
+template <int TS, typename Seg, typename Add>
+__device__ __forceinline__ void team_walk(const SideCSR &S, const SideCSR &O, int64_t rb,
+                                          uint32_t m0, uint32_t m1, WalkSmem<TS> &sm, int t,
+                                          Seg &&seg, Add &&add) {
+    constexpr int NW = TS / 32;
+    const int lane = t & 31, w = t >> 5;
+    for (uint32_t mc = m0; mc < m1; mc += TS) {
+        const uint32_t j = mc + (uint32_t)t;
         long long st = 0;
+        uint32_t len = 0, sw = 0;
         if (j < m1) {
-            uint32_t ent = S.adj[rb + j];
-            uint32_t v = ent >> 1;
+            const uint32_t ent = S.adj[rb + j];
             sw = ent & 1u;
-            long long ve = O.off[v + 1];
-            st = O.off[v] + S.sfx[rb + j];
-            if (CLIP) {
-                long long a = lower_bound_u32(O.adj, st, ve, e0 << 1);
-                ve = lower_bound_u32(O.adj, a, ve, e1 << 1);
-                st = a;
-            }
-            len = (uint32_t)(ve - st);
+            seg(ent >> 1, S.sfx[rb + j], st, len);
         }
-        uint32_t incl = warp_incl_scan(len);
-        uint32_t total = __shfl_sync(FULL, incl, 31);
-        uint32_t excl = incl - len;
-        for (uint32_t k = 0; k < total; k += 32) {
-            uint32_t i = k + lane;
-            uint32_t m = 0;
+        // inclusive team scan of (len, nonzero) packed in one u64
+        unsigned long long x = (unsigned long long)len | ((unsigned long long)(len > 0) << 32);
 #pragma unroll
-            for (int b = 16; b >= 1; b >>= 1) {
-                uint32_t c = __shfl_sync(FULL, incl, m + b - 1);
-                if (c <= i) m += b;
+        for (int d = 1; d < 32; d <<= 1) {
+            unsigned long long y = __shfl_up_sync(FULL, x, d);
+            if (lane >= d) x += y;
+        }
+        if constexpr (NW > 1) {
+            if (lane == 31) sm.warp_part[w] = x;
+            team_sync<TS>();
+            unsigned long long add_w = 0;
+            for (int k = 0; k < w; k++) add_w += sm.warp_part[k];
+            x += add_w;
+        }
+        const uint32_t incl = (uint32_t)x, nzi = (uint32_t)(x >> 32);
+        if (len > 0) {
+            sm.desc[nzi - 1] = Desc{st, incl - len, sw};
+            sm.incl[nzi - 1] = incl;
+        }
+        if (t == TS - 1) { sm.tot[0] = incl; sm.tot[1] = nzi; }
+        team_sync<TS>();
+        const uint32_t T = sm.tot[0], NZ = sm.tot[1];
+        if (T > 0) {
+            const uint32_t a = (uint32_t)((unsigned long long)T * w / NW);
+            const uint32_t b = (uint32_t)((unsigned long long)T * (w + 1) / NW);
+            // first middle whose running sum exceeds a
+            uint32_t lo = 0, hi = NZ;
+            while (lo < hi) {
+                uint32_t mid = (lo + hi) >> 1;
+                if (sm.incl[mid] <= a) lo = mid + 1; else hi = mid;
             }
-            long long stm = __shfl_sync(FULL, st, m);
-            uint32_t exm = __shfl_sync(FULL, excl, m);
-            uint32_t swm = __shfl_sync(FULL, sw, m);
-            if (i < total) {
-                uint32_t x = O.adj[stm + (i - exm)];
-                add(x >> 1, (x ^ swm) & 1u);
+            uint32_t m = lo;
+            for (uint32_t base = a; base < b;) {
+                long long addr[UNROLL];
+                uint32_t swv[UNROLL];
+                bool ok[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; u++) {
+                    ok[u] = false;
+                    if (base < b) {
+                        const uint32_t wi = m + lane < NZ ? m + lane : NZ - 1;
+                        const uint32_t wv = sm.incl[wi];
+                        const uint32_t i = base + lane;
+                        uint32_t k = 0;
+#pragma unroll
+                        for (int s2 = 16; s2 >= 1; s2 >>= 1) {
+                            uint32_t c = __shfl_sync(FULL, wv, k + s2 - 1);
+                            if (c <= i) k += s2;
+                        }
+                        if (i < b) {
+                            const Desc d = sm.desc[m + k];
+                            addr[u] = d.st + (long long)(i - d.excl);
+                            swv[u] = d.sw;
+                            ok[u] = true;
+                        }
+                        m += __popc(__ballot_sync(FULL, wv <= base + 32));
+                        base += 32;
+                    }
+                }
+                uint32_t xv[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; u++)
+                    if (ok[u]) xv[u] = O.adj[addr[u]];
+#pragma unroll
+                for (int u = 0; u < UNROLL; u++)
+                    if (ok[u]) add(xv[u] >> 1, (xv[u] ^ swv[u]) & 1u);
             }
         }
+        team_sync<TS>();
     }
 }
 
@@ -140,156 +208,250 @@ __device__ __forceinline__ void hash_add(unsigned long long *tab, uint32_t shift
     set_error(err, E_PROBE);
 }
 
-__device__ __forceinline__ void table_geometry(uint64_t dh, uint32_t min_cap, uint32_t &cap,
-                                               uint32_t &shift) {
+// table of 2^k slots, 2^k >= max(min_cap, need + need/4 + 1), at most max_cap
+__device__ __forceinline__ void table_geometry(uint64_t need, uint32_t min_cap, uint32_t max_cap,
+                                               uint32_t &cap, uint32_t &shift) {
+    uint64_t want = need + need / 4 + 1;
     cap = min_cap;
     shift = 32 - (31 - __clz(min_cap));
-    while ((uint64_t)cap < 2 * dh) { cap <<= 1; shift--; }
+    while ((uint64_t)cap < want && cap < max_cap) { cap <<= 1; shift--; }
+}
+
+struct Anchor {
+    SideCSR S, O;
+    uint32_t r;
+    int64_t rb;
+    uint32_t deg;
+};
+
+__device__ __forceinline__ Anchor load_anchor(const DevGraph &G, uint32_t anchor) {
+    Anchor a;
+    const int sd = anchor & 1u;
+    a.S = sd ? G.side[1] : G.side[0];
+    a.O = sd ? G.side[0] : G.side[1];
+    a.r = anchor >> 1;
+    a.rb = a.S.off[a.r];
+    a.deg = (uint32_t)(a.S.off[a.r + 1] - a.rb);
+    return a;
+}
+
+// the whole wedge suffix of a middle
+struct FullSeg {
+    const SideCSR &O;
+    __device__ void operator()(uint32_t v, uint32_t sfx, long long &st, uint32_t &len) const {
+        const long long b = O.off[v];
+        st = b + sfx;
+        len = (uint32_t)(O.off[v + 1] - st);
+    }
+};
+
+// ------------------------------------------------------------ warp class
+struct WarpSmem {
+    unsigned long long tab[WARP_CAP];
+    WalkSmem<32> walk;
+};
+
+__global__ void __launch_bounds__(WARP_THREADS) k_warp(DevGraph G) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[threadIdx.x >> 5];
+    const unsigned lane = lane_id();
+    for (uint32_t i = lane; i < WARP_CAP; i += 32) sm.tab[i] = 0ull;
+    __syncwarp();
+    const uint32_t n = G.ctr[CTR_WARP];
+    const uint32_t gw = (blockIdx.x * WARP_THREADS + threadIdx.x) >> 5;
+    const uint32_t GW = (gridDim.x * WARP_THREADS) >> 5;
+    uint32_t *err = &G.scratch->err;
+    unsigned long long bal = 0, tot = 0;
+    for (uint32_t idx = gw; idx < n; idx += GW) {
+        const Anchor A = load_anchor(G, G.warp_list[idx]);
+        const uint64_t W = A.S.work[A.r], above = (uint64_t)(A.S.n - A.r - 1);
+        uint32_t cap, shift;
+        table_geometry(W < above ? W : above, 32, WARP_CAP, cap, shift);
+        const uint32_t mask = cap - 1;
+        team_walk<32>(A.S, A.O, A.rb, 0, A.deg, sm.walk, (int)lane, FullSeg{A.O},
+                      [&](uint32_t u, uint32_t asym) {
+                          hash_add(sm.tab, shift, mask, u + 1, asym ? INC_ASYM : INC_SYM, err);
+                      });
+        for (uint32_t i = lane; i < cap; i += 32) {
+            unsigned long long t = sm.tab[i];
+            if (t) { pair_terms((uint32_t)t, bal, tot); sm.tab[i] = 0ull; }
+        }
+        __syncwarp();
+    }
+    block_sum2<WARP_THREADS>(bal, tot);
+    if (threadIdx.x == 0) acc_add(G.scratch, bal, tot);
+}
+
+// ------------------------------------------------- team and CTA-hash classes
+template <int TS, uint32_t HCAP>
+struct HybSmem {
+    uint32_t win[HUB_WINDOW];          // hub window counters
+    uint16_t touched[HUB_WINDOW];      // window indices touched by this anchor
+    unsigned long long tab[HCAP];      // hash for endpoints below the window
+    WalkSmem<TS> walk;
+    uint32_t ntouched;
+    uint32_t job;
+};
+
+template <int TS, uint32_t HCAP, int CTR, int CLS>
+__global__ void __launch_bounds__(TS) k_hybrid(DevGraph G, const uint32_t *list) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    HybSmem<TS, HCAP> &sm = *reinterpret_cast<HybSmem<TS, HCAP> *>(smem_raw);
+    const int t = threadIdx.x;
+    const unsigned lane = lane_id();
+    for (uint32_t i = t; i < HUB_WINDOW; i += TS) sm.win[i] = 0;
+    for (uint32_t i = t; i < HCAP; i += TS) sm.tab[i] = 0ull;
+    if (t == 0) sm.ntouched = 0;
+    const uint32_t n = G.ctr[CTR];
+    uint32_t *err = &G.scratch->err;
+    unsigned long long bal = 0, tot = 0;
+    for (;;) {
+        if (t == 0) sm.job = atomicAdd(&G.scratch->job_next[CLS], 1u);
+        __syncthreads();
+        const uint32_t jid = sm.job;
+        __syncthreads();
+        if (jid >= n) break;
+        const Anchor A = load_anchor(G, list[jid]);
+        const int64_t ns = A.S.n;
+        const uint32_t wb = ns > (int64_t)HUB_WINDOW ? (uint32_t)(ns - HUB_WINDOW) : 0u;
+        const uint64_t W = A.S.work[A.r], wnh = A.S.work_nh[A.r];
+        const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
+        if (W > wnh) {  // endpoints inside the hub window
+            team_walk<TS>(
+                A.S, A.O, A.rb, 0, A.deg, sm.walk, t,
+                [&](uint32_t v, uint32_t sfx, long long &st, uint32_t &len) {
+                    const long long b = A.O.off[v];
+                    const long long s0 = b + sfx, hs = b + A.O.hstart[v];
+                    st = s0 > hs ? s0 : hs;
+                    len = (uint32_t)(A.O.off[v + 1] - st);
+                },
+                [&](uint32_t u, uint32_t asym) {
+                    const uint32_t idx = u - wb;
+                    const bool in = idx < HUB_WINDOW;
+                    if (!in) set_error(err, E_INTERNAL);
+                    const uint32_t old =
+                        in ? atomicAdd(&sm.win[idx], asym ? INC_ASYM : INC_SYM) : 1u;
+                    const bool first = old == 0;
+                    const unsigned act = __activemask();
+                    const unsigned fm = __ballot_sync(act, first);
+                    if (first) {
+                        const unsigned ldr = __ffs(fm) - 1;
+                        uint32_t base = 0;
+                        if (lane == ldr) base = atomicAdd(&sm.ntouched, (uint32_t)__popc(fm));
+                        base = __shfl_sync(fm, base, ldr);
+                        sm.touched[base + __popc(fm & ((1u << lane) - 1u))] = (uint16_t)idx;
+                    }
+                });
+        }
+        if (wnh > 0) {  // endpoints below the window
+            uint32_t cap, shift;
+            table_geometry(wnh < above_nh ? wnh : above_nh, 32, HCAP, cap, shift);
+            const uint32_t mask = cap - 1;
+            team_walk<TS>(
+                A.S, A.O, A.rb, 0, A.deg, sm.walk, t,
+                [&](uint32_t v, uint32_t sfx, long long &st, uint32_t &len) {
+                    const long long b = A.O.off[v];
+                    st = b + sfx;
+                    const long long hs = b + A.O.hstart[v];
+                    len = hs > st ? (uint32_t)(hs - st) : 0u;
+                },
+                [&](uint32_t u, uint32_t asym) {
+                    hash_add(sm.tab, shift, mask, u + 1, asym ? INC_ASYM : INC_SYM, err);
+                });
+            for (uint32_t i = t; i < cap; i += TS) {
+                unsigned long long x = sm.tab[i];
+                if (x) { pair_terms((uint32_t)x, bal, tot); sm.tab[i] = 0ull; }
+            }
+        }
+        __syncthreads();
+        const uint32_t nt = sm.ntouched;
+        for (uint32_t i = t; i < nt; i += TS) {
+            const uint32_t idx = sm.touched[i];
+            pair_terms(sm.win[idx], bal, tot);
+            sm.win[idx] = 0;
+        }
+        __syncthreads();
+        if (t == 0) sm.ntouched = 0;
+    }
+    block_sum2<TS>(bal, tot);
+    if (t == 0) acc_add(G.scratch, bal, tot);
 }
 
 // ------------------------------------------------------------ dense class
+struct DenseSmem {
+    uint32_t cnt[DENSE_CAP];
+    WalkSmem<DENSE_THREADS> walk;
+    uint32_t job, last;
+};
+
 __global__ void __launch_bounds__(DENSE_THREADS) k_dense(DevGraph G) {
-    extern __shared__ uint32_t cnt[];
-    __shared__ uint32_t s_job, s_last;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DenseSmem &sm = *reinterpret_cast<DenseSmem *>(smem_raw);
     const uint32_t njobs = G.ctr[CTR_DENSE];
-    const uint32_t warp = threadIdx.x >> 5, nwarps = DENSE_THREADS / 32;
+    const int t = threadIdx.x;
     CountScratch *sc = G.scratch;
     for (;;) {
-        if (threadIdx.x == 0) s_job = atomicAdd(&sc->job_next[CLS_DENSE], 1u);
+        if (t == 0) sm.job = atomicAdd(&sc->job_next[CLS_DENSE], 1u);
         __syncthreads();
-        const uint32_t jid = s_job;
+        const uint32_t jid = sm.job;
+        __syncthreads();
         if (jid >= njobs) break;
         const DenseJob J = G.dense_jobs[jid];
-        const int sd = J.anchor & 1u;
-        const uint32_t r = J.anchor >> 1;
-        const SideCSR S = sd ? G.side[1] : G.side[0];
-        const SideCSR O = sd ? G.side[0] : G.side[1];
-        const int64_t rb = S.off[r];
-        const uint32_t e_lo = r + 1, e_hi = (uint32_t)S.n;
+        const Anchor A = load_anchor(G, J.anchor);
+        const uint32_t e_lo = A.r + 1, e_hi = (uint32_t)A.S.n;
         const bool windows = (e_hi - e_lo) > DENSE_CAP;
         for (uint32_t e0 = e_lo; e0 < e_hi; e0 += DENSE_CAP) {
             const uint32_t e1 = e_hi - e0 > DENSE_CAP ? e0 + DENSE_CAP : e_hi;
             const uint32_t len = e1 - e0;
-            for (uint32_t i = threadIdx.x; i < len; i += DENSE_THREADS) cnt[i] = 0;
+            for (uint32_t i = t; i < len; i += DENSE_THREADS) sm.cnt[i] = 0;
             __syncthreads();
             auto add = [&](uint32_t u, uint32_t asym) {
-                uint32_t idx = u - e0;
-                if (idx < len) atomicAdd(&cnt[idx], asym ? INC_ASYM : INC_SYM);
+                const uint32_t idx = u - e0;
+                if (idx < len) atomicAdd(&sm.cnt[idx], asym ? INC_ASYM : INC_SYM);
                 else set_error(&sc->err, E_INTERNAL);
             };
-            if (windows) walk<true>(S, O, rb, J.m0, J.m1, e0, e1, warp, nwarps, add);
-            else walk<false>(S, O, rb, J.m0, J.m1, e0, e1, warp, nwarps, add);
-            __syncthreads();
+            if (windows) {
+                team_walk<DENSE_THREADS>(
+                    A.S, A.O, A.rb, J.m0, J.m1, sm.walk, t,
+                    [&](uint32_t v, uint32_t sfx, long long &st, uint32_t &l) {
+                        const long long b = A.O.off[v], ve = A.O.off[v + 1];
+                        const long long s0 = lower_bound_u32(A.O.adj, b + sfx, ve, e0 << 1);
+                        st = s0;
+                        l = (uint32_t)(lower_bound_u32(A.O.adj, s0, ve, e1 << 1) - s0);
+                    },
+                    add);
+            } else {
+                team_walk<DENSE_THREADS>(A.S, A.O, A.rb, J.m0, J.m1, sm.walk, t, FullSeg{A.O}, add);
+            }
             unsigned long long bal = 0, tot = 0;
             if (J.group == NO_GROUP) {
-                for (uint32_t i = threadIdx.x; i < len; i += DENSE_THREADS) pair_terms(cnt[i], bal, tot);
+                for (uint32_t i = t; i < len; i += DENSE_THREADS) pair_terms(sm.cnt[i], bal, tot);
             } else {
                 const SplitGroup grp = G.groups[J.group];
                 uint32_t *part = G.gpart + grp.goff;
-                for (uint32_t i = threadIdx.x; i < len; i += DENSE_THREADS)
-                    if (cnt[i]) atomicAdd(&part[i], cnt[i]);
+                for (uint32_t i = t; i < len; i += DENSE_THREADS)
+                    if (sm.cnt[i]) atomicAdd(&part[i], sm.cnt[i]);
                 __threadfence();
                 __syncthreads();
-                if (threadIdx.x == 0) {
+                if (t == 0) {
                     uint32_t ticket = atomicAdd(&G.gdone[J.group], 1u);
-                    s_last = ticket == grp.parts - 1 ? 1u : 0u;
+                    sm.last = ticket == grp.parts - 1 ? 1u : 0u;
                 }
                 __syncthreads();
-                if (s_last) {
+                if (sm.last) {
                     __threadfence();
-                    for (uint32_t i = threadIdx.x; i < len; i += DENSE_THREADS) {
+                    for (uint32_t i = t; i < len; i += DENSE_THREADS) {
                         uint32_t c = __ldcg(&part[i]);
                         pair_terms(c, bal, tot);
                         part[i] = 0;
                     }
-                    if (threadIdx.x == 0) G.gdone[J.group] = 0;
+                    if (t == 0) G.gdone[J.group] = 0;
                 }
             }
             block_sum2<DENSE_THREADS>(bal, tot);
-            if (threadIdx.x == 0) acc_add(sc, bal, tot);
+            if (t == 0) acc_add(sc, bal, tot);
         }
     }
-}
-
-// --------------------------------------------------------- CTA hash class
-__global__ void __launch_bounds__(CTAH_THREADS) k_ctah(DevGraph G) {
-    extern __shared__ unsigned long long tab[];
-    __shared__ uint32_t s_job;
-    const uint32_t njobs = G.ctr[CTR_CTAH];
-    const uint32_t warp = threadIdx.x >> 5, nwarps = CTAH_THREADS / 32;
-    CountScratch *sc = G.scratch;
-    for (uint32_t i = threadIdx.x; i < CTAH_CAP; i += CTAH_THREADS) tab[i] = 0ull;
-    for (;;) {
-        if (threadIdx.x == 0) s_job = atomicAdd(&sc->job_next[CLS_CTAH], 1u);
-        __syncthreads();
-        const uint32_t jid = s_job;
-        if (jid >= njobs) break;
-        const uint32_t anchor = G.ctah_list[jid];
-        const int sd = anchor & 1u;
-        const uint32_t r = anchor >> 1;
-        const SideCSR S = sd ? G.side[1] : G.side[0];
-        const SideCSR O = sd ? G.side[0] : G.side[1];
-        const int64_t rb = S.off[r];
-        const uint32_t deg = (uint32_t)(S.off[r + 1] - rb);
-        uint64_t W = S.work[r], above = (uint64_t)(S.n - r - 1);
-        uint32_t cap, shift;
-        table_geometry(W < above ? W : above, 64, cap, shift);
-        if (cap > CTAH_CAP) { cap = CTAH_CAP; shift = 32 - 14; }
-        const uint32_t mask = cap - 1;
-        uint32_t *err = &sc->err;
-        walk<false>(S, O, rb, 0, deg, 0, 0, warp, nwarps, [&](uint32_t u, uint32_t asym) {
-            hash_add(tab, shift, mask, u + 1, asym ? INC_ASYM : INC_SYM, err);
-        });
-        __syncthreads();
-        unsigned long long bal = 0, tot = 0;
-        for (uint32_t i = threadIdx.x; i < cap; i += CTAH_THREADS) {
-            unsigned long long t = tab[i];
-            if (t) { pair_terms((uint32_t)t, bal, tot); tab[i] = 0ull; }
-        }
-        block_sum2<CTAH_THREADS>(bal, tot);
-        if (threadIdx.x == 0) acc_add(sc, bal, tot);
-    }
-}
-
-// -------------------------------------------------------- warp hash class
-__global__ void __launch_bounds__(WARPH_THREADS) k_warph(DevGraph G) {
-    extern __shared__ unsigned long long tabs[];
-    const uint32_t warp = threadIdx.x >> 5;
-    const unsigned lane = lane_id();
-    unsigned long long *tab = tabs + (size_t)warp * WARPH_CAP;
-    for (uint32_t i = lane; i < WARPH_CAP; i += 32) tab[i] = 0ull;
-    __syncwarp();
-    const uint32_t n = G.ctr[CTR_WARP];
-    const uint32_t gw = (blockIdx.x * WARPH_THREADS + threadIdx.x) >> 5;
-    const uint32_t GW = (gridDim.x * WARPH_THREADS) >> 5;
-    CountScratch *sc = G.scratch;
-    uint32_t *err = &sc->err;
-    unsigned long long bal = 0, tot = 0;
-    for (uint32_t idx = gw; idx < n; idx += GW) {
-        const uint32_t anchor = G.warp_list[idx];
-        const int sd = anchor & 1u;
-        const uint32_t r = anchor >> 1;
-        const SideCSR S = sd ? G.side[1] : G.side[0];
-        const SideCSR O = sd ? G.side[0] : G.side[1];
-        const int64_t rb = S.off[r];
-        const uint32_t deg = (uint32_t)(S.off[r + 1] - rb);
-        uint64_t W = S.work[r], above = (uint64_t)(S.n - r - 1);
-        uint32_t cap, shift;
-        table_geometry(W < above ? W : above, 32, cap, shift);
-        if (cap > WARPH_CAP) { cap = WARPH_CAP; shift = 32 - 10; }
-        const uint32_t mask = cap - 1;
-        walk<false>(S, O, rb, 0, deg, 0, 0, 0, 1, [&](uint32_t u, uint32_t asym) {
-            hash_add(tab, shift, mask, u + 1, asym ? INC_ASYM : INC_SYM, err);
-        });
-        __syncwarp();
-        for (uint32_t i = lane; i < cap; i += 32) {
-            unsigned long long t = tab[i];
-            if (t) { pair_terms((uint32_t)t, bal, tot); tab[i] = 0ull; }
-        }
-        __syncwarp();
-    }
-    block_sum2<WARPH_THREADS>(bal, tot);
-    if (threadIdx.x == 0) acc_add(sc, bal, tot);
 }
 
 // ------------------------------------------------------------ sign flips
@@ -303,10 +465,10 @@ __global__ void k_flip(DevGraph G, const int64_t *edge_idx, int64_t n) {
             int64_t m = (lo + hi) >> 1;
             if (G.rowptr[m] <= e) lo = m; else hi = m;
         }
-        uint32_t ru = G.side[0].sr_of_id[lo];
-        uint32_t rv = G.side[1].sr_of_id[G.col[e]];
         const SideCSR &U = G.side[0];
         const SideCSR &V = G.side[1];
+        uint32_t ru = U.sr_of_id[lo];
+        uint32_t rv = V.sr_of_id[G.col[e]];
         int64_t p = lower_bound_u32(U.adj, U.off[ru], U.off[ru + 1], rv << 1);
         int64_t q = lower_bound_u32(V.adj, V.off[rv], V.off[rv + 1], ru << 1);
         atomicXor(&U.adj[p], 1u);
@@ -314,12 +476,28 @@ __global__ void k_flip(DevGraph G, const int64_t *edge_idx, int64_t n) {
     }
 }
 
+constexpr size_t WARP_SMEM = (WARP_THREADS / 32) * sizeof(WarpSmem);
+constexpr size_t TEAM_SMEM = sizeof(HybSmem<TEAM_THREADS, TEAM_CAP>);
+constexpr size_t CTAH_SMEM = sizeof(HybSmem<CTAH_THREADS, CTAH_CAP>);
+constexpr size_t DENSE_SMEM = sizeof(DenseSmem);
+
+auto *const k_team = k_hybrid<TEAM_THREADS, TEAM_CAP, CTR_TEAM, CLS_TEAM>;
+auto *const k_ctah = k_hybrid<CTAH_THREADS, CTAH_CAP, CTR_CTAH, CLS_CTAH>;
+
 struct LaunchCfg {
-    int dense_blocks = 0, ctah_blocks = 0, warph_blocks = 0;
+    int warp_blocks = 0, team_blocks = 0, ctah_blocks = 0, dense_blocks = 0;
 };
 
 LaunchCfg g_cfg;
 int g_cfg_device = -1;
+
+template <typename K>
+int blocks_for(K kernel, int threads, size_t smem, int sms) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem);
+    return std::max(1, b) * sms;
+}
 
 void init_cfg() {
     int dev = 0;
@@ -328,18 +506,10 @@ void init_cfg() {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, dev);
     const int sms = prop.multiProcessorCount;
-    size_t dense_smem = DENSE_CAP * 4, ctah_smem = CTAH_CAP * 8,
-           warph_smem = (size_t)(WARPH_THREADS / 32) * WARPH_CAP * 8;
-    cudaFuncSetAttribute(k_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem);
-    cudaFuncSetAttribute(k_ctah, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctah_smem);
-    cudaFuncSetAttribute(k_warph, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warph_smem);
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dense, DENSE_THREADS, dense_smem);
-    g_cfg.dense_blocks = std::max(1, b) * sms;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ctah, CTAH_THREADS, ctah_smem);
-    g_cfg.ctah_blocks = std::max(1, b) * sms;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_warph, WARPH_THREADS, warph_smem);
-    g_cfg.warph_blocks = std::max(1, b) * sms;
+    g_cfg.warp_blocks = blocks_for(k_warp, WARP_THREADS, WARP_SMEM, sms);
+    g_cfg.team_blocks = blocks_for(k_team, TEAM_THREADS, TEAM_SMEM, sms);
+    g_cfg.ctah_blocks = blocks_for(k_ctah, CTAH_THREADS, CTAH_SMEM, sms);
+    g_cfg.dense_blocks = blocks_for(k_dense, DENSE_THREADS, DENSE_SMEM, sms);
     g_cfg_device = dev;
 }
 
@@ -347,19 +517,25 @@ void init_cfg() {
 
 void count_init() { init_cfg(); build_init(); }
 
-void launch_count(const DevGraph &g, cudaStream_t s, int64_t *per_vertex_dev) {
+void launch_count(const DevGraph &g, cudaStream_t s, int64_t *per_vertex_dev, cudaEvent_t *ev) {
     (void)per_vertex_dev;
     init_cfg();
     cudaMemsetAsync(g.scratch, 0, sizeof(CountScratch), s);
-    k_dense<<<g_cfg.dense_blocks, DENSE_THREADS, DENSE_CAP * 4, s>>>(g);
-    k_ctah<<<g_cfg.ctah_blocks, CTAH_THREADS, CTAH_CAP * 8, s>>>(g);
-    k_warph<<<g_cfg.warph_blocks, WARPH_THREADS, (WARPH_THREADS / 32) * WARPH_CAP * 8, s>>>(g);
+    if (ev) cudaEventRecord(ev[0], s);
+    k_dense<<<g_cfg.dense_blocks, DENSE_THREADS, DENSE_SMEM, s>>>(g); note_launch();
+    if (ev) cudaEventRecord(ev[1], s);
+    k_ctah<<<g_cfg.ctah_blocks, CTAH_THREADS, CTAH_SMEM, s>>>(g, g.ctah_list); note_launch();
+    if (ev) cudaEventRecord(ev[2], s);
+    k_team<<<g_cfg.team_blocks, TEAM_THREADS, TEAM_SMEM, s>>>(g, g.team_list); note_launch();
+    if (ev) cudaEventRecord(ev[3], s);
+    k_warp<<<g_cfg.warp_blocks, WARP_THREADS, WARP_SMEM, s>>>(g); note_launch();
+    if (ev) cudaEventRecord(ev[4], s);
 }
 
 void launch_flip(DevGraph &g, const int64_t *edge_idx_dev, int64_t n, cudaStream_t s) {
     if (n <= 0) return;
     int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
-    k_flip<<<(unsigned)blocks, 256, 0, s>>>(g, edge_idx_dev, n);
+    k_flip<<<(unsigned)blocks, 256, 0, s>>>(g, edge_idx_dev, n); note_launch();
 }
 
 }  // namespace bb

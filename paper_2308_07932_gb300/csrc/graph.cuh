@@ -17,15 +17,21 @@
 
 namespace bb {
 
-// dense counters per job: 48Ki u32 (192 KiB of shared memory)
+// Hub window: the top HUB_WINDOW side ranks of the anchor's side. Wedge
+// endpoints concentrate on these high-degree vertices, so team kernels keep
+// them in dense counters and hash only the rest.
+constexpr uint32_t HUB_WINDOW = 2048;
+// dense counters per CTA job: 48Ki u32 (192 KiB of shared memory)
 constexpr uint32_t DENSE_CAP = 49152;
-// hash classes: per-warp table of at most 1024 slots, per-CTA table of at
-// most 16384 slots (u64 each), sized at 2x the distinct-endpoint bound
-constexpr uint32_t WARP_D_MAX = 512;
-constexpr uint32_t CTA_D_MAX = 8192;
-// prefer dense counters when the endpoint range is at most this many times
-// the distinct-endpoint bound
-constexpr uint32_t DENSE_RATIO = 4;
+// warp class: wedges <= WARP_W_MAX, hash of at most WARP_CAP slots
+constexpr uint64_t WARP_W_MAX = 400;
+constexpr uint32_t WARP_CAP = 512;
+// team class (4 warps): wedges <= TEAM_W_MAX and below-window wedges that fit
+// a TEAM_CAP-slot hash
+constexpr uint64_t TEAM_W_MAX = 16384;
+constexpr uint32_t TEAM_CAP = 1024;
+// CTA hash class: below-window wedges that fit a CTAH_CAP-slot hash
+constexpr uint32_t CTAH_CAP = 16384;
 // split one dense anchor over several CTAs when its wedges exceed both this
 // and 4x its endpoint range; parts are merged before the C(.,2) step
 constexpr uint64_t SPLIT_WEDGES = 65536;
@@ -33,7 +39,7 @@ constexpr uint32_t MAX_PARTS = 64;
 constexpr uint32_t MAX_SPLIT_JOBS = 1u << 16;
 constexpr uint32_t MAX_GPART = 1u << 24;
 
-enum Cls : uint32_t { CLS_WARP = 0, CLS_CTAH = 1, CLS_DENSE = 2, NCLS = 3 };
+enum Cls : uint32_t { CLS_WARP = 0, CLS_TEAM = 1, CLS_CTAH = 2, CLS_DENSE = 3, NCLS = 4 };
 
 // One CTA job over dense counters: anchor (side rank << 1 | side), its
 // middle slice [m0, m1) of the anchor's row, and the split group (or
@@ -55,8 +61,8 @@ struct SplitGroup {
 
 // counters written by the classifier
 enum Ctr : uint32_t {
-    CTR_WARP = 0, CTR_CTAH = 1, CTR_DENSE = 2, CTR_GROUPS = 3, CTR_GPART = 4, CTR_SPLITJOBS = 5,
-    NCTR = 8
+    CTR_WARP = 0, CTR_TEAM = 1, CTR_CTAH = 2, CTR_DENSE = 3, CTR_GROUPS = 4, CTR_GPART = 5,
+    CTR_SPLITJOBS = 6, NCTR = 8
 };
 
 // per-count scratch (zeroed before each count)
@@ -76,6 +82,7 @@ struct DevGraph {
     int8_t *sign = nullptr;
     // classification
     uint32_t *warp_list = nullptr;   // anchors
+    uint32_t *team_list = nullptr;   // anchors
     uint32_t *ctah_list = nullptr;   // anchors
     DenseJob *dense_jobs = nullptr;
     SplitGroup *groups = nullptr;
@@ -84,6 +91,8 @@ struct DevGraph {
     uint32_t *gdone = nullptr;       // per group arrival counters
     uint32_t *ctr = nullptr;         // [NCTR]
     unsigned long long *wedges = nullptr;  // [1]
+    // per work class (warp, team, CTA-hash, dense): wedges, middle steps, anchors
+    unsigned long long *cls_stats = nullptr;  // [3 * NCLS]
     uint32_t *err = nullptr;         // build error word
     CountScratch *scratch = nullptr;
     // host copies after the build
@@ -108,8 +117,11 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
                      void *temp_mem, cudaStream_t s);
 
 // Count balanced/total butterflies of a built graph on stream s. Writes the
-// 128-bit sums to g.scratch->acc (device); per_vertex may be null.
-void launch_count(const DevGraph &g, cudaStream_t s, int64_t *per_vertex_dev);
+// 128-bit sums to g.scratch->acc (device); per_vertex may be null. When ev
+// is not null, ev[0..4] are recorded before the dense, CTA-hash, team and
+// warp kernels and after the last one.
+void launch_count(const DevGraph &g, cudaStream_t s, int64_t *per_vertex_dev,
+                  cudaEvent_t *ev = nullptr);
 
 // Flip the signs of listed input edges (device list of n indices).
 void launch_flip(DevGraph &g, const int64_t *edge_idx_dev, int64_t n, cudaStream_t s);

@@ -77,9 +77,6 @@ __global__ void k_scan_tile(const TIn *in, TOut *out, int64_t n, const uint64_t 
     }
 }
 
-__global__ void k_write_zero_total(int64_t *out) { out[0] = 0; }
-__global__ void k_write_zero_total_u64(uint64_t *out) { out[0] = 0; }
-
 // exclusive scan of n uint64 block sums in place (recursive through temp)
 void scan_blocks(uint64_t *sums, int64_t n, uint64_t *temp, cudaStream_t s);
 
@@ -94,9 +91,9 @@ void scan_impl(const TIn *in, TOut *out, int64_t n, void *temp, cudaStream_t s) 
     int64_t nb = ceil_div(n, SCAN_TILE);
     uint64_t *sums = (uint64_t *)temp;
     uint64_t *rest = sums + ceil_div(nb + 1, 32) * 32;
-    k_scan_reduce<TIn><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, sums);
+    k_scan_reduce<TIn><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, sums); note_launch();
     scan_blocks(sums, nb, rest, s);
-    k_scan_tile<TIn, TOut><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, sums);
+    k_scan_tile<TIn, TOut><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, sums); note_launch();
 }
 
 void scan_blocks(uint64_t *sums, int64_t n, uint64_t *temp, cudaStream_t s) {
@@ -105,13 +102,13 @@ void scan_blocks(uint64_t *sums, int64_t n, uint64_t *temp, cudaStream_t s) {
     int64_t nb = ceil_div(n, SCAN_TILE);
     uint64_t *bsums = temp;
     uint64_t *rest = bsums + ceil_div(nb + 1, 32) * 32;
-    k_scan_reduce<uint64_t><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(sums, n, bsums);
+    k_scan_reduce<uint64_t><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(sums, n, bsums); note_launch();
     if (nb > 1) {
         scan_blocks(bsums, nb, rest, s);
     } else {
         cudaMemsetAsync(bsums, 0, sizeof(uint64_t), s);
     }
-    k_scan_tile<uint64_t, uint64_t><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(sums, sums, n, bsums);
+    k_scan_tile<uint64_t, uint64_t><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(sums, sums, n, bsums); note_launch();
 }
 
 // ---------------------------------------------------------------- radix sort
@@ -218,10 +215,10 @@ void radix_sort_pairs_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, ui
     uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
     for (int p = 0; p < passes; p++) {
         int shift = 8 * p;
-        k_radix_hist<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ki, n, shift, hist, ntiles);
+        k_radix_hist<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ki, n, shift, hist, ntiles); note_launch();
         scan_impl<uint64_t, uint64_t>(hist, hist, 256 * ntiles, scan_tmp, s);
         k_radix_scatter<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, hist,
-                                                                ntiles);
+                                                                ntiles); note_launch();
         uint32_t *tk = ki; ki = ko; ko = tk;
         uint32_t *tv = vi; vi = vo; vo = tv;
     }
