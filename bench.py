@@ -310,6 +310,7 @@ def run_ours(args, world, rank, local_rank):
         },
         "phases_ms": {"build": build_ms, "count": count_ms,
                       **{k: v["ms"] for k, v in kern.items()}},
+        "kernels": kern,
         "roofline": {"bound": "hbm", "kernel": top, "achieved": ach, "peak": peak, "unit": "GB/s",
                      "frac": ach / peak, "peak_kind": peak_kind,
                      "algorithmic_bytes": algorithmic_bytes(kern[top]),

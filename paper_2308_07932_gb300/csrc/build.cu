@@ -101,27 +101,33 @@ __global__ void k_global_rank(SideCSR S, const uint32_t *other_deg, int64_t n_ot
 }
 
 // --------------------------------------------------------------- 3. rows
-// warp per input row u: the U-side entry keeps the input position within the
-// row; the V-side entry takes the next free slot of v's row.
-__global__ void k_fill(const int64_t *rowptr, const int32_t *col, const int8_t *sign, int64_t nU,
-                       SideCSR U, SideCSR V, uint32_t *cursorV, uint32_t *eidU, uint32_t *eidV) {
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const unsigned lane = lane_id();
-    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < nU; u += warps) {
-        uint32_t r = U.sr_of_id[u];
-        int64_t base = U.off[r];
-        int64_t a = rowptr[u], d = rowptr[u + 1] - a;
-        for (int64_t i = lane; i < d; i += 32) {
-            int64_t e = a + i;
-            uint32_t v = (uint32_t)col[e];
-            uint32_t neg = sign[e] < 0 ? 1u : 0u;
-            uint32_t rv = V.sr_of_id[v];
-            U.adj[base + i] = (rv << 1) | neg;
-            eidU[base + i] = (uint32_t)e;
-            int64_t p = V.off[rv] + atomicAdd(&cursorV[rv], 1u);
-            V.adj[p] = (r << 1) | neg;
-            eidV[p] = (uint32_t)e;
+// One thread per input edge e (its row u found by binary search in rowptr):
+// the U-side entry keeps the input position within u's row; the V-side
+// entry takes the next free slot of v's row. Each entry also records its
+// row (side rank) and input edge id.
+__global__ void k_fill(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                       const int8_t *__restrict__ sign, int64_t nU, int64_t nE, SideCSR U,
+                       SideCSR V, uint32_t *cursorV, uint32_t *eidU, uint32_t *eidV,
+                       uint32_t *rowU, uint32_t *rowV) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nE;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = nU;  // last u with rowptr[u] <= e
+        while (hi - lo > 1) {
+            const int64_t m = (lo + hi) >> 1;
+            if (rowptr[m] <= e) lo = m; else hi = m;
         }
+        const uint32_t r = U.sr_of_id[lo];
+        const int64_t pu = U.off[r] + (e - rowptr[lo]);
+        const uint32_t v = (uint32_t)col[e];
+        const uint32_t neg = sign[e] < 0 ? 1u : 0u;
+        const uint32_t rv = V.sr_of_id[v];
+        U.adj[pu] = (rv << 1) | neg;
+        eidU[pu] = (uint32_t)e;
+        rowU[pu] = r;
+        const int64_t pv = V.off[rv] + atomicAdd(&cursorV[rv], 1u);
+        V.adj[pv] = (r << 1) | neg;
+        eidV[pv] = (uint32_t)e;
+        rowV[pv] = rv;
     }
 }
 
@@ -317,35 +323,62 @@ __global__ void k_epos(const uint32_t *eid, int64_t nE, uint32_t *epos) {
 // For the entry w -> v at position p of anchor w's row: the wedge suffix of
 // v's row holds the neighbours ranked above max(v, w). If v outranks w that
 // is v's own upper part (from lo(v)); otherwise it starts right after w's
-// position in v's row (w and the suffix are on the same side).
-__global__ void k_sfx_work(SideCSR S, SideCSR O, const uint32_t *eid_s, const uint32_t *epos_o,
-                           unsigned long long *wedges) {
+// position in v's row (w and the suffix are on the same side). One thread
+// per entry; the per-row sums of suffix lengths (wedges) and of their parts
+// below the hub window are reduced per warp segment, then added per row.
+__global__ void k_md_work(SideCSR S, SideCSR O, const uint32_t *__restrict__ eid_s,
+                          const uint32_t *__restrict__ epos_o, const uint32_t *__restrict__ row_s,
+                          int64_t nE, unsigned long long *wedges) {
     __shared__ unsigned long long block_sum;
     if (threadIdx.x == 0) block_sum = 0;
     __syncthreads();
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const unsigned lane = lane_id();
     unsigned long long mine = 0;
-    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < S.n; r += warps) {
-        int64_t b = S.off[r], e = S.off[r + 1];
-        uint32_t g = S.grank[r];
-        uint64_t sum = 0, nh = 0;
-        for (int64_t p = b + lane; p < e; p += 32) {
-            uint32_t v = S.adj[p] >> 1;
-            int64_t vb = O.off[v];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // all lanes of a warp run the same number of iterations (shuffles below)
+    const int64_t start = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t iters = (nE + stride - 1) / stride;
+    for (int64_t it = 0; it < iters; it++) {
+        const int64_t p = start + it * stride;
+        const bool valid = p < nE;
+        uint32_t r = 0xffffffffu, len = 0, nh = 0;
+        if (valid) {
+            r = row_s[p];
+            const uint32_t ent = S.adj[p];
+            const uint32_t v = ent >> 1;
+            const int64_t ob = O.off[v], oe = O.off[v + 1];
             uint32_t st;
-            if (O.grank[v] > g) st = O.lo[v];
-            else st = (uint32_t)(epos_o[eid_s[p]] - vb) + 1u;
-            S.sfx[p] = st;
-            sum += (uint64_t)(O.deg[v] - st);
-            uint32_t hs = O.hstart[v];
-            nh += hs > st ? (uint64_t)(hs - st) : 0ull;
+            if (O.grank[v] > S.grank[r]) st = O.lo[v];
+            else st = (uint32_t)(epos_o[eid_s[p]] - ob) + 1u;
+            const uint32_t hst = O.hstart[v];
+            const uint32_t hs = hst > st ? hst : st;
+            S.md[p] = make_uint4((uint32_t)(ob + st), (uint32_t)(ob + hs), (uint32_t)oe, ent & 1u);
+            len = (uint32_t)(oe - ob) - st;
+            nh = hs - st;
         }
-        sum = warp_sum_u64(sum);
-        nh = warp_sum_u64(nh);
-        if (lane == 0) { S.work[r] = sum; S.work_nh[r] = nh; }
-        mine += sum;
+        // segmented sums over runs of equal r within the warp
+        const uint32_t rprev = __shfl_up_sync(FULL, r, 1);
+        const bool head = lane == 0 || rprev != r;
+        const unsigned heads = __ballot_sync(FULL, head);
+        uint32_t a = len, b = nh;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t ya = __shfl_up_sync(FULL, a, d), yb = __shfl_up_sync(FULL, b, d);
+            if (lane >= (unsigned)d) { a += ya; b += yb; }
+        }
+        const unsigned below = heads & ((2u << lane) - 1u);     // heads at or before me
+        const int sstart = 31 - __clz(below);                    // my segment's head
+        const uint32_t pa = __shfl_sync(FULL, a, sstart > 0 ? sstart - 1 : 0);
+        const uint32_t pb = __shfl_sync(FULL, b, sstart > 0 ? sstart - 1 : 0);
+        const uint32_t seg_a = a - (sstart > 0 ? pa : 0u), seg_b = b - (sstart > 0 ? pb : 0u);
+        const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+        if (valid && tail) {
+            if (seg_a) atomicAdd((unsigned long long *)&S.work[r], (unsigned long long)seg_a);
+            if (seg_b) atomicAdd((unsigned long long *)&S.work_nh[r], (unsigned long long)seg_b);
+        }
+        mine += len;
     }
+    mine = warp_sum_u64(mine);
     if (lane == 0 && mine) atomicAdd(&block_sum, mine);
     __syncthreads();
     if (threadIdx.x == 0 && block_sum) atomicAdd(wedges, block_sum);
@@ -380,8 +413,12 @@ __global__ void k_classify(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
             const uint64_t above_nh = wb > (uint64_t)r + 1 ? wb - (uint64_t)r - 1 : 0;
             const uint64_t wnh = S.work_nh[r];
             const uint64_t dnh = wnh < above_nh ? wnh : above_nh;
+            const uint64_t dh = W < above ? W : above;
+            const uint32_t deg = (uint32_t)(S.off[r + 1] - S.off[r]);
             uint32_t cls;
-            if (W <= WARP_W_MAX) cls = CLS_WARP;
+            if (deg <= WARP_DEG_MAX && W <= WARP_W_MAX &&
+                (W <= WARP_SMALL_W ? dh * 5 / 4 < WARP_CAP : dnh * 5 / 4 < WARP_CAP))
+                cls = CLS_WARP;
             else if (W <= TEAM_W_MAX && dnh * 5 / 4 < TEAM_CAP) cls = CLS_TEAM;
             else if (above <= DENSE_CAP) cls = CLS_DENSE;
             else if (dnh * 2 < CTAH_CAP) cls = CLS_CTAH;
@@ -459,11 +496,20 @@ __global__ void k_emit(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
             uint32_t cls = key / NB;
             uint32_t pos = base[key] + local;
             uint32_t anchor = (uint32_t)r << 1 | (uint32_t)side;
-            if (cls == CLS_WARP) G.warp_list[pos] = anchor;
-            else if (cls == CLS_TEAM) G.team_list[pos] = anchor;
-            else if (cls == CLS_CTAH) G.ctah_list[pos] = anchor;
-            else {
-                uint32_t deg = (uint32_t)(S.off[r + 1] - S.off[r]);
+            const uint32_t deg = (uint32_t)(S.off[r + 1] - S.off[r]);
+            if (cls != CLS_DENSE) {
+                const uint64_t W = S.work[r], wnh = S.work_nh[r];
+                AnchorRec rec;
+                rec.anchor = anchor;
+                rec.rb = (uint32_t)S.off[r];
+                rec.deg = deg;
+                rec.W = W > 0xffffffffull ? 0xffffffffu : (uint32_t)W;
+                rec.wnh = wnh > 0xffffffffull ? 0xffffffffu : (uint32_t)wnh;
+                rec.pad0 = rec.pad1 = rec.pad2 = 0;
+                AnchorRec *list = cls == CLS_WARP ? G.warp_list
+                                  : cls == CLS_TEAM ? G.team_list : G.ctah_list;
+                list[pos] = rec;
+            } else {
                 uint32_t grp = parts > 1 ? T.grp[r] : NO_GROUP;
                 for (uint32_t i = 0; i < parts; i++) {
                     uint32_t m0 = (uint32_t)((uint64_t)deg * i / parts);
@@ -489,7 +535,7 @@ struct Carver {
 };
 
 size_t side_bytes(int64_t n, int64_t nE) {
-    return align256((size_t)(n + 1) * 8) + 2 * align256((size_t)nE * 4) +
+    return align256((size_t)(n + 1) * 8) + align256((size_t)nE * 4) + align256((size_t)nE * 16) +
            6 * align256((size_t)(n > 0 ? n : 1) * 4) + 2 * align256((size_t)(n > 0 ? n : 1) * 8);
 }
 
@@ -504,7 +550,7 @@ BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE) {
     int64_t n = nU + nV;
     int64_t nmax = std::max<int64_t>(std::max(nU, nV), 1);
     size_t g = side_bytes(nU, nE) + side_bytes(nV, nE);
-    g += 3 * align256((size_t)(n + 1) * 4);                                  // warp/team/ctah lists
+    g += 3 * align256((size_t)(n + 1) * sizeof(AnchorRec));                  // warp/team/ctah lists
     g += align256((size_t)(n + MAX_SPLIT_JOBS) * sizeof(DenseJob));          // dense jobs
     g += align256((size_t)MAX_SPLIT_JOBS * sizeof(SplitGroup));              // groups
     g += align256((size_t)MAX_SPLIT_JOBS * 4);                               // gdone
@@ -512,7 +558,7 @@ BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE) {
     g += align256(NCTR * 4) + 256 + 256 + 256 + align256(sizeof(CountScratch));
     size_t t = 0;
     t += align256((size_t)nU * 4 + 4) + align256((size_t)nV * 4 + 4);      // deg by id
-    t += 2 * align256((size_t)nE * 4 + 4);                                   // eid
+    t += 4 * align256((size_t)nE * 4 + 4);                                   // eid, row ids
     t += align256((size_t)nV * 4 + 4);                                       // cursor
     t += 2 * align256((size_t)nE * 8 + 8);                                   // row sort buffers / epos
     t += 2 * align256((size_t)nmax * 4 + 4);                                 // rank sort alt
@@ -532,7 +578,7 @@ void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_m
         S.n = n;
         S.off = c.take<int64_t>(n + 1);
         S.adj = c.take<uint32_t>(nE);
-        S.sfx = c.take<uint32_t>(nE);
+        S.md = c.take<uint4>(nE);
         S.id_of_sr = c.take<uint32_t>(n1);
         S.sr_of_id = c.take<uint32_t>(n1);
         S.grank = c.take<uint32_t>(n1);
@@ -543,9 +589,9 @@ void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_m
         S.work_nh = c.take<uint64_t>(n1);
     }
     int64_t n = nU + nV;
-    g.warp_list = c.take<uint32_t>(n + 1);
-    g.team_list = c.take<uint32_t>(n + 1);
-    g.ctah_list = c.take<uint32_t>(n + 1);
+    g.warp_list = c.take<AnchorRec>(n + 1);
+    g.team_list = c.take<AnchorRec>(n + 1);
+    g.ctah_list = c.take<AnchorRec>(n + 1);
     g.dense_jobs = c.take<DenseJob>(n + MAX_SPLIT_JOBS);
     g.groups = c.take<SplitGroup>(MAX_SPLIT_JOBS);
     g.gdone = c.take<uint32_t>(MAX_SPLIT_JOBS);
@@ -565,6 +611,7 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
     Carver c{(char *)temp_mem};
     uint32_t *deg_in[2] = {c.take<uint32_t>(nU + 1), c.take<uint32_t>(nV + 1)};
     uint32_t *eid[2] = {c.take<uint32_t>(nE + 1), c.take<uint32_t>(nE + 1)};
+    uint32_t *rowid[2] = {c.take<uint32_t>(nE + 1), c.take<uint32_t>(nE + 1)};
     uint32_t *cursorV = c.take<uint32_t>(nV + 1);
     uint64_t *bufA = c.take<uint64_t>(nE + 1);
     uint64_t *bufB = c.take<uint64_t>(nE + 1);
@@ -615,8 +662,9 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
     for (int sd = 0; sd < 2; sd++)
         scan_exclusive_u32_to_i64(g.side[sd].deg, g.side[sd].off, ns[sd], ptemp, s);
     if (nU > 0 && nE > 0)
-        k_fill<<<grid_for(nU * 32, BT, 16384), BT, 0, s>>>(rowptr, col, sign, nU, g.side[0],
-                                                          g.side[1], cursorV, eid[0], eid[1]); note_launch();
+        k_fill<<<grid_for(nE, BT, 32768), BT, 0, s>>>(rowptr, col, sign, nU, nE, g.side[0],
+                                                     g.side[1], cursorV, eid[0], eid[1],
+                                                     rowid[0], rowid[1]); note_launch();
     for (int sd = 0; sd < 2; sd++) {
         int64_t n = ns[sd];
         if (n == 0 || nE == 0) continue;
@@ -645,10 +693,14 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
     if (nE > 0) {
         for (int sd = 0; sd < 2; sd++)
             k_epos<<<grid_for(nE, BT, 16384), BT, 0, s>>>(eid[sd], nE, epos[sd]); note_launch();
-        for (int sd = 0; sd < 2; sd++)
-            if (ns[sd] > 0)
-                k_sfx_work<<<grid_for(ns[sd] * 32, BT, 4096), BT, 0, s>>>(
-                    g.side[sd], g.side[1 - sd], eid[sd], epos[1 - sd], g.wedges); note_launch();
+        for (int sd = 0; sd < 2; sd++) {
+            if (ns[sd] == 0) continue;
+            cudaMemsetAsync(g.side[sd].work, 0, (size_t)ns[sd] * 8, s);
+            cudaMemsetAsync(g.side[sd].work_nh, 0, (size_t)ns[sd] * 8, s);
+            k_md_work<<<grid_for(nE, BT, 8192), BT, 0, s>>>(g.side[sd], g.side[1 - sd], eid[sd],
+                                                           epos[1 - sd], rowid[sd], nE,
+                                                           g.wedges); note_launch();
+        }
     } else {
         for (int sd = 0; sd < 2; sd++)
             if (ns[sd] > 0) {

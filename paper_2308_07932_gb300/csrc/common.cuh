@@ -38,8 +38,11 @@ struct SideCSR {
     int64_t n;            // vertices on this side
     int64_t *off;         // [n+1] row offsets
     uint32_t *adj;        // [nE]  (neighbour side rank << 1) | negative
-    uint32_t *sfx;        // [nE]  per entry (w -> v): first index in v's row of the
-                          //       wedge suffix, i.e. neighbours of v ranked above both
+    uint4 *md;            // [nE]  per entry (w -> v), the wedges it starts, as absolute
+                          //       positions in the other side's adj: x = first
+                          //       neighbour of v ranked above both v and w, y = first of
+                          //       those inside the hub window, z = end of v's row,
+                          //       w = sign bit of the edge (w, v)
     uint32_t *id_of_sr;   // [n]   side rank -> input id
     uint32_t *sr_of_id;   // [n]   input id -> side rank
     uint32_t *grank;      // [n]   side rank -> global priority rank

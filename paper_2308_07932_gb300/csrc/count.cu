@@ -16,8 +16,9 @@
 //
 // Counters, per class (all in shared memory; S in bits 0..15, A in bits
 // 16..31 of a u32, both bounded by the anchor's degree):
-//   warp  - small anchors, one per warp, open-addressing hash (u64 slots:
-//           endpoint + 1 in the high half);
+//   warp  - anchors of degree <= 255, one per warp: the hub window in
+//           16-bit counters and an open-addressing hash (u64 slots:
+//           endpoint + 1 in the high half) for the rest;
 //   team  - medium anchors, one per 128-thread CTA: dense counters for the
 //           hub window (top HUB_WINDOW ranks of the side, where most
 //           endpoints fall) with a list of touched counters, and a hash for
@@ -37,8 +38,7 @@ namespace {
 constexpr int WARP_THREADS = 256;    // 8 independent warps per CTA
 constexpr int TEAM_THREADS = 128;    // one team per CTA
 constexpr int CTAH_THREADS = 512;
-constexpr int DENSE_THREADS = 512;
-constexpr int UNROLL = 4;            // wedge loads in flight per lane
+constexpr int DENSE_THREADS = 1024;
 
 __device__ __forceinline__ void acc_add(CountScratch *sc, unsigned long long bal,
                                         unsigned long long tot) {
@@ -83,11 +83,13 @@ __device__ __forceinline__ void team_sync() {
     else __syncthreads();   // teams of more than one warp are whole CTAs
 }
 
-// A chunk of middles, compacted to those with a non-empty segment.
+// A chunk of middles, compacted to those with a non-empty segment: the
+// first entry of the segment in the other side's adjacency (absolute index,
+// below 2^32 because nE is), and the wedges of the chunk before this middle
+// (below 2^31) with the sign bit of the anchor's edge in bit 31.
 struct Desc {
-    long long st;     // first entry of the segment in the middle's row (absolute)
-    uint32_t excl;    // wedges of the chunk before this middle
-    uint32_t sw;      // sign bit of the anchor's edge to the middle
+    uint32_t st;
+    uint32_t excl_sw;
 };
 
 template <int TS>
@@ -98,12 +100,14 @@ struct WalkSmem {
     uint32_t tot[2];
 };
 
-// Walk the wedges of one anchor's middles [m0, m1) (row starting at rb in
-// side S) as a team of TS threads (t = thread index in the team). seg(v,
-// sfx, st, len) gives middle v's segment [st, st+len) of its row;
+// Walk the wedges of one anchor's middles [m0, m1) (its row starts at rb in
+// the anchor side's descriptors smd; the middles' rows are in oadj) as a
+// team of TS threads (t = thread index in the team). seg(md, st, len) picks
+// the segment [st, st+len) of a middle's row from its descriptor;
 // add(u_side_rank, asymmetric) is called once per wedge.
-template <int TS, typename Seg, typename Add>
-__device__ __forceinline__ void team_walk(const SideCSR &S, const SideCSR &O, int64_t rb,
+template <int TS, int UNROLL = 4, typename Seg, typename Add>
+__device__ __forceinline__ void team_walk(const uint4 *__restrict__ smd,
+                                          const uint32_t *__restrict__ oadj, int64_t rb,
                                           uint32_t m0, uint32_t m1, WalkSmem<TS> &sm, int t,
                                           Seg &&seg, Add &&add) {
     constexpr int NW = TS / 32;
@@ -113,9 +117,9 @@ __device__ __forceinline__ void team_walk(const SideCSR &S, const SideCSR &O, in
         long long st = 0;
         uint32_t len = 0, sw = 0;
         if (j < m1) {
-            const uint32_t ent = S.adj[rb + j];
-            sw = ent & 1u;
-            seg(ent >> 1, S.sfx[rb + j], st, len);
+            const uint4 d = smd[rb + j];
+            sw = d.w;
+            seg(d, st, len);
         }
         // inclusive team scan of (len, nonzero) packed in one u64
         unsigned long long x = (unsigned long long)len | ((unsigned long long)(len > 0) << 32);
@@ -133,7 +137,7 @@ __device__ __forceinline__ void team_walk(const SideCSR &S, const SideCSR &O, in
         }
         const uint32_t incl = (uint32_t)x, nzi = (uint32_t)(x >> 32);
         if (len > 0) {
-            sm.desc[nzi - 1] = Desc{st, incl - len, sw};
+            sm.desc[nzi - 1] = Desc{(uint32_t)st, (incl - len) | (sw << 31)};
             sm.incl[nzi - 1] = incl;
         }
         if (t == TS - 1) { sm.tot[0] = incl; sm.tot[1] = nzi; }
@@ -150,8 +154,7 @@ __device__ __forceinline__ void team_walk(const SideCSR &S, const SideCSR &O, in
             }
             uint32_t m = lo;
             for (uint32_t base = a; base < b;) {
-                long long addr[UNROLL];
-                uint32_t swv[UNROLL];
+                uint32_t addr[UNROLL], swv[UNROLL];
                 bool ok[UNROLL];
 #pragma unroll
                 for (int u = 0; u < UNROLL; u++) {
@@ -161,15 +164,19 @@ __device__ __forceinline__ void team_walk(const SideCSR &S, const SideCSR &O, in
                         const uint32_t wv = sm.incl[wi];
                         const uint32_t i = base + lane;
                         uint32_t k = 0;
+                        // all 32 wedges in middle m: no search needed
+                        if (__shfl_sync(FULL, wv, 0) < base + 32) {
 #pragma unroll
-                        for (int s2 = 16; s2 >= 1; s2 >>= 1) {
-                            uint32_t c = __shfl_sync(FULL, wv, k + s2 - 1);
-                            if (c <= i) k += s2;
+                            for (int s2 = 16; s2 >= 1; s2 >>= 1) {
+                                uint32_t c = __shfl_sync(FULL, wv, k + s2 - 1);
+                                if (c <= i) k += s2;
+                            }
                         }
                         if (i < b) {
                             const Desc d = sm.desc[m + k];
-                            addr[u] = d.st + (long long)(i - d.excl);
-                            swv[u] = d.sw;
+                            const uint32_t ex = d.excl_sw & 0x7fffffffu;
+                            addr[u] = d.st + (i - ex);
+                            swv[u] = d.excl_sw >> 31;
                             ok[u] = true;
                         }
                         m += __popc(__ballot_sync(FULL, wv <= base + 32));
@@ -179,7 +186,7 @@ __device__ __forceinline__ void team_walk(const SideCSR &S, const SideCSR &O, in
                 uint32_t xv[UNROLL];
 #pragma unroll
                 for (int u = 0; u < UNROLL; u++)
-                    if (ok[u]) xv[u] = O.adj[addr[u]];
+                    if (ok[u]) xv[u] = oadj[addr[u]];
 #pragma unroll
                 for (int u = 0; u < UNROLL; u++)
                     if (ok[u]) add(xv[u] >> 1, (xv[u] ^ swv[u]) & 1u);
@@ -217,45 +224,76 @@ __device__ __forceinline__ void table_geometry(uint64_t need, uint32_t min_cap, 
     while ((uint64_t)cap < want && cap < max_cap) { cap <<= 1; shift--; }
 }
 
+// The few values one anchor's walk needs (anchor side S, middle side O).
 struct Anchor {
-    SideCSR S, O;
-    uint32_t r;
-    int64_t rb;
-    uint32_t deg;
+    const uint4 *smd;
+    const uint32_t *oadj;
+    int64_t rb, ns;
+    uint32_t r, deg;
+    uint64_t W, wnh;
 };
 
-__device__ __forceinline__ Anchor load_anchor(const DevGraph &G, uint32_t anchor) {
+__device__ __forceinline__ Anchor load_anchor(const DevGraph &G, const AnchorRec &rec) {
     Anchor a;
-    const int sd = anchor & 1u;
-    a.S = sd ? G.side[1] : G.side[0];
-    a.O = sd ? G.side[0] : G.side[1];
-    a.r = anchor >> 1;
-    a.rb = a.S.off[a.r];
-    a.deg = (uint32_t)(a.S.off[a.r + 1] - a.rb);
+    const bool v = rec.anchor & 1u;
+    a.smd = v ? G.side[1].md : G.side[0].md;
+    a.oadj = v ? G.side[0].adj : G.side[1].adj;
+    a.ns = v ? G.side[1].n : G.side[0].n;
+    a.r = rec.anchor >> 1;
+    a.rb = rec.rb;
+    a.deg = rec.deg;
+    a.W = rec.W;
+    a.wnh = rec.wnh;
     return a;
 }
 
 // the whole wedge suffix of a middle
 struct FullSeg {
-    const SideCSR &O;
-    __device__ void operator()(uint32_t v, uint32_t sfx, long long &st, uint32_t &len) const {
-        const long long b = O.off[v];
-        st = b + sfx;
-        len = (uint32_t)(O.off[v + 1] - st);
+    __device__ void operator()(const uint4 &d, long long &st, uint32_t &len) const {
+        st = d.x;
+        len = d.z - d.x;
+    }
+};
+
+// the part of a middle's suffix inside the hub window
+struct HubSeg {
+    __device__ void operator()(const uint4 &d, long long &st, uint32_t &len) const {
+        st = d.y;
+        len = d.z - d.y;
+    }
+};
+
+// the part of a middle's suffix below the hub window
+struct LowSeg {
+    __device__ void operator()(const uint4 &d, long long &st, uint32_t &len) const {
+        st = d.x;
+        len = d.y - d.x;
     }
 };
 
 // ------------------------------------------------------------ warp class
+// Per warp: the hub window as 16-bit counters, two per word (S in the low
+// byte, A in the high byte; both <= the anchor's degree <= 255), a small
+// hash for endpoints below the window, and the walker's chunk.
 struct WarpSmem {
+    uint32_t win[HUB_WINDOW / 2];
     unsigned long long tab[WARP_CAP];
     WalkSmem<32> walk;
 };
 
-__global__ void __launch_bounds__(WARP_THREADS) k_warp(DevGraph G) {
+__device__ __forceinline__ void pair_terms8(uint32_t c, unsigned long long &bal,
+                                            unsigned long long &tot) {
+    uint32_t S = c & 0xffu, A = (c >> 8) & 0xffu;
+    bal += c2(S) + c2(A);
+    tot += c2(S + A);
+}
+
+__global__ void __launch_bounds__(WARP_THREADS, 4) k_warp(DevGraph G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[threadIdx.x >> 5];
     const unsigned lane = lane_id();
     for (uint32_t i = lane; i < WARP_CAP; i += 32) sm.tab[i] = 0ull;
+    for (uint32_t i = lane; i < HUB_WINDOW / 2; i += 32) sm.win[i] = 0u;
     __syncwarp();
     const uint32_t n = G.ctr[CTR_WARP];
     const uint32_t gw = (blockIdx.x * WARP_THREADS + threadIdx.x) >> 5;
@@ -264,14 +302,50 @@ __global__ void __launch_bounds__(WARP_THREADS) k_warp(DevGraph G) {
     unsigned long long bal = 0, tot = 0;
     for (uint32_t idx = gw; idx < n; idx += GW) {
         const Anchor A = load_anchor(G, G.warp_list[idx]);
-        const uint64_t W = A.S.work[A.r], above = (uint64_t)(A.S.n - A.r - 1);
-        uint32_t cap, shift;
-        table_geometry(W < above ? W : above, 32, WARP_CAP, cap, shift);
-        const uint32_t mask = cap - 1;
-        team_walk<32>(A.S, A.O, A.rb, 0, A.deg, sm.walk, (int)lane, FullSeg{A.O},
-                      [&](uint32_t u, uint32_t asym) {
-                          hash_add(sm.tab, shift, mask, u + 1, asym ? INC_ASYM : INC_SYM, err);
-                      });
+        const uint64_t W = A.W, above = (uint64_t)(A.ns - A.r - 1);
+        uint32_t cap = 0, shift = 0;
+        if (W <= WARP_SMALL_W) {  // hash every endpoint
+            table_geometry(W < above ? W : above, 32, WARP_CAP, cap, shift);
+            const uint32_t mask = cap - 1;
+            team_walk<32, 2>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane,
+                          FullSeg{}, [&](uint32_t u, uint32_t asym) {
+                              hash_add(sm.tab, shift, mask, u + 1, asym ? INC_ASYM : INC_SYM, err);
+                          });
+        } else {
+            const int64_t ns = A.ns;
+            const uint32_t wb = ns > (int64_t)HUB_WINDOW ? (uint32_t)(ns - HUB_WINDOW) : 0u;
+            const uint64_t wnh = A.wnh;
+            const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
+            team_walk<32, 2>(
+                A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, HubSeg{},
+                [&](uint32_t u, uint32_t asym) {
+                    const uint32_t wi = u - wb;
+                    if (wi >= HUB_WINDOW) { set_error(err, E_INTERNAL); return; }
+                    atomicAdd(&sm.win[wi >> 1], (asym ? 256u : 1u) << ((wi & 1u) * 16u));
+                });
+            if (wnh > 0) {
+                table_geometry(wnh < above_nh ? wnh : above_nh, 32, WARP_CAP, cap, shift);
+                const uint32_t mask = cap - 1;
+                team_walk<32, 2>(
+                    A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, LowSeg{},
+                    [&](uint32_t u, uint32_t asym) {
+                        hash_add(sm.tab, shift, mask, u + 1, asym ? INC_ASYM : INC_SYM, err);
+                    });
+            }
+            // window epilogue from the first word that can hold an endpoint
+            const uint32_t first = (A.r + 1 > wb ? A.r + 1 - wb : 0u) >> 3;  // uint4 index
+            uint4 *w4 = reinterpret_cast<uint4 *>(sm.win);
+            for (uint32_t q = first + lane; q < HUB_WINDOW / 8; q += 32) {
+                uint4 v = w4[q];
+                if (v.x | v.y | v.z | v.w) {
+                    pair_terms8(v.x & 0xffffu, bal, tot); pair_terms8(v.x >> 16, bal, tot);
+                    pair_terms8(v.y & 0xffffu, bal, tot); pair_terms8(v.y >> 16, bal, tot);
+                    pair_terms8(v.z & 0xffffu, bal, tot); pair_terms8(v.z >> 16, bal, tot);
+                    pair_terms8(v.w & 0xffffu, bal, tot); pair_terms8(v.w >> 16, bal, tot);
+                    w4[q] = make_uint4(0u, 0u, 0u, 0u);
+                }
+            }
+        }
         for (uint32_t i = lane; i < cap; i += 32) {
             unsigned long long t = sm.tab[i];
             if (t) { pair_terms((uint32_t)t, bal, tot); sm.tab[i] = 0ull; }
@@ -294,7 +368,7 @@ struct HybSmem {
 };
 
 template <int TS, uint32_t HCAP, int CTR, int CLS>
-__global__ void __launch_bounds__(TS) k_hybrid(DevGraph G, const uint32_t *list) {
+__device__ __forceinline__ void hybrid_body(DevGraph &G, const AnchorRec *list) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HybSmem<TS, HCAP> &sm = *reinterpret_cast<HybSmem<TS, HCAP> *>(smem_raw);
     const int t = threadIdx.x;
@@ -312,19 +386,13 @@ __global__ void __launch_bounds__(TS) k_hybrid(DevGraph G, const uint32_t *list)
         __syncthreads();
         if (jid >= n) break;
         const Anchor A = load_anchor(G, list[jid]);
-        const int64_t ns = A.S.n;
+        const int64_t ns = A.ns;
         const uint32_t wb = ns > (int64_t)HUB_WINDOW ? (uint32_t)(ns - HUB_WINDOW) : 0u;
-        const uint64_t W = A.S.work[A.r], wnh = A.S.work_nh[A.r];
+        const uint64_t W = A.W, wnh = A.wnh;
         const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
         if (W > wnh) {  // endpoints inside the hub window
             team_walk<TS>(
-                A.S, A.O, A.rb, 0, A.deg, sm.walk, t,
-                [&](uint32_t v, uint32_t sfx, long long &st, uint32_t &len) {
-                    const long long b = A.O.off[v];
-                    const long long s0 = b + sfx, hs = b + A.O.hstart[v];
-                    st = s0 > hs ? s0 : hs;
-                    len = (uint32_t)(A.O.off[v + 1] - st);
-                },
+                A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, HubSeg{},
                 [&](uint32_t u, uint32_t asym) {
                     const uint32_t idx = u - wb;
                     const bool in = idx < HUB_WINDOW;
@@ -348,13 +416,7 @@ __global__ void __launch_bounds__(TS) k_hybrid(DevGraph G, const uint32_t *list)
             table_geometry(wnh < above_nh ? wnh : above_nh, 32, HCAP, cap, shift);
             const uint32_t mask = cap - 1;
             team_walk<TS>(
-                A.S, A.O, A.rb, 0, A.deg, sm.walk, t,
-                [&](uint32_t v, uint32_t sfx, long long &st, uint32_t &len) {
-                    const long long b = A.O.off[v];
-                    st = b + sfx;
-                    const long long hs = b + A.O.hstart[v];
-                    len = hs > st ? (uint32_t)(hs - st) : 0u;
-                },
+                A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, LowSeg{},
                 [&](uint32_t u, uint32_t asym) {
                     hash_add(sm.tab, shift, mask, u + 1, asym ? INC_ASYM : INC_SYM, err);
                 });
@@ -377,6 +439,14 @@ __global__ void __launch_bounds__(TS) k_hybrid(DevGraph G, const uint32_t *list)
     if (t == 0) acc_add(G.scratch, bal, tot);
 }
 
+__global__ void __launch_bounds__(TEAM_THREADS) k_team(DevGraph G) {
+    hybrid_body<TEAM_THREADS, TEAM_CAP, CTR_TEAM, CLS_TEAM>(G, G.team_list);
+}
+
+__global__ void __launch_bounds__(CTAH_THREADS) k_ctah(DevGraph G) {
+    hybrid_body<CTAH_THREADS, CTAH_CAP, CTR_CTAH, CLS_CTAH>(G, G.ctah_list);
+}
+
 // ------------------------------------------------------------ dense class
 struct DenseSmem {
     uint32_t cnt[DENSE_CAP];
@@ -397,8 +467,14 @@ __global__ void __launch_bounds__(DENSE_THREADS) k_dense(DevGraph G) {
         __syncthreads();
         if (jid >= njobs) break;
         const DenseJob J = G.dense_jobs[jid];
-        const Anchor A = load_anchor(G, J.anchor);
-        const uint32_t e_lo = A.r + 1, e_hi = (uint32_t)A.S.n;
+        const bool sv = J.anchor & 1u;
+        const SideCSR &S = sv ? G.side[1] : G.side[0];
+        AnchorRec rec;
+        rec.anchor = J.anchor;
+        rec.rb = (uint32_t)S.off[J.anchor >> 1];
+        rec.deg = 0; rec.W = 0; rec.wnh = 0;
+        const Anchor A = load_anchor(G, rec);
+        const uint32_t e_lo = A.r + 1, e_hi = (uint32_t)A.ns;
         const bool windows = (e_hi - e_lo) > DENSE_CAP;
         for (uint32_t e0 = e_lo; e0 < e_hi; e0 += DENSE_CAP) {
             const uint32_t e1 = e_hi - e0 > DENSE_CAP ? e0 + DENSE_CAP : e_hi;
@@ -412,16 +488,16 @@ __global__ void __launch_bounds__(DENSE_THREADS) k_dense(DevGraph G) {
             };
             if (windows) {
                 team_walk<DENSE_THREADS>(
-                    A.S, A.O, A.rb, J.m0, J.m1, sm.walk, t,
-                    [&](uint32_t v, uint32_t sfx, long long &st, uint32_t &l) {
-                        const long long b = A.O.off[v], ve = A.O.off[v + 1];
-                        const long long s0 = lower_bound_u32(A.O.adj, b + sfx, ve, e0 << 1);
+                    A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t,
+                    [&](const uint4 &d, long long &st, uint32_t &l) {
+                        const long long s0 = lower_bound_u32(A.oadj, d.x, d.z, e0 << 1);
                         st = s0;
-                        l = (uint32_t)(lower_bound_u32(A.O.adj, s0, ve, e1 << 1) - s0);
+                        l = (uint32_t)(lower_bound_u32(A.oadj, s0, d.z, e1 << 1) - s0);
                     },
                     add);
             } else {
-                team_walk<DENSE_THREADS>(A.S, A.O, A.rb, J.m0, J.m1, sm.walk, t, FullSeg{A.O}, add);
+                team_walk<DENSE_THREADS>(A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t, FullSeg{},
+                                         add);
             }
             unsigned long long bal = 0, tot = 0;
             if (J.group == NO_GROUP) {
@@ -473,6 +549,8 @@ __global__ void k_flip(DevGraph G, const int64_t *edge_idx, int64_t n) {
         int64_t q = lower_bound_u32(V.adj, V.off[rv], V.off[rv + 1], ru << 1);
         atomicXor(&U.adj[p], 1u);
         atomicXor(&V.adj[q], 1u);
+        atomicXor(&U.md[p].w, 1u);   // the descriptors carry the edge's sign too
+        atomicXor(&V.md[q].w, 1u);
     }
 }
 
@@ -481,8 +559,6 @@ constexpr size_t TEAM_SMEM = sizeof(HybSmem<TEAM_THREADS, TEAM_CAP>);
 constexpr size_t CTAH_SMEM = sizeof(HybSmem<CTAH_THREADS, CTAH_CAP>);
 constexpr size_t DENSE_SMEM = sizeof(DenseSmem);
 
-auto *const k_team = k_hybrid<TEAM_THREADS, TEAM_CAP, CTR_TEAM, CLS_TEAM>;
-auto *const k_ctah = k_hybrid<CTAH_THREADS, CTAH_CAP, CTR_CTAH, CLS_CTAH>;
 
 struct LaunchCfg {
     int warp_blocks = 0, team_blocks = 0, ctah_blocks = 0, dense_blocks = 0;
@@ -524,9 +600,9 @@ void launch_count(const DevGraph &g, cudaStream_t s, int64_t *per_vertex_dev, cu
     if (ev) cudaEventRecord(ev[0], s);
     k_dense<<<g_cfg.dense_blocks, DENSE_THREADS, DENSE_SMEM, s>>>(g); note_launch();
     if (ev) cudaEventRecord(ev[1], s);
-    k_ctah<<<g_cfg.ctah_blocks, CTAH_THREADS, CTAH_SMEM, s>>>(g, g.ctah_list); note_launch();
+    k_ctah<<<g_cfg.ctah_blocks, CTAH_THREADS, CTAH_SMEM, s>>>(g); note_launch();
     if (ev) cudaEventRecord(ev[2], s);
-    k_team<<<g_cfg.team_blocks, TEAM_THREADS, TEAM_SMEM, s>>>(g, g.team_list); note_launch();
+    k_team<<<g_cfg.team_blocks, TEAM_THREADS, TEAM_SMEM, s>>>(g); note_launch();
     if (ev) cudaEventRecord(ev[3], s);
     k_warp<<<g_cfg.warp_blocks, WARP_THREADS, WARP_SMEM, s>>>(g); note_launch();
     if (ev) cudaEventRecord(ev[4], s);

@@ -23,9 +23,14 @@ namespace bb {
 constexpr uint32_t HUB_WINDOW = 2048;
 // dense counters per CTA job: 48Ki u32 (192 KiB of shared memory)
 constexpr uint32_t DENSE_CAP = 49152;
-// warp class: wedges <= WARP_W_MAX, hash of at most WARP_CAP slots
-constexpr uint64_t WARP_W_MAX = 400;
-constexpr uint32_t WARP_CAP = 512;
+// warp class: one warp per anchor of degree <= WARP_DEG_MAX (its per-pair
+// counts then fit 8 bits) and at most WARP_W_MAX wedges. Anchors with at
+// most WARP_SMALL_W wedges hash every endpoint; larger ones keep the hub
+// window in 16-bit counters and hash the rest; the hash has WARP_CAP slots.
+constexpr uint32_t WARP_DEG_MAX = 255;
+constexpr uint64_t WARP_W_MAX = 16384;
+constexpr uint64_t WARP_SMALL_W = 200;
+constexpr uint32_t WARP_CAP = 256;
 // team class (4 warps): wedges <= TEAM_W_MAX and below-window wedges that fit
 // a TEAM_CAP-slot hash
 constexpr uint64_t TEAM_W_MAX = 16384;
@@ -40,6 +45,13 @@ constexpr uint32_t MAX_SPLIT_JOBS = 1u << 16;
 constexpr uint32_t MAX_GPART = 1u << 24;
 
 enum Cls : uint32_t { CLS_WARP = 0, CLS_TEAM = 1, CLS_CTAH = 2, CLS_DENSE = 3, NCLS = 4 };
+
+// One anchor in a class list: (side rank << 1 | side), start of its row,
+// degree, wedges and below-window wedges (saturated to 32 bits).
+struct alignas(16) AnchorRec {
+    uint32_t anchor, rb, deg, W;
+    uint32_t wnh, pad0, pad1, pad2;
+};
 
 // One CTA job over dense counters: anchor (side rank << 1 | side), its
 // middle slice [m0, m1) of the anchor's row, and the split group (or
@@ -81,9 +93,9 @@ struct DevGraph {
     int32_t *col = nullptr;
     int8_t *sign = nullptr;
     // classification
-    uint32_t *warp_list = nullptr;   // anchors
-    uint32_t *team_list = nullptr;   // anchors
-    uint32_t *ctah_list = nullptr;   // anchors
+    AnchorRec *warp_list = nullptr;
+    AnchorRec *team_list = nullptr;
+    AnchorRec *ctah_list = nullptr;
     DenseJob *dense_jobs = nullptr;
     SplitGroup *groups = nullptr;
     uint32_t *gpart = nullptr;       // merged partial counters of split anchors
