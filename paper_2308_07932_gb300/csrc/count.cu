@@ -5,9 +5,13 @@
 // For an anchor w every wedge w - v - u (v a neighbour of w, u in the suffix
 // of v's row ranked above both) adds 1 to the symmetric tally of the pair
 // (w, u) when sign(w,v) == sign(v,u) (Def. 5) and to the asymmetric tally
-// otherwise (Def. 6). Once all of w's wedges are in, each pair with S
-// symmetric and A asymmetric wedges adds C(S,2) + C(A,2) balanced and
-// C(S+A,2) total butterflies (Lemma 2).
+// otherwise (Def. 6). A pair with S symmetric and A asymmetric wedges holds
+// C(S,2) + C(A,2) balanced and C(S+A,2) total butterflies (Lemma 2). Since
+// C(n,2) = 0 + 1 + ... + (n-1), those sums are taken wedge by wedge: each
+// wedge adds the count its own tally held before it (returned by the
+// counter's atomic add) to the balanced sum and the count both tallies held
+// to the total, which is exact in any order and needs no pass over the
+// counters afterwards, only their reset.
 //
 // Work is spread by a team walker: a team (a warp, or a whole CTA) loads a
 // chunk of the anchor's middles, scans their suffix lengths, and splits the
@@ -21,13 +25,12 @@
 //           endpoint + 1 in the high half) for the rest;
 //   team  - medium anchors, one per 128-thread CTA: dense counters for the
 //           hub window (top HUB_WINDOW ranks of the side, where most
-//           endpoints fall) with a list of touched counters, and a hash for
-//           the endpoints below the window;
+//           endpoints fall) and a hash for the endpoints below the window;
 //   ctah  - like team with a 512-thread CTA and a 16Ki-slot hash;
 //   dense - heavy anchors with a short endpoint range: dense counters over
 //           the whole range (walked in windows when longer than DENSE_CAP);
-//           the heaviest are split over CTAs and merged in global memory
-//           before the C(.,2) step (C is not additive).
+//           the heaviest are split over CTAs whose partial counts are
+//           merged in global memory, adding the pairs formed across parts.
 #include <algorithm>
 #include "graph.cuh"
 
@@ -52,12 +55,11 @@ __device__ __forceinline__ void acc_add(CountScratch *sc, unsigned long long bal
     }
 }
 
-// per-pair contribution of one packed counter (Lemma 2)
-__device__ __forceinline__ void pair_terms(uint32_t c, unsigned long long &bal,
-                                           unsigned long long &tot) {
-    uint32_t S = c & 0xffffu, A = c >> 16;
-    bal += c2(S) + c2(A);
-    tot += c2(S + A);
+// contribution of one wedge given its pair's counts before it
+__device__ __forceinline__ void wedge_terms(uint32_t oldS, uint32_t oldA, uint32_t asym,
+                                            unsigned long long &bal, unsigned long long &tot) {
+    bal += asym ? oldA : oldS;
+    tot += oldS + oldA;
 }
 
 // block-wide sum of two u64 values, result valid in thread 0
@@ -196,23 +198,42 @@ __device__ __forceinline__ void team_walk(const uint4 *__restrict__ smd,
     }
 }
 
-// insert-or-increment in a shared-memory table of 2^(32-shift) u64 slots
-__device__ __forceinline__ void hash_add(unsigned long long *tab, uint32_t shift, uint32_t mask,
-                                         uint32_t key, uint32_t inc, uint32_t *err) {
+// insert-or-increment in a shared-memory table of 2^(32-shift) u64 slots;
+// returns the packed (S | A << 16) count the key held before
+__device__ __forceinline__ uint32_t hash_add(unsigned long long *tab, uint32_t shift,
+                                             uint32_t mask, uint32_t key, uint32_t inc,
+                                             uint32_t *err) {
     uint32_t h = hash_slot(key, shift);
     for (uint32_t probe = 0; probe <= mask; probe++) {
         unsigned long long cur = *((volatile unsigned long long *)&tab[h]);
         uint32_t k = (uint32_t)(cur >> 32);
-        if (k == key) { atomicAdd(&tab[h], (unsigned long long)inc); return; }
+        if (k == key) return (uint32_t)atomicAdd(&tab[h], (unsigned long long)inc);
         if (k == 0) {
             unsigned long long want = ((unsigned long long)key << 32) | inc;
             unsigned long long old = atomicCAS(&tab[h], 0ull, want);
-            if (old == 0ull) return;
-            if ((uint32_t)(old >> 32) == key) { atomicAdd(&tab[h], (unsigned long long)inc); return; }
+            if (old == 0ull) return 0u;
+            if ((uint32_t)(old >> 32) == key)
+                return (uint32_t)atomicAdd(&tab[h], (unsigned long long)inc);
         }
         h = (h + 1) & mask;
     }
     set_error(err, E_PROBE);
+    return 0u;
+}
+
+// hash add plus the wedge's contribution
+__device__ __forceinline__ void hash_wedge(unsigned long long *tab, uint32_t shift, uint32_t mask,
+                                           uint32_t u, uint32_t asym, uint32_t *err,
+                                           unsigned long long &bal, unsigned long long &tot) {
+    const uint32_t old = hash_add(tab, shift, mask, u + 1, asym ? INC_ASYM : INC_SYM, err);
+    wedge_terms(old & 0xffffu, old >> 16, asym, bal, tot);
+}
+
+// zero the first `cap` slots of a table (cap a multiple of 2) as a team
+template <int TS>
+__device__ __forceinline__ void clear_table(unsigned long long *tab, uint32_t cap, int t) {
+    ulonglong2 *t2 = reinterpret_cast<ulonglong2 *>(tab);
+    for (uint32_t i = t; i < cap / 2; i += TS) t2[i] = make_ulonglong2(0ull, 0ull);
 }
 
 // table of 2^k slots, 2^k >= max(min_cap, need + need/4 + 1), at most max_cap
@@ -281,18 +302,11 @@ struct WarpSmem {
     WalkSmem<32> walk;
 };
 
-__device__ __forceinline__ void pair_terms8(uint32_t c, unsigned long long &bal,
-                                            unsigned long long &tot) {
-    uint32_t S = c & 0xffu, A = (c >> 8) & 0xffu;
-    bal += c2(S) + c2(A);
-    tot += c2(S + A);
-}
-
 __global__ void __launch_bounds__(WARP_THREADS, 4) k_warp(DevGraph G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[threadIdx.x >> 5];
     const unsigned lane = lane_id();
-    for (uint32_t i = lane; i < WARP_CAP; i += 32) sm.tab[i] = 0ull;
+    clear_table<32>(sm.tab, WARP_CAP, (int)lane);
     for (uint32_t i = lane; i < HUB_WINDOW / 2; i += 32) sm.win[i] = 0u;
     __syncwarp();
     const uint32_t n = G.ctr[CTR_WARP];
@@ -307,10 +321,10 @@ __global__ void __launch_bounds__(WARP_THREADS, 4) k_warp(DevGraph G) {
         if (W <= WARP_SMALL_W) {  // hash every endpoint
             table_geometry(W < above ? W : above, 32, WARP_CAP, cap, shift);
             const uint32_t mask = cap - 1;
-            team_walk<32, 2>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane,
-                          FullSeg{}, [&](uint32_t u, uint32_t asym) {
-                              hash_add(sm.tab, shift, mask, u + 1, asym ? INC_ASYM : INC_SYM, err);
-                          });
+            team_walk<32, 2>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, FullSeg{},
+                             [&](uint32_t u, uint32_t asym) {
+                                 hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
+                             });
         } else {
             const int64_t ns = A.ns;
             const uint32_t wb = ns > (int64_t)HUB_WINDOW ? (uint32_t)(ns - HUB_WINDOW) : 0u;
@@ -321,35 +335,25 @@ __global__ void __launch_bounds__(WARP_THREADS, 4) k_warp(DevGraph G) {
                 [&](uint32_t u, uint32_t asym) {
                     const uint32_t wi = u - wb;
                     if (wi >= HUB_WINDOW) { set_error(err, E_INTERNAL); return; }
-                    atomicAdd(&sm.win[wi >> 1], (asym ? 256u : 1u) << ((wi & 1u) * 16u));
+                    const uint32_t sh = (wi & 1u) * 16u;
+                    const uint32_t old = atomicAdd(&sm.win[wi >> 1], (asym ? 256u : 1u) << sh) >> sh;
+                    wedge_terms(old & 0xffu, (old >> 8) & 0xffu, asym, bal, tot);
                 });
             if (wnh > 0) {
                 table_geometry(wnh < above_nh ? wnh : above_nh, 32, WARP_CAP, cap, shift);
                 const uint32_t mask = cap - 1;
-                team_walk<32, 2>(
-                    A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, LowSeg{},
-                    [&](uint32_t u, uint32_t asym) {
-                        hash_add(sm.tab, shift, mask, u + 1, asym ? INC_ASYM : INC_SYM, err);
-                    });
+                team_walk<32, 2>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, LowSeg{},
+                                 [&](uint32_t u, uint32_t asym) {
+                                     hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
+                                 });
             }
-            // window epilogue from the first word that can hold an endpoint
+            // reset the window words an endpoint can have reached
             const uint32_t first = (A.r + 1 > wb ? A.r + 1 - wb : 0u) >> 3;  // uint4 index
             uint4 *w4 = reinterpret_cast<uint4 *>(sm.win);
-            for (uint32_t q = first + lane; q < HUB_WINDOW / 8; q += 32) {
-                uint4 v = w4[q];
-                if (v.x | v.y | v.z | v.w) {
-                    pair_terms8(v.x & 0xffffu, bal, tot); pair_terms8(v.x >> 16, bal, tot);
-                    pair_terms8(v.y & 0xffffu, bal, tot); pair_terms8(v.y >> 16, bal, tot);
-                    pair_terms8(v.z & 0xffffu, bal, tot); pair_terms8(v.z >> 16, bal, tot);
-                    pair_terms8(v.w & 0xffffu, bal, tot); pair_terms8(v.w >> 16, bal, tot);
-                    w4[q] = make_uint4(0u, 0u, 0u, 0u);
-                }
-            }
+            for (uint32_t q = first + lane; q < HUB_WINDOW / 8; q += 32)
+                w4[q] = make_uint4(0u, 0u, 0u, 0u);
         }
-        for (uint32_t i = lane; i < cap; i += 32) {
-            unsigned long long t = sm.tab[i];
-            if (t) { pair_terms((uint32_t)t, bal, tot); sm.tab[i] = 0ull; }
-        }
+        clear_table<32>(sm.tab, cap, (int)lane);
         __syncwarp();
     }
     block_sum2<WARP_THREADS>(bal, tot);
@@ -360,10 +364,8 @@ __global__ void __launch_bounds__(WARP_THREADS, 4) k_warp(DevGraph G) {
 template <int TS, uint32_t HCAP>
 struct HybSmem {
     uint32_t win[HUB_WINDOW];          // hub window counters
-    uint16_t touched[HUB_WINDOW];      // window indices touched by this anchor
     unsigned long long tab[HCAP];      // hash for endpoints below the window
     WalkSmem<TS> walk;
-    uint32_t ntouched;
     uint32_t job;
 };
 
@@ -372,10 +374,8 @@ __device__ __forceinline__ void hybrid_body(DevGraph &G, const AnchorRec *list) 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HybSmem<TS, HCAP> &sm = *reinterpret_cast<HybSmem<TS, HCAP> *>(smem_raw);
     const int t = threadIdx.x;
-    const unsigned lane = lane_id();
     for (uint32_t i = t; i < HUB_WINDOW; i += TS) sm.win[i] = 0;
-    for (uint32_t i = t; i < HCAP; i += TS) sm.tab[i] = 0ull;
-    if (t == 0) sm.ntouched = 0;
+    clear_table<TS>(sm.tab, HCAP, t);
     const uint32_t n = G.ctr[CTR];
     uint32_t *err = &G.scratch->err;
     unsigned long long bal = 0, tot = 0;
@@ -391,49 +391,33 @@ __device__ __forceinline__ void hybrid_body(DevGraph &G, const AnchorRec *list) 
         const uint64_t W = A.W, wnh = A.wnh;
         const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
         if (W > wnh) {  // endpoints inside the hub window
-            team_walk<TS>(
-                A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, HubSeg{},
-                [&](uint32_t u, uint32_t asym) {
-                    const uint32_t idx = u - wb;
-                    const bool in = idx < HUB_WINDOW;
-                    if (!in) set_error(err, E_INTERNAL);
-                    const uint32_t old =
-                        in ? atomicAdd(&sm.win[idx], asym ? INC_ASYM : INC_SYM) : 1u;
-                    const bool first = old == 0;
-                    const unsigned act = __activemask();
-                    const unsigned fm = __ballot_sync(act, first);
-                    if (first) {
-                        const unsigned ldr = __ffs(fm) - 1;
-                        uint32_t base = 0;
-                        if (lane == ldr) base = atomicAdd(&sm.ntouched, (uint32_t)__popc(fm));
-                        base = __shfl_sync(fm, base, ldr);
-                        sm.touched[base + __popc(fm & ((1u << lane) - 1u))] = (uint16_t)idx;
-                    }
-                });
+            team_walk<TS>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, HubSeg{},
+                          [&](uint32_t u, uint32_t asym) {
+                              const uint32_t idx = u - wb;
+                              if (idx >= HUB_WINDOW) { set_error(err, E_INTERNAL); return; }
+                              const uint32_t old =
+                                  atomicAdd(&sm.win[idx], asym ? INC_ASYM : INC_SYM);
+                              wedge_terms(old & 0xffffu, old >> 16, asym, bal, tot);
+                          });
         }
+        uint32_t cap = 0;
         if (wnh > 0) {  // endpoints below the window
-            uint32_t cap, shift;
+            uint32_t shift;
             table_geometry(wnh < above_nh ? wnh : above_nh, 32, HCAP, cap, shift);
             const uint32_t mask = cap - 1;
-            team_walk<TS>(
-                A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, LowSeg{},
-                [&](uint32_t u, uint32_t asym) {
-                    hash_add(sm.tab, shift, mask, u + 1, asym ? INC_ASYM : INC_SYM, err);
-                });
-            for (uint32_t i = t; i < cap; i += TS) {
-                unsigned long long x = sm.tab[i];
-                if (x) { pair_terms((uint32_t)x, bal, tot); sm.tab[i] = 0ull; }
-            }
+            team_walk<TS>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, LowSeg{},
+                          [&](uint32_t u, uint32_t asym) {
+                              hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
+                          });
         }
         __syncthreads();
-        const uint32_t nt = sm.ntouched;
-        for (uint32_t i = t; i < nt; i += TS) {
-            const uint32_t idx = sm.touched[i];
-            pair_terms(sm.win[idx], bal, tot);
-            sm.win[idx] = 0;
+        if (W > wnh) {
+            const uint32_t first = (A.r + 1 > wb ? A.r + 1 - wb : 0u) >> 2;  // uint4 index
+            uint4 *w4 = reinterpret_cast<uint4 *>(sm.win);
+            for (uint32_t q = first + t; q < HUB_WINDOW / 4; q += TS)
+                w4[q] = make_uint4(0u, 0u, 0u, 0u);
         }
-        __syncthreads();
-        if (t == 0) sm.ntouched = 0;
+        clear_table<TS>(sm.tab, cap, t);
     }
     block_sum2<TS>(bal, tot);
     if (t == 0) acc_add(G.scratch, bal, tot);
@@ -481,10 +465,12 @@ __global__ void __launch_bounds__(DENSE_THREADS) k_dense(DevGraph G) {
             const uint32_t len = e1 - e0;
             for (uint32_t i = t; i < len; i += DENSE_THREADS) sm.cnt[i] = 0;
             __syncthreads();
+            unsigned long long bal = 0, tot = 0;
             auto add = [&](uint32_t u, uint32_t asym) {
                 const uint32_t idx = u - e0;
-                if (idx < len) atomicAdd(&sm.cnt[idx], asym ? INC_ASYM : INC_SYM);
-                else set_error(&sc->err, E_INTERNAL);
+                if (idx >= len) { set_error(&sc->err, E_INTERNAL); return; }
+                const uint32_t old = atomicAdd(&sm.cnt[idx], asym ? INC_ASYM : INC_SYM);
+                wedge_terms(old & 0xffffu, old >> 16, asym, bal, tot);
             };
             if (windows) {
                 team_walk<DENSE_THREADS>(
@@ -499,28 +485,33 @@ __global__ void __launch_bounds__(DENSE_THREADS) k_dense(DevGraph G) {
                 team_walk<DENSE_THREADS>(A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t, FullSeg{},
                                          add);
             }
-            unsigned long long bal = 0, tot = 0;
-            if (J.group == NO_GROUP) {
-                for (uint32_t i = t; i < len; i += DENSE_THREADS) pair_terms(sm.cnt[i], bal, tot);
-            } else {
+            if (J.group != NO_GROUP) {
+                // merge this part's counts into the group's global counters; a
+                // count p added to c already there closes c*p new pairs
                 const SplitGroup grp = G.groups[J.group];
                 uint32_t *part = G.gpart + grp.goff;
-                for (uint32_t i = t; i < len; i += DENSE_THREADS)
-                    if (sm.cnt[i]) atomicAdd(&part[i], sm.cnt[i]);
+                __syncthreads();
+                for (uint32_t i = t; i < len; i += DENSE_THREADS) {
+                    const uint32_t p = sm.cnt[i];
+                    if (p) {
+                        const uint32_t c = atomicAdd(&part[i], p);
+                        const unsigned long long cS = c & 0xffffu, cA = c >> 16;
+                        const unsigned long long pS = p & 0xffffu, pA = p >> 16;
+                        bal += cS * pS + cA * pA;
+                        tot += (cS + cA) * (pS + pA);
+                    }
+                }
+                // the last part to arrive resets the group's counters
                 __threadfence();
                 __syncthreads();
                 if (t == 0) {
-                    uint32_t ticket = atomicAdd(&G.gdone[J.group], 1u);
+                    const uint32_t ticket = atomicAdd(&G.gdone[J.group], 1u);
                     sm.last = ticket == grp.parts - 1 ? 1u : 0u;
                 }
                 __syncthreads();
                 if (sm.last) {
                     __threadfence();
-                    for (uint32_t i = t; i < len; i += DENSE_THREADS) {
-                        uint32_t c = __ldcg(&part[i]);
-                        pair_terms(c, bal, tot);
-                        part[i] = 0;
-                    }
+                    for (uint32_t i = t; i < len; i += DENSE_THREADS) part[i] = 0;
                     if (t == 0) G.gdone[J.group] = 0;
                 }
             }
