@@ -32,6 +32,7 @@
 //           the heaviest are split over CTAs whose partial counts are
 //           merged in global memory, adding the pairs formed across parts.
 #include <algorithm>
+#include <cstddef>
 #include "graph.cuh"
 
 namespace bb {
@@ -95,24 +96,37 @@ struct Desc {
 };
 
 template <int TS>
-struct WalkSmem {
+struct alignas(16) WalkSmem {
     Desc desc[TS];
     uint32_t incl[TS];
     unsigned long long warp_part[TS / 32];
+    uint32_t stage[TS / 32][3][32];   // per warp: compacted remainders (start, length, sign)
     uint32_t tot[2];
+    uint32_t item_next;               // next work item of the chunk (teams of several warps)
 };
+
+// wedges per work item when a team's warps share a chunk dynamically
+constexpr uint32_t WALK_ITEM = 256;
 
 // Walk the wedges of one anchor's middles [m0, m1) (its row starts at rb in
 // the anchor side's descriptors smd; the middles' rows are in oadj) as a
 // team of TS threads (t = thread index in the team). seg(md, st, len) picks
 // the segment [st, st+len) of a middle's row from its descriptor;
 // add(u_side_rank, asymmetric) is called once per wedge.
+//
+// Per chunk of TS middles the team scans the segment lengths and compacts
+// the non-empty segments; its warps then take 256-wedge slices of the
+// chunk in turn (a lone warp takes the whole chunk). A warp walks the whole
+// 32-wedge blocks of every segment in its slice together (coalesced, no
+// search), then the remainders (< 32 each) of up to 32 segments as one flat
+// range, each lane finding its segment from a bitmask of segment starts.
 template <int TS, int UNROLL = 4, typename Seg, typename Add>
 __device__ __forceinline__ void team_walk(const uint4 *__restrict__ smd,
                                           const uint32_t *__restrict__ oadj, int64_t rb,
                                           uint32_t m0, uint32_t m1, WalkSmem<TS> &sm, int t,
                                           Seg &&seg, Add &&add) {
     constexpr int NW = TS / 32;
+    constexpr uint32_t EXMASK = 0x7fffffffu;
     const int lane = t & 31, w = t >> 5;
     for (uint32_t mc = m0; mc < m1; mc += TS) {
         const uint32_t j = mc + (uint32_t)t;
@@ -142,57 +156,123 @@ __device__ __forceinline__ void team_walk(const uint4 *__restrict__ smd,
             sm.desc[nzi - 1] = Desc{(uint32_t)st, (incl - len) | (sw << 31)};
             sm.incl[nzi - 1] = incl;
         }
-        if (t == TS - 1) { sm.tot[0] = incl; sm.tot[1] = nzi; }
+        if (t == TS - 1) { sm.tot[0] = incl; sm.tot[1] = nzi; sm.item_next = 0; }
         team_sync<TS>();
         const uint32_t T = sm.tot[0], NZ = sm.tot[1];
-        if (T > 0) {
-            const uint32_t a = (uint32_t)((unsigned long long)T * w / NW);
-            const uint32_t b = (uint32_t)((unsigned long long)T * (w + 1) / NW);
-            // first middle whose running sum exceeds a
+        // a warp takes the whole chunk when alone, else 256-wedge items in turn
+        for (uint32_t item = 0;; item++) {
+        uint32_t a, b;
+        if constexpr (NW == 1) {
+            if (item > 0) break;
+            a = 0; b = T;
+        } else {
+            uint32_t it = 0;
+            if (lane == 0) it = atomicAdd(&sm.item_next, 1u);
+            it = __shfl_sync(FULL, it, 0);
+            a = it * WALK_ITEM;
+            if (a >= T) break;
+            b = T - a > WALK_ITEM ? a + WALK_ITEM : T;
+        }
+        if (a < b) {
+            // first segment holding wedge a
             uint32_t lo = 0, hi = NZ;
             while (lo < hi) {
-                uint32_t mid = (lo + hi) >> 1;
+                const uint32_t mid = (lo + hi) >> 1;
                 if (sm.incl[mid] <= a) lo = mid + 1; else hi = mid;
             }
-            uint32_t m = lo;
-            for (uint32_t base = a; base < b;) {
-                uint32_t addr[UNROLL], swv[UNROLL];
-                bool ok[UNROLL];
-#pragma unroll
-                for (int u = 0; u < UNROLL; u++) {
-                    ok[u] = false;
-                    if (base < b) {
-                        const uint32_t wi = m + lane < NZ ? m + lane : NZ - 1;
-                        const uint32_t wv = sm.incl[wi];
-                        const uint32_t i = base + lane;
-                        uint32_t k = 0;
-                        // all 32 wedges in middle m: no search needed
-                        if (__shfl_sync(FULL, wv, 0) < base + 32) {
-#pragma unroll
-                            for (int s2 = 16; s2 >= 1; s2 >>= 1) {
-                                uint32_t c = __shfl_sync(FULL, wv, k + s2 - 1);
-                                if (c <= i) k += s2;
-                            }
-                        }
-                        if (i < b) {
-                            const Desc d = sm.desc[m + k];
-                            const uint32_t ex = d.excl_sw & 0x7fffffffu;
-                            addr[u] = d.st + (i - ex);
-                            swv[u] = d.excl_sw >> 31;
-                            ok[u] = true;
-                        }
-                        m += __popc(__ballot_sync(FULL, wv <= base + 32));
-                        base += 32;
+            uint32_t(&stage)[3][32] = sm.stage[w];
+            const unsigned lt = (1u << lane) - 1u;
+            // segments [g, g+32) of the slice, one per lane
+            for (uint32_t g = lo; g < NZ; g += 32) {
+                const uint32_t kk = g + (uint32_t)lane;
+                uint32_t st0 = 0, full = 0, rl = 0, swk = 0;
+                bool valid = false;
+                if (kk < NZ) {
+                    const Desc d = sm.desc[kk];
+                    const uint32_t ex = d.excl_sw & EXMASK;
+                    if (ex < b) {
+                        valid = true;
+                        const uint32_t in = sm.incl[kk];
+                        const uint32_t s0 = ex > a ? ex : a, s1 = in < b ? in : b;
+                        const uint32_t n = s1 - s0;
+                        full = n & ~31u;
+                        rl = n - full;
+                        st0 = d.st + (s0 - ex);
+                        swk = d.excl_sw >> 31;
                     }
                 }
-                uint32_t xv[UNROLL];
+                const unsigned vm = __ballot_sync(FULL, valid);
+                // whole 32-wedge blocks of the long segments, warp-wide
+                unsigned lm = __ballot_sync(FULL, full > 0);
+                while (lm) {
+                    const int jl = __ffs(lm) - 1;
+                    lm &= lm - 1;
+                    const uint32_t bst = __shfl_sync(FULL, st0, jl) + (uint32_t)lane;
+                    const uint32_t bfull = __shfl_sync(FULL, full, jl);
+                    const uint32_t bsw = __shfl_sync(FULL, swk, jl);
+                    for (uint32_t o = 0; o < bfull; o += 32u * UNROLL) {
+                        uint32_t xv[UNROLL];
 #pragma unroll
-                for (int u = 0; u < UNROLL; u++)
-                    if (ok[u]) xv[u] = oadj[addr[u]];
+                        for (int q = 0; q < UNROLL; q++)
+                            if (o + 32u * q < bfull) xv[q] = oadj[bst + o + 32u * q];
 #pragma unroll
-                for (int u = 0; u < UNROLL; u++)
-                    if (ok[u]) add(xv[u] >> 1, (xv[u] ^ swv[u]) & 1u);
+                        for (int q = 0; q < UNROLL; q++)
+                            if (o + 32u * q < bfull) add(xv[q] >> 1, (xv[q] ^ bsw) & 1u);
+                    }
+                }
+                // the remainders (< 32 wedges each), compacted and walked flat
+                const unsigned nzm = __ballot_sync(FULL, rl > 0);
+                if (nzm) {
+                    const uint32_t nc = __popc(nzm);
+                    if (rl > 0) {
+                        const uint32_t cp = __popc(nzm & lt);
+                        stage[0][cp] = st0 + full; stage[1][cp] = rl; stage[2][cp] = swk;
+                    }
+                    __syncwarp();
+                    const uint32_t rs = lane < (int)nc ? stage[0][lane] : 0u;
+                    const uint32_t rlc = lane < (int)nc ? stage[1][lane] : 0u;
+                    const uint32_t swc = lane < (int)nc ? stage[2][lane] : 0u;
+                    __syncwarp();
+                    uint32_t ri = rlc;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const uint32_t y = __shfl_up_sync(FULL, ri, d);
+                        if (lane >= d) ri += y;
+                    }
+                    const uint32_t R = __shfl_sync(FULL, ri, 31);
+                    const uint32_t rx = (ri - rlc) | (swc << 31);
+                    for (uint32_t base0 = 0; base0 < R; base0 += 32u * UNROLL) {
+                        uint32_t addr[UNROLL], swq[UNROLL];
+                        bool ok[UNROLL];
+#pragma unroll
+                        for (int u = 0; u < UNROLL; u++) {
+                            // segment of wedge base+lane: those ending by `base`, plus
+                            // the segment starts inside this step up to my position
+                            const uint32_t base = base0 + 32u * u;
+                            const uint32_t c0 = __popc(__ballot_sync(FULL, ri <= base));
+                            const uint32_t p = ri - base;
+                            const uint32_t bit = (ri > base && p < 32u) ? (1u << p) : 0u;
+                            const uint32_t B = __reduce_or_sync(FULL, bit);
+                            const uint32_t sgi = (c0 + __popc(B & ((2u << lane) - 1u))) & 31u;
+                            const uint32_t srs = __shfl_sync(FULL, rs, sgi);
+                            const uint32_t srx = __shfl_sync(FULL, rx, sgi);
+                            const uint32_t q = base + (uint32_t)lane;
+                            ok[u] = q < R;
+                            addr[u] = srs + (q - (srx & EXMASK));
+                            swq[u] = srx >> 31;
+                        }
+                        uint32_t xv[UNROLL];
+#pragma unroll
+                        for (int u = 0; u < UNROLL; u++)
+                            if (ok[u]) xv[u] = oadj[addr[u]];
+#pragma unroll
+                        for (int u = 0; u < UNROLL; u++)
+                            if (ok[u]) add(xv[u] >> 1, (xv[u] ^ swq[u]) & 1u);
+                    }
+                }
+                if (vm != FULL) break;  // the slice ended inside this group
             }
+        }
         }
         team_sync<TS>();
     }
@@ -296,11 +376,15 @@ struct LowSeg {
 // Per warp: the hub window as 16-bit counters, two per word (S in the low
 // byte, A in the high byte; both <= the anchor's degree <= 255), a small
 // hash for endpoints below the window, and the walker's chunk.
-struct WarpSmem {
+struct alignas(16) WarpSmem {
     uint32_t win[HUB_WINDOW / 2];
     unsigned long long tab[WARP_CAP];
     WalkSmem<32> walk;
 };
+
+// per-warp copies are laid out back to back and reset with 16-byte stores
+static_assert(sizeof(WarpSmem) % 16 == 0, "WarpSmem must keep 16-byte alignment");
+static_assert(offsetof(WarpSmem, tab) % 16 == 0, "table needs 16-byte alignment");
 
 __global__ void __launch_bounds__(WARP_THREADS, 4) k_warp(DevGraph G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -362,7 +446,7 @@ __global__ void __launch_bounds__(WARP_THREADS, 4) k_warp(DevGraph G) {
 
 // ------------------------------------------------- team and CTA-hash classes
 template <int TS, uint32_t HCAP>
-struct HybSmem {
+struct alignas(16) HybSmem {
     uint32_t win[HUB_WINDOW];          // hub window counters
     unsigned long long tab[HCAP];      // hash for endpoints below the window
     WalkSmem<TS> walk;
@@ -371,6 +455,8 @@ struct HybSmem {
 
 template <int TS, uint32_t HCAP, int CTR, int CLS>
 __device__ __forceinline__ void hybrid_body(DevGraph &G, const AnchorRec *list) {
+    using Smem = HybSmem<TS, HCAP>;
+    static_assert(offsetof(Smem, tab) % 16 == 0, "table needs 16-byte alignment");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HybSmem<TS, HCAP> &sm = *reinterpret_cast<HybSmem<TS, HCAP> *>(smem_raw);
     const int t = threadIdx.x;
@@ -432,7 +518,7 @@ __global__ void __launch_bounds__(CTAH_THREADS) k_ctah(DevGraph G) {
 }
 
 // ------------------------------------------------------------ dense class
-struct DenseSmem {
+struct alignas(16) DenseSmem {
     uint32_t cnt[DENSE_CAP];
     WalkSmem<DENSE_THREADS> walk;
     uint32_t job, last;
