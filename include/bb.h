@@ -137,6 +137,31 @@ BB_API bb_status bb_graph_info(const bb_graph *g, int64_t *nU, int64_t *nV, int6
 
 BB_API void bb_graph_free(bb_graph *g);
 
+/* ------------------------------------------------ allocation-free count
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot ask for device memory at the time they count: processes whose
+ * device memory is already handed out by another allocator (a request would
+ * fail or fragment it), and services that forbid allocation once they are
+ * running (an allocation may block and synchronize the device).
+ *
+ * It runs the same path as bb_count_csr_device on csr_dev/signs_dev (device
+ * memory of the current device) and writes the counts to host memory, but
+ * needs no context and allocates nothing: every intermediate buffer is
+ * carved out of one device array of BB_NOALLOC_SCRATCH_BYTES that the
+ * library reserves on every GPU it is loaded on until the process exits.
+ * A graph whose workspace does not fit is rejected with BB_ERR_TOO_LARGE
+ * (roughly 1M edges fit). The first call on a device looks the array's
+ * device address up (a one-time set-up); make that first call before any
+ * stream capture. Work is queued on `stream` (NULL = the legacy default
+ * stream) and the call returns when it is done. All calls share the array
+ * and it keeps the last call's contents: the call clears what must start
+ * at zero itself, and two calls whose work overlaps on the GPU (another
+ * thread, another stream) race and give wrong results. */
+#define BB_NOALLOC_SCRATCH_BYTES (128u << 20)
+BB_API bb_status bb_count_csr_device_noalloc(const bb_csr *csr_dev, const int8_t *signs_dev,
+                                             void *stream, int64_t *balanced, int64_t *total,
+                                             int64_t *wedges_opt);
+
 /* ------------------------------------------------------------- tracing
  * Phase timings of the last count on a context, from CUDA events recorded
  * on the context's stream while timing is enabled (bb_ctx_set_timing).

@@ -104,6 +104,13 @@ bb_status map_build_error(uint32_t e) {
     return BB_OK;
 }
 
+}  // namespace
+
+// lets other translation units of the library set bb_last_error()
+bb_status bb::report_error(bb_status st, const char *msg) { return fail(st, "%s", msg); }
+
+namespace {
+
 // results copied back after a count
 struct HostResult {
     unsigned long long acc[4];

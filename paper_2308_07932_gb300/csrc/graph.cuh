@@ -13,6 +13,7 @@
 // than there are vertices above it on its side.
 #pragma once
 #include <cstdint>
+#include "../../include/bb.h"
 #include "common.cuh"
 
 namespace bb {
@@ -141,6 +142,9 @@ void launch_flip(DevGraph &g, const int64_t *edge_idx_dev, int64_t n, cudaStream
 // One-time per-device kernel attributes (shared-memory opt-ins).
 void build_init();
 void count_init();
+
+// Sets the calling thread's bb_last_error() message; returns st.
+bb_status report_error(bb_status st, const char *msg);
 
 // entries of the split-merge buffer for a graph with nE edges
 inline size_t gpart_entries(int64_t nE) {
