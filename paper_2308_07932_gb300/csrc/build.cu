@@ -103,12 +103,11 @@ __global__ void k_global_rank(SideCSR S, const uint32_t *other_deg, int64_t n_ot
 // --------------------------------------------------------------- 3. rows
 // One thread per input edge e (its row u found by binary search in rowptr):
 // the U-side entry keeps the input position within u's row; the V-side
-// entry takes the next free slot of v's row. Each entry also records its
-// row (side rank) and input edge id.
+// entry takes the next free slot of v's row. Each entry is written as one
+// key (packed entry << 32 | input edge id) for the row sorts.
 __global__ void k_fill(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                        const int8_t *__restrict__ sign, int64_t nU, int64_t nE, SideCSR U,
-                       SideCSR V, uint32_t *cursorV, uint32_t *eidU, uint32_t *eidV,
-                       uint32_t *rowU, uint32_t *rowV) {
+                       SideCSR V, uint32_t *cursorV, uint64_t *keyU, uint64_t *keyV) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nE;
          e += (int64_t)gridDim.x * blockDim.x) {
         int64_t lo = 0, hi = nU;  // last u with rowptr[u] <= e
@@ -121,66 +120,129 @@ __global__ void k_fill(const int64_t *__restrict__ rowptr, const int32_t *__rest
         const uint32_t v = (uint32_t)col[e];
         const uint32_t neg = sign[e] < 0 ? 1u : 0u;
         const uint32_t rv = V.sr_of_id[v];
-        U.adj[pu] = (rv << 1) | neg;
-        eidU[pu] = (uint32_t)e;
-        rowU[pu] = r;
+        keyU[pu] = ((uint64_t)((rv << 1) | neg) << 32) | (uint32_t)e;
         const int64_t pv = V.off[rv] + atomicAdd(&cursorV[rv], 1u);
-        V.adj[pv] = (r << 1) | neg;
-        eidV[pv] = (uint32_t)e;
-        rowV[pv] = rv;
+        keyV[pv] = ((uint64_t)((r << 1) | neg) << 32) | (uint32_t)e;
     }
 }
 
 // Row length classes of a side (rows are in ascending degree, so each class
 // is a contiguous range of side ranks): bounds[k] = first side rank whose
-// degree exceeds ROW_LIMS[k]; bounds[4] = n.
-__constant__ uint32_t ROW_LIMS[4] = {1u, 32u, 2048u, 16384u};
+// degree exceeds ROW_LIMS[k]; bounds[NLIMS] = n.
+constexpr int NLIMS = 9;
+__constant__ uint32_t ROW_LIMS[NLIMS] = {1u, 2u, 4u, 8u, 16u, 32u, 256u, 2048u, 16384u};
 
 __global__ void k_row_bounds(const uint32_t *deg, int64_t n, int64_t *bounds) {
     int k = threadIdx.x;
-    if (k == 4) bounds[4] = n;
-    if (k >= 4) return;
+    if (k == NLIMS) bounds[NLIMS] = n;
+    if (k >= NLIMS) return;
     uint32_t lim = ROW_LIMS[k];
     int64_t lo = 0, hi = n;
     while (lo < hi) { int64_t m = (lo + hi) >> 1; if (deg[m] <= lim) lo = m + 1; else hi = m; }
     bounds[k] = lo;
 }
 
-__device__ __forceinline__ uint64_t pack_entry(uint32_t entry, uint32_t eid) {
-    return ((uint64_t)entry << 32) | eid;
+
+// writes one sorted key back as the entry, its edge id and its row
+__device__ __forceinline__ void put_entry(SideCSR &S, uint32_t *eid, uint32_t *rowid, int64_t p,
+                                          uint64_t x, uint32_t r) {
+    S.adj[p] = (uint32_t)(x >> 32);
+    eid[p] = (uint32_t)x;
+    rowid[p] = r;
 }
 
-// rows of 2..32 entries: one warp per row, bitonic sort in registers
-__global__ void k_sort_rows_warp(SideCSR S, uint32_t *eid, const int64_t *bounds, uint32_t *err) {
-    const int64_t r0 = bounds[0], r1 = bounds[1];
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+// rows of degree 0 or 1: nothing to sort, unpack the key
+__global__ void k_rows_single(SideCSR S, const uint64_t *keys, uint32_t *eid, uint32_t *rowid,
+                              const int64_t *bounds) {
+    const int64_t r1 = bounds[0];
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < r1;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = S.off[r];
+        if (S.off[r + 1] > b) put_entry(S, eid, rowid, b, keys[b], (uint32_t)r);
+    }
+}
+
+// rows of (WIDTH/2, WIDTH] entries, WIDTH <= 32: 32/WIDTH rows per warp,
+// bitonic sort in registers across WIDTH lanes
+template <int WIDTH>
+__global__ void k_sort_rows_sub(SideCSR S, const uint64_t *keys, uint32_t *eid, uint32_t *rowid,
+                                const int64_t *bounds, int lo_k, uint32_t *err) {
+    constexpr int PER = 32 / WIDTH;
+    const int64_t r0 = bounds[lo_k], r1 = bounds[lo_k + 1];
     const unsigned lane = lane_id();
-    for (int64_t r = r0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); r < r1;
-         r += warps) {
-        int64_t b = S.off[r];
-        uint32_t d = (uint32_t)(S.off[r + 1] - b);
-        uint64_t x = lane < d ? pack_entry(S.adj[b + lane], eid[b + lane]) : ~0ull;
+    const uint32_t el = lane % WIDTH;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t rb = r0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * PER; rb < r1;
+         rb += warps * PER) {
+        const int64_t r = rb + lane / WIDTH;
+        int64_t b = 0;
+        uint32_t d = 0;
+        if (r < r1) {
+            b = S.off[r];
+            d = (uint32_t)(S.off[r + 1] - b);
+        }
+        uint64_t x = el < d ? keys[b + el] : ~0ull;
 #pragma unroll
-        for (int k = 2; k <= 32; k <<= 1) {
+        for (int k = 2; k <= WIDTH; k <<= 1) {
 #pragma unroll
             for (int j = k >> 1; j > 0; j >>= 1) {
-                uint64_t y = __shfl_xor_sync(FULL, x, j);
-                bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+                const uint64_t y = __shfl_xor_sync(FULL, x, j);
+                const bool keep_min = ((el & j) == 0) == ((el & k) == 0);
                 x = keep_min ? (x < y ? x : y) : (x < y ? y : x);
             }
         }
-        uint64_t prev = __shfl_up_sync(FULL, x, 1);
-        if (lane < d) {
-            S.adj[b + lane] = (uint32_t)(x >> 32);
-            eid[b + lane] = (uint32_t)x;
-            if (lane > 0 && (prev >> 33) == (x >> 33)) set_error(err, E_DUP);
+        const uint64_t prev = __shfl_up_sync(FULL, x, 1);
+        if (el < d) {
+            put_entry(S, eid, rowid, b + el, x, (uint32_t)r);
+            if (el > 0 && (prev >> 33) == (x >> 33)) set_error(err, E_DUP);
         }
     }
 }
 
-// rows of (32, CAP] entries: one CTA per row, bitonic sort in shared memory
+// rows of (32, 256] entries: one warp per row, bitonic sort in shared memory
+constexpr int WS_THREADS = 256;
+__global__ void __launch_bounds__(WS_THREADS) k_sort_rows_warpsmem(SideCSR S, const uint64_t *keys,
+                                                                   uint32_t *eid, uint32_t *rowid,
+                                                                   const int64_t *bounds, int lo_k,
+                                                                   uint32_t *err) {
+    __shared__ uint64_t sbuf[WS_THREADS / 32][256];
+    uint64_t *buf = sbuf[threadIdx.x >> 5];
+    const unsigned lane = lane_id();
+    const int64_t r0 = bounds[lo_k], r1 = bounds[lo_k + 1];
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = r0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); r < r1;
+         r += warps) {
+        const int64_t b = S.off[r];
+        const uint32_t d = (uint32_t)(S.off[r + 1] - b);
+        uint32_t P = 64;
+        while (P < d) P <<= 1;
+        for (uint32_t i = lane; i < P; i += 32) buf[i] = i < d ? keys[b + i] : ~0ull;
+        __syncwarp();
+        for (uint32_t k = 2; k <= P; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t i = lane; i < P; i += 32) {
+                    const uint32_t ixj = i ^ j;
+                    if (ixj > i) {
+                        const uint64_t a = buf[i], c = buf[ixj];
+                        if ((a > c) == ((i & k) == 0)) { buf[i] = c; buf[ixj] = a; }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (uint32_t i = lane; i < d; i += 32) {
+            const uint64_t x = buf[i];
+            put_entry(S, eid, rowid, b + i, x, (uint32_t)r);
+            if (i > 0 && (buf[i - 1] >> 33) == (x >> 33)) set_error(err, E_DUP);
+        }
+        __syncwarp();
+    }
+}
+
+// rows of (256, CAP] entries: one CTA per row, bitonic sort in shared memory
 template <int CAP, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_sort_rows_smem(SideCSR S, uint32_t *eid,
+__global__ void __launch_bounds__(THREADS) k_sort_rows_smem(SideCSR S, const uint64_t *keys,
+                                                            uint32_t *eid, uint32_t *rowid,
                                                             const int64_t *bounds, int lo_k,
                                                             uint32_t *err) {
     extern __shared__ uint64_t sbuf[];
@@ -191,7 +253,7 @@ __global__ void __launch_bounds__(THREADS) k_sort_rows_smem(SideCSR S, uint32_t 
         uint32_t P = 1;
         while (P < d) P <<= 1;
         for (uint32_t i = threadIdx.x; i < P; i += THREADS)
-            sbuf[i] = i < d ? pack_entry(S.adj[b + i], eid[b + i]) : ~0ull;
+            sbuf[i] = i < d ? keys[b + i] : ~0ull;
         __syncthreads();
         for (uint32_t k = 2; k <= P; k <<= 1) {
             for (uint32_t j = k >> 1; j > 0; j >>= 1) {
@@ -208,8 +270,7 @@ __global__ void __launch_bounds__(THREADS) k_sort_rows_smem(SideCSR S, uint32_t 
         }
         for (uint32_t i = threadIdx.x; i < d; i += THREADS) {
             uint64_t x = sbuf[i];
-            S.adj[b + i] = (uint32_t)(x >> 32);
-            eid[b + i] = (uint32_t)x;
+            put_entry(S, eid, rowid, b + i, x, (uint32_t)r);
             if (i > 0 && (sbuf[i - 1] >> 33) == (x >> 33)) set_error(err, E_DUP);
         }
         __syncthreads();
@@ -221,9 +282,10 @@ __global__ void __launch_bounds__(THREADS) k_sort_rows_smem(SideCSR S, uint32_t 
 constexpr int RR_THREADS = 1024;
 constexpr int RR_WARPS = RR_THREADS / 32;
 
-__global__ void __launch_bounds__(RR_THREADS) k_sort_rows_radix(SideCSR S, uint32_t *eid,
+__global__ void __launch_bounds__(RR_THREADS) k_sort_rows_radix(SideCSR S, uint64_t *keys,
+                                                                uint64_t *alt, uint32_t *eid,
+                                                                uint32_t *rowid,
                                                                 const int64_t *bounds, int lo_k,
-                                                                uint64_t *bufA, uint64_t *bufB,
                                                                 int key_bits, uint32_t *err) {
     __shared__ uint32_t wcnt[RR_WARPS][256];
     __shared__ uint32_t run[256];
@@ -235,8 +297,7 @@ __global__ void __launch_bounds__(RR_THREADS) k_sort_rows_radix(SideCSR S, uint3
     for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
         int64_t b = S.off[r];
         int64_t d = S.off[r + 1] - b;
-        uint64_t *A = bufA + b, *B = bufB + b;
-        for (int64_t i = t; i < d; i += RR_THREADS) A[i] = pack_entry(S.adj[b + i], eid[b + i]);
+        uint64_t *A = keys + b, *B = alt + b;
         for (int k = t; k < RR_WARPS * 256; k += RR_THREADS) (&wcnt[0][0])[k] = 0;
         __syncthreads();
         uint64_t *src = A, *dst = B;
@@ -281,8 +342,7 @@ __global__ void __launch_bounds__(RR_THREADS) k_sort_rows_radix(SideCSR S, uint3
         }
         for (int64_t i = t; i < d; i += RR_THREADS) {
             uint64_t x = src[i];
-            S.adj[b + i] = (uint32_t)(x >> 32);
-            eid[b + i] = (uint32_t)x;
+            put_entry(S, eid, rowid, b + i, x, (uint32_t)r);
             if (i > 0 && (src[i - 1] >> 33) == (x >> 33)) set_error(err, E_DUP);
         }
         __syncthreads();
@@ -560,7 +620,7 @@ BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE) {
     t += align256((size_t)nU * 4 + 4) + align256((size_t)nV * 4 + 4);      // deg by id
     t += 4 * align256((size_t)nE * 4 + 4);                                   // eid, row ids
     t += align256((size_t)nV * 4 + 4);                                       // cursor
-    t += 2 * align256((size_t)nE * 8 + 8);                                   // row sort buffers / epos
+    t += 3 * align256((size_t)nE * 8 + 8);                                   // row keys, sort buffer, epos
     t += 2 * align256((size_t)nmax * 4 + 4);                                 // rank sort alt
     t += align256(std::max(radix_temp_bytes(nmax), scan_temp_bytes(nmax + 1)));
     t += 2 * align256((size_t)nmax * 4 + 4) * 2;                             // classify meta/grp
@@ -613,8 +673,10 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
     uint32_t *eid[2] = {c.take<uint32_t>(nE + 1), c.take<uint32_t>(nE + 1)};
     uint32_t *rowid[2] = {c.take<uint32_t>(nE + 1), c.take<uint32_t>(nE + 1)};
     uint32_t *cursorV = c.take<uint32_t>(nV + 1);
-    uint64_t *bufA = c.take<uint64_t>(nE + 1);
-    uint64_t *bufB = c.take<uint64_t>(nE + 1);
+    uint64_t *bufA = c.take<uint64_t>(nE + 1);   // U-side row keys, later twin positions
+    uint64_t *bufB = c.take<uint64_t>(nE + 1);   // V-side row keys
+    uint64_t *bufC = c.take<uint64_t>(nE + 1);   // radix sort alternate buffer
+    uint64_t *keys[2] = {bufA, bufB};
     uint32_t *ralt_k = c.take<uint32_t>(nmax + 1);
     uint32_t *ralt_v = c.take<uint32_t>(nmax + 1);
     void *ptemp = c.take<char>(std::max(radix_temp_bytes(nmax), scan_temp_bytes(nmax + 1)));
@@ -623,7 +685,7 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
     uint32_t *grp[2] = {c.take<uint32_t>(nmax + 1), c.take<uint32_t>(nmax + 1)};
     T.bucket_cnt = c.take<uint32_t>(NCLS * NB);
     T.bucket_base = c.take<uint32_t>(NCLS * NB);
-    int64_t *bounds = c.take<int64_t>(64);
+    int64_t *bounds = c.take<int64_t>(32);
 
     cudaMemsetAsync(g.err, 0, 4, s);
     cudaMemsetAsync(g.ctr, 0, NCTR * 4, s);
@@ -663,22 +725,28 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
         scan_exclusive_u32_to_i64(g.side[sd].deg, g.side[sd].off, ns[sd], ptemp, s);
     if (nU > 0 && nE > 0)
         k_fill<<<grid_for(nE, BT, 32768), BT, 0, s>>>(rowptr, col, sign, nU, nE, g.side[0],
-                                                     g.side[1], cursorV, eid[0], eid[1],
-                                                     rowid[0], rowid[1]); note_launch();
+                                                     g.side[1], cursorV, keys[0], keys[1]); note_launch();
     for (int sd = 0; sd < 2; sd++) {
         int64_t n = ns[sd];
         if (n == 0 || nE == 0) continue;
         SideCSR &S = g.side[sd];
-        int64_t *bd = bounds + sd * 8;
-        // bd[0..3]: first rank with degree > 1, > 32, > 2048, > 16384; bd[4] = n
+        int64_t *bd = bounds + sd * 16;
+        // bd[k]: first rank with degree > ROW_LIMS[k]; bd[NLIMS] = n
         k_row_bounds<<<1, 32, 0, s>>>(S.deg, n, bd); note_launch();
-        k_sort_rows_warp<<<grid_for(n * 32, BT, 16384), BT, 0, s>>>(S, eid[sd], bd, g.err); note_launch();
-        k_sort_rows_smem<2048, 256><<<4096, 256, 2048 * 8, s>>>(S, eid[sd], bd, 1, g.err); note_launch();
-        k_sort_rows_smem<16384, 1024><<<1024, 1024, 16384 * 8, s>>>(S, eid[sd], bd, 2, g.err); note_launch();
+        uint64_t *ky = keys[sd];
+        k_rows_single<<<grid_for(n, BT, 4096), BT, 0, s>>>(S, ky, eid[sd], rowid[sd], bd); note_launch();
+        k_sort_rows_sub<2><<<grid_for(n * 2, BT, 8192), BT, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 0, g.err); note_launch();
+        k_sort_rows_sub<4><<<grid_for(n * 4, BT, 8192), BT, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 1, g.err); note_launch();
+        k_sort_rows_sub<8><<<grid_for(n * 8, BT, 8192), BT, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 2, g.err); note_launch();
+        k_sort_rows_sub<16><<<grid_for(n * 16, BT, 8192), BT, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 3, g.err); note_launch();
+        k_sort_rows_sub<32><<<grid_for(n * 32, BT, 8192), BT, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 4, g.err); note_launch();
+        k_sort_rows_warpsmem<<<1024, WS_THREADS, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 5, g.err); note_launch();
+        k_sort_rows_smem<2048, 256><<<2048, 256, 2048 * 8, s>>>(S, ky, eid[sd], rowid[sd], bd, 6, g.err); note_launch();
+        k_sort_rows_smem<16384, 1024><<<1024, 1024, 16384 * 8, s>>>(S, ky, eid[sd], rowid[sd], bd, 7, g.err); note_launch();
         int64_t n_other = ns[1 - sd];
         int key_bits = 1;
         while (key_bits < 32 && ((uint64_t)1 << key_bits) < (uint64_t)(2 * n_other + 2)) key_bits++;
-        k_sort_rows_radix<<<512, RR_THREADS, 0, s>>>(S, eid[sd], bd, 3, bufA, bufB, key_bits, g.err); note_launch();
+        k_sort_rows_radix<<<512, RR_THREADS, 0, s>>>(S, ky, bufC, eid[sd], rowid[sd], bd, 8, key_bits, g.err); note_launch();
     }
     for (int sd = 0; sd < 2; sd++) {
         if (ns[sd] == 0) continue;
