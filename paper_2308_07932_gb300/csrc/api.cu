@@ -281,8 +281,8 @@ bb_status count_device(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int6
         ctx->layout_key[0] = -1;  // leave the merge buffers to be re-zeroed
         return map_build_error(verr);
     }
-    if (pv_dev) return fail(BB_ERR_INVALID_ARG, "per-vertex counts are not available in this build");
     launch_count(g, s, pv_dev, ctx->timing ? ctx->ev + 2 : nullptr);
+    if (pv_dev) launch_per_vertex(g, pv_dev, s);
     BB_CUDA(cudaGetLastError(), "count launch");
     return finish_count(ctx, g, s, balanced, total, wedges_opt);
 }
@@ -502,11 +502,22 @@ bb_status bb_count(bb_graph *G, int64_t *balanced, int64_t *total, int64_t *per_
     std::lock_guard<std::mutex> lk(ctx->mu);
     bb_status st = set_device(ctx);
     if (st != BB_OK) return st;
-    if (per_vertex_opt) return fail(BB_ERR_INVALID_ARG, "per-vertex counts are not available in this build");
     ctx->have_build_ev = false;
+    int64_t *pv_dev = nullptr;
+    if (per_vertex_opt) {
+        const size_t need = (size_t)(G->g.nU + G->g.nV) * 8;
+        st = ensure(ctx, (void **)&ctx->ws_pv, &ctx->ws_pv_cap, need, "per-vertex workspace");
+        if (st != BB_OK) return st;
+        pv_dev = ctx->ws_pv;
+    }
     launch_count(G->g, ctx->stream, nullptr, ctx->timing ? ctx->ev + 2 : nullptr);
+    if (pv_dev) launch_per_vertex(G->g, pv_dev, ctx->stream);
     BB_CUDA(cudaGetLastError(), "count launch");
-    return finish_count(ctx, G->g, ctx->stream, balanced, total, nullptr);
+    st = finish_count(ctx, G->g, ctx->stream, balanced, total, nullptr);
+    if (st != BB_OK || !pv_dev) return st;
+    BB_CUDA(cudaMemcpyAsync(per_vertex_opt, pv_dev, (size_t)(G->g.nU + G->g.nV) * 8,
+                            cudaMemcpyDeviceToHost, ctx->stream), "copy per-vertex");
+    return wait_bounded(ctx->stream, "per-vertex copy");
 }
 
 bb_status bb_graph_flip_signs(bb_graph *G, const int64_t *edge_idx, int64_t n) {

@@ -596,7 +596,7 @@ struct Carver {
 
 size_t side_bytes(int64_t n, int64_t nE) {
     return align256((size_t)(n + 1) * 8) + align256((size_t)nE * 4) + align256((size_t)nE * 16) +
-           6 * align256((size_t)(n > 0 ? n : 1) * 4) + 2 * align256((size_t)(n > 0 ? n : 1) * 8);
+           6 * align256((size_t)(n > 0 ? n : 1) * 4) + 3 * align256((size_t)(n > 0 ? n : 1) * 8);
 }
 
 }  // namespace
@@ -647,6 +647,7 @@ void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_m
         S.hstart = c.take<uint32_t>(n1);
         S.work = c.take<uint64_t>(n1);
         S.work_nh = c.take<uint64_t>(n1);
+        S.pv = c.take<unsigned long long>(n1);
     }
     int64_t n = nU + nV;
     g.warp_list = c.take<AnchorRec>(n + 1);

@@ -52,6 +52,7 @@ struct SideCSR {
                           //       the other side's hub window (top HUB_WINDOW ranks)
     uint64_t *work;       // [n]   side rank -> wedges anchored at this vertex
     uint64_t *work_nh;    // [n]   of those, wedges whose endpoint lies below the hub window
+    unsigned long long *pv;  // [n] balanced butterflies containing each vertex (when asked)
 };
 
 __host__ __device__ __forceinline__ uint64_t c2(uint64_t n) {

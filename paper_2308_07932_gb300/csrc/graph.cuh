@@ -81,10 +81,11 @@ enum Ctr : uint32_t {
 // per-count scratch (zeroed before each count)
 struct CountScratch {
     unsigned long long acc[4];   // balanced lo/hi, total lo/hi (128-bit sums)
-    uint32_t job_next[4];        // dynamic job cursors
+    uint32_t job_next[5];        // dynamic job cursors: one per class, then per-vertex
     uint32_t err;
-    uint32_t pad[3];
+    uint32_t pad[2];
 };
+constexpr int JOB_PER_VERTEX = 4;
 
 struct DevGraph {
     int64_t nU = 0, nV = 0, nE = 0;
@@ -135,6 +136,10 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
 // warp kernels and after the last one.
 void launch_count(const DevGraph &g, cudaStream_t s, int64_t *per_vertex_dev,
                   cudaEvent_t *ev = nullptr);
+
+// Balanced butterflies containing each vertex (Algorithm 3's quantity) for
+// a built graph: written to out_dev (device int64[nU+nV], U ids then V ids).
+void launch_per_vertex(const DevGraph &g, int64_t *out_dev, cudaStream_t s);
 
 // Flip the signs of listed input edges (device list of n indices).
 void launch_flip(DevGraph &g, const int64_t *edge_idx_dev, int64_t n, cudaStream_t s);

@@ -1,0 +1,217 @@
+// pervertex.cu - balanced butterflies containing each vertex (the quantity
+// Algorithm 3 computes for one vertex), for every vertex at once.
+//
+// Each balanced butterfly is tallied at exactly one pair (w, u) of same-side
+// vertices (w the anchor, u the higher-priority one; see graph.cuh) and has
+// two middles of the same wedge type. A pair with S symmetric and A
+// asymmetric middles holds C(S,2) + C(A,2) balanced butterflies: every one
+// contains w and u, and a middle of type t lies in cnt_t - 1 of them (it
+// pairs with each other middle of its type). Per anchor the kernel tallies
+// the pairs (pass 1), walks the wedges again reading the final tallies and
+// adds cnt_t - 1 to each middle (pass 2), then adds each pair's balanced
+// count to u and their sum to w.
+//
+// This runs only when per-vertex counts are requested, after the regular
+// count; its walk is simple (one warp per middle) rather than fast.
+#include <algorithm>
+#include "graph.cuh"
+
+namespace bb {
+
+namespace {
+
+constexpr int PV_THREADS = 512;
+constexpr uint32_t PV_HASH_CAP = 16384;   // u64 slots (128 KiB), shares memory with the counters
+
+struct PvSmem {
+    union {
+        uint32_t cnt[DENSE_CAP];
+        unsigned long long tab[PV_HASH_CAP];
+    };
+    unsigned long long red[PV_THREADS / 32];
+    uint32_t job;
+};
+
+__device__ __forceinline__ uint32_t pv_hash_add(unsigned long long *tab, uint32_t shift,
+                                                uint32_t mask, uint32_t key, uint32_t inc,
+                                                uint32_t *err) {
+    uint32_t h = hash_slot(key, shift);
+    for (uint32_t probe = 0; probe <= mask; probe++) {
+        unsigned long long cur = *((volatile unsigned long long *)&tab[h]);
+        uint32_t k = (uint32_t)(cur >> 32);
+        if (k == key) { atomicAdd(&tab[h], (unsigned long long)inc); return 0; }
+        if (k == 0) {
+            unsigned long long old = atomicCAS(&tab[h], 0ull, ((unsigned long long)key << 32) | inc);
+            if (old == 0ull) return 0;
+            if ((uint32_t)(old >> 32) == key) { atomicAdd(&tab[h], (unsigned long long)inc); return 0; }
+        }
+        h = (h + 1) & mask;
+    }
+    set_error(err, E_PROBE);
+    return 0;
+}
+
+__device__ __forceinline__ uint32_t pv_hash_find(const unsigned long long *tab, uint32_t shift,
+                                                 uint32_t mask, uint32_t key, uint32_t *err) {
+    uint32_t h = hash_slot(key, shift);
+    for (uint32_t probe = 0; probe <= mask; probe++) {
+        const unsigned long long cur = tab[h];
+        if ((uint32_t)(cur >> 32) == key) return (uint32_t)cur;
+        if (cur == 0ull) break;
+        h = (h + 1) & mask;
+    }
+    set_error(err, E_PROBE);
+    return 0;
+}
+
+__global__ void __launch_bounds__(PV_THREADS) k_pv(DevGraph G) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PvSmem &sm = *reinterpret_cast<PvSmem *>(smem_raw);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = PV_THREADS / 32;
+    uint32_t *err = &G.scratch->err;
+    const int64_t nA = G.nU + G.nV;
+    for (;;) {
+        if (t == 0) sm.job = atomicAdd(&G.scratch->job_next[JOB_PER_VERTEX], 1u);
+        __syncthreads();
+        const int64_t a = sm.job;
+        __syncthreads();
+        if (a >= nA) break;
+        const int sd = a < G.nU ? 0 : 1;
+        const SideCSR &S = sd ? G.side[1] : G.side[0];
+        const SideCSR &O = sd ? G.side[0] : G.side[1];
+        const uint32_t r = (uint32_t)(sd ? a - G.nU : a);
+        const uint64_t W = S.work[r];
+        if (W == 0) continue;
+        const int64_t rb = S.off[r];
+        const uint32_t deg = (uint32_t)(S.off[r + 1] - rb);
+        const uint64_t above = (uint64_t)(S.n - r - 1);
+        const uint64_t dh = W < above ? W : above;
+        const bool dense = above <= DENSE_CAP || dh * 5 / 4 >= PV_HASH_CAP;
+        uint32_t cap = 32, shift = 27;
+        if (!dense)
+            while ((uint64_t)cap < dh + dh / 4 + 1) { cap <<= 1; shift--; }
+        const uint32_t mask = cap - 1;
+        unsigned long long wsum = 0;  // balanced butterflies containing the anchor
+        const uint32_t e_lo = r + 1, e_hi = (uint32_t)S.n;
+        for (uint32_t e0 = e_lo; e0 < e_hi; e0 += dense ? DENSE_CAP : (e_hi - e_lo)) {
+            const uint32_t e1 = dense && e_hi - e0 > DENSE_CAP ? e0 + DENSE_CAP : e_hi;
+            const bool clip = dense && (e_hi - e_lo) > DENSE_CAP;
+            const uint32_t len = dense ? e1 - e0 : cap;
+            if (dense) for (uint32_t i = t; i < len; i += PV_THREADS) sm.cnt[i] = 0;
+            else for (uint32_t i = t; i < cap; i += PV_THREADS) sm.tab[i] = 0ull;
+            __syncthreads();
+            // segment of middle j's row: the wedge suffix, clipped to [e0, e1)
+            auto segment = [&](uint32_t j, int64_t &st, int64_t &en, uint32_t &sw, uint32_t &v) {
+                const uint4 d = S.md[rb + j];
+                st = d.x; en = d.z; sw = d.w;
+                v = S.adj[rb + j] >> 1;
+                if (clip) {
+                    st = lower_bound_u32(O.adj, st, en, e0 << 1);
+                    en = lower_bound_u32(O.adj, st, en, e1 << 1);
+                }
+            };
+            // pass 1: tally
+            for (uint32_t j = warp; j < deg; j += nwarps) {
+                int64_t st, en; uint32_t sw, v;
+                segment(j, st, en, sw, v);
+                for (int64_t p = st + lane; p < en; p += 32) {
+                    const uint32_t x = O.adj[p];
+                    const uint32_t u = x >> 1;
+                    const uint32_t inc = ((x ^ sw) & 1u) ? INC_ASYM : INC_SYM;
+                    if (dense) {
+                        const uint32_t idx = u - e0;
+                        if (idx < len) atomicAdd(&sm.cnt[idx], inc); else set_error(err, E_INTERNAL);
+                    } else {
+                        pv_hash_add(sm.tab, shift, mask, u + 1, inc, err);
+                    }
+                }
+            }
+            __syncthreads();
+            // pass 2: each middle of type t lies in cnt_t - 1 butterflies of its pair
+            for (uint32_t j = warp; j < deg; j += nwarps) {
+                int64_t st, en; uint32_t sw, v;
+                segment(j, st, en, sw, v);
+                unsigned long long msum = 0;
+                for (int64_t p = st + lane; p < en; p += 32) {
+                    const uint32_t x = O.adj[p];
+                    const uint32_t u = x >> 1;
+                    uint32_t c = 0;
+                    if (dense) {
+                        const uint32_t idx = u - e0;
+                        if (idx < len) c = sm.cnt[idx];
+                    } else {
+                        c = pv_hash_find(sm.tab, shift, mask, u + 1, err);
+                    }
+                    const uint32_t ct = ((x ^ sw) & 1u) ? (c >> 16) : (c & 0xffffu);
+                    msum += ct > 0 ? ct - 1 : 0;
+                }
+                msum = warp_sum_u64(msum);
+                if (lane == 0 && msum) atomicAdd(&O.pv[v], msum);
+            }
+            __syncthreads();
+            // each pair's balanced butterflies contain both of its endpoints
+            for (uint32_t i = t; i < len; i += PV_THREADS) {
+                uint32_t c, u;
+                if (dense) { c = sm.cnt[i]; u = e0 + i; }
+                else {
+                    const unsigned long long x = sm.tab[i];
+                    c = (uint32_t)x; u = (uint32_t)(x >> 32) - 1u;
+                    if (x == 0ull) c = 0;
+                }
+                if (c) {
+                    const unsigned long long b = c2(c & 0xffffu) + c2(c >> 16);
+                    if (b) { atomicAdd(&S.pv[u], b); wsum += b; }
+                }
+            }
+            __syncthreads();
+            if (!dense) break;
+        }
+        wsum = warp_sum_u64(wsum);
+        if (lane == 0) sm.red[warp] = wsum;
+        __syncthreads();
+        if (t == 0) {
+            unsigned long long tot = 0;
+            for (int k = 0; k < nwarps; k++) tot += sm.red[k];
+            if (tot) atomicAdd(&S.pv[r], tot);
+        }
+        __syncthreads();
+    }
+}
+
+// per-vertex counts from side-rank order to the caller's id order
+__global__ void k_pv_out(SideCSR S, int64_t base, int64_t *out) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < S.n;
+         r += (int64_t)gridDim.x * blockDim.x)
+        out[base + S.id_of_sr[r]] = (int64_t)S.pv[r];
+}
+
+int g_pv_blocks = 0, g_pv_device = -1;
+
+}  // namespace
+
+void launch_per_vertex(const DevGraph &g, int64_t *out_dev, cudaStream_t s) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (g_pv_device != dev) {
+        cudaDeviceProp prop;
+        cudaGetDeviceProperties(&prop, dev);
+        cudaFuncSetAttribute(k_pv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PvSmem));
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pv, PV_THREADS, sizeof(PvSmem));
+        g_pv_blocks = std::max(1, b) * prop.multiProcessorCount;
+        g_pv_device = dev;
+    }
+    for (int sd = 0; sd < 2; sd++)
+        if (g.side[sd].n > 0)
+            cudaMemsetAsync(g.side[sd].pv, 0, (size_t)g.side[sd].n * 8, s);
+    // the job cursor lives in the count scratch; launch_count has zeroed it
+    k_pv<<<g_pv_blocks, PV_THREADS, sizeof(PvSmem), s>>>(g); note_launch();
+    for (int sd = 0; sd < 2; sd++) {
+        const int64_t n = g.side[sd].n;
+        if (n == 0) continue;
+        const int64_t blocks = std::min<int64_t>((n + 255) / 256, 8192);
+        k_pv_out<<<(unsigned)blocks, 256, 0, s>>>(g.side[sd], sd ? g.nU : 0, out_dev); note_launch();
+    }
+}
+
+}  // namespace bb

@@ -286,3 +286,66 @@ def test_chunglu_2m_x_500k_full(ctx):
     g3 = synth.SignedBipartite(g.nU, g.nV, g.rowptr, g.col, np.ones_like(g.sign))
     c3 = ctx.count(g3)
     assert c3.balanced == c3.total == c.total
+
+
+# ------------------------------------------------------- per-vertex counts
+@pytest.mark.parametrize("make", [
+    lambda: synth.uniform(61, 30, 25, 300, 0.6),
+    lambda: synth.uniform_2k_1k(),
+    lambda: synth.chung_lu_scaled(62, 60_000),
+    lambda: synth.vote(63, 80, 6_000, 0.4, 2, 0.55, 0.8),
+])
+def test_per_vertex_matches_oracle(ctx, make):
+    g = make()
+    c = ctx.count(g, per_vertex=True)
+    want = oracle.per_vertex(g, threads=4)
+    assert np.array_equal(c.per_vertex, want)
+    assert c.per_vertex[: g.nU].sum() == 2 * c.balanced
+    assert c.per_vertex[g.nU:].sum() == 2 * c.balanced
+
+
+def test_per_vertex_tiny_and_windowed(ctx):
+    for seed in range(40):
+        rng = np.random.default_rng(700 + seed)
+        nU, nV = int(rng.integers(1, 12)), int(rng.integers(1, 12))
+        g = synth.uniform(700 + seed, nU, nV, int(rng.integers(0, nU * nV + 1)), 0.5)
+        assert np.array_equal(ctx.count(g, per_vertex=True).per_vertex, oracle.per_vertex(g))
+    # K_{60000,4}: dense windows over the endpoint range
+    rng = np.random.default_rng(8)
+    u = np.repeat(np.arange(60_000), 4)
+    v = np.tile(np.arange(4), 60_000)
+    g = synth.from_edges(60_000, 4, u, v, rng.choice([-1, 1], size=u.size))
+    ids = np.array([0, 1, 59_999, 30_000, 60_000, 60_001, 60_003])
+    pv = ctx.count(g, per_vertex=True).per_vertex
+    assert np.array_equal(pv[ids], oracle.per_vertex(g, ids))
+
+
+def test_per_vertex_resident_and_device(ctx):
+    torch = pytest.importorskip("torch")
+    g = synth.chung_lu_scaled(64, 80_000)
+    want = oracle.per_vertex(g, threads=4)
+    G = ctx.upload(g)
+    assert np.array_equal(G.count(per_vertex=True).per_vertex, want)
+    G.free()
+    rp = torch.from_numpy(g.rowptr).cuda()
+    cl = torch.from_numpy(g.col).cuda()
+    sg = torch.from_numpy(g.sign).cuda()
+    out = torch.zeros(g.nU + g.nV, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    ctx.count_tensors(g.nV, rp, cl, sg, per_vertex=out)
+    assert np.array_equal(out.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("name,make", [
+    ("vote_500x50000_p0.4_b2", synth.vote_500_50k),
+    ("chunglu_2Mx500k_e20M_a2.1_p0.8", synth.chung_lu_2m),
+])
+def test_per_vertex_full_size_sampled(ctx, name, make):
+    rec = EXPECTED[name]
+    g = make()
+    c = ctx.count(g, per_vertex=True)
+    assert (c.balanced, c.total) == (rec["balanced"], rec["total"])
+    ids = np.array(rec["per_vertex_gids"])
+    assert np.array_equal(c.per_vertex[ids], np.array(rec["per_vertex"]))
+    assert c.per_vertex[: g.nU].sum() == 2 * c.balanced
+    assert c.per_vertex[g.nU:].sum() == 2 * c.balanced
