@@ -321,6 +321,8 @@ def run_ours(args, world, rank, local_rank):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if rank == 0 and world == 1 and args.batch_graphs > 0:
+        line["batch"] = run_batch_leg(args, local_rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, secs, desc = oracle_rate(g, c.wedges, args.cpu_stride, 0, os.cpu_count() or 1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count() or 1,
@@ -328,6 +330,85 @@ def run_ours(args, world, rank, local_rank):
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------- batched counting
+BATCH_GRAPHS = 4096
+
+
+def run_batch_leg(args, dev_index: int) -> dict:
+    """Many-graph leg: the batched mix (graph i seeded 4+i; |E| log-uniform in
+    [1e3, 2e6], |U|:|V| in [1, 10], exponent in [2.1, 2.8], p(+) in [0.5,
+    0.9]) uploaded once, then every graph counted per step, two ways: one
+    batched launch sequence (class-queue kernels, captured CUDA graph, shapes
+    from the autotuner) and one bb_count per graph. Both give identical
+    counts (checked); graphs/s is graphs per second of device time."""
+    import torch
+    import paper_2308_07932_gb300 as pkg
+    from paper_2308_07932_gb300 import synth
+
+    n = args.batch_graphs
+    t0 = time.perf_counter()
+    hosts = synth.batch_graphs(n)
+    gen_s = time.perf_counter() - t0
+    dev = torch.device("cuda", dev_index)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = pkg.Context(dev_index)
+    ctx.set_stream(stream.cuda_stream)
+    t0 = time.perf_counter()
+    graphs = [ctx.upload(g) for g in hosts]
+    upload_s = time.perf_counter() - t0
+    edges = sum(g.nE for g in hosts)
+    wedges = sum(g.info()[3] for g in graphs)
+    del hosts
+    batch = pkg.Batch(ctx, graphs)
+    tune, tune_ms = batch.autotune(reps=3)
+    bal, tot = batch.count()                     # capture + first replay
+    for _ in range(args.warmup):
+        batch.count()
+    launches0 = pkg.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.batch_steps)]
+    wall0 = time.perf_counter()
+    with ClockSampler(dev_index) as clk:
+        for k in range(args.batch_steps):
+            ev[k][0].record(stream)
+            b2, t2 = batch.count()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    wall = (time.perf_counter() - wall0) / args.batch_steps
+    launches = pkg.launch_count() - launches0
+    assert (b2 == bal).all() and (t2 == tot).all()
+    ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    # one bb_count per graph, on the same resident graphs
+    per_ms = []
+    for k in range(max(1, args.batch_single_steps) + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        single = [g.count() for g in graphs]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k > 0:                                 # first pass is a warm-up
+            per_ms.append(e0.elapsed_time(e1))
+    assert [(c.balanced, c.total) for c in single] == list(zip(bal.tolist(), tot.tolist()))
+    single_ms = statistics.median(per_ms)
+    batch.free()
+    for g in graphs:
+        g.free()
+    ctx.close()
+    return {
+        "graphs": n, "edges": edges, "wedges": wedges,
+        "graphs_per_s": n / (ms / 1e3), "wedges_per_s": wedges / (ms / 1e3), "ms_per_step": ms,
+        "wall_ms_per_step": wall * 1e3, "steps": args.batch_steps,
+        "per_graph_launches": {"graphs_per_s": n / (single_ms / 1e3), "ms_per_step": single_ms,
+                               "steps": len(per_ms)},
+        "speedup_vs_per_graph": single_ms / ms,
+        "tune": tune.to_dict(), "tune_ms": tune_ms, "gpu_launches": launches,
+        "setup_s": {"generate": gen_s, "upload_and_build": upload_s},
+        "l2": "working set larger than L2 (no flush needed)" if edges * 13 > 256e6
+              else "working set may fit L2 (not flushed)",
+        "clocks": clk.summary(),
+    }
 
 
 def main():
@@ -340,6 +421,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-stride", type=int, default=8,
                     help="oracle sample: every k-th endpoint vertex")
+    ap.add_argument("--batch-graphs", type=int, default=BATCH_GRAPHS,
+                    help="graphs in the batched leg (0 = skip the leg)")
+    ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--batch-single-steps", type=int, default=2)
     ap.add_argument("--ref-stride", type=int, default=64,
                     help="reference arm: every k-th endpoint vertex per step")
     args = ap.parse_args()

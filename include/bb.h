@@ -183,6 +183,51 @@ typedef struct {
 BB_API bb_status bb_ctx_set_timing(bb_ctx *ctx, int enable);
 BB_API bb_status bb_ctx_last_timing(const bb_ctx *ctx, bb_timing *out);
 
+/* ------------------------------------------------------------- batches
+ * Many resident graphs counted together: every graph's wedge work goes
+ * into one shared work queue per work class (dense-counter, CTA-hash, team
+ * and warp anchors; the classes come from each anchor's wedge count and
+ * endpoint range, Algorithm 2's per-start work), and one persistent kernel
+ * per class drains its queue across all graphs. The whole sequence (reset,
+ * four class kernels, result gather and copy-back) is captured once as a
+ * CUDA graph and replayed by each bb_batch_count. Each graph's counts are
+ * exactly what bb_count gives for it alone. The paper counts one graph at
+ * a time; batching is this library's addition.
+ *
+ * bb_batch_create: `graphs` (host array of n resident graphs of one context)
+ *   is copied; the graphs must outlive the batch and must not be freed
+ *   while it exists. Sign flips of member graphs are seen by later counts.
+ *   Device memory: ~n*600 bytes plus 40 bytes per graph of results, within
+ *   the context's budget (BB_ERR_BUDGET otherwise).
+ * bb_batch_count: blocking. balanced/total: host int64[n]; status_opt: NULL
+ *   or host bb_status[n]. A graph whose count fails gets -1 in both outputs
+ *   and its status; the call then returns the first such status (message
+ *   names the graph index). The first call captures the CUDA graph on the
+ *   context's stream, which must not be the legacy default stream.
+ * bb_batch_tune: launch shapes per work class, index order as in bb_timing
+ *   (dense, CTA-hash, team, warp). warp_chunk: warp anchors a warp takes
+ *   per grab (1..1024); concurrent: 1 = the class kernels run on separate
+ *   streams at once, 0 = one after another; grid_frac: each class kernel's
+ *   grid as a fraction (0, 1] of its full-occupancy grid.
+ * bb_batch_autotune: times candidate shapes on this batch (each `reps`
+ *   times, median) by coordinate descent, keeps the fastest (also written to
+ *   best_opt) and its time (best_ms_opt). Runs the counts it times. */
+typedef struct bb_batch bb_batch;
+typedef struct {
+    uint32_t warp_chunk;
+    uint32_t concurrent;
+    float grid_frac[BB_NKERNELS];
+} bb_batch_tune;
+
+BB_API bb_status bb_batch_create(bb_ctx *ctx, bb_graph *const *graphs, int64_t n, bb_batch **out);
+BB_API bb_status bb_batch_count(bb_batch *b, int64_t *balanced, int64_t *total,
+                                bb_status *status_opt);
+BB_API bb_status bb_batch_set_tune(bb_batch *b, const bb_batch_tune *tune);
+BB_API bb_status bb_batch_get_tune(const bb_batch *b, bb_batch_tune *out);
+BB_API bb_status bb_batch_autotune(bb_batch *b, int reps, bb_batch_tune *best_opt,
+                                   double *best_ms_opt);
+BB_API void bb_batch_free(bb_batch *b);
+
 /* Kernel launches the library has issued in this process. */
 BB_API uint64_t bb_launch_count(void);
 

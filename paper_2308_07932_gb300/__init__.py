@@ -53,6 +53,26 @@ class _Timing(ctypes.Structure):
                 ("middles", ctypes.c_int64 * len(KERNELS)),
                 ("anchors", ctypes.c_int64 * len(KERNELS))]
 
+class BatchTune(ctypes.Structure):
+    """Launch shapes of a batch (``bb_batch_tune``); per-class fields in
+    ``KERNELS`` order."""
+    _fields_ = [("warp_chunk", ctypes.c_uint32), ("concurrent", ctypes.c_uint32),
+                ("grid_frac", ctypes.c_float * len(KERNELS))]
+
+    def to_dict(self) -> dict:
+        return {"warp_chunk": int(self.warp_chunk), "concurrent": int(self.concurrent),
+                "grid_frac": {k: round(float(f), 4) for k, f in zip(KERNELS, self.grid_frac)}}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "BatchTune":
+        t = cls()
+        t.warp_chunk = int(d["warp_chunk"])
+        t.concurrent = int(d["concurrent"])
+        for i, k in enumerate(KERNELS):
+            t.grid_frac[i] = float(d["grid_frac"][k])
+        return t
+
+
 _lib = None
 _VP = ctypes.c_void_p
 _I64P = ctypes.POINTER(ctypes.c_int64)
@@ -85,6 +105,13 @@ def lib() -> ctypes.CDLL:
             "bb_ctx_set_timing": (S, [_VP, ctypes.c_int]),
             "bb_ctx_last_timing": (S, [_VP, ctypes.POINTER(_Timing)]),
             "bb_launch_count": (ctypes.c_uint64, []),
+            "bb_batch_create": (S, [_VP, ctypes.POINTER(_VP), ctypes.c_int64, ctypes.POINTER(_VP)]),
+            "bb_batch_count": (S, [_VP, _I64P, _I64P, ctypes.POINTER(ctypes.c_int)]),
+            "bb_batch_set_tune": (S, [_VP, ctypes.POINTER(BatchTune)]),
+            "bb_batch_get_tune": (S, [_VP, ctypes.POINTER(BatchTune)]),
+            "bb_batch_autotune": (S, [_VP, ctypes.c_int, ctypes.POINTER(BatchTune),
+                                      ctypes.POINTER(ctypes.c_double)]),
+            "bb_batch_free": (None, [_VP]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -242,6 +269,60 @@ class Graph:
     def free(self):
         if getattr(self, "_h", None):
             lib().bb_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Resident graphs counted together in one captured launch sequence
+    (``bb_batch``). Holds references to its graphs so they outlive it."""
+
+    def __init__(self, ctx: Context, graphs: list):
+        self.ctx = ctx
+        self.graphs = list(graphs)
+        arr = (_VP * len(self.graphs))(*[g._h for g in self.graphs])
+        h = _VP()
+        _check(lib().bb_batch_create(ctx._h, arr, len(self.graphs), ctypes.byref(h)))
+        self._h = h
+
+    def count(self, with_status: bool = False):
+        """(balanced, total) int64 arrays, one entry per graph; with_status
+        also returns the per-graph status array instead of raising."""
+        n = len(self.graphs)
+        b = np.empty(n, np.int64)
+        t = np.empty(n, np.int64)
+        st = np.zeros(n, np.int32)
+        r = lib().bb_batch_count(self._h, b.ctypes.data_as(_I64P), t.ctypes.data_as(_I64P),
+                                 st.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        if with_status:
+            return b, t, st
+        _check(r)
+        return b, t
+
+    def tune(self) -> BatchTune:
+        t = BatchTune()
+        _check(lib().bb_batch_get_tune(self._h, ctypes.byref(t)))
+        return t
+
+    def set_tune(self, t: BatchTune | dict):
+        if isinstance(t, dict):
+            t = BatchTune.from_dict(t)
+        _check(lib().bb_batch_set_tune(self._h, ctypes.byref(t)))
+
+    def autotune(self, reps: int = 3) -> tuple[BatchTune, float]:
+        t = BatchTune()
+        ms = ctypes.c_double()
+        _check(lib().bb_batch_autotune(self._h, reps, ctypes.byref(t), ctypes.byref(ms)))
+        return t, ms.value
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().bb_batch_free(self._h)
             self._h = None
 
     def __del__(self):

@@ -12,23 +12,22 @@
 #include <string>
 #include <thread>
 
-#include "../../include/bb.h"
-#include "graph.cuh"
+#include "runtime.h"
 
 using namespace bb;
 
 namespace {
 std::atomic<uint64_t> g_launches{0};
-}
+thread_local std::string t_err;
+// limit of a bounded wait on device work
+double g_timeout_s = 600.0;
+}  // namespace
 
 void bb::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void bb::note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+uint64_t bb::launches() { return g_launches.load(std::memory_order_relaxed); }
 
-namespace {
-
-thread_local std::string t_err;
-
-bb_status fail(bb_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
-bb_status fail(bb_status st, const char *fmt, ...) {
+bb_status bb::fail(bb_status st, const char *fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -38,22 +37,14 @@ bb_status fail(bb_status st, const char *fmt, ...) {
     return st;
 }
 
-bb_status cuda_fail(cudaError_t e, const char *what) {
+bb_status bb::cuda_fail(cudaError_t e, const char *what) {
     cudaGetLastError();  // clear sticky-free errors
     return fail(BB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define BB_CUDA(call, what)                                  \
-    do {                                                     \
-        cudaError_t e_ = (call);                             \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what);   \
-    } while (0)
-
 // Waits for all work queued so far on `s`, polling an event so that a stuck
 // device turns into BB_ERR_TIMEOUT instead of a hang of the caller.
-double g_timeout_s = 600.0;
-
-bb_status wait_bounded(cudaStream_t s, const char *what) {
+bb_status bb::wait_bounded(cudaStream_t s, const char *what) {
     cudaEvent_t ev;
     BB_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event create");
     cudaError_t e = cudaEventRecord(ev, s);
@@ -76,6 +67,8 @@ bb_status wait_bounded(cudaStream_t s, const char *what) {
     return BB_OK;
 }
 
+namespace {
+
 bb_status check_csr(const bb_csr *csr, const int8_t *signs) {
     if (!csr) return fail(BB_ERR_INVALID_ARG, "csr is NULL");
     if (csr->nU < 0 || csr->nV < 0 || csr->nE < 0)
@@ -94,7 +87,9 @@ bb_status check_csr(const bb_csr *csr, const int8_t *signs) {
     return BB_OK;
 }
 
-bb_status map_build_error(uint32_t e) {
+}  // namespace
+
+bb_status bb::map_build_error(uint32_t e) {
     if (e & E_ROWPTR) return fail(BB_ERR_INVALID_ARG, "rowptr is not a valid CSR row pointer");
     if (e & E_COL) return fail(BB_ERR_INVALID_ARG, "a column id is outside [0, nV)");
     if (e & E_SIGN) return fail(BB_ERR_INVALID_ARG, "a sign is not +1 or -1");
@@ -104,62 +99,10 @@ bb_status map_build_error(uint32_t e) {
     return BB_OK;
 }
 
-}  // namespace
-
 // lets other translation units of the library set bb_last_error()
 bb_status bb::report_error(bb_status st, const char *msg) { return fail(st, "%s", msg); }
 
-namespace {
-
-// results copied back after a count
-struct HostResult {
-    unsigned long long acc[4];
-    uint32_t count_err;
-    uint32_t build_err;
-    unsigned long long wedges;
-    unsigned long long cls_stats[3 * NCLS];
-};
-
-constexpr int NEV = 7;  // build begin/end, count kernel boundaries (5)
-
-}  // namespace
-
-struct bb_ctx {
-    int device = 0;
-    uint64_t budget = 0;
-    uint64_t used = 0;
-    cudaStream_t own = nullptr, stream = nullptr;
-    // one-shot workspace
-    void *ws_graph = nullptr;
-    size_t ws_graph_cap = 0;
-    void *ws_temp = nullptr;
-    size_t ws_temp_cap = 0;
-    void *ws_in = nullptr;  // device copies of host inputs (bb_count_csr)
-    size_t ws_in_cap = 0;
-    int64_t *ws_pv = nullptr;  // device per-vertex output for host requests
-    size_t ws_pv_cap = 0;
-    DevGraph oneshot;
-    int64_t layout_key[3] = {-1, -1, -1};
-    HostResult *h_res = nullptr;  // pinned
-    std::mutex mu;
-    bool timing = false;
-    cudaEvent_t ev[NEV] = {};
-    bool have_build_ev = false;
-    bb_timing last = {};
-};
-
-struct bb_graph {
-    bb_ctx *ctx = nullptr;
-    DevGraph g;
-    void *mem = nullptr;
-    size_t bytes = 0;
-    void *raw = nullptr;
-    size_t raw_bytes = 0;
-};
-
-namespace {
-
-bb_status dev_alloc(bb_ctx *ctx, void **p, size_t bytes, const char *what) {
+bb_status bb::dev_alloc(bb_ctx *ctx, void **p, size_t bytes, const char *what) {
     if (bytes == 0) bytes = 256;
     if (ctx->used + bytes > ctx->budget)
         return fail(BB_ERR_BUDGET, "%s: %zu bytes would exceed the budget (%llu of %llu used)",
@@ -175,12 +118,19 @@ bb_status dev_alloc(bb_ctx *ctx, void **p, size_t bytes, const char *what) {
     return BB_OK;
 }
 
-void dev_free(bb_ctx *ctx, void *p, size_t bytes) {
+void bb::dev_free(bb_ctx *ctx, void *p, size_t bytes) {
     if (!p) return;
     cudaFree(p);
     if (bytes == 0) bytes = 256;
     ctx->used -= bytes;
 }
+
+bb_status bb::set_device(bb_ctx *ctx) {
+    BB_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    return BB_OK;
+}
+
+namespace {
 
 // grow-only workspace buffer
 bb_status ensure(bb_ctx *ctx, void **buf, size_t *cap, size_t need, const char *what) {
@@ -197,11 +147,6 @@ bb_status ensure(bb_ctx *ctx, void **buf, size_t *cap, size_t need, const char *
         want = need;
     }
     *cap = want;
-    return BB_OK;
-}
-
-bb_status set_device(bb_ctx *ctx) {
-    BB_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     return BB_OK;
 }
 
@@ -363,7 +308,7 @@ bb_status bb_ctx_last_timing(const bb_ctx *ctx, bb_timing *out) {
     return BB_OK;
 }
 
-uint64_t bb_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+uint64_t bb_launch_count(void) { return launches(); }
 
 bb_status bb_ctx_set_stream(bb_ctx *ctx, void *stream) {
     if (!ctx) return fail(BB_ERR_INVALID_ARG, "ctx is NULL");
@@ -474,6 +419,8 @@ static bb_status upload_impl(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs
     if (verr) { bb_graph_free(G); return map_build_error(verr); }
     e = cudaMemcpyAsync(&ctx->h_res->build_err, G->g.err, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&ctx->h_res->wedges, G->g.wedges, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->h_res->ctr, G->g.ctr, sizeof(ctx->h_res->ctr), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) { bb_graph_free(G); return cuda_fail(e, "copy build status"); }
     st = wait_bounded(s, "graph build");
     if (st != BB_OK) { bb_graph_free(G); return st; }
@@ -483,6 +430,7 @@ static bb_status upload_impl(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs
         return map_build_error(be);
     }
     G->g.h_wedges = ctx->h_res->wedges;
+    memcpy(G->g.h_ctr, ctx->h_res->ctr, sizeof(G->g.h_ctr));
     *out = G;
     return BB_OK;
 }

@@ -386,60 +386,70 @@ struct alignas(16) WarpSmem {
 static_assert(sizeof(WarpSmem) % 16 == 0, "WarpSmem must keep 16-byte alignment");
 static_assert(offsetof(WarpSmem, tab) % 16 == 0, "table needs 16-byte alignment");
 
-__global__ void __launch_bounds__(WARP_THREADS, 4) k_warp(DevGraph G) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[threadIdx.x >> 5];
-    const unsigned lane = lane_id();
-    clear_table<32>(sm.tab, WARP_CAP, (int)lane);
-    for (uint32_t i = lane; i < HUB_WINDOW / 2; i += 32) sm.win[i] = 0u;
-    __syncwarp();
-    const uint32_t n = G.ctr[CTR_WARP];
-    const uint32_t gw = (blockIdx.x * WARP_THREADS + threadIdx.x) >> 5;
-    const uint32_t GW = (gridDim.x * WARP_THREADS) >> 5;
+// one warp-class anchor, walked by one warp
+__device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, const AnchorRec &rec,
+                                            unsigned lane, unsigned long long &bal,
+                                            unsigned long long &tot) {
     uint32_t *err = &G.scratch->err;
-    unsigned long long bal = 0, tot = 0;
-    for (uint32_t idx = gw; idx < n; idx += GW) {
-        const Anchor A = load_anchor(G, G.warp_list[idx]);
-        const uint64_t W = A.W, above = (uint64_t)(A.ns - A.r - 1);
-        uint32_t cap = 0, shift = 0;
-        if (W <= WARP_SMALL_W) {  // hash every endpoint
-            table_geometry(W < above ? W : above, 32, WARP_CAP, cap, shift);
+    const Anchor A = load_anchor(G, rec);
+    const uint64_t W = A.W, above = (uint64_t)(A.ns - A.r - 1);
+    uint32_t cap = 0, shift = 0;
+    if (W <= WARP_SMALL_W) {  // hash every endpoint
+        table_geometry(W < above ? W : above, 32, WARP_CAP, cap, shift);
+        const uint32_t mask = cap - 1;
+        team_walk<32, 2>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, FullSeg{},
+                         [&](uint32_t u, uint32_t asym) {
+                             hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
+                         });
+    } else {
+        const int64_t ns = A.ns;
+        const uint32_t wb = ns > (int64_t)HUB_WINDOW ? (uint32_t)(ns - HUB_WINDOW) : 0u;
+        const uint64_t wnh = A.wnh;
+        const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
+        team_walk<32, 2>(
+            A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, HubSeg{},
+            [&](uint32_t u, uint32_t asym) {
+                const uint32_t wi = u - wb;
+                if (wi >= HUB_WINDOW) { set_error(err, E_INTERNAL); return; }
+                const uint32_t sh = (wi & 1u) * 16u;
+                const uint32_t old = atomicAdd(&sm.win[wi >> 1], (asym ? 256u : 1u) << sh) >> sh;
+                wedge_terms(old & 0xffu, (old >> 8) & 0xffu, asym, bal, tot);
+            });
+        if (wnh > 0) {
+            table_geometry(wnh < above_nh ? wnh : above_nh, 32, WARP_CAP, cap, shift);
             const uint32_t mask = cap - 1;
-            team_walk<32, 2>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, FullSeg{},
+            team_walk<32, 2>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, LowSeg{},
                              [&](uint32_t u, uint32_t asym) {
                                  hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
                              });
-        } else {
-            const int64_t ns = A.ns;
-            const uint32_t wb = ns > (int64_t)HUB_WINDOW ? (uint32_t)(ns - HUB_WINDOW) : 0u;
-            const uint64_t wnh = A.wnh;
-            const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
-            team_walk<32, 2>(
-                A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, HubSeg{},
-                [&](uint32_t u, uint32_t asym) {
-                    const uint32_t wi = u - wb;
-                    if (wi >= HUB_WINDOW) { set_error(err, E_INTERNAL); return; }
-                    const uint32_t sh = (wi & 1u) * 16u;
-                    const uint32_t old = atomicAdd(&sm.win[wi >> 1], (asym ? 256u : 1u) << sh) >> sh;
-                    wedge_terms(old & 0xffu, (old >> 8) & 0xffu, asym, bal, tot);
-                });
-            if (wnh > 0) {
-                table_geometry(wnh < above_nh ? wnh : above_nh, 32, WARP_CAP, cap, shift);
-                const uint32_t mask = cap - 1;
-                team_walk<32, 2>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, LowSeg{},
-                                 [&](uint32_t u, uint32_t asym) {
-                                     hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
-                                 });
-            }
-            // reset the window words an endpoint can have reached
-            const uint32_t first = (A.r + 1 > wb ? A.r + 1 - wb : 0u) >> 3;  // uint4 index
-            uint4 *w4 = reinterpret_cast<uint4 *>(sm.win);
-            for (uint32_t q = first + lane; q < HUB_WINDOW / 8; q += 32)
-                w4[q] = make_uint4(0u, 0u, 0u, 0u);
         }
-        clear_table<32>(sm.tab, cap, (int)lane);
-        __syncwarp();
+        // reset the window words an endpoint can have reached
+        const uint32_t first = (A.r + 1 > wb ? A.r + 1 - wb : 0u) >> 3;  // uint4 index
+        uint4 *w4 = reinterpret_cast<uint4 *>(sm.win);
+        for (uint32_t q = first + lane; q < HUB_WINDOW / 8; q += 32)
+            w4[q] = make_uint4(0u, 0u, 0u, 0u);
     }
+    clear_table<32>(sm.tab, cap, (int)lane);
+    __syncwarp();
+}
+
+__device__ __forceinline__ WarpSmem &warp_smem_init(unsigned char *smem_raw, unsigned lane) {
+    WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[threadIdx.x >> 5];
+    clear_table<32>(sm.tab, WARP_CAP, (int)lane);
+    for (uint32_t i = lane; i < HUB_WINDOW / 2; i += 32) sm.win[i] = 0u;
+    __syncwarp();
+    return sm;
+}
+
+__global__ void __launch_bounds__(WARP_THREADS, 4) k_warp(DevGraph G) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const unsigned lane = lane_id();
+    WarpSmem &sm = warp_smem_init(smem_raw, lane);
+    const uint32_t n = G.ctr[CTR_WARP];
+    const uint32_t gw = (blockIdx.x * WARP_THREADS + threadIdx.x) >> 5;
+    const uint32_t GW = (gridDim.x * WARP_THREADS) >> 5;
+    unsigned long long bal = 0, tot = 0;
+    for (uint32_t idx = gw; idx < n; idx += GW) warp_anchor(G, sm, G.warp_list[idx], lane, bal, tot);
     block_sum2<WARP_THREADS>(bal, tot);
     if (threadIdx.x == 0) acc_add(G.scratch, bal, tot);
 }
@@ -453,60 +463,73 @@ struct alignas(16) HybSmem {
     uint32_t job;
 };
 
-template <int TS, uint32_t HCAP, int CTR, int CLS>
-__device__ __forceinline__ void hybrid_body(DevGraph &G, const AnchorRec *list) {
+template <int TS, uint32_t HCAP>
+__device__ __forceinline__ HybSmem<TS, HCAP> &hybrid_smem_init(unsigned char *smem_raw) {
     using Smem = HybSmem<TS, HCAP>;
     static_assert(offsetof(Smem, tab) % 16 == 0, "table needs 16-byte alignment");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    HybSmem<TS, HCAP> &sm = *reinterpret_cast<HybSmem<TS, HCAP> *>(smem_raw);
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    for (uint32_t i = threadIdx.x; i < HUB_WINDOW; i += TS) sm.win[i] = 0;
+    clear_table<TS>(sm.tab, HCAP, (int)threadIdx.x);
+    return sm;
+}
+
+// one team/CTA-hash anchor, walked by the whole CTA
+template <int TS, uint32_t HCAP>
+__device__ __forceinline__ void hybrid_anchor(const DevGraph &G, HybSmem<TS, HCAP> &sm,
+                                              const AnchorRec &rec, unsigned long long &bal,
+                                              unsigned long long &tot) {
     const int t = threadIdx.x;
-    for (uint32_t i = t; i < HUB_WINDOW; i += TS) sm.win[i] = 0;
-    clear_table<TS>(sm.tab, HCAP, t);
-    const uint32_t n = G.ctr[CTR];
     uint32_t *err = &G.scratch->err;
+    const Anchor A = load_anchor(G, rec);
+    const int64_t ns = A.ns;
+    const uint32_t wb = ns > (int64_t)HUB_WINDOW ? (uint32_t)(ns - HUB_WINDOW) : 0u;
+    const uint64_t W = A.W, wnh = A.wnh;
+    const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
+    if (W > wnh) {  // endpoints inside the hub window
+        team_walk<TS>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, HubSeg{},
+                      [&](uint32_t u, uint32_t asym) {
+                          const uint32_t idx = u - wb;
+                          if (idx >= HUB_WINDOW) { set_error(err, E_INTERNAL); return; }
+                          const uint32_t old = atomicAdd(&sm.win[idx], asym ? INC_ASYM : INC_SYM);
+                          wedge_terms(old & 0xffffu, old >> 16, asym, bal, tot);
+                      });
+    }
+    uint32_t cap = 0;
+    if (wnh > 0) {  // endpoints below the window
+        uint32_t shift;
+        table_geometry(wnh < above_nh ? wnh : above_nh, 32, HCAP, cap, shift);
+        const uint32_t mask = cap - 1;
+        team_walk<TS>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, LowSeg{},
+                      [&](uint32_t u, uint32_t asym) {
+                          hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
+                      });
+    }
+    __syncthreads();
+    if (W > wnh) {
+        const uint32_t first = (A.r + 1 > wb ? A.r + 1 - wb : 0u) >> 2;  // uint4 index
+        uint4 *w4 = reinterpret_cast<uint4 *>(sm.win);
+        for (uint32_t q = first + t; q < HUB_WINDOW / 4; q += TS)
+            w4[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    clear_table<TS>(sm.tab, cap, t);
+}
+
+template <int TS, uint32_t HCAP, int CTR, int CLS>
+__device__ __forceinline__ void hybrid_body(DevGraph &G, const AnchorRec *list) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    HybSmem<TS, HCAP> &sm = hybrid_smem_init<TS, HCAP>(smem_raw);
+    const uint32_t n = G.ctr[CTR];
     unsigned long long bal = 0, tot = 0;
     for (;;) {
-        if (t == 0) sm.job = atomicAdd(&G.scratch->job_next[CLS], 1u);
+        if (threadIdx.x == 0) sm.job = atomicAdd(&G.scratch->job_next[CLS], 1u);
         __syncthreads();
         const uint32_t jid = sm.job;
         __syncthreads();
         if (jid >= n) break;
-        const Anchor A = load_anchor(G, list[jid]);
-        const int64_t ns = A.ns;
-        const uint32_t wb = ns > (int64_t)HUB_WINDOW ? (uint32_t)(ns - HUB_WINDOW) : 0u;
-        const uint64_t W = A.W, wnh = A.wnh;
-        const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
-        if (W > wnh) {  // endpoints inside the hub window
-            team_walk<TS>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, HubSeg{},
-                          [&](uint32_t u, uint32_t asym) {
-                              const uint32_t idx = u - wb;
-                              if (idx >= HUB_WINDOW) { set_error(err, E_INTERNAL); return; }
-                              const uint32_t old =
-                                  atomicAdd(&sm.win[idx], asym ? INC_ASYM : INC_SYM);
-                              wedge_terms(old & 0xffffu, old >> 16, asym, bal, tot);
-                          });
-        }
-        uint32_t cap = 0;
-        if (wnh > 0) {  // endpoints below the window
-            uint32_t shift;
-            table_geometry(wnh < above_nh ? wnh : above_nh, 32, HCAP, cap, shift);
-            const uint32_t mask = cap - 1;
-            team_walk<TS>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, LowSeg{},
-                          [&](uint32_t u, uint32_t asym) {
-                              hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
-                          });
-        }
-        __syncthreads();
-        if (W > wnh) {
-            const uint32_t first = (A.r + 1 > wb ? A.r + 1 - wb : 0u) >> 2;  // uint4 index
-            uint4 *w4 = reinterpret_cast<uint4 *>(sm.win);
-            for (uint32_t q = first + t; q < HUB_WINDOW / 4; q += TS)
-                w4[q] = make_uint4(0u, 0u, 0u, 0u);
-        }
-        clear_table<TS>(sm.tab, cap, t);
+        hybrid_anchor<TS, HCAP>(G, sm, list[jid], bal, tot);
     }
     block_sum2<TS>(bal, tot);
-    if (t == 0) acc_add(G.scratch, bal, tot);
+    if (threadIdx.x == 0) acc_add(G.scratch, bal, tot);
 }
 
 __global__ void __launch_bounds__(TEAM_THREADS) k_team(DevGraph G) {
@@ -524,86 +547,212 @@ struct alignas(16) DenseSmem {
     uint32_t job, last;
 };
 
+// one dense job (an anchor, or one middle slice of a split anchor), walked
+// by the whole CTA; adds its sums to the graph's accumulators
+__device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, const DenseJob &J) {
+    const int t = threadIdx.x;
+    CountScratch *sc = G.scratch;
+    const bool sv = J.anchor & 1u;
+    const SideCSR &S = sv ? G.side[1] : G.side[0];
+    AnchorRec rec;
+    rec.anchor = J.anchor;
+    rec.rb = (uint32_t)S.off[J.anchor >> 1];
+    rec.deg = 0; rec.W = 0; rec.wnh = 0;
+    const Anchor A = load_anchor(G, rec);
+    const uint32_t e_lo = A.r + 1, e_hi = (uint32_t)A.ns;
+    const bool windows = (e_hi - e_lo) > DENSE_CAP;
+    for (uint32_t e0 = e_lo; e0 < e_hi; e0 += DENSE_CAP) {
+        const uint32_t e1 = e_hi - e0 > DENSE_CAP ? e0 + DENSE_CAP : e_hi;
+        const uint32_t len = e1 - e0;
+        for (uint32_t i = t; i < len; i += DENSE_THREADS) sm.cnt[i] = 0;
+        __syncthreads();
+        unsigned long long bal = 0, tot = 0;
+        auto add = [&](uint32_t u, uint32_t asym) {
+            const uint32_t idx = u - e0;
+            if (idx >= len) { set_error(&sc->err, E_INTERNAL); return; }
+            const uint32_t old = atomicAdd(&sm.cnt[idx], asym ? INC_ASYM : INC_SYM);
+            wedge_terms(old & 0xffffu, old >> 16, asym, bal, tot);
+        };
+        if (windows) {
+            team_walk<DENSE_THREADS>(
+                A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t,
+                [&](const uint4 &d, long long &st, uint32_t &l) {
+                    const long long s0 = lower_bound_u32(A.oadj, d.x, d.z, e0 << 1);
+                    st = s0;
+                    l = (uint32_t)(lower_bound_u32(A.oadj, s0, d.z, e1 << 1) - s0);
+                },
+                add);
+        } else {
+            team_walk<DENSE_THREADS>(A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t, FullSeg{}, add);
+        }
+        if (J.group != NO_GROUP) {
+            // merge this part's counts into the group's global counters; a
+            // count p added to c already there closes c*p new pairs
+            const SplitGroup grp = G.groups[J.group];
+            uint32_t *part = G.gpart + grp.goff;
+            __syncthreads();
+            for (uint32_t i = t; i < len; i += DENSE_THREADS) {
+                const uint32_t p = sm.cnt[i];
+                if (p) {
+                    const uint32_t c = atomicAdd(&part[i], p);
+                    const unsigned long long cS = c & 0xffffu, cA = c >> 16;
+                    const unsigned long long pS = p & 0xffffu, pA = p >> 16;
+                    bal += cS * pS + cA * pA;
+                    tot += (cS + cA) * (pS + pA);
+                }
+            }
+            // the last part to arrive resets the group's counters
+            __threadfence();
+            __syncthreads();
+            if (t == 0) {
+                const uint32_t ticket = atomicAdd(&G.gdone[J.group], 1u);
+                sm.last = ticket == grp.parts - 1 ? 1u : 0u;
+            }
+            __syncthreads();
+            if (sm.last) {
+                __threadfence();
+                for (uint32_t i = t; i < len; i += DENSE_THREADS) part[i] = 0;
+                if (t == 0) G.gdone[J.group] = 0;
+            }
+        }
+        block_sum2<DENSE_THREADS>(bal, tot);
+        if (t == 0) acc_add(sc, bal, tot);
+    }
+}
+
 __global__ void __launch_bounds__(DENSE_THREADS) k_dense(DevGraph G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DenseSmem &sm = *reinterpret_cast<DenseSmem *>(smem_raw);
     const uint32_t njobs = G.ctr[CTR_DENSE];
-    const int t = threadIdx.x;
-    CountScratch *sc = G.scratch;
     for (;;) {
-        if (t == 0) sm.job = atomicAdd(&sc->job_next[CLS_DENSE], 1u);
+        if (threadIdx.x == 0) sm.job = atomicAdd(&G.scratch->job_next[CLS_DENSE], 1u);
         __syncthreads();
         const uint32_t jid = sm.job;
         __syncthreads();
         if (jid >= njobs) break;
-        const DenseJob J = G.dense_jobs[jid];
-        const bool sv = J.anchor & 1u;
-        const SideCSR &S = sv ? G.side[1] : G.side[0];
-        AnchorRec rec;
-        rec.anchor = J.anchor;
-        rec.rb = (uint32_t)S.off[J.anchor >> 1];
-        rec.deg = 0; rec.W = 0; rec.wnh = 0;
-        const Anchor A = load_anchor(G, rec);
-        const uint32_t e_lo = A.r + 1, e_hi = (uint32_t)A.ns;
-        const bool windows = (e_hi - e_lo) > DENSE_CAP;
-        for (uint32_t e0 = e_lo; e0 < e_hi; e0 += DENSE_CAP) {
-            const uint32_t e1 = e_hi - e0 > DENSE_CAP ? e0 + DENSE_CAP : e_hi;
-            const uint32_t len = e1 - e0;
-            for (uint32_t i = t; i < len; i += DENSE_THREADS) sm.cnt[i] = 0;
-            __syncthreads();
-            unsigned long long bal = 0, tot = 0;
-            auto add = [&](uint32_t u, uint32_t asym) {
-                const uint32_t idx = u - e0;
-                if (idx >= len) { set_error(&sc->err, E_INTERNAL); return; }
-                const uint32_t old = atomicAdd(&sm.cnt[idx], asym ? INC_ASYM : INC_SYM);
-                wedge_terms(old & 0xffffu, old >> 16, asym, bal, tot);
-            };
-            if (windows) {
-                team_walk<DENSE_THREADS>(
-                    A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t,
-                    [&](const uint4 &d, long long &st, uint32_t &l) {
-                        const long long s0 = lower_bound_u32(A.oadj, d.x, d.z, e0 << 1);
-                        st = s0;
-                        l = (uint32_t)(lower_bound_u32(A.oadj, s0, d.z, e1 << 1) - s0);
-                    },
-                    add);
-            } else {
-                team_walk<DENSE_THREADS>(A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t, FullSeg{},
-                                         add);
+        dense_job(G, sm, G.dense_jobs[jid]);
+    }
+}
+
+// ---------------------------------------------------- batched (many graphs)
+// The same per-item work over the items of many resident graphs at once:
+// items of class c of graph i are numbered prefix[c][i] .. prefix[c][i+1)-1
+// in one space and handed out from a cursor per class. Sums go to each
+// item's own graph.
+struct BatchArgs {
+    const DevGraph *graphs;
+    const uint32_t *prefix;   // [NCLS][n + 1]
+    uint32_t *next;           // [NCLS] item cursors, zeroed before the launch
+    uint32_t n;
+    uint32_t warp_chunk;      // anchors a warp takes per grab
+};
+
+__device__ __forceinline__ uint32_t batch_graph_of(const uint32_t *p, uint32_t n, uint32_t item) {
+    uint32_t lo = 0, hi = n;  // last i with p[i] <= item (p[0] = 0 <= item < p[n])
+    while (hi - lo > 1) {
+        const uint32_t m = (lo + hi) >> 1;
+        if (p[m] <= item) lo = m; else hi = m;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(WARP_THREADS, 4) k_warp_batch(BatchArgs B) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const unsigned lane = lane_id();
+    WarpSmem &sm = warp_smem_init(smem_raw, lane);
+    const uint32_t *p = B.prefix + (size_t)CLS_WARP * (B.n + 1);
+    const uint32_t total = p[B.n];
+    for (;;) {
+        uint32_t c0 = 0;
+        if (lane == 0) c0 = atomicAdd(&B.next[CLS_WARP], B.warp_chunk);
+        c0 = __shfl_sync(FULL, c0, 0);
+        if (c0 >= total) break;
+        const uint32_t c1 = total - c0 > B.warp_chunk ? c0 + B.warp_chunk : total;
+        uint32_t gi = batch_graph_of(p, B.n, c0);
+        uint32_t gbeg = p[gi], gend = p[gi + 1];
+        unsigned long long bal = 0, tot = 0;
+        for (uint32_t it = c0; it < c1; it++) {
+            if (it >= gend) {  // next graph (skipping any without items): flush this one
+                bal = warp_sum_u64(bal); tot = warp_sum_u64(tot);
+                if (lane == 0) acc_add(B.graphs[gi].scratch, bal, tot);
+                bal = tot = 0;
+                do { gi++; gbeg = gend; gend = p[gi + 1]; } while (it >= gend);
             }
-            if (J.group != NO_GROUP) {
-                // merge this part's counts into the group's global counters; a
-                // count p added to c already there closes c*p new pairs
-                const SplitGroup grp = G.groups[J.group];
-                uint32_t *part = G.gpart + grp.goff;
-                __syncthreads();
-                for (uint32_t i = t; i < len; i += DENSE_THREADS) {
-                    const uint32_t p = sm.cnt[i];
-                    if (p) {
-                        const uint32_t c = atomicAdd(&part[i], p);
-                        const unsigned long long cS = c & 0xffffu, cA = c >> 16;
-                        const unsigned long long pS = p & 0xffffu, pA = p >> 16;
-                        bal += cS * pS + cA * pA;
-                        tot += (cS + cA) * (pS + pA);
-                    }
-                }
-                // the last part to arrive resets the group's counters
-                __threadfence();
-                __syncthreads();
-                if (t == 0) {
-                    const uint32_t ticket = atomicAdd(&G.gdone[J.group], 1u);
-                    sm.last = ticket == grp.parts - 1 ? 1u : 0u;
-                }
-                __syncthreads();
-                if (sm.last) {
-                    __threadfence();
-                    for (uint32_t i = t; i < len; i += DENSE_THREADS) part[i] = 0;
-                    if (t == 0) G.gdone[J.group] = 0;
-                }
-            }
-            block_sum2<DENSE_THREADS>(bal, tot);
-            if (t == 0) acc_add(sc, bal, tot);
+            const DevGraph &G = B.graphs[gi];
+            warp_anchor(G, sm, G.warp_list[it - gbeg], lane, bal, tot);
         }
+        bal = warp_sum_u64(bal); tot = warp_sum_u64(tot);
+        if (lane == 0) acc_add(B.graphs[gi].scratch, bal, tot);
+    }
+}
+
+template <int TS, uint32_t HCAP, int CLS>
+__device__ __forceinline__ void hybrid_batch_body(const BatchArgs &B) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    HybSmem<TS, HCAP> &sm = hybrid_smem_init<TS, HCAP>(smem_raw);
+    const uint32_t *p = B.prefix + (size_t)CLS * (B.n + 1);
+    const uint32_t total = p[B.n];
+    for (;;) {
+        if (threadIdx.x == 0) sm.job = atomicAdd(&B.next[CLS], 1u);
+        __syncthreads();
+        const uint32_t it = sm.job;
+        __syncthreads();
+        if (it >= total) break;
+        const uint32_t gi = batch_graph_of(p, B.n, it);
+        const DevGraph &G = B.graphs[gi];
+        const AnchorRec *list = CLS == CLS_TEAM ? G.team_list : G.ctah_list;
+        unsigned long long bal = 0, tot = 0;
+        hybrid_anchor<TS, HCAP>(G, sm, list[it - p[gi]], bal, tot);
+        block_sum2<TS>(bal, tot);
+        if (threadIdx.x == 0) acc_add(G.scratch, bal, tot);
+    }
+}
+
+__global__ void __launch_bounds__(TEAM_THREADS) k_team_batch(BatchArgs B) {
+    hybrid_batch_body<TEAM_THREADS, TEAM_CAP, CLS_TEAM>(B);
+}
+
+__global__ void __launch_bounds__(CTAH_THREADS) k_ctah_batch(BatchArgs B) {
+    hybrid_batch_body<CTAH_THREADS, CTAH_CAP, CLS_CTAH>(B);
+}
+
+__global__ void __launch_bounds__(DENSE_THREADS) k_dense_batch(BatchArgs B) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DenseSmem &sm = *reinterpret_cast<DenseSmem *>(smem_raw);
+    const uint32_t *p = B.prefix + (size_t)CLS_DENSE * (B.n + 1);
+    const uint32_t total = p[B.n];
+    for (;;) {
+        if (threadIdx.x == 0) sm.job = atomicAdd(&B.next[CLS_DENSE], 1u);
+        __syncthreads();
+        const uint32_t it = sm.job;
+        __syncthreads();
+        if (it >= total) break;
+        const uint32_t gi = batch_graph_of(p, B.n, it);
+        const DevGraph &G = B.graphs[gi];
+        dense_job(G, sm, G.dense_jobs[it - p[gi]]);
+    }
+}
+
+// zero every graph's count scratch and the class cursors
+__global__ void k_batch_prep(BatchArgs B) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < NCLS) B.next[i] = 0;
+    for (uint32_t g = i; g < B.n; g += gridDim.x * blockDim.x) {
+        CountScratch *sc = B.graphs[g].scratch;
+        for (int k = 0; k < 4; k++) sc->acc[k] = 0;
+        for (int k = 0; k < 5; k++) sc->job_next[k] = 0;
+        sc->err = 0;
+    }
+}
+
+// per graph, BATCH_OUT words: balanced lo/hi, total lo/hi, count error |
+// build error << 32
+__global__ void k_batch_results(BatchArgs B, unsigned long long *out) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n; i += gridDim.x * blockDim.x) {
+        const DevGraph &G = B.graphs[i];
+        unsigned long long *o = out + (size_t)i * BATCH_OUT;
+        for (int k = 0; k < 4; k++) o[k] = G.scratch->acc[k];
+        o[4] = (unsigned long long)G.scratch->err | ((unsigned long long)*G.err << 32);
     }
 }
 
@@ -639,6 +788,8 @@ constexpr size_t DENSE_SMEM = sizeof(DenseSmem);
 
 struct LaunchCfg {
     int warp_blocks = 0, team_blocks = 0, ctah_blocks = 0, dense_blocks = 0;
+    int batch_blocks[NCLS] = {};
+    int sms = 0;
 };
 
 LaunchCfg g_cfg;
@@ -659,10 +810,15 @@ void init_cfg() {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, dev);
     const int sms = prop.multiProcessorCount;
+    g_cfg.sms = sms;
     g_cfg.warp_blocks = blocks_for(k_warp, WARP_THREADS, WARP_SMEM, sms);
     g_cfg.team_blocks = blocks_for(k_team, TEAM_THREADS, TEAM_SMEM, sms);
     g_cfg.ctah_blocks = blocks_for(k_ctah, CTAH_THREADS, CTAH_SMEM, sms);
     g_cfg.dense_blocks = blocks_for(k_dense, DENSE_THREADS, DENSE_SMEM, sms);
+    g_cfg.batch_blocks[CLS_WARP] = blocks_for(k_warp_batch, WARP_THREADS, WARP_SMEM, sms);
+    g_cfg.batch_blocks[CLS_TEAM] = blocks_for(k_team_batch, TEAM_THREADS, TEAM_SMEM, sms);
+    g_cfg.batch_blocks[CLS_CTAH] = blocks_for(k_ctah_batch, CTAH_THREADS, CTAH_SMEM, sms);
+    g_cfg.batch_blocks[CLS_DENSE] = blocks_for(k_dense_batch, DENSE_THREADS, DENSE_SMEM, sms);
     g_cfg_device = dev;
 }
 
@@ -683,6 +839,61 @@ void launch_count(const DevGraph &g, cudaStream_t s, int64_t *per_vertex_dev, cu
     if (ev) cudaEventRecord(ev[3], s);
     k_warp<<<g_cfg.warp_blocks, WARP_THREADS, WARP_SMEM, s>>>(g); note_launch();
     if (ev) cudaEventRecord(ev[4], s);
+}
+
+int batch_max_blocks(int cls) {
+    init_cfg();
+    return g_cfg.batch_blocks[cls];
+}
+
+void launch_count_batch(const BatchLaunch &L, const BatchTune &T, cudaStream_t s,
+                        const cudaStream_t *side, const cudaEvent_t *ev) {
+    init_cfg();
+    BatchArgs B;
+    B.graphs = L.graphs;
+    B.prefix = L.prefix;
+    B.next = L.next;
+    B.n = L.n;
+    B.warp_chunk = T.warp_chunk ? T.warp_chunk : 1;
+    const uint32_t prep_blocks = std::min<uint32_t>((L.n + 255) / 256 + 1, 1024);
+    k_batch_prep<<<prep_blocks, 256, 0, s>>>(B); note_launch();
+    // classes in descending item size, so the long dense jobs start first
+    const int order[NCLS] = {CLS_DENSE, CLS_CTAH, CLS_TEAM, CLS_WARP};
+    int nlaunch = 0;
+    for (int k = 0; k < NCLS; k++) nlaunch += L.items[order[k]] ? 1 : 0;
+    const bool conc = T.concurrent && side && ev && nlaunch > 1;
+    if (conc) {  // fork exactly the side streams that get a kernel (a capture must join them all)
+        cudaEventRecord(ev[0], s);
+        for (int k = 0; k + 1 < nlaunch; k++) cudaStreamWaitEvent(side[k], ev[0], 0);
+    }
+    int used = 0;
+    for (int k = 0; k < NCLS; k++) {
+        const int c = order[k];
+        if (L.items[c] == 0) continue;
+        // with concurrency the first class stays on s, the others go to side streams
+        cudaStream_t cs = conc && used > 0 ? side[used - 1] : s;
+        used++;
+        int blocks = std::max(1, (int)(g_cfg.batch_blocks[c] * T.grid_frac[c] + 0.5f));
+        blocks = std::min(blocks, g_cfg.batch_blocks[c]);
+        if (c == CLS_WARP) {
+            const uint64_t warps = ((uint64_t)L.items[c] + B.warp_chunk - 1) / B.warp_chunk;
+            blocks = (int)std::min<uint64_t>(blocks, (warps + WARP_THREADS / 32 - 1) / (WARP_THREADS / 32));
+            k_warp_batch<<<blocks, WARP_THREADS, WARP_SMEM, cs>>>(B);
+        } else {
+            blocks = (int)std::min<uint64_t>(blocks, L.items[c]);
+            if (c == CLS_TEAM) k_team_batch<<<blocks, TEAM_THREADS, TEAM_SMEM, cs>>>(B);
+            else if (c == CLS_CTAH) k_ctah_batch<<<blocks, CTAH_THREADS, CTAH_SMEM, cs>>>(B);
+            else k_dense_batch<<<blocks, DENSE_THREADS, DENSE_SMEM, cs>>>(B);
+        }
+        note_launch();
+    }
+    if (conc)
+        for (int k = 0; k + 1 < used; k++) {
+            cudaEventRecord(ev[1 + k], side[k]);
+            cudaStreamWaitEvent(s, ev[1 + k], 0);
+        }
+    const uint32_t res_blocks = std::min<uint32_t>((L.n + 255) / 256, 1024);
+    if (L.n) { k_batch_results<<<res_blocks, 256, 0, s>>>(B, L.out); note_launch(); }
 }
 
 void launch_flip(DevGraph &g, const int64_t *edge_idx_dev, int64_t n, cudaStream_t s) {

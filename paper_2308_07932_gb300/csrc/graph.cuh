@@ -137,6 +137,34 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
 void launch_count(const DevGraph &g, cudaStream_t s, int64_t *per_vertex_dev,
                   cudaEvent_t *ev = nullptr);
 
+// Many resident graphs counted in one launch per work class. Items of class
+// c of graph i are numbered prefix[c*(n+1)+i] .. prefix[c*(n+1)+i+1]-1 in
+// one space (prefix built from each graph's class counters). After the
+// launch, out[i*BATCH_OUT ..] holds graph i's 128-bit balanced and total
+// sums and its error words (count | build << 32).
+constexpr int BATCH_OUT = 5;
+struct BatchLaunch {
+    const DevGraph *graphs;   // device [n]
+    const uint32_t *prefix;   // device [NCLS * (n + 1)]
+    uint32_t *next;           // device [NCLS]
+    unsigned long long *out;  // device [n * BATCH_OUT]
+    uint32_t n;
+    uint32_t items[NCLS];     // host copy of the prefix totals
+};
+// Launch shapes: items a warp takes per grab, whether the classes run on
+// separate streams at once, and each class's grid as a fraction of its
+// full-occupancy grid.
+struct BatchTune {
+    uint32_t warp_chunk = 8;
+    uint32_t concurrent = 1;
+    float grid_frac[NCLS] = {1.f, 1.f, 1.f, 1.f};
+};
+// side: NCLS-1 streams and ev: NCLS events, used when T.concurrent is set
+// (both may be null otherwise). Works under stream capture.
+void launch_count_batch(const BatchLaunch &L, const BatchTune &T, cudaStream_t s,
+                        const cudaStream_t *side, const cudaEvent_t *ev);
+int batch_max_blocks(int cls);
+
 // Balanced butterflies containing each vertex (Algorithm 3's quantity) for
 // a built graph: written to out_dev (device int64[nU+nV], U ids then V ids).
 void launch_per_vertex(const DevGraph &g, int64_t *out_dev, cudaStream_t s);

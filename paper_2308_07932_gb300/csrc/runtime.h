@@ -1,0 +1,82 @@
+// runtime.h - host-side state behind the C ABI (contexts, resident graphs)
+// and the helpers the ABI's translation units share: error reporting,
+// bounded waits and budgeted device allocation.
+#pragma once
+#include <cstdint>
+#include <mutex>
+
+#include "../../include/bb.h"
+#include "graph.cuh"
+
+namespace bb {
+
+// results copied back after a count or a build
+struct HostResult {
+    unsigned long long acc[4];
+    uint32_t count_err;
+    uint32_t build_err;
+    unsigned long long wedges;
+    unsigned long long cls_stats[3 * NCLS];
+    uint32_t ctr[NCTR];
+};
+
+constexpr int NEV = 7;  // build begin/end, count kernel boundaries (5)
+
+}  // namespace bb
+
+struct bb_ctx {
+    int device = 0;
+    uint64_t budget = 0;
+    uint64_t used = 0;
+    cudaStream_t own = nullptr, stream = nullptr;
+    // one-shot workspace
+    void *ws_graph = nullptr;
+    size_t ws_graph_cap = 0;
+    void *ws_temp = nullptr;
+    size_t ws_temp_cap = 0;
+    void *ws_in = nullptr;  // device copies of host inputs (bb_count_csr)
+    size_t ws_in_cap = 0;
+    int64_t *ws_pv = nullptr;  // device per-vertex output for host requests
+    size_t ws_pv_cap = 0;
+    bb::DevGraph oneshot;
+    int64_t layout_key[3] = {-1, -1, -1};
+    bb::HostResult *h_res = nullptr;  // pinned
+    std::mutex mu;
+    bool timing = false;
+    cudaEvent_t ev[bb::NEV] = {};
+    bool have_build_ev = false;
+    bb_timing last = {};
+};
+
+struct bb_graph {
+    bb_ctx *ctx = nullptr;
+    bb::DevGraph g;
+    void *mem = nullptr;
+    size_t bytes = 0;
+    void *raw = nullptr;
+    size_t raw_bytes = 0;
+};
+
+namespace bb {
+
+// sets the calling thread's bb_last_error() text; returns st
+bb_status fail(bb_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+bb_status cuda_fail(cudaError_t e, const char *what);
+// waits for the work queued so far on s; BB_ERR_TIMEOUT after the limit
+bb_status wait_bounded(cudaStream_t s, const char *what);
+// cudaMalloc within the context's budget (BB_ERR_BUDGET / BB_ERR_OOM)
+bb_status dev_alloc(bb_ctx *ctx, void **p, size_t bytes, const char *what);
+void dev_free(bb_ctx *ctx, void *p, size_t bytes);
+bb_status set_device(bb_ctx *ctx);
+bb_status map_build_error(uint32_t e);
+// adds launches made by replaying a captured CUDA graph to bb_launch_count
+void note_launches(uint64_t n);
+uint64_t launches();
+
+}  // namespace bb
+
+#define BB_CUDA(call, what)                                      \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return bb::cuda_fail(e_, what);   \
+    } while (0)
