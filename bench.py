@@ -323,6 +323,8 @@ def run_ours(args, world, rank, local_rank):
     }
     if rank == 0 and world == 1 and args.batch_graphs > 0:
         line["batch"] = run_batch_leg(args, local_rank)
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        line["serving"] = run_serve_leg(args, local_rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, secs, desc = oracle_rate(g, c.wedges, args.cpu_stride, 0, os.cpu_count() or 1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count() or 1,
@@ -411,6 +413,140 @@ def run_batch_leg(args, dev_index: int) -> dict:
     }
 
 
+# ------------------------------------------------------------------ serving
+SERVE_BUDGET = 120 << 30
+
+
+def serve_trace(n_req: int, rate: float, pool_n: int, seed: int, requery: float = 0.2,
+                flip_frac: float = 0.01):
+    """Poisson arrivals at `rate` req/s. A request is a re-query (probability
+    `requery`, once some graph was requested) of a random earlier key with
+    `flip_frac` of its edge signs flipped, else a new key whose graph is the
+    next pool graph (pool graphs repeat under new keys once used up)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    reqs, keys = [], []
+    for k in range(n_req):
+        if keys and rng.random() < requery:
+            key = keys[int(rng.integers(len(keys)))]
+            reqs.append((float(t[k]), key, None, float(rng.random())))
+        else:
+            key = len(keys) + 1
+            keys.append(key)
+            reqs.append((float(t[k]), key, (key - 1) % pool_n, None))
+    return reqs
+
+
+def flip_list(nE: int, frac: float, u: float):
+    """Deterministic flip list for a re-query: `frac` of the edges, seeded by u."""
+    rng = np.random.default_rng(int(u * 2**31))
+    return rng.choice(nE, size=max(1, int(nE * frac)), replace=False)
+
+
+def pctl(xs, q):
+    return float(np.percentile(np.asarray(xs), q)) if xs else None
+
+
+def run_serve_leg(args, dev_index: int) -> dict:
+    """Request-loop leg: graphs drawn as the 2M x 500k workload at |E|
+    log-uniform in [1e4, 5e7], Poisson arrivals at each swept rate, 20%
+    re-queries of a resident graph with 1% of its edge signs flipped, a
+    120 GiB HBM budget. Served = the engine (4 slots, managed cache in a
+    120 GiB arena); plain = per request upload + count + free, one at a
+    time. Latency = arrival to result; both paths must agree on every count."""
+    import paper_2308_07932_gb300 as pkg
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2308_07932_gb300 import synth
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(min(32, os.cpu_count() or 4)) as ex:
+        pool = list(ex.map(synth.serving_graph, range(args.serve_pool)))
+    gen_s = time.perf_counter() - t0
+    rates = [float(x) for x in args.serve_rates.split(",")]
+    out = {"pool_graphs": len(pool), "pool_edges": int(sum(g.nE for g in pool)),
+           "requests_per_rate": args.serve_requests, "slots": args.serve_slots,
+           "budget_bytes": SERVE_BUDGET, "setup_s": {"generate": gen_s}, "rates": []}
+
+    def host_graph(state, key, gidx):
+        g = pool[gidx]
+        return synth.SignedBipartite(g.nU, g.nV, g.rowptr, g.col, state.get(key, g.sign), g.name)
+
+    for ri, rate in enumerate(rates):
+        reqs = serve_trace(args.serve_requests, rate, len(pool), seed=100 + ri)
+        # ---- served
+        ctx = pkg.Context(dev_index, budget_bytes=SERVE_BUDGET + (4 << 30))
+        ctx.serve(slots=args.serve_slots, arena_bytes=SERVE_BUDGET)
+        key_graph = {}
+        lat, got, pending = [0.0] * len(reqs), [None] * len(reqs), []
+        start = time.perf_counter()
+        i = 0
+        with ClockSampler(dev_index) as clk:
+            while i < len(reqs) or pending:
+                now = time.perf_counter() - start
+                busy = False
+                while i < len(reqs) and reqs[i][0] <= now:
+                    at, key, gidx, u = reqs[i]
+                    late = (time.perf_counter() - start) - at
+                    if gidx is not None:
+                        key_graph[key] = gidx
+                        tk = ctx.submit_request(key, pool[gidx])
+                    else:
+                        tk = ctx.submit_request(key, None, flip_list(pool[key_graph[key]].nE, 0.01, u))
+                    pending.append((i, tk, late))
+                    i += 1
+                    busy = True
+                still = []
+                for j, tk, late in pending:
+                    r = tk.poll()
+                    if r is None:
+                        still.append((j, tk, late))
+                    else:
+                        lat[j] = late * 1e3 + r.queue_ms + r.run_ms
+                        got[j] = (r.balanced, r.total)
+                        busy = True
+                pending = still
+                if not busy:
+                    time.sleep(50e-6)
+        served_s = time.perf_counter() - start
+        stats = ctx.serve_stats()
+        ctx.close()
+        # ---- plain: upload + count + free per request, one at a time
+        ctx = pkg.Context(dev_index, budget_bytes=SERVE_BUDGET)
+        state, plat, pgot = {}, [0.0] * len(reqs), [None] * len(reqs)
+        key_graph = {}
+        start = time.perf_counter()
+        for j, (at, key, gidx, u) in enumerate(reqs):
+            now = time.perf_counter() - start
+            if now < at:
+                time.sleep(at - now)
+            if gidx is not None:
+                key_graph[key] = gidx
+            else:
+                g0 = pool[key_graph[key]]
+                idx = flip_list(g0.nE, 0.01, u)
+                s = state.get(key, g0.sign).copy()
+                s[idx] = -s[idx]
+                state[key] = s
+            gr = ctx.upload(host_graph(state, key, key_graph[key]))
+            c = gr.count()
+            gr.free()
+            pgot[j] = (c.balanced, c.total)
+            plat[j] = (time.perf_counter() - start - at) * 1e3
+        plain_s = time.perf_counter() - start
+        ctx.close()
+        assert got == pgot, "served and plain counts differ"
+        out["rates"].append({
+            "rate_req_s": rate,
+            "served": {"graphs_per_s": len(reqs) / served_s, "p50_ms": pctl(lat, 50),
+                       "p99_ms": pctl(lat, 99), "cache_hits": stats["cache_hits"],
+                       "uploads": stats["uploads"], "evictions": stats["evictions"],
+                       "clocks": clk.summary()},
+            "plain": {"graphs_per_s": len(reqs) / plain_s, "p50_ms": pctl(plat, 50),
+                      "p99_ms": pctl(plat, 99)},
+        })
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -425,6 +561,11 @@ def main():
                     help="graphs in the batched leg (0 = skip the leg)")
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--batch-single-steps", type=int, default=2)
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests per rate in the serving leg (0 = skip the leg)")
+    ap.add_argument("--serve-rates", default="25,50,100,200", help="arrival rates, req/s")
+    ap.add_argument("--serve-pool", type=int, default=24)
+    ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--ref-stride", type=int, default=64,
                     help="reference arm: every k-th endpoint vertex per step")
     args = ap.parse_args()

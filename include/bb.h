@@ -60,12 +60,12 @@ typedef enum {
     BB_ERR_OVERFLOW = 6,    /* a count does not fit in int64 */
     BB_ERR_CUDA = 7,        /* a CUDA runtime call failed */
     BB_ERR_NO_DEVICE = 8,   /* no usable CUDA device of compute capability 10.3 */
-    BB_ERR_BUSY = 9         /* no free request slot (bb_submit) */
+    BB_ERR_BUSY = 9         /* the serving engine stopped before running a request */
 } bb_status;
 
 typedef struct bb_ctx bb_ctx;
 typedef struct bb_graph bb_graph;
-typedef uint64_t bb_ticket;
+typedef struct bb_ticket_s *bb_ticket;  /* an asynchronous request (bb_submit) */
 
 /* U-side CSR of a signed bipartite graph (layout above). */
 typedef struct {
@@ -132,6 +132,12 @@ BB_API bb_status bb_count(bb_graph *g, int64_t *balanced, int64_t *total, int64_
 BB_API bb_status bb_graph_flip_signs(bb_graph *g, const int64_t *edge_idx, int64_t n);
 
 /* Graph facts: vertex and edge counts, wedges the count aggregates. */
+/* Device bytes a graph of these sizes needs: `resident_opt` for as long as
+ * it is kept (a bb_graph holds this plus its input copy, rowptr + col +
+ * signs), `workspace_opt` during its build only. BB_ERR_INVALID_ARG on
+ * negative sizes. */
+BB_API bb_status bb_graph_bytes(int64_t nU, int64_t nV, int64_t nE, uint64_t *resident_opt,
+                                uint64_t *workspace_opt);
 BB_API bb_status bb_graph_info(const bb_graph *g, int64_t *nU, int64_t *nV, int64_t *nE,
                         int64_t *wedges);
 
@@ -227,6 +233,71 @@ BB_API bb_status bb_batch_get_tune(const bb_batch *b, bb_batch_tune *out);
 BB_API bb_status bb_batch_autotune(bb_batch *b, int reps, bb_batch_tune *best_opt,
                                    double *best_ms_opt);
 BB_API void bb_batch_free(bb_batch *b);
+
+/* ------------------------------------------------------------- serving
+ * Asynchronous counts for a request loop. A context's serving engine runs
+ * `slots` worker slots, each with its own CUDA stream: requests are queued
+ * in arrival order and admitted as soon as a slot is free and their device
+ * memory fits, so the uploads, builds and counts of several requests
+ * overlap on the device (continuous batching: admission never waits for a
+ * whole batch to finish). Two requests on the same graph run one after the
+ * other. A request's counts are exactly what bb_count gives for the graph.
+ * The paper counts one graph per call; the serving engine is this
+ * library's addition.
+ *
+ * bb_ctx_serve: starts (or restarts, after draining) the engine. arena_bytes
+ *   is reserved at once from the context's budget and holds every graph of
+ *   the managed cache with its input copy and build workspace (0 = no
+ *   managed cache: only bb_submit of caller-owned graphs). Optional: the
+ *   first bb_submit starts an engine with 2 slots and no cache.
+ * bb_submit: count of a resident graph the caller owns (bb_graph_upload);
+ *   the graph must not be freed, counted, flipped or batched until the
+ *   ticket is done. flags must be 0.
+ * bb_submit_request: count of the graph the caller names by `key`. A key
+ *   not in the cache is uploaded from csr/signs (host pointers, borrowed
+ *   until the ticket is done) into the arena, evicting the least recently
+ *   used idle graphs as needed; a key in the cache is counted in place,
+ *   after flipping the signs of the listed input edges (host int64
+ *   indices, borrowed likewise; the flips stay). csr may be NULL when the
+ *   caller knows the key is resident (the request fails with
+ *   BB_ERR_INVALID_ARG if it is not). A graph larger than the arena fails
+ *   with BB_ERR_BUDGET. flags: 0, or BB_REQ_NO_CACHE to drop the graph
+ *   from the cache once counted.
+ * bb_poll: never blocks. *done = 1 when the request has finished; then the
+ *   return value is its status, balanced/total are written on success, and
+ *   the ticket is released (it must not be used again). *done = 0: BB_OK,
+ *   nothing else written. bb_poll_timed adds the milliseconds from submit
+ *   to admission (queue_ms_opt) and from admission to completion
+ *   (run_ms_opt), from the library's steady clock.
+ * Threading: submit from one thread, poll from one (possibly the same).
+ * bb_ctx_destroy waits for running requests; queued ones finish with
+ * BB_ERR_BUSY and still need a bb_poll to be released. */
+typedef struct {
+    uint64_t key;
+    const bb_csr *csr;
+    const int8_t *signs;
+    const int64_t *flip_idx;
+    int64_t n_flip;
+} bb_request;
+
+#define BB_REQ_NO_CACHE 1u
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t cache_hits, uploads, evictions;
+    int64_t resident_graphs;
+    uint64_t arena_bytes, arena_used, arena_largest_free;
+    int64_t queued, running;
+} bb_serve_stats;
+
+BB_API bb_status bb_ctx_serve(bb_ctx *ctx, int slots, uint64_t arena_bytes);
+BB_API bb_status bb_submit(bb_ctx *ctx, bb_graph *g, uint32_t flags, bb_ticket *out);
+BB_API bb_status bb_submit_request(bb_ctx *ctx, const bb_request *req, uint32_t flags,
+                                   bb_ticket *out);
+BB_API bb_status bb_poll(bb_ticket t, int *done, int64_t *balanced, int64_t *total);
+BB_API bb_status bb_poll_timed(bb_ticket t, int *done, int64_t *balanced, int64_t *total,
+                               double *queue_ms_opt, double *run_ms_opt);
+BB_API bb_status bb_ctx_serve_stats(bb_ctx *ctx, bb_serve_stats *out);
 
 /* Kernel launches the library has issued in this process. */
 BB_API uint64_t bb_launch_count(void);

@@ -73,6 +73,20 @@ class BatchTune(ctypes.Structure):
         return t
 
 
+class _Request(ctypes.Structure):
+    _fields_ = [("key", ctypes.c_uint64), ("csr", ctypes.POINTER(_Csr)), ("signs", ctypes.c_void_p),
+                ("flip_idx", ctypes.c_void_p), ("n_flip", ctypes.c_int64)]
+
+
+class _ServeStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "cache_hits",
+                                              "uploads", "evictions", "resident_graphs")] + \
+               [(n, ctypes.c_uint64) for n in ("arena_bytes", "arena_used", "arena_largest_free")] + \
+               [(n, ctypes.c_int64) for n in ("queued", "running")]
+
+
+REQ_NO_CACHE = 1
+
 _lib = None
 _VP = ctypes.c_void_p
 _I64P = ctypes.POINTER(ctypes.c_int64)
@@ -112,6 +126,16 @@ def lib() -> ctypes.CDLL:
             "bb_batch_autotune": (S, [_VP, ctypes.c_int, ctypes.POINTER(BatchTune),
                                       ctypes.POINTER(ctypes.c_double)]),
             "bb_batch_free": (None, [_VP]),
+            "bb_ctx_serve": (S, [_VP, ctypes.c_int, ctypes.c_uint64]),
+            "bb_submit": (S, [_VP, _VP, ctypes.c_uint32, ctypes.POINTER(_VP)]),
+            "bb_submit_request": (S, [_VP, ctypes.POINTER(_Request), ctypes.c_uint32,
+                                      ctypes.POINTER(_VP)]),
+            "bb_poll": (S, [_VP, ctypes.POINTER(ctypes.c_int), _I64P, _I64P]),
+            "bb_poll_timed": (S, [_VP, ctypes.POINTER(ctypes.c_int), _I64P, _I64P,
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+            "bb_ctx_serve_stats": (S, [_VP, ctypes.POINTER(_ServeStats)]),
+            "bb_graph_bytes": (S, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                   ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -233,6 +257,47 @@ class Context:
                                  sign.data_ptr(),
                                  per_vertex.data_ptr() if per_vertex is not None else None)
 
+    # ------------------------------------------------------------ serving
+    def serve(self, slots: int = 4, arena_bytes: int = 0):
+        """Start the serving engine (``bb_ctx_serve``): `slots` concurrent
+        requests, `arena_bytes` of device memory for the managed cache."""
+        _check(lib().bb_ctx_serve(self._h, slots, arena_bytes))
+
+    def submit(self, graph: "Graph") -> "Ticket":
+        """Asynchronous count of a resident graph (``bb_submit``)."""
+        h = _VP()
+        _check(lib().bb_submit(self._h, graph._h, 0, ctypes.byref(h)))
+        return Ticket(h, (graph,))
+
+    def submit_request(self, key: int, g=None, flips=None, no_cache: bool = False) -> "Ticket":
+        """Asynchronous count of the graph named `key` (``bb_submit_request``):
+        uploaded from host graph `g` unless resident; `flips` (edge indices)
+        flip signs of the resident graph first. The host arrays are kept
+        alive by the ticket until it is done."""
+        keep = []
+        req = _Request()
+        req.key = key
+        if g is not None:
+            csr, sign, arrays = _host_arrays(g)
+            keep += [csr, sign, arrays]
+            req.csr = ctypes.pointer(csr)
+            req.signs = sign.ctypes.data
+        if flips is not None:
+            f = np.ascontiguousarray(flips, dtype=np.int64)
+            keep.append(f)
+            req.flip_idx = f.ctypes.data
+            req.n_flip = f.size
+        keep.append(req)
+        h = _VP()
+        _check(lib().bb_submit_request(self._h, ctypes.byref(req), REQ_NO_CACHE if no_cache else 0,
+                                       ctypes.byref(h)))
+        return Ticket(h, tuple(keep))
+
+    def serve_stats(self) -> dict:
+        st = _ServeStats()
+        _check(lib().bb_ctx_serve_stats(self._h, ctypes.byref(st)))
+        return {n: int(getattr(st, n)) for n, _ in _ServeStats._fields_}
+
     def upload(self, g) -> "Graph":
         """Resident graph from a host graph (``bb_graph_upload``)."""
         csr, sign, keep = _host_arrays(g)
@@ -240,6 +305,52 @@ class Context:
         _check(lib().bb_graph_upload(self._h, ctypes.byref(csr), sign.ctypes.data, ctypes.byref(h)))
         del keep
         return Graph(self, h)
+
+
+@dataclass
+class Served:
+    balanced: int
+    total: int
+    queue_ms: float
+    run_ms: float
+
+
+class Ticket:
+    """An asynchronous request. ``poll()`` returns None until it is done,
+    then its counts (or raises its error); the handle is released then."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep
+        self.result: Served | None = None
+
+    def poll(self) -> Served | None:
+        if self.result is not None:
+            return self.result
+        done = ctypes.c_int()
+        b, t = ctypes.c_int64(), ctypes.c_int64()
+        q, r = ctypes.c_double(), ctypes.c_double()
+        st = lib().bb_poll_timed(self._h, ctypes.byref(done), ctypes.byref(b), ctypes.byref(t),
+                                 ctypes.byref(q), ctypes.byref(r))
+        if not done.value:
+            _check(st)
+            return None
+        self._h = None
+        self._keep = None
+        _check(st)
+        self.result = Served(b.value, t.value, q.value, r.value)
+        return self.result
+
+    def wait(self, timeout: float = 600.0) -> Served:
+        import time
+        t0 = time.monotonic()
+        while True:
+            r = self.poll()
+            if r is not None:
+                return r
+            if time.monotonic() - t0 > timeout:
+                raise TimeoutError("request did not finish")
+            time.sleep(50e-6)
 
 
 class Graph:
@@ -330,6 +441,21 @@ class Batch:
             self.free()
         except Exception:
             pass
+
+
+def graph_bytes(nU: int, nV: int, nE: int) -> tuple[int, int]:
+    """(resident, build workspace) device bytes of a graph of these sizes."""
+    r, w = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().bb_graph_bytes(nU, nV, nE, ctypes.byref(r), ctypes.byref(w)))
+    return r.value, w.value
+
+
+def request_bytes(g) -> int:
+    """Arena bytes a served request for host graph g needs while it builds:
+    resident graph, input copy and build workspace, each 256-byte aligned."""
+    r, w = graph_bytes(g.nU, g.nV, g.nE)
+    a = lambda x: (x + 255) // 256 * 256  # noqa: E731
+    return a(r) + a(w) + a((g.nU + 1) * 8) + a(g.nE * 4) + a(g.nE)
 
 
 def version() -> str:

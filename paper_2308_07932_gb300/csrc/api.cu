@@ -67,9 +67,7 @@ bb_status bb::wait_bounded(cudaStream_t s, const char *what) {
     return BB_OK;
 }
 
-namespace {
-
-bb_status check_csr(const bb_csr *csr, const int8_t *signs) {
+bb_status bb::check_csr(const bb_csr *csr, const int8_t *signs) {
     if (!csr) return fail(BB_ERR_INVALID_ARG, "csr is NULL");
     if (csr->nU < 0 || csr->nV < 0 || csr->nE < 0)
         return fail(BB_ERR_INVALID_ARG, "negative size (nU=%lld nV=%lld nE=%lld)",
@@ -86,8 +84,6 @@ bb_status check_csr(const bb_csr *csr, const int8_t *signs) {
         return fail(BB_ERR_INVALID_ARG, "col or signs is NULL");
     return BB_OK;
 }
-
-}  // namespace
 
 bb_status bb::map_build_error(uint32_t e) {
     if (e & E_ROWPTR) return fail(BB_ERR_INVALID_ARG, "rowptr is not a valid CSR row pointer");
@@ -283,6 +279,7 @@ bb_status bb_ctx_create(int device, uint64_t hbm_budget_bytes, bb_ctx **out) {
 
 void bb_ctx_destroy(bb_ctx *ctx) {
     if (!ctx) return;
+    engine_stop(ctx);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     dev_free(ctx, ctx->ws_graph, ctx->ws_graph_cap);
@@ -491,6 +488,15 @@ bb_status bb_graph_flip_signs(bb_graph *G, const int64_t *edge_idx, int64_t n) {
     st = e == cudaSuccess ? wait_bounded(s, "sign flip") : cuda_fail(e, "sign flip");
     dev_free(ctx, d, (size_t)n * 8);
     return st;
+}
+
+bb_status bb_graph_bytes(int64_t nU, int64_t nV, int64_t nE, uint64_t *resident_opt,
+                         uint64_t *workspace_opt) {
+    if (nU < 0 || nV < 0 || nE < 0) return fail(BB_ERR_INVALID_ARG, "negative size");
+    const BuildSizes bs = build_sizes(nU, nV, nE);
+    if (resident_opt) *resident_opt = bs.graph_bytes;
+    if (workspace_opt) *workspace_opt = bs.temp_bytes;
+    return BB_OK;
 }
 
 bb_status bb_graph_info(const bb_graph *G, int64_t *nU, int64_t *nV, int64_t *nE,

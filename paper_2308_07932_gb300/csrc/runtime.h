@@ -10,6 +10,8 @@
 
 namespace bb {
 
+struct Engine;  // serving engine (serve.cu)
+
 // results copied back after a count or a build
 struct HostResult {
     unsigned long long acc[4];
@@ -46,6 +48,7 @@ struct bb_ctx {
     cudaEvent_t ev[bb::NEV] = {};
     bool have_build_ev = false;
     bb_timing last = {};
+    bb::Engine *engine = nullptr;  // started by bb_ctx_serve or the first bb_submit
 };
 
 struct bb_graph {
@@ -69,6 +72,10 @@ bb_status dev_alloc(bb_ctx *ctx, void **p, size_t bytes, const char *what);
 void dev_free(bb_ctx *ctx, void *p, size_t bytes);
 bb_status set_device(bb_ctx *ctx);
 bb_status map_build_error(uint32_t e);
+// argument checks of a CSR given to the library (sizes, NULLs, id limits)
+bb_status check_csr(const bb_csr *csr, const int8_t *signs);
+// stops the context's serving engine (waits for running requests)
+void engine_stop(bb_ctx *ctx);
 // adds launches made by replaying a captured CUDA graph to bb_launch_count
 void note_launches(uint64_t n);
 uint64_t launches();

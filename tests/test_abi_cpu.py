@@ -64,3 +64,18 @@ def test_context_without_device_fails_loudly(built):
     with pytest.raises(pkg.BBError) as ei:
         pkg.Context(0)
     assert ei.value.name in ("BB_ERR_NO_DEVICE", "BB_ERR_CUDA")
+
+
+def test_sizes_and_serving_arguments_without_device(built):
+    r, w = pkg.graph_bytes(2_000_000, 500_000, 20_000_000)
+    r2, w2 = pkg.graph_bytes(200_000, 50_000, 2_000_000)
+    assert r > r2 > 0 and w > w2 > 0
+    with pytest.raises(pkg.BBError):
+        pkg.graph_bytes(-1, 2, 3)
+    t = ctypes.c_void_p()
+    assert built.bb_submit(None, None, 0, ctypes.byref(t)) == 1
+    assert built.bb_submit_request(None, None, 0, ctypes.byref(t)) == 1
+    done = ctypes.c_int()
+    b = ctypes.c_int64()
+    assert built.bb_poll(None, ctypes.byref(done), ctypes.byref(b), ctypes.byref(b)) == 1
+    assert built.bb_batch_create(None, None, 0, ctypes.byref(t)) == 1
