@@ -173,6 +173,23 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- multi-rank helpers
+def reduce_max(x: float, dist, device) -> float:
+    """Max of x over all ranks (x itself when dist is None)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, slowest_ms: float) -> float:
+    """Units of all ranks per second of the slowest rank (replicas each do
+    the same work, so the job ends with the slowest one)."""
+    return world * units_per_rank / (slowest_ms / 1e3)
+
+
 # ---------------------------------------------------------------- our path
 def count_sha() -> str:
     h = hashlib.sha256()
@@ -257,13 +274,9 @@ def run_ours(args, world, rank, local_rank):
     if dist:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(sum(step_ms), dist, dev)
     ms_per_step = total_ms / args.steps
-    value = world * c.wedges / (ms_per_step / 1e3)
+    value = whole_job_rate(c.wedges, world, ms_per_step)
 
     # end to end through the public host-pointer call, pinned host inputs
     h_rowptr = torch.from_numpy(g.rowptr).pin_memory()
@@ -280,11 +293,7 @@ def run_ours(args, world, rank, local_rank):
     for _ in range(e2e_steps):
         ce = ctx.count_host_ptrs(g.nU, g.nV, g.nE, h_rowptr.data_ptr(), h_col.data_ptr(),
                                  h_sign.data_ptr())
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, dist, dev)
     assert (ce.balanced, ce.total) == (c.balanced, c.total)
 
     # dominant wedge kernel and its roofline
@@ -297,6 +306,9 @@ def run_ours(args, world, rank, local_rank):
     peak, peak_kind = load_peaks()
     ach = algorithmic_bytes(kern[top]) / (kern[top]["ms"] / 1e3) / 1e9
     clocks = clk.summary()
+    # second ceiling: shared-memory atomic throughput (one atomic per wedge)
+    atomics = {w: pkg.probe_shared_atomics(local_rank, w) for w in (2048, 49152)}
+    count_rate = c.wedges / (count_ms / 1e3)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -314,8 +326,13 @@ def run_ours(args, world, rank, local_rank):
         "roofline": {"bound": "hbm", "kernel": top, "achieved": ach, "peak": peak, "unit": "GB/s",
                      "frac": ach / peak, "peak_kind": peak_kind,
                      "algorithmic_bytes": algorithmic_bytes(kern[top]),
-                     "traffic": traffic_for(top, args.workload)},
-        "e2e": {"value": world * c.wedges / e2e_s, "unit": UNIT,
+                     "traffic": traffic_for(top, args.workload),
+                     "atomic_ceiling": {
+                         "unit": "shared-memory atomics/s (one per wedge)",
+                         "window_2048": atomics[2048], "window_49152": atomics[49152],
+                         "count_phase_wedges_per_s": count_rate,
+                         "frac": count_rate / atomics[2048]}},
+        "e2e": {"value": whole_job_rate(c.wedges, world, e2e_s * 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": g.rowptr.nbytes + g.col.nbytes + g.sign.nbytes,
                 "d2h_bytes_per_step": 52},
         "gpu_launches": launches,
@@ -329,6 +346,9 @@ def run_ours(args, world, rank, local_rank):
         rate, secs, desc = oracle_rate(g, c.wedges, args.cpu_stride, 0, os.cpu_count() or 1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count() or 1,
                                 "kind": "oracle", "sample": desc, "seconds": secs}
+        r1, s1, d1 = oracle_rate(g, c.wedges, args.cpu_stride * 16, 0, 1)
+        line["cpu_baseline"]["single_thread"] = {"value": r1, "cores": 1, "sample": d1,
+                                                 "seconds": s1}
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -382,6 +402,14 @@ def run_batch_leg(args, dev_index: int) -> dict:
     launches = pkg.launch_count() - launches0
     assert (b2 == bal).all() and (t2 == tot).all()
     ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    # one traced count: each class kernel's time (uncaptured, serial)
+    ctx.set_timing(True)
+    b3, t3 = batch.count()
+    tr = ctx.last_timing()
+    ctx.set_timing(False)
+    assert (b3 == bal).all() and (t3 == tot).all()
+    classes = {k: {"ms": tr["kernels"][k]["ms"], "items": tr["kernels"][k]["anchors"]}
+               for k in pkg.KERNELS}
     # one bb_count per graph, on the same resident graphs
     per_ms = []
     for k in range(max(1, args.batch_single_steps) + 1):
@@ -405,6 +433,7 @@ def run_batch_leg(args, dev_index: int) -> dict:
         "per_graph_launches": {"graphs_per_s": n / (single_ms / 1e3), "ms_per_step": single_ms,
                                "steps": len(per_ms)},
         "speedup_vs_per_graph": single_ms / ms,
+        "traced_classes": classes, "traced_count_ms": tr["count_ms"],
         "tune": tune.to_dict(), "tune_ms": tune_ms, "gpu_launches": launches,
         "setup_s": {"generate": gen_s, "upload_and_build": upload_s},
         "l2": "working set larger than L2 (no flush needed)" if edges * 13 > 256e6

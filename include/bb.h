@@ -209,7 +209,11 @@ BB_API bb_status bb_ctx_last_timing(const bb_ctx *ctx, bb_timing *out);
  *   or host bb_status[n]. A graph whose count fails gets -1 in both outputs
  *   and its status; the call then returns the first such status (message
  *   names the graph index). The first call captures the CUDA graph on the
- *   context's stream, which must not be the legacy default stream.
+ *   context's stream, which must not be the legacy default stream. With
+ *   timing enabled on the context (bb_ctx_set_timing) the count runs
+ *   uncaptured, classes one after another, and bb_ctx_last_timing gives
+ *   each class kernel's time (anchors[] = the class's items; other
+ *   per-class counters 0).
  * bb_batch_tune: launch shapes per work class, index order as in bb_timing
  *   (dense, CTA-hash, team, warp). warp_chunk: warp anchors a warp takes
  *   per grab (1..1024); concurrent: 1 = the class kernels run on separate
@@ -298,6 +302,20 @@ BB_API bb_status bb_poll(bb_ticket t, int *done, int64_t *balanced, int64_t *tot
 BB_API bb_status bb_poll_timed(bb_ticket t, int *done, int64_t *balanced, int64_t *total,
                                double *queue_ms_opt, double *run_ms_opt);
 BB_API bb_status bb_ctx_serve_stats(bb_ctx *ctx, bb_serve_stats *out);
+
+/* Process-wide limit, in seconds, on how long a blocking call waits for its
+ * device work (default 600). When it runs out the call returns
+ * BB_ERR_TIMEOUT and its outputs are untouched; the work it queued still
+ * runs, and later calls on the same context's stream run after it.
+ * BB_ERR_INVALID_ARG unless 0 < seconds <= 86400. */
+BB_API bb_status bb_set_wait_timeout(double seconds);
+
+/* Measurement probe: shared-memory atomic adds per second on `device`, each
+ * a u32 atomicAdd whose previous value is used (the wedge kernels' inner
+ * step) on a pseudo-random counter of a `window`-entry array (32..49152),
+ * the whole GPU busy. The best of three timed runs after a warm-up. The
+ * paper has no counterpart; it gives the count kernels' second ceiling. */
+BB_API bb_status bb_probe_shared_atomics(int device, uint32_t window, double *atomics_per_s);
 
 /* Kernel launches the library has issued in this process. */
 BB_API uint64_t bb_launch_count(void);

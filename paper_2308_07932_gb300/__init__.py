@@ -134,6 +134,9 @@ def lib() -> ctypes.CDLL:
             "bb_poll_timed": (S, [_VP, ctypes.POINTER(ctypes.c_int), _I64P, _I64P,
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
             "bb_ctx_serve_stats": (S, [_VP, ctypes.POINTER(_ServeStats)]),
+            "bb_set_wait_timeout": (S, [ctypes.c_double]),
+            "bb_probe_shared_atomics": (S, [ctypes.c_int, ctypes.c_uint32,
+                                            ctypes.POINTER(ctypes.c_double)]),
             "bb_graph_bytes": (S, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                    ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
         }
@@ -456,6 +459,18 @@ def request_bytes(g) -> int:
     r, w = graph_bytes(g.nU, g.nV, g.nE)
     a = lambda x: (x + 255) // 256 * 256  # noqa: E731
     return a(r) + a(w) + a((g.nU + 1) * 8) + a(g.nE * 4) + a(g.nE)
+
+
+def set_wait_timeout(seconds: float):
+    """Limit on how long blocking calls wait for device work (process-wide)."""
+    _check(lib().bb_set_wait_timeout(seconds))
+
+
+def probe_shared_atomics(device: int = 0, window: int = 2048) -> float:
+    """Shared-memory atomic adds per second on the device (all SMs)."""
+    r = ctypes.c_double()
+    _check(lib().bb_probe_shared_atomics(device, window, ctypes.byref(r)))
+    return r.value
 
 
 def version() -> str:

@@ -20,7 +20,7 @@ namespace {
 std::atomic<uint64_t> g_launches{0};
 thread_local std::string t_err;
 // limit of a bounded wait on device work
-double g_timeout_s = 600.0;
+std::atomic<double> g_timeout_s{600.0};
 }  // namespace
 
 void bb::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -56,10 +56,10 @@ bb_status bb::wait_bounded(cudaStream_t s, const char *what) {
         if (e == cudaSuccess) break;
         if (e != cudaErrorNotReady) { cudaEventDestroy(ev); return cuda_fail(e, what); }
         double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        if (dt > g_timeout_s) {
+        const double limit = g_timeout_s.load(std::memory_order_relaxed);
+        if (dt > limit) {
             cudaEventDestroy(ev);
-            return fail(BB_ERR_TIMEOUT, "%s: device work did not finish within %.0f s", what,
-                        g_timeout_s);
+            return fail(BB_ERR_TIMEOUT, "%s: device work did not finish within %g s", what, limit);
         }
         if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
@@ -306,6 +306,13 @@ bb_status bb_ctx_last_timing(const bb_ctx *ctx, bb_timing *out) {
 }
 
 uint64_t bb_launch_count(void) { return launches(); }
+
+bb_status bb_set_wait_timeout(double seconds) {
+    if (!(seconds > 0.0 && seconds <= 86400.0))
+        return fail(BB_ERR_INVALID_ARG, "timeout %g s outside (0, 86400]", seconds);
+    g_timeout_s.store(seconds, std::memory_order_relaxed);
+    return BB_OK;
+}
 
 bb_status bb_ctx_set_stream(bb_ctx *ctx, void *stream) {
     if (!ctx) return fail(BB_ERR_INVALID_ARG, "ctx is NULL");

@@ -183,11 +183,30 @@ bb_status bb_batch_count(bb_batch *b, int64_t *balanced, int64_t *total, bb_stat
     std::lock_guard<std::mutex> lk(ctx->mu);
     bb_status st = set_device(ctx);
     if (st != BB_OK) return st;
-    if (!b->exec || b->exec_stream != ctx->stream)
-        if ((st = capture(b)) != BB_OK) return st;
-    BB_CUDA(cudaGraphLaunch(b->exec, ctx->stream), "batch graph launch");
-    note_launches(b->exec_launches);
-    if ((st = wait_bounded(ctx->stream, "batch count")) != BB_OK) return st;
+    if (ctx->timing) {
+        // traced count: uncaptured, classes one after another between events
+        launch_count_batch(b->L, b->tune, ctx->stream, b->side, b->ev, ctx->ev + 2);
+        BB_CUDA(cudaGetLastError(), "batch launch");
+        BB_CUDA(cudaMemcpyAsync(b->h_out, b->L.out, (size_t)b->n * BATCH_OUT * 8,
+                                cudaMemcpyDeviceToHost, ctx->stream), "copy batch results");
+        if ((st = wait_bounded(ctx->stream, "batch count")) != BB_OK) return st;
+        bb_timing &T = ctx->last;
+        T = bb_timing{};
+        float ms = 0;
+        for (int k = 0; k < BB_NKERNELS; k++)
+            if (cudaEventElapsedTime(&ms, ctx->ev[2 + k], ctx->ev[3 + k]) == cudaSuccess)
+                T.kernel_ms[k] = ms;
+        if (cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[2 + BB_NKERNELS]) == cudaSuccess)
+            T.count_ms = ms;
+        for (int k = 0; k < BB_NKERNELS; k++) T.anchors[k] = b->L.items[KERNEL_CLS[k]];
+        cudaGetLastError();
+    } else {
+        if (!b->exec || b->exec_stream != ctx->stream)
+            if ((st = capture(b)) != BB_OK) return st;
+        BB_CUDA(cudaGraphLaunch(b->exec, ctx->stream), "batch graph launch");
+        note_launches(b->exec_launches);
+        if ((st = wait_bounded(ctx->stream, "batch count")) != BB_OK) return st;
+    }
     bb_status first = BB_OK;
     int64_t first_i = -1;
     for (uint32_t i = 0; i < b->n; i++) {

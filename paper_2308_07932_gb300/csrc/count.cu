@@ -847,7 +847,7 @@ int batch_max_blocks(int cls) {
 }
 
 void launch_count_batch(const BatchLaunch &L, const BatchTune &T, cudaStream_t s,
-                        const cudaStream_t *side, const cudaEvent_t *ev) {
+                        const cudaStream_t *side, const cudaEvent_t *ev, const cudaEvent_t *tev) {
     init_cfg();
     BatchArgs B;
     B.graphs = L.graphs;
@@ -861,7 +861,7 @@ void launch_count_batch(const BatchLaunch &L, const BatchTune &T, cudaStream_t s
     const int order[NCLS] = {CLS_DENSE, CLS_CTAH, CLS_TEAM, CLS_WARP};
     int nlaunch = 0;
     for (int k = 0; k < NCLS; k++) nlaunch += L.items[order[k]] ? 1 : 0;
-    const bool conc = T.concurrent && side && ev && nlaunch > 1;
+    const bool conc = T.concurrent && side && ev && nlaunch > 1 && !tev;
     if (conc) {  // fork exactly the side streams that get a kernel (a capture must join them all)
         cudaEventRecord(ev[0], s);
         for (int k = 0; k + 1 < nlaunch; k++) cudaStreamWaitEvent(side[k], ev[0], 0);
@@ -869,6 +869,7 @@ void launch_count_batch(const BatchLaunch &L, const BatchTune &T, cudaStream_t s
     int used = 0;
     for (int k = 0; k < NCLS; k++) {
         const int c = order[k];
+        if (tev) cudaEventRecord(tev[k], s);
         if (L.items[c] == 0) continue;
         // with concurrency the first class stays on s, the others go to side streams
         cudaStream_t cs = conc && used > 0 ? side[used - 1] : s;
@@ -892,6 +893,7 @@ void launch_count_batch(const BatchLaunch &L, const BatchTune &T, cudaStream_t s
             cudaEventRecord(ev[1 + k], side[k]);
             cudaStreamWaitEvent(s, ev[1 + k], 0);
         }
+    if (tev) cudaEventRecord(tev[NCLS], s);
     const uint32_t res_blocks = std::min<uint32_t>((L.n + 255) / 256, 1024);
     if (L.n) { k_batch_results<<<res_blocks, 256, 0, s>>>(B, L.out); note_launch(); }
 }

@@ -160,9 +160,12 @@ struct BatchTune {
     float grid_frac[NCLS] = {1.f, 1.f, 1.f, 1.f};
 };
 // side: NCLS-1 streams and ev: NCLS events, used when T.concurrent is set
-// (both may be null otherwise). Works under stream capture.
+// (both may be null otherwise). Works under stream capture. tev (optional,
+// NCLS+1 timing events) turns concurrency off and brackets the class
+// kernels in the order dense, CTA-hash, team, warp.
 void launch_count_batch(const BatchLaunch &L, const BatchTune &T, cudaStream_t s,
-                        const cudaStream_t *side, const cudaEvent_t *ev);
+                        const cudaStream_t *side, const cudaEvent_t *ev,
+                        const cudaEvent_t *tev = nullptr);
 int batch_max_blocks(int cls);
 
 // Balanced butterflies containing each vertex (Algorithm 3's quantity) for

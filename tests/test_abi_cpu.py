@@ -79,3 +79,11 @@ def test_sizes_and_serving_arguments_without_device(built):
     b = ctypes.c_int64()
     assert built.bb_poll(None, ctypes.byref(done), ctypes.byref(b), ctypes.byref(b)) == 1
     assert built.bb_batch_create(None, None, 0, ctypes.byref(t)) == 1
+
+
+def test_wait_timeout_argument_checks(built):
+    with pytest.raises(pkg.BBError):
+        pkg.set_wait_timeout(0.0)
+    with pytest.raises(pkg.BBError):
+        pkg.set_wait_timeout(-1.0)
+    pkg.set_wait_timeout(600.0)

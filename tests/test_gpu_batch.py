@@ -69,6 +69,23 @@ def test_batch_shapes_do_not_change_counts(ctx, mix, chunk, conc, frac):
     b.free()
 
 
+def test_traced_batch_count(ctx, mix):
+    hosts, graphs, want = mix
+    b = pkg.Batch(ctx, graphs)
+    ctx.set_timing(True)
+    try:
+        bal, tot = b.count()
+        tr = ctx.last_timing()
+    finally:
+        ctx.set_timing(False)
+    assert [(int(x), int(y)) for x, y in zip(bal, tot)] == want
+    assert tr["count_ms"] > 0
+    assert sum(tr["kernels"][k]["anchors"] for k in pkg.KERNELS) > 0
+    bal, tot = b.count()  # captured again afterwards
+    assert [(int(x), int(y)) for x, y in zip(bal, tot)] == want
+    b.free()
+
+
 def test_batch_order_and_subsets(ctx, mix):
     hosts, graphs, want = mix
     rng = np.random.default_rng(5)
