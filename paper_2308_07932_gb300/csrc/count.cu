@@ -13,10 +13,12 @@
 // to the total, which is exact in any order and needs no pass over the
 // counters afterwards, only their reset.
 //
-// Work is spread by a team walker: a team (a warp, or a whole CTA) loads a
-// chunk of the anchor's middles, scans their suffix lengths, and splits the
-// chunk's wedges evenly across its warps; each warp finds the middle of each
-// of its wedges with a shuffle search over a 32-middle window.
+// Work is spread by walkers: a team (a warp, or a whole CTA) loads a chunk
+// of the anchor's middles, scans their suffix lengths and compacts the
+// non-empty ones. The dense class's team_walk then steps through the
+// chunk's wedges 32 at a time per warp (coalesced, one segment lookup per
+// step); the other classes' lane_walk gives each thread an equal contiguous
+// share of the chunk's wedges to stream through.
 //
 // Counters, per class (all in shared memory; S in bits 0..15, A in bits
 // 16..31 of a u32, both bounded by the anchor's degree):
@@ -99,8 +101,7 @@ template <int TS>
 struct alignas(16) WalkSmem {
     Desc desc[TS];
     uint32_t incl[TS];
-    unsigned long long warp_part[TS / 32];
-    uint32_t stage[TS / 32][3][32];   // per warp: compacted remainders (start, length, sign)
+    unsigned long long warp_part[TS / 32];  // per warp: wedges (low half), segments (high half)
     uint32_t tot[2];
     uint32_t item_next;               // next work item of the chunk (teams of several warps)
 };
@@ -115,11 +116,15 @@ constexpr uint32_t WALK_ITEM = 256;
 // add(u_side_rank, asymmetric) is called once per wedge.
 //
 // Per chunk of TS middles the team scans the segment lengths and compacts
-// the non-empty segments; its warps then take 256-wedge slices of the
-// chunk in turn (a lone warp takes the whole chunk). A warp walks the whole
-// 32-wedge blocks of every segment in its slice together (coalesced, no
-// search), then the remainders (< 32 each) of up to 32 segments as one flat
-// range, each lane finding its segment from a bitmask of segment starts.
+// the non-empty segments (their ends, incl[], are the chunk's wedge
+// prefix); its warps then take 256-wedge slices of the chunk in turn (a
+// lone warp takes the whole chunk). A warp walks its slice flat, 32
+// consecutive wedges per step, lane l taking wedge base + l (coalesced
+// loads). The step's wedges lie in at most 32 consecutive segments from
+// `cur`, the segment of the step's first wedge: each lane reads one of
+// their ends, the ends that fall inside the step form a bitmask, and a lane's
+// segment is cur plus the ends at or before its wedge. When the whole step
+// lies in segment cur (long segments) that reduces to one broadcast read.
 template <int TS, int UNROLL = 4, typename Seg, typename Add>
 __device__ __forceinline__ void team_walk(const uint4 *__restrict__ smd,
                                           const uint32_t *__restrict__ oadj, int64_t rb,
@@ -128,6 +133,7 @@ __device__ __forceinline__ void team_walk(const uint4 *__restrict__ smd,
     constexpr int NW = TS / 32;
     constexpr uint32_t EXMASK = 0x7fffffffu;
     const int lane = t & 31, w = t >> 5;
+    const unsigned upto = (2u << lane) - 1u;   // bits 0..lane
     for (uint32_t mc = m0; mc < m1; mc += TS) {
         const uint32_t j = mc + (uint32_t)t;
         long long st = 0;
@@ -137,144 +143,260 @@ __device__ __forceinline__ void team_walk(const uint4 *__restrict__ smd,
             sw = d.w;
             seg(d, st, len);
         }
-        // inclusive team scan of (len, nonzero) packed in one u64
-        unsigned long long x = (unsigned long long)len | ((unsigned long long)(len > 0) << 32);
+        // inclusive team scan of the lengths; compacted index from a ballot
+        uint32_t x = len;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            unsigned long long y = __shfl_up_sync(FULL, x, d);
+            const uint32_t y = __shfl_up_sync(FULL, x, d);
             if (lane >= d) x += y;
         }
+        const unsigned nzb = __ballot_sync(FULL, len > 0);
+        uint32_t nzi = __popc(nzb & upto);
         if constexpr (NW > 1) {
-            if (lane == 31) sm.warp_part[w] = x;
+            if (lane == 31) sm.warp_part[w] = x | ((unsigned long long)__popc(nzb) << 32);
             team_sync<TS>();
-            unsigned long long add_w = 0;
-            for (int k = 0; k < w; k++) add_w += sm.warp_part[k];
-            x += add_w;
+            uint32_t add_x = 0, add_n = 0;
+            for (int k = 0; k < w; k++) {
+                const unsigned long long v = sm.warp_part[k];
+                add_x += (uint32_t)v;
+                add_n += (uint32_t)(v >> 32);
+            }
+            x += add_x;
+            nzi += add_n;
         }
-        const uint32_t incl = (uint32_t)x, nzi = (uint32_t)(x >> 32);
         if (len > 0) {
-            sm.desc[nzi - 1] = Desc{(uint32_t)st, (incl - len) | (sw << 31)};
-            sm.incl[nzi - 1] = incl;
+            sm.desc[nzi - 1] = Desc{(uint32_t)st, (x - len) | (sw << 31)};
+            sm.incl[nzi - 1] = x;
         }
-        if (t == TS - 1) { sm.tot[0] = incl; sm.tot[1] = nzi; sm.item_next = 0; }
+        if (t == TS - 1) { sm.tot[0] = x; sm.tot[1] = nzi; sm.item_next = 0; }
         team_sync<TS>();
         const uint32_t T = sm.tot[0], NZ = sm.tot[1];
         // a warp takes the whole chunk when alone, else 256-wedge items in turn
         for (uint32_t item = 0;; item++) {
-        uint32_t a, b;
-        if constexpr (NW == 1) {
-            if (item > 0) break;
-            a = 0; b = T;
-        } else {
-            uint32_t it = 0;
-            if (lane == 0) it = atomicAdd(&sm.item_next, 1u);
-            it = __shfl_sync(FULL, it, 0);
-            a = it * WALK_ITEM;
-            if (a >= T) break;
-            b = T - a > WALK_ITEM ? a + WALK_ITEM : T;
-        }
-        if (a < b) {
-            // first segment holding wedge a
-            uint32_t lo = 0, hi = NZ;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (sm.incl[mid] <= a) lo = mid + 1; else hi = mid;
+            uint32_t a, b;
+            if constexpr (NW == 1) {
+                if (item > 0) break;
+                a = 0; b = T;
+            } else {
+                uint32_t it = 0;
+                if (lane == 0) it = atomicAdd(&sm.item_next, 1u);
+                it = __shfl_sync(FULL, it, 0);
+                a = it * WALK_ITEM;
+                if (a >= T) break;
+                b = T - a > WALK_ITEM ? a + WALK_ITEM : T;
             }
-            uint32_t(&stage)[3][32] = sm.stage[w];
-            const unsigned lt = (1u << lane) - 1u;
-            // segments [g, g+32) of the slice, one per lane
-            for (uint32_t g = lo; g < NZ; g += 32) {
-                const uint32_t kk = g + (uint32_t)lane;
-                uint32_t st0 = 0, full = 0, rl = 0, swk = 0;
-                bool valid = false;
-                if (kk < NZ) {
-                    const Desc d = sm.desc[kk];
-                    const uint32_t ex = d.excl_sw & EXMASK;
-                    if (ex < b) {
-                        valid = true;
-                        const uint32_t in = sm.incl[kk];
-                        const uint32_t s0 = ex > a ? ex : a, s1 = in < b ? in : b;
-                        const uint32_t n = s1 - s0;
-                        full = n & ~31u;
-                        rl = n - full;
-                        st0 = d.st + (s0 - ex);
-                        swk = d.excl_sw >> 31;
-                    }
+            // segment holding wedge a: the first whose end is past a
+            uint32_t cur = 0;
+            if (a > 0) {
+                uint32_t hi = NZ;
+                while (cur < hi) {
+                    const uint32_t mid = (cur + hi) >> 1;
+                    if (sm.incl[mid] <= a) cur = mid + 1; else hi = mid;
                 }
-                const unsigned vm = __ballot_sync(FULL, valid);
-                // whole 32-wedge blocks of the long segments, warp-wide
-                unsigned lm = __ballot_sync(FULL, full > 0);
-                while (lm) {
-                    const int jl = __ffs(lm) - 1;
-                    lm &= lm - 1;
-                    const uint32_t bst = __shfl_sync(FULL, st0, jl) + (uint32_t)lane;
-                    const uint32_t bfull = __shfl_sync(FULL, full, jl);
-                    const uint32_t bsw = __shfl_sync(FULL, swk, jl);
-                    for (uint32_t o = 0; o < bfull; o += 32u * UNROLL) {
-                        uint32_t xv[UNROLL];
+            }
+            for (uint32_t base = a; base < b; base += 32u * UNROLL) {
+                uint32_t addr[UNROLL], swq[UNROLL];
+                bool ok[UNROLL];
 #pragma unroll
-                        for (int q = 0; q < UNROLL; q++)
-                            if (o + 32u * q < bfull) xv[q] = oadj[bst + o + 32u * q];
-#pragma unroll
-                        for (int q = 0; q < UNROLL; q++)
-                            if (o + 32u * q < bfull) add(xv[q] >> 1, (xv[q] ^ bsw) & 1u);
-                    }
-                }
-                // the remainders (< 32 wedges each), compacted and walked flat
-                const unsigned nzm = __ballot_sync(FULL, rl > 0);
-                if (nzm) {
-                    const uint32_t nc = __popc(nzm);
-                    if (rl > 0) {
-                        const uint32_t cp = __popc(nzm & lt);
-                        stage[0][cp] = st0 + full; stage[1][cp] = rl; stage[2][cp] = swk;
-                    }
-                    __syncwarp();
-                    const uint32_t rs = lane < (int)nc ? stage[0][lane] : 0u;
-                    const uint32_t rlc = lane < (int)nc ? stage[1][lane] : 0u;
-                    const uint32_t swc = lane < (int)nc ? stage[2][lane] : 0u;
-                    __syncwarp();
-                    uint32_t ri = rlc;
-#pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const uint32_t y = __shfl_up_sync(FULL, ri, d);
-                        if (lane >= d) ri += y;
-                    }
-                    const uint32_t R = __shfl_sync(FULL, ri, 31);
-                    const uint32_t rx = (ri - rlc) | (swc << 31);
-                    for (uint32_t base0 = 0; base0 < R; base0 += 32u * UNROLL) {
-                        uint32_t addr[UNROLL], swq[UNROLL];
-                        bool ok[UNROLL];
-#pragma unroll
-                        for (int u = 0; u < UNROLL; u++) {
-                            // segment of wedge base+lane: those ending by `base`, plus
-                            // the segment starts inside this step up to my position
-                            const uint32_t base = base0 + 32u * u;
-                            const uint32_t c0 = __popc(__ballot_sync(FULL, ri <= base));
-                            const uint32_t p = ri - base;
-                            const uint32_t bit = (ri > base && p < 32u) ? (1u << p) : 0u;
-                            const uint32_t B = __reduce_or_sync(FULL, bit);
-                            const uint32_t sgi = (c0 + __popc(B & ((2u << lane) - 1u))) & 31u;
-                            const uint32_t srs = __shfl_sync(FULL, rs, sgi);
-                            const uint32_t srx = __shfl_sync(FULL, rx, sgi);
-                            const uint32_t q = base + (uint32_t)lane;
-                            ok[u] = q < R;
-                            addr[u] = srs + (q - (srx & EXMASK));
-                            swq[u] = srx >> 31;
+                for (int u = 0; u < UNROLL; u++) {
+                    const uint32_t bq = base + 32u * u;
+                    ok[u] = false;
+                    addr[u] = 0;
+                    swq[u] = 0;
+                    if (bq < b) {
+                        const uint32_t ecur = sm.incl[cur];
+                        uint32_t sg, nxt;
+                        if (ecur >= bq + 32u) {  // the whole step is in segment cur
+                            sg = cur;
+                            nxt = ecur == bq + 32u ? cur + 1 : cur;
+                        } else {
+                            const uint32_t jj = cur + (uint32_t)lane;
+                            const uint32_t p = (jj < NZ ? sm.incl[jj] : 0xffffffffu) - bq;  // >= 1
+                            const unsigned M = __reduce_or_sync(FULL, p < 32u ? (1u << p) : 0u);
+                            sg = cur + __popc(M & upto);
+                            nxt = cur + __popc(__ballot_sync(FULL, p <= 32u));
                         }
-                        uint32_t xv[UNROLL];
-#pragma unroll
-                        for (int u = 0; u < UNROLL; u++)
-                            if (ok[u]) xv[u] = oadj[addr[u]];
-#pragma unroll
-                        for (int u = 0; u < UNROLL; u++)
-                            if (ok[u]) add(xv[u] >> 1, (xv[u] ^ swq[u]) & 1u);
+                        const uint32_t q = bq + (uint32_t)lane;
+                        if (q < b) {
+                            const Desc dd = sm.desc[sg];
+                            ok[u] = true;
+                            addr[u] = dd.st + (q - (dd.excl_sw & EXMASK));
+                            swq[u] = dd.excl_sw >> 31;
+                        }
+                        cur = nxt;
                     }
                 }
-                if (vm != FULL) break;  // the slice ended inside this group
+                uint32_t xv[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; u++)
+                    if (ok[u]) xv[u] = oadj[addr[u]];
+#pragma unroll
+                for (int u = 0; u < UNROLL; u++)
+                    if (ok[u]) add(xv[u] >> 1, (xv[u] ^ swq[u]) & 1u);
             }
-        }
         }
         team_sync<TS>();
+    }
+}
+
+// Lane walker. After the same chunk scan and compaction, each thread takes
+// an equal contiguous part [a, b) of the chunk's flat wedge range and
+// streams through it, stepping to the next segment when one ends: no
+// per-step segment search, and the threads of a team get equal wedge
+// counts. Used where anchors are small or medium (warp, team and CTA-hash
+// classes); the dense class keeps team_walk's coalesced steps.
+template <int U, typename Add>
+__device__ __forceinline__ void lane_range(const uint32_t *__restrict__ oadj, const Desc *desc,
+                                           const uint32_t *incl, uint32_t NZ, uint32_t a,
+                                           uint32_t b, Add &&add) {
+    constexpr uint32_t EXMASK = 0x7fffffffu;
+    if (a >= b) return;
+    uint32_t k = 0, hi = NZ;  // segment holding wedge a
+    while (k < hi) {
+        const uint32_t mid = (k + hi) >> 1;
+        if (incl[mid] <= a) k = mid + 1; else hi = mid;
+    }
+    Desc d = desc[k];
+    uint32_t ex = d.excl_sw & EXMASK;
+    uint32_t p = d.st + (a - ex);
+    uint32_t pend = d.st + (incl[k] - ex);
+    uint32_t cs = d.excl_sw >> 31;
+    auto next_segment = [&]() {
+        k++;
+        d = desc[k];
+        ex = d.excl_sw & EXMASK;
+        p = d.st;
+        pend = d.st + (incl[k] - ex);
+        cs = d.excl_sw >> 31;
+    };
+    uint32_t i = a;
+    for (; i + U <= b; i += U) {
+        uint32_t pa[U], sq[U];
+        if (pend - p >= U) {  // the U wedges lie in the current segment
+#pragma unroll
+            for (int u = 0; u < U; u++) { pa[u] = p + u; sq[u] = cs; }
+            p += U;
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (p == pend) next_segment();
+                pa[u] = p++;
+                sq[u] = cs;
+            }
+        }
+        uint32_t xv[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) xv[u] = oadj[pa[u]];
+#pragma unroll
+        for (int u = 0; u < U; u++) add(xv[u] >> 1, (xv[u] ^ sq[u]) & 1u);
+    }
+    for (; i < b; i++) {
+        if (p == pend) next_segment();
+        const uint32_t x = oadj[p++];
+        add(x >> 1, (x ^ cs) & 1u);
+    }
+}
+
+// equal share t of n among TS threads
+template <int TS>
+__device__ __forceinline__ uint32_t share(uint32_t n, uint32_t t) {
+    return (uint32_t)((unsigned long long)n * t / TS);
+}
+
+template <int TS, int U = 4, typename Seg, typename Add>
+__device__ __forceinline__ void lane_walk(const uint4 *__restrict__ smd,
+                                          const uint32_t *__restrict__ oadj, int64_t rb,
+                                          uint32_t m0, uint32_t m1, WalkSmem<TS> &sm, int t,
+                                          Seg &&seg, Add &&add) {
+    constexpr int NW = TS / 32;
+    const int lane = t & 31, w = t >> 5;
+    const unsigned upto = (2u << lane) - 1u;
+    for (uint32_t mc = m0; mc < m1; mc += TS) {
+        const uint32_t j = mc + (uint32_t)t;
+        long long st = 0;
+        uint32_t len = 0, sw = 0;
+        if (j < m1) {
+            const uint4 d = smd[rb + j];
+            sw = d.w;
+            seg(d, st, len);
+        }
+        uint32_t x = len;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, x, d);
+            if (lane >= d) x += y;
+        }
+        const unsigned nzb = __ballot_sync(FULL, len > 0);
+        uint32_t nzi = __popc(nzb & upto);
+        if constexpr (NW > 1) {
+            if (lane == 31) sm.warp_part[w] = x | ((unsigned long long)__popc(nzb) << 32);
+            team_sync<TS>();
+            uint32_t add_x = 0, add_n = 0;
+            for (int k = 0; k < w; k++) {
+                const unsigned long long v = sm.warp_part[k];
+                add_x += (uint32_t)v;
+                add_n += (uint32_t)(v >> 32);
+            }
+            x += add_x;
+            nzi += add_n;
+        }
+        if (len > 0) {
+            sm.desc[nzi - 1] = Desc{(uint32_t)st, (x - len) | (sw << 31)};
+            sm.incl[nzi - 1] = x;
+        }
+        if (t == TS - 1) { sm.tot[0] = x; sm.tot[1] = nzi; }
+        team_sync<TS>();
+        const uint32_t T = sm.tot[0], NZ = sm.tot[1];
+        lane_range<U>(oadj, sm.desc, sm.incl, NZ, share<TS>(T, t), share<TS>(T, t + 1), add);
+        team_sync<TS>();
+    }
+}
+
+// One warp, two segment families of the same middles (the hub-window part
+// and the part below it) from one chunk scan: each lane walks its share of
+// the first family with addA, then its share of the second with addB.
+template <int U = 4, typename SegA, typename AddA, typename SegB, typename AddB>
+__device__ __forceinline__ void lane_walk2(const uint4 *__restrict__ smd,
+                                           const uint32_t *__restrict__ oadj, int64_t rb,
+                                           uint32_t m0, uint32_t m1, WalkSmem<32> &sa,
+                                           WalkSmem<32> &sb, int lane, SegA &&sega, AddA &&adda,
+                                           SegB &&segb, AddB &&addb) {
+    const unsigned upto = (2u << lane) - 1u;
+    for (uint32_t mc = m0; mc < m1; mc += 32) {
+        const uint32_t j = mc + (uint32_t)lane;
+        long long sta = 0, stb = 0;
+        uint32_t la = 0, lb = 0, sw = 0;
+        if (j < m1) {
+            const uint4 d = smd[rb + j];
+            sw = d.w;
+            sega(d, sta, la);
+            segb(d, stb, lb);
+        }
+        unsigned long long x = (unsigned long long)la | ((unsigned long long)lb << 32);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long y = __shfl_up_sync(FULL, x, d);
+            if (lane >= d) x += y;
+        }
+        const uint32_t xa = (uint32_t)x, xb = (uint32_t)(x >> 32);
+        const unsigned nza = __ballot_sync(FULL, la > 0), nzb = __ballot_sync(FULL, lb > 0);
+        if (la > 0) {
+            const uint32_t i = __popc(nza & upto) - 1;
+            sa.desc[i] = Desc{(uint32_t)sta, (xa - la) | (sw << 31)};
+            sa.incl[i] = xa;
+        }
+        if (lb > 0) {
+            const uint32_t i = __popc(nzb & upto) - 1;
+            sb.desc[i] = Desc{(uint32_t)stb, (xb - lb) | (sw << 31)};
+            sb.incl[i] = xb;
+        }
+        const uint32_t TA = __shfl_sync(FULL, xa, 31), TB = __shfl_sync(FULL, xb, 31);
+        __syncwarp();
+        lane_range<U>(oadj, sa.desc, sa.incl, __popc(nza), share<32>(TA, lane),
+                      share<32>(TA, lane + 1), adda);
+        lane_range<U>(oadj, sb.desc, sb.incl, __popc(nzb), share<32>(TB, lane),
+                      share<32>(TB, lane + 1), addb);
+        __syncwarp();
     }
 }
 
@@ -316,10 +438,11 @@ __device__ __forceinline__ void clear_table(unsigned long long *tab, uint32_t ca
     for (uint32_t i = t; i < cap / 2; i += TS) t2[i] = make_ulonglong2(0ull, 0ull);
 }
 
-// table of 2^k slots, 2^k >= max(min_cap, need + need/4 + 1), at most max_cap
+// table of 2^k slots, 2^k >= max(min_cap, 2 need + 1), at most max_cap (load <= 1/2
+// unless capped: linear probes stay short)
 __device__ __forceinline__ void table_geometry(uint64_t need, uint32_t min_cap, uint32_t max_cap,
                                                uint32_t &cap, uint32_t &shift) {
-    uint64_t want = need + need / 4 + 1;
+    uint64_t want = 2 * need + 1;
     cap = min_cap;
     shift = 32 - (31 - __clz(min_cap));
     while ((uint64_t)cap < want && cap < max_cap) { cap <<= 1; shift--; }
@@ -379,7 +502,7 @@ struct LowSeg {
 struct alignas(16) WarpSmem {
     uint32_t win[HUB_WINDOW / 2];
     unsigned long long tab[WARP_CAP];
-    WalkSmem<32> walk;
+    WalkSmem<32> walk, walk2;  // hub-window and below-window segments
 };
 
 // per-warp copies are laid out back to back and reset with 16-byte stores
@@ -397,32 +520,38 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
     if (W <= WARP_SMALL_W) {  // hash every endpoint
         table_geometry(W < above ? W : above, 32, WARP_CAP, cap, shift);
         const uint32_t mask = cap - 1;
-        team_walk<32, 2>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, FullSeg{},
-                         [&](uint32_t u, uint32_t asym) {
-                             hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
-                         });
+        lane_walk<32>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, FullSeg{},
+                      [&](uint32_t u, uint32_t asym) {
+                          hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
+                      });
     } else {
         const int64_t ns = A.ns;
         const uint32_t wb = ns > (int64_t)HUB_WINDOW ? (uint32_t)(ns - HUB_WINDOW) : 0u;
         const uint64_t wnh = A.wnh;
         const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
-        team_walk<32, 2>(
-            A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, HubSeg{},
+        if (wnh > 0) table_geometry(wnh < above_nh ? wnh : above_nh, 32, WARP_CAP, cap, shift);
+        const uint32_t mask = cap - 1;
+        bool bad_any = false;
+        lane_walk2(
+            A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, sm.walk2, (int)lane, HubSeg{},
             [&](uint32_t u, uint32_t asym) {
-                const uint32_t wi = u - wb;
-                if (wi >= HUB_WINDOW) { set_error(err, E_INTERNAL); return; }
-                const uint32_t sh = (wi & 1u) * 16u;
-                const uint32_t old = atomicAdd(&sm.win[wi >> 1], (asym ? 256u : 1u) << sh) >> sh;
-                wedge_terms(old & 0xffu, (old >> 8) & 0xffu, asym, bal, tot);
+                // S in bits 0..7 and A in bits 8..15 of the endpoint's 16-bit
+                // half-word (both <= the degree <= 255, so S + A fits 8 bits)
+                uint32_t wi = u - wb;
+                const bool bad = wi >= HUB_WINDOW;  // checked, not branched on
+                bad_any |= bad;
+                wi = bad ? 0u : wi;
+                const uint32_t sh = (wi & 1u) << 4;
+                const uint32_t old =
+                    (atomicAdd(&sm.win[wi >> 1], (1u + asym * 255u) << sh) >> sh) & 0xffffu;
+                bal += (old >> (asym << 3)) & 0xffu;
+                tot += ((old * 0x101u) >> 8) & 0xffu;  // S + A
+            },
+            LowSeg{},
+            [&](uint32_t u, uint32_t asym) {
+                hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
             });
-        if (wnh > 0) {
-            table_geometry(wnh < above_nh ? wnh : above_nh, 32, WARP_CAP, cap, shift);
-            const uint32_t mask = cap - 1;
-            team_walk<32, 2>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, LowSeg{},
-                             [&](uint32_t u, uint32_t asym) {
-                                 hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
-                             });
-        }
+        if (bad_any) set_error(err, E_INTERNAL);
         // reset the window words an endpoint can have reached
         const uint32_t first = (A.r + 1 > wb ? A.r + 1 - wb : 0u) >> 3;  // uint4 index
         uint4 *w4 = reinterpret_cast<uint4 *>(sm.win);
@@ -486,7 +615,7 @@ __device__ __forceinline__ void hybrid_anchor(const DevGraph &G, HybSmem<TS, HCA
     const uint64_t W = A.W, wnh = A.wnh;
     const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
     if (W > wnh) {  // endpoints inside the hub window
-        team_walk<TS>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, HubSeg{},
+        lane_walk<TS>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, HubSeg{},
                       [&](uint32_t u, uint32_t asym) {
                           const uint32_t idx = u - wb;
                           if (idx >= HUB_WINDOW) { set_error(err, E_INTERNAL); return; }
@@ -499,7 +628,7 @@ __device__ __forceinline__ void hybrid_anchor(const DevGraph &G, HybSmem<TS, HCA
         uint32_t shift;
         table_geometry(wnh < above_nh ? wnh : above_nh, 32, HCAP, cap, shift);
         const uint32_t mask = cap - 1;
-        team_walk<TS>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, LowSeg{},
+        lane_walk<TS>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, LowSeg{},
                       [&](uint32_t u, uint32_t asym) {
                           hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
                       });

@@ -30,7 +30,7 @@ constexpr uint32_t DENSE_CAP = 49152;
 // window in 16-bit counters and hash the rest; the hash has WARP_CAP slots.
 constexpr uint32_t WARP_DEG_MAX = 255;
 constexpr uint64_t WARP_W_MAX = 16384;
-constexpr uint64_t WARP_SMALL_W = 200;
+constexpr uint64_t WARP_SMALL_W = 32;
 constexpr uint32_t WARP_CAP = 256;
 // team class (4 warps): wedges <= TEAM_W_MAX and below-window wedges that fit
 // a TEAM_CAP-slot hash
