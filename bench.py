@@ -408,8 +408,7 @@ def run_batch_leg(args, dev_index: int) -> dict:
     tr = ctx.last_timing()
     ctx.set_timing(False)
     assert (b3 == bal).all() and (t3 == tot).all()
-    classes = {k: {"ms": tr["kernels"][k]["ms"], "items": tr["kernels"][k]["anchors"]}
-               for k in pkg.KERNELS}
+    classes = {k: dict(tr["kernels"][k]) for k in pkg.KERNELS}
     # one bb_count per graph, on the same resident graphs
     per_ms = []
     for k in range(max(1, args.batch_single_steps) + 1):

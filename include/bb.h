@@ -212,8 +212,8 @@ BB_API bb_status bb_ctx_last_timing(const bb_ctx *ctx, bb_timing *out);
  *   context's stream, which must not be the legacy default stream. With
  *   timing enabled on the context (bb_ctx_set_timing) the count runs
  *   uncaptured, classes one after another, and bb_ctx_last_timing gives
- *   each class kernel's time (anchors[] = the class's items; other
- *   per-class counters 0).
+ *   each class kernel's time and work (wedges, middles, anchors) summed
+ *   over the members.
  * bb_batch_tune: launch shapes per work class, index order as in bb_timing
  *   (dense, CTA-hash, team, warp). warp_chunk: warp anchors a warp takes
  *   per grab (1..1024); concurrent: 1 = the class kernels run on separate

@@ -425,6 +425,9 @@ static bb_status upload_impl(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs
     if (e == cudaSuccess) e = cudaMemcpyAsync(&ctx->h_res->wedges, G->g.wedges, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->h_res->ctr, G->g.ctr, sizeof(ctx->h_res->ctr), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->h_res->cls_stats, G->g.cls_stats, sizeof(ctx->h_res->cls_stats),
+                            cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) { bb_graph_free(G); return cuda_fail(e, "copy build status"); }
     st = wait_bounded(s, "graph build");
     if (st != BB_OK) { bb_graph_free(G); return st; }
@@ -435,6 +438,7 @@ static bb_status upload_impl(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs
     }
     G->g.h_wedges = ctx->h_res->wedges;
     memcpy(G->g.h_ctr, ctx->h_res->ctr, sizeof(G->g.h_ctr));
+    memcpy(G->g.h_cls_stats, ctx->h_res->cls_stats, sizeof(G->g.h_cls_stats));
     *out = G;
     return BB_OK;
 }

@@ -19,6 +19,7 @@ struct bb_batch {
     void *mem = nullptr;
     size_t bytes = 0;
     BatchLaunch L{};
+    unsigned long long cls_stats[3 * NCLS] = {};  // summed over the members
     unsigned long long *h_out = nullptr;  // pinned [n * BATCH_OUT]
     BatchTune tune;
     cudaStream_t side[NCLS - 1] = {};
@@ -125,6 +126,8 @@ bb_status bb_batch_create(bb_ctx *ctx, bb_graph *const *graphs, int64_t n, bb_ba
     b->ctx = ctx;
     b->n = (uint32_t)n;
     b->graphs.assign(graphs, graphs + n);
+    for (int64_t i = 0; i < n; i++)
+        for (int k = 0; k < 3 * NCLS; k++) b->cls_stats[k] += graphs[i]->g.h_cls_stats[k];
     // class item prefixes over the graphs
     std::vector<uint32_t> prefix((size_t)NCLS * (n + 1));
     for (int c = 0; c < NCLS; c++) {
@@ -198,7 +201,11 @@ bb_status bb_batch_count(bb_batch *b, int64_t *balanced, int64_t *total, bb_stat
                 T.kernel_ms[k] = ms;
         if (cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[2 + BB_NKERNELS]) == cudaSuccess)
             T.count_ms = ms;
-        for (int k = 0; k < BB_NKERNELS; k++) T.anchors[k] = b->L.items[KERNEL_CLS[k]];
+        for (int k = 0; k < BB_NKERNELS; k++) {
+            T.wedges[k] = (int64_t)b->cls_stats[KERNEL_CLS[k]];
+            T.middles[k] = (int64_t)b->cls_stats[NCLS + KERNEL_CLS[k]];
+            T.anchors[k] = (int64_t)b->cls_stats[2 * NCLS + KERNEL_CLS[k]];
+        }
         cudaGetLastError();
     } else {
         if (!b->exec || b->exec_stream != ctx->stream)

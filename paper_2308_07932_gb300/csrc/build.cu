@@ -277,8 +277,8 @@ __global__ void __launch_bounds__(THREADS) k_sort_rows_smem(SideCSR S, const uin
     }
 }
 
-// rows longer than the shared-memory sort: one CTA per row, stable LSD
-// radix sort (8-bit digits) through two global buffers
+// rows of more than 2048 entries: one CTA per row, stable LSD radix sort
+// (8-bit digits) through two global buffers
 constexpr int RR_THREADS = 1024;
 constexpr int RR_WARPS = RR_THREADS / 32;
 
@@ -286,10 +286,11 @@ __global__ void __launch_bounds__(RR_THREADS) k_sort_rows_radix(SideCSR S, uint6
                                                                 uint64_t *alt, uint32_t *eid,
                                                                 uint32_t *rowid,
                                                                 const int64_t *bounds, int lo_k,
-                                                                int key_bits, uint32_t *err) {
+                                                                int hi_k, int key_bits,
+                                                                uint32_t *err) {
     __shared__ uint32_t wcnt[RR_WARPS][256];
     __shared__ uint32_t run[256];
-    const int64_t r0 = bounds[lo_k], r1 = bounds[lo_k + 1];
+    const int64_t r0 = bounds[lo_k], r1 = bounds[hi_k];
     const int t = threadIdx.x, warp = t >> 5;
     const unsigned lane = lane_id();
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -601,10 +602,7 @@ size_t side_bytes(int64_t n, int64_t nE) {
 
 }  // namespace
 
-void build_init() {
-    cudaFuncSetAttribute(k_sort_rows_smem<16384, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         16384 * 8);
-}
+void build_init() {}
 
 BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE) {
     int64_t n = nU + nV;
@@ -743,11 +741,12 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
         k_sort_rows_sub<32><<<grid_for(n * 32, BT, 8192), BT, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 4, g.err); note_launch();
         k_sort_rows_warpsmem<<<1024, WS_THREADS, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 5, g.err); note_launch();
         k_sort_rows_smem<2048, 256><<<2048, 256, 2048 * 8, s>>>(S, ky, eid[sd], rowid[sd], bd, 6, g.err); note_launch();
-        k_sort_rows_smem<16384, 1024><<<1024, 1024, 16384 * 8, s>>>(S, ky, eid[sd], rowid[sd], bd, 7, g.err); note_launch();
         int64_t n_other = ns[1 - sd];
         int key_bits = 1;
         while (key_bits < 32 && ((uint64_t)1 << key_bits) < (uint64_t)(2 * n_other + 2)) key_bits++;
-        k_sort_rows_radix<<<512, RR_THREADS, 0, s>>>(S, ky, bufC, eid[sd], rowid[sd], bd, 8, key_bits, g.err); note_launch();
+        // rows above 2048 entries: per-row radix sort (faster there than bitonic)
+        k_sort_rows_radix<<<1024, RR_THREADS, 0, s>>>(S, ky, bufC, eid[sd], rowid[sd], bd, 7, NLIMS,
+                                                       key_bits, g.err); note_launch();
     }
     for (int sd = 0; sd < 2; sd++) {
         if (ns[sd] == 0) continue;

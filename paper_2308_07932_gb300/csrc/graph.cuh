@@ -112,6 +112,7 @@ struct DevGraph {
     // host copies after the build
     uint32_t h_ctr[NCTR] = {};
     uint64_t h_wedges = 0;
+    unsigned long long h_cls_stats[3 * NCLS] = {};  // resident graphs: copy of cls_stats
 };
 
 // Bytes of device memory a graph of this size needs (graph + build temps).
@@ -125,7 +126,7 @@ BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE);
 void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_mem);
 
 // Build from device CSR (rowptr/col/sign on the device). Returns 0 or the
-// error bits; on success g.h_ctr / g.h_wedges are filled. Blocking only on
+// error bits. Blocking only on
 // the validation check and at the end.
 uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
                      void *temp_mem, cudaStream_t s);

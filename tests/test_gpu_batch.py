@@ -81,6 +81,7 @@ def test_traced_batch_count(ctx, mix):
     assert [(int(x), int(y)) for x, y in zip(bal, tot)] == want
     assert tr["count_ms"] > 0
     assert sum(tr["kernels"][k]["anchors"] for k in pkg.KERNELS) > 0
+    assert sum(tr["kernels"][k]["wedges"] for k in pkg.KERNELS) == sum(g.info()[3] for g in graphs)
     bal, tot = b.count()  # captured again afterwards
     assert [(int(x), int(y)) for x, y in zip(bal, tot)] == want
     b.free()
