@@ -58,6 +58,26 @@ __device__ __forceinline__ void acc_add(CountScratch *sc, unsigned long long bal
     }
 }
 
+// Per-thread partial sums are kept below 2^53 + 2^50 (larger ones go to the
+// 128-bit accumulator at once; one anchor or job adds less than 2^50 to a
+// thread's sums), so that the sum of up to 1024 threads' partials cannot
+// wrap a u64 however large the graph's counts are.
+__device__ __forceinline__ void spill_if_large(CountScratch *sc, unsigned long long &bal,
+                                               unsigned long long &tot) {
+    if ((bal | tot) >> 53) {
+        acc_add(sc, bal, tot);
+        bal = tot = 0;
+    }
+}
+
+// adds the partial sums of a warp's threads to the accumulator
+__device__ __forceinline__ void flush_warp(CountScratch *sc, unsigned long long bal,
+                                           unsigned long long tot) {
+    bal = warp_sum_u64(bal);
+    tot = warp_sum_u64(tot);
+    if (lane_id() == 0) acc_add(sc, bal, tot);
+}
+
 // contribution of one wedge given its pair's counts before it
 __device__ __forceinline__ void wedge_terms(uint32_t oldS, uint32_t oldA, uint32_t asym,
                                             unsigned long long &bal, unsigned long long &tot) {
@@ -578,9 +598,11 @@ __global__ void __launch_bounds__(WARP_THREADS, 4) k_warp(DevGraph G) {
     const uint32_t gw = (blockIdx.x * WARP_THREADS + threadIdx.x) >> 5;
     const uint32_t GW = (gridDim.x * WARP_THREADS) >> 5;
     unsigned long long bal = 0, tot = 0;
-    for (uint32_t idx = gw; idx < n; idx += GW) warp_anchor(G, sm, G.warp_list[idx], lane, bal, tot);
-    block_sum2<WARP_THREADS>(bal, tot);
-    if (threadIdx.x == 0) acc_add(G.scratch, bal, tot);
+    for (uint32_t idx = gw; idx < n; idx += GW) {
+        warp_anchor(G, sm, G.warp_list[idx], lane, bal, tot);
+        spill_if_large(G.scratch, bal, tot);
+    }
+    flush_warp(G.scratch, bal, tot);
 }
 
 // ------------------------------------------------- team and CTA-hash classes
@@ -656,6 +678,7 @@ __device__ __forceinline__ void hybrid_body(DevGraph &G, const AnchorRec *list) 
         __syncthreads();
         if (jid >= n) break;
         hybrid_anchor<TS, HCAP>(G, sm, list[jid], bal, tot);
+        spill_if_large(G.scratch, bal, tot);
     }
     block_sum2<TS>(bal, tot);
     if (threadIdx.x == 0) acc_add(G.scratch, bal, tot);
@@ -677,8 +700,9 @@ struct alignas(16) DenseSmem {
 };
 
 // one dense job (an anchor, or one middle slice of a split anchor), walked
-// by the whole CTA; adds its sums to the graph's accumulators
-__device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, const DenseJob &J) {
+// by the whole CTA; adds each thread's part of its sums to bal and tot
+__device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, const DenseJob &J,
+                                          unsigned long long &bal, unsigned long long &tot) {
     const int t = threadIdx.x;
     CountScratch *sc = G.scratch;
     const bool sv = J.anchor & 1u;
@@ -695,7 +719,6 @@ __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, cons
         const uint32_t len = e1 - e0;
         for (uint32_t i = t; i < len; i += DENSE_THREADS) sm.cnt[i] = 0;
         __syncthreads();
-        unsigned long long bal = 0, tot = 0;
         auto add = [&](uint32_t u, uint32_t asym) {
             const uint32_t idx = u - e0;
             if (idx >= len) { set_error(&sc->err, E_INTERNAL); return; }
@@ -744,8 +767,7 @@ __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, cons
                 if (t == 0) G.gdone[J.group] = 0;
             }
         }
-        block_sum2<DENSE_THREADS>(bal, tot);
-        if (t == 0) acc_add(sc, bal, tot);
+        __syncthreads();  // the next window or job rewrites the counters
     }
 }
 
@@ -753,14 +775,17 @@ __global__ void __launch_bounds__(DENSE_THREADS) k_dense(DevGraph G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DenseSmem &sm = *reinterpret_cast<DenseSmem *>(smem_raw);
     const uint32_t njobs = G.ctr[CTR_DENSE];
+    unsigned long long bal = 0, tot = 0;  // summed over all jobs of this CTA
     for (;;) {
         if (threadIdx.x == 0) sm.job = atomicAdd(&G.scratch->job_next[CLS_DENSE], 1u);
         __syncthreads();
         const uint32_t jid = sm.job;
         __syncthreads();
         if (jid >= njobs) break;
-        dense_job(G, sm, G.dense_jobs[jid]);
+        dense_job(G, sm, G.dense_jobs[jid], bal, tot);
+        spill_if_large(G.scratch, bal, tot);
     }
+    flush_warp(G.scratch, bal, tot);
 }
 
 // ---------------------------------------------------- batched (many graphs)
@@ -858,7 +883,10 @@ __global__ void __launch_bounds__(DENSE_THREADS) k_dense_batch(BatchArgs B) {
         if (it >= total) break;
         const uint32_t gi = batch_graph_of(p, B.n, it);
         const DevGraph &G = B.graphs[gi];
-        dense_job(G, sm, G.dense_jobs[it - p[gi]]);
+        unsigned long long bal = 0, tot = 0;
+        dense_job(G, sm, G.dense_jobs[it - p[gi]], bal, tot);
+        block_sum2<DENSE_THREADS>(bal, tot);
+        if (threadIdx.x == 0) acc_add(G.scratch, bal, tot);
     }
 }
 
