@@ -9,6 +9,8 @@ Every function here computes a quantity the paper defines:
                       pair enumeration without degree priority;
   * ``per_vertex``  - balanced butterflies containing each vertex
                       (Algorithm 3, vBBFC, read with w != x);
+  * ``per_edge``    - balanced butterflies containing each edge (the
+                      edge-level extension, eBBFC), from the definition;
   * ``bb_base``     - the same counts by Algorithm 1 (BB-Base), an
                       independent enumeration used as a cross-check;
   * ``brute``       - Defs. 1-2 by brute force over all vertex 4-tuples.
@@ -68,11 +70,13 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
                                           I64P, I64P, I64P, I64P]
         L.oracle_per_vertex.argtypes = [ctypes.c_int64, ctypes.c_int64, I64P, I32P, I8P,
                                         I64P, ctypes.c_int64, ctypes.c_int, I64P]
+        L.oracle_per_edge.argtypes = [ctypes.c_int64, ctypes.c_int64, I64P, I32P, I8P,
+                                      I64P, ctypes.c_int64, ctypes.c_int, I64P]
         L.oracle_bb_base.argtypes = [ctypes.c_int64, ctypes.c_int64, I64P, I32P, I8P, I64P, I64P]
         L.oracle_brute.argtypes = [ctypes.c_int64, ctypes.c_int64, I64P, I32P, I8P, I64P, I64P,
                                    I64P]
-        for f in (L.oracle_count, L.oracle_count_sample, L.oracle_per_vertex, L.oracle_bb_base,
-                  L.oracle_brute):
+        for f in (L.oracle_count, L.oracle_count_sample, L.oracle_per_vertex, L.oracle_per_edge,
+                  L.oracle_bb_base, L.oracle_brute):
             f.restype = ctypes.c_int
         _libs[mutant] = L
     return _libs[mutant]
@@ -144,6 +148,29 @@ def per_vertex(g, gids=None, threads: int = 1) -> np.ndarray:
                                       threads, out.ctypes.data_as(I64P))
     del keep
     _check(rc, "per_vertex")
+    return out
+
+
+def per_edge(g, edges=None, threads: int = 1, mutant: int = 0) -> np.ndarray:
+    """Balanced butterflies containing each edge (the paper's edge-level
+    extension, eBBFC), from the definition: every butterfly through the edge
+    enumerated by its other two vertices and tested with Def. 2.
+
+    edges: None for every edge in input CSR order, or a list of positions in
+    the input CSR. Returns int64 counts in the same order.
+    """
+    _, _, _, (rp, c, s) = keep = _arrays(g)
+    if edges is None:
+        out = np.zeros(g.nE, np.int64)
+        rc = _lib(mutant).oracle_per_edge(g.nU, g.nV, rp, c, s, None, 0, threads,
+                                          out.ctypes.data_as(I64P))
+    else:
+        ids = np.ascontiguousarray(edges, dtype=np.int64)
+        out = np.zeros(ids.size, np.int64)
+        rc = _lib(mutant).oracle_per_edge(g.nU, g.nV, rp, c, s, ids.ctypes.data_as(I64P),
+                                          ids.size, threads, out.ctypes.data_as(I64P))
+    del keep
+    _check(rc, "per_edge")
     return out
 
 

@@ -337,6 +337,88 @@ def test_planted_mistakes_are_caught(mutant):
     assert failed, f"mutant {mutant} passed every pin"
 
 
+# ---------------------------------------------------------- per-edge pins
+def brute_per_edge(g):
+    """Defs. 1-2 written out per edge: every balanced (u1<u2, v1<v2) adds one
+    to each of its four edges. Returned in input CSR edge order."""
+    u, v, s = g.edges()
+    sign = {(a, b): c for a, b, c in zip(u.tolist(), v.tolist(), s.tolist())}
+    pe = {k: 0 for k in sign}
+    for u1, u2 in itertools.combinations(range(g.nU), 2):
+        for v1, v2 in itertools.combinations(range(g.nV), 2):
+            e = [(u1, v1), (u1, v2), (u2, v1), (u2, v2)]
+            if all(x in sign for x in e) and sign[e[0]] * sign[e[1]] * sign[e[2]] * sign[e[3]] == 1:
+                for x in e:
+                    pe[x] += 1
+    return np.array([pe[(a, b)] for a, b in zip(u.tolist(), v.tolist())], dtype=np.int64)
+
+
+def pin_per_edge_fig1(per_edge):
+    for panel, caption, signs, bal, tot in read_fig1():
+        assert list(per_edge(fig1_graph(signs))) == [bal] * 4, panel
+
+
+def pin_per_edge_complete(per_edge):
+    for mU, nV in [(2, 3), (4, 4), (5, 7)]:
+        g = synth.from_dense(np.ones((mU, nV), dtype=np.int8))
+        assert set(per_edge(g).tolist()) == {(mU - 1) * (nV - 1)}, (mU, nV)
+
+
+def pin_per_edge_brute(per_edge, seeds=range(30)):
+    for seed in seeds:
+        rng = np.random.default_rng(seed)
+        nU, nV = int(rng.integers(2, 9)), int(rng.integers(2, 9))
+        g = synth.uniform(3000 + seed, nU, nV, int(rng.integers(0, nU * nV + 1)), 0.55)
+        assert np.array_equal(per_edge(g), brute_per_edge(g)), seed
+
+
+def pin_per_edge_sum(per_edge):
+    for g in (synth.uniform(7, 60, 40, 900, 0.6), synth.chung_lu_scaled(13, 20_000)):
+        assert int(per_edge(g).sum()) == 4 * oracle.count(g)[0], g.name
+
+
+PE_PINS = [pin_per_edge_fig1, pin_per_edge_complete, pin_per_edge_brute, pin_per_edge_sum]
+
+
+def test_per_edge_pins():
+    for pin in PE_PINS:
+        pin(lambda g: oracle.per_edge(g, threads=2))
+
+
+def test_per_edge_lemma2_and_switching():
+    # K_{2,n} with l symmetric and m asymmetric middles: an edge at a middle of
+    # type t lies in (count of t) - 1 balanced butterflies
+    for l, m in [(0, 0), (2, 0), (3, 4), (5, 1)]:
+        g = k2n(l, m, seed=l * 5 + m)
+        pe = oracle.per_edge(g)
+        u, v, _ = g.edges()
+        pv = oracle.per_vertex(g)
+        for k in range(g.nE):
+            assert pe[k] == pv[g.nU + v[k]], (l, m, k)
+    # negating every edge at one vertex leaves every per-edge count unchanged
+    g = synth.chung_lu_scaled(21, 30_000)
+    u, v, s = g.edges()
+    s2 = np.where(u == 3, -s, s).astype(np.int8)
+    h = synth.SignedBipartite(g.nU, g.nV, g.rowptr, g.col, s2, g.name + "/sw")
+    assert np.array_equal(oracle.per_edge(g, threads=4), oracle.per_edge(h, threads=4))
+    # a listed subset gives the same values as the full run
+    idx = np.random.default_rng(1).choice(g.nE, 50, replace=False)
+    assert np.array_equal(oracle.per_edge(g, idx), oracle.per_edge(g, threads=4)[idx])
+
+
+@pytest.mark.parametrize("mutant", [6, 7])
+def test_planted_per_edge_mistakes_are_caught(mutant):
+    """6 admits u2 == u1 (the edge's own row as the second U vertex), 7
+    ignores the fourth sign; some per-edge pin must fail."""
+    failed = []
+    for pin in PE_PINS:
+        try:
+            pin(lambda g: oracle.per_edge(g, mutant=mutant))
+        except AssertionError:
+            failed.append(pin.__name__)
+    assert failed, f"mutant {mutant} passed every per-edge pin"
+
+
 def test_generator_fingerprints():
     """The generators are deterministic: their graphs match stored digests,
     so stored oracle values refer to the same inputs on every machine."""
