@@ -126,6 +126,15 @@ BB_API bb_status bb_graph_upload_device(bb_ctx *ctx, const bb_csr *csr_dev, cons
  * per_vertex_opt: NULL or host int64[nU+nV] as above. */
 BB_API bb_status bb_count(bb_graph *g, int64_t *balanced, int64_t *total, int64_t *per_vertex_opt);
 
+/* Balanced butterflies containing each edge of a resident graph (the
+ * paper's edge-level extension of the per-vertex count, eBBFC; every
+ * balanced butterfly adds one to each of its four edges, so the values sum
+ * to 4 * balanced). per_edge: host int64[nE] in the input CSR's edge order.
+ * balanced_opt / total_opt: NULL or the graph's counts. Blocking; device
+ * workspace 24 bytes per edge (grow-only, within the context's budget). */
+BB_API bb_status bb_count_edges(bb_graph *g, int64_t *per_edge, int64_t *balanced_opt,
+                                int64_t *total_opt);
+
 /* Negate the sign of the listed input edges (indices into the CSR's col
  * array, host int64[n]) in the resident graph, both directions. Repeated
  * indices flip repeatedly. Later counts see the new signs. */

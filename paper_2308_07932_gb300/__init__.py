@@ -114,6 +114,7 @@ def lib() -> ctypes.CDLL:
             "bb_graph_upload_device": (S, [_VP, ctypes.POINTER(_Csr), _VP, ctypes.POINTER(_VP)]),
             "bb_count": (S, [_VP, _I64P, _I64P, _VP]),
             "bb_graph_flip_signs": (S, [_VP, _VP, ctypes.c_int64]),
+            "bb_count_edges": (S, [_VP, _VP, _I64P, _I64P]),
             "bb_graph_info": (S, [_VP, _I64P, _I64P, _I64P, _I64P]),
             "bb_graph_free": (None, [_VP]),
             "bb_ctx_set_timing": (S, [_VP, ctypes.c_int]),
@@ -370,6 +371,15 @@ class Graph:
         _check(lib().bb_count(self._h, ctypes.byref(b), ctypes.byref(t),
                               pv.ctypes.data if pv is not None else None))
         return Counts(b.value, t.value, w, pv)
+
+    def count_edges(self) -> tuple[np.ndarray, int, int]:
+        """Balanced butterflies containing each edge (input CSR order), and
+        the graph's (balanced, total) counts (``bb_count_edges``)."""
+        nU, nV, nE, w = self.info()
+        pe = np.zeros(max(nE, 1), np.int64)
+        b, t = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().bb_count_edges(self._h, pe.ctypes.data, ctypes.byref(b), ctypes.byref(t)))
+        return pe[:nE], b.value, t.value
 
     def flip(self, edge_idx):
         e = np.ascontiguousarray(edge_idx, dtype=np.int64)

@@ -286,6 +286,7 @@ void bb_ctx_destroy(bb_ctx *ctx) {
     dev_free(ctx, ctx->ws_temp, ctx->ws_temp_cap);
     dev_free(ctx, ctx->ws_in, ctx->ws_in_cap);
     dev_free(ctx, ctx->ws_pv, ctx->ws_pv_cap);
+    dev_free(ctx, ctx->ws_pe, ctx->ws_pe_cap);
     if (ctx->h_res) cudaFreeHost(ctx->h_res);
     for (int k = 0; k < NEV; k++)
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
@@ -474,6 +475,38 @@ bb_status bb_count(bb_graph *G, int64_t *balanced, int64_t *total, int64_t *per_
     BB_CUDA(cudaMemcpyAsync(per_vertex_opt, pv_dev, (size_t)(G->g.nU + G->g.nV) * 8,
                             cudaMemcpyDeviceToHost, ctx->stream), "copy per-vertex");
     return wait_bounded(ctx->stream, "per-vertex copy");
+}
+
+bb_status bb_count_edges(bb_graph *G, int64_t *per_edge, int64_t *balanced_opt,
+                         int64_t *total_opt) {
+    if (!G || !per_edge) return fail(BB_ERR_INVALID_ARG, "NULL argument");
+    bb_ctx *ctx = G->ctx;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    bb_status st = set_device(ctx);
+    if (st != BB_OK) return st;
+    ctx->have_build_ev = false;
+    const int64_t nE = G->g.nE;
+    const size_t b_out = ((size_t)nE * 8 + 255) & ~(size_t)255;
+    st = ensure(ctx, &ctx->ws_pe, &ctx->ws_pe_cap, b_out + (size_t)nE * 16 + 256,
+                "per-edge workspace");
+    if (st != BB_OK) return st;
+    int64_t *out_dev = (int64_t *)ctx->ws_pe;
+    unsigned long long *acc = (unsigned long long *)((char *)ctx->ws_pe + b_out);
+    cudaStream_t s = ctx->stream;
+    launch_count(G->g, s, nullptr, ctx->timing ? ctx->ev + 2 : nullptr);
+    launch_per_edge(G->g, out_dev, acc, s);
+    BB_CUDA(cudaGetLastError(), "per-edge launch");
+    int64_t b = 0, t = 0;
+    st = finish_count(ctx, G->g, s, &b, &t, nullptr);
+    if (st != BB_OK) return st;
+    if (nE > 0)
+        BB_CUDA(cudaMemcpyAsync(per_edge, out_dev, (size_t)nE * 8, cudaMemcpyDeviceToHost, s),
+                "copy per-edge");
+    st = wait_bounded(s, "per-edge copy");
+    if (st != BB_OK) return st;
+    if (balanced_opt) *balanced_opt = b;
+    if (total_opt) *total_opt = t;
+    return BB_OK;
 }
 
 bb_status bb_graph_flip_signs(bb_graph *G, const int64_t *edge_idx, int64_t n) {

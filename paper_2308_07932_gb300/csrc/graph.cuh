@@ -173,6 +173,12 @@ int batch_max_blocks(int cls);
 // a built graph: written to out_dev (device int64[nU+nV], U ids then V ids).
 void launch_per_vertex(const DevGraph &g, int64_t *out_dev, cudaStream_t s);
 
+// Balanced butterflies containing each input edge for a built graph that
+// keeps its raw input (rowptr/col): written to out_dev (device int64[nE],
+// input CSR order); pe_ws is device scratch of 2 * nE u64.
+void launch_per_edge(const DevGraph &g, int64_t *out_dev, unsigned long long *pe_ws,
+                     cudaStream_t s);
+
 // Flip the signs of listed input edges (device list of n indices).
 void launch_flip(DevGraph &g, const int64_t *edge_idx_dev, int64_t n, cudaStream_t s);
 

@@ -1,5 +1,6 @@
 // pervertex.cu - balanced butterflies containing each vertex (the quantity
-// Algorithm 3 computes for one vertex), for every vertex at once.
+// Algorithm 3 computes for one vertex), for every vertex at once, and
+// containing each edge.
 //
 // Each balanced butterfly is tallied at exactly one pair (w, u) of same-side
 // vertices (w the anchor, u the higher-priority one; see graph.cuh) and has
@@ -11,8 +12,14 @@
 // adds cnt_t - 1 to each middle (pass 2), then adds each pair's balanced
 // count to u and their sum to w.
 //
-// This runs only when per-vertex counts are requested, after the regular
-// count; its walk is simple (one warp per middle) rather than fast.
+// The same two passes give per-edge counts (the paper's edge-level
+// extension): a middle v of type t at pair (w, u) puts its cnt_t - 1
+// balanced butterflies on the edges w-v and v-u as well, accumulated per
+// adjacency entry of each side and summed per input edge at the end.
+//
+// This runs only when per-vertex or per-edge counts are requested, after
+// the regular count; its walk is simple (one warp per middle) rather than
+// fast.
 #include <algorithm>
 #include "graph.cuh"
 
@@ -64,7 +71,15 @@ __device__ __forceinline__ uint32_t pv_hash_find(const unsigned long long *tab, 
     return 0;
 }
 
-__global__ void __launch_bounds__(PV_THREADS) k_pv(DevGraph G) {
+// What k_pv accumulates: per-vertex counts (into each side's pv array)
+// and/or per-edge counts (into pe[side][position of the entry in that
+// side's adjacency]; null when not wanted).
+struct PvOut {
+    int vertex;
+    unsigned long long *pe[2];
+};
+
+__global__ void __launch_bounds__(PV_THREADS) k_pv(DevGraph G, PvOut out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PvSmem &sm = *reinterpret_cast<PvSmem *>(smem_raw);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = PV_THREADS / 32;
@@ -79,6 +94,7 @@ __global__ void __launch_bounds__(PV_THREADS) k_pv(DevGraph G) {
         const int sd = a < G.nU ? 0 : 1;
         const SideCSR &S = sd ? G.side[1] : G.side[0];
         const SideCSR &O = sd ? G.side[0] : G.side[1];
+        unsigned long long *peS = out.pe[sd], *peO = out.pe[1 - sd];
         const uint32_t r = (uint32_t)(sd ? a - G.nU : a);
         const uint64_t W = S.work[r];
         if (W == 0) continue;
@@ -127,7 +143,8 @@ __global__ void __launch_bounds__(PV_THREADS) k_pv(DevGraph G) {
                 }
             }
             __syncthreads();
-            // pass 2: each middle of type t lies in cnt_t - 1 butterflies of its pair
+            // pass 2: each middle v of type t lies in cnt_t - 1 balanced
+            // butterflies of its pair (w, u), and so do the edges w-v and v-u
             for (uint32_t j = warp; j < deg; j += nwarps) {
                 int64_t st, en; uint32_t sw, v;
                 segment(j, st, en, sw, v);
@@ -143,12 +160,21 @@ __global__ void __launch_bounds__(PV_THREADS) k_pv(DevGraph G) {
                         c = pv_hash_find(sm.tab, shift, mask, u + 1, err);
                     }
                     const uint32_t ct = ((x ^ sw) & 1u) ? (c >> 16) : (c & 0xffffu);
-                    msum += ct > 0 ? ct - 1 : 0;
+                    const unsigned long long k = ct > 0 ? ct - 1 : 0;
+                    msum += k;
+                    if (peO && k) atomicAdd(&peO[p], k);   // edge v-u
                 }
                 msum = warp_sum_u64(msum);
-                if (lane == 0 && msum) atomicAdd(&O.pv[v], msum);
+                if (lane == 0 && msum) {
+                    if (out.vertex) atomicAdd(&O.pv[v], msum);
+                    if (peS) atomicAdd(&peS[rb + j], msum);  // edge w-v
+                }
             }
             __syncthreads();
+            if (!out.vertex) {
+                if (!dense) break;
+                continue;
+            }
             // each pair's balanced butterflies contain both of its endpoints
             for (uint32_t i = t; i < len; i += PV_THREADS) {
                 uint32_t c, u;
@@ -166,15 +192,39 @@ __global__ void __launch_bounds__(PV_THREADS) k_pv(DevGraph G) {
             __syncthreads();
             if (!dense) break;
         }
-        wsum = warp_sum_u64(wsum);
-        if (lane == 0) sm.red[warp] = wsum;
-        __syncthreads();
-        if (t == 0) {
-            unsigned long long tot = 0;
-            for (int k = 0; k < nwarps; k++) tot += sm.red[k];
-            if (tot) atomicAdd(&S.pv[r], tot);
+        if (out.vertex) {
+            wsum = warp_sum_u64(wsum);
+            if (lane == 0) sm.red[warp] = wsum;
+            __syncthreads();
+            if (t == 0) {
+                unsigned long long tot = 0;
+                for (int k = 0; k < nwarps; k++) tot += sm.red[k];
+                if (tot) atomicAdd(&S.pv[r], tot);
+            }
         }
         __syncthreads();
+    }
+}
+
+// per-edge counts in the caller's edge order: an input edge (u, v) is the
+// entry of v in u's U-side row and the entry of u in v's V-side row; its
+// count is the sum of the two entries' counts
+__global__ void k_pe_out(DevGraph G, const unsigned long long *peU,
+                         const unsigned long long *peV, int64_t *out) {
+    const SideCSR &U = G.side[0];
+    const SideCSR &V = G.side[1];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < G.nE;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = G.nU;  // last u with rowptr[u] <= e
+        while (hi - lo > 1) {
+            const int64_t m = (lo + hi) >> 1;
+            if (G.rowptr[m] <= e) lo = m; else hi = m;
+        }
+        const uint32_t ru = U.sr_of_id[lo];
+        const uint32_t rv = V.sr_of_id[G.col[e]];
+        const int64_t p = lower_bound_u32(U.adj, U.off[ru], U.off[ru + 1], rv << 1);
+        const int64_t q = lower_bound_u32(V.adj, V.off[rv], V.off[rv + 1], ru << 1);
+        out[e] = (int64_t)(peU[p] + peV[q]);
     }
 }
 
@@ -187,9 +237,7 @@ __global__ void k_pv_out(SideCSR S, int64_t base, int64_t *out) {
 
 int g_pv_blocks = 0, g_pv_device = -1;
 
-}  // namespace
-
-void launch_per_vertex(const DevGraph &g, int64_t *out_dev, cudaStream_t s) {
+void pv_init() {
     int dev = 0;
     cudaGetDevice(&dev);
     if (g_pv_device != dev) {
@@ -201,11 +249,31 @@ void launch_per_vertex(const DevGraph &g, int64_t *out_dev, cudaStream_t s) {
         g_pv_blocks = std::max(1, b) * prop.multiProcessorCount;
         g_pv_device = dev;
     }
+}
+
+}  // namespace
+
+void launch_per_edge(const DevGraph &g, int64_t *out_dev, unsigned long long *pe_ws,
+                     cudaStream_t s) {
+    pv_init();
+    if (g.nE == 0) return;
+    unsigned long long *peU = pe_ws, *peV = pe_ws + g.nE;
+    cudaMemsetAsync(pe_ws, 0, (size_t)g.nE * 16, s);
+    cudaMemsetAsync(&g.scratch->job_next[JOB_PER_VERTEX], 0, 4, s);  // job cursor
+    PvOut o{0, {peU, peV}};
+    k_pv<<<g_pv_blocks, PV_THREADS, sizeof(PvSmem), s>>>(g, o); note_launch();
+    const int64_t blocks = std::min<int64_t>((g.nE + 255) / 256, 16384);
+    k_pe_out<<<(unsigned)blocks, 256, 0, s>>>(g, peU, peV, out_dev); note_launch();
+}
+
+void launch_per_vertex(const DevGraph &g, int64_t *out_dev, cudaStream_t s) {
+    pv_init();
     for (int sd = 0; sd < 2; sd++)
         if (g.side[sd].n > 0)
             cudaMemsetAsync(g.side[sd].pv, 0, (size_t)g.side[sd].n * 8, s);
-    // the job cursor lives in the count scratch; launch_count has zeroed it
-    k_pv<<<g_pv_blocks, PV_THREADS, sizeof(PvSmem), s>>>(g); note_launch();
+    cudaMemsetAsync(&g.scratch->job_next[JOB_PER_VERTEX], 0, 4, s);  // job cursor
+    PvOut o{1, {nullptr, nullptr}};
+    k_pv<<<g_pv_blocks, PV_THREADS, sizeof(PvSmem), s>>>(g, o); note_launch();
     for (int sd = 0; sd < 2; sd++) {
         const int64_t n = g.side[sd].n;
         if (n == 0) continue;

@@ -40,6 +40,8 @@ struct bb_ctx {
     size_t ws_in_cap = 0;
     int64_t *ws_pv = nullptr;  // device per-vertex output for host requests
     size_t ws_pv_cap = 0;
+    void *ws_pe = nullptr;     // per-edge output and entry accumulators
+    size_t ws_pe_cap = 0;
     bb::DevGraph oneshot;
     int64_t layout_key[3] = {-1, -1, -1};
     bb::HostResult *h_res = nullptr;  // pinned

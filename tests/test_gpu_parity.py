@@ -349,3 +349,69 @@ def test_per_vertex_full_size_sampled(ctx, name, make):
     assert np.array_equal(c.per_vertex[ids], np.array(rec["per_vertex"]))
     assert c.per_vertex[: g.nU].sum() == 2 * c.balanced
     assert c.per_vertex[g.nU:].sum() == 2 * c.balanced
+
+
+# ------------------------------------------------------------- per edge
+@pytest.mark.parametrize("make", [
+    lambda: synth.uniform_2k_1k(),
+    lambda: synth.chung_lu_scaled(41, 200_000),
+    lambda: synth.vote(7, 40, 3_000, 0.4, 2, 0.55, 0.8),
+    lambda: synth.from_dense(np.ones((5, 7), dtype=np.int8)),
+])
+def test_per_edge_matches_oracle(ctx, make):
+    g = make()
+    r = ctx.upload(g)
+    pe, b, t = r.count_edges()
+    want = oracle.per_edge(g, threads=8)
+    assert np.array_equal(pe, want), g.name
+    assert (b, t) == oracle.count(g, threads=4)
+    assert int(pe.sum()) == 4 * b
+    # after sign flips of 1 % of the edges, and back
+    idx = np.random.default_rng(3).choice(g.nE, max(1, g.nE // 100), replace=False)
+    r.flip(idx)
+    s = g.sign.copy()
+    s[idx] = -s[idx]
+    h = synth.SignedBipartite(g.nU, g.nV, g.rowptr, g.col, s, g.name + "/f")
+    assert np.array_equal(r.count_edges()[0], oracle.per_edge(h, threads=8))
+    r.flip(idx)
+    assert np.array_equal(r.count_edges()[0], want)
+    r.free()
+
+
+def test_per_edge_tiny_and_degenerate(ctx):
+    for signs in ([1, 1, 1, 1], [1, -1, 1, 1], [-1, -1, 1, 1]):
+        g = synth.from_edges(2, 2, [0, 1, 0, 1], [0, 0, 1, 1], signs)
+        r = ctx.upload(g)
+        assert np.array_equal(r.count_edges()[0], oracle.per_edge(g))
+        r.free()
+    for g in (synth.from_edges(3, 4, [], [], []), synth.from_edges(1, 5, [0] * 5, range(5), [1] * 5)):
+        r = ctx.upload(g)
+        pe, b, t = r.count_edges()
+        assert pe.size == g.nE and not pe.any() and (b, t) == (0, 0)
+        r.free()
+    for seed in range(20):
+        rng = np.random.default_rng(seed)
+        nU, nV = int(rng.integers(2, 12)), int(rng.integers(2, 12))
+        g = synth.uniform(4000 + seed, nU, nV, int(rng.integers(0, nU * nV + 1)), 0.5)
+        r = ctx.upload(g)
+        assert np.array_equal(r.count_edges()[0], oracle.per_edge(g)), seed
+        r.free()
+
+
+@pytest.mark.parametrize("name,make", [("chunglu_2Mx500k_e20M_a2.1_p0.8", "chung_lu_2m"),
+                                       ("vote_500x50000_p0.4_b2", "vote_500_50k")])
+def test_per_edge_full_size_sampled(ctx, name, make):
+    g = getattr(synth, make)()
+    r = ctx.upload(g)
+    pe, b, t = r.count_edges()
+    want = EXPECTED[name]
+    assert (b, t) == (want["balanced"], want["total"])
+    assert int(pe.sum()) == 4 * b
+    # sampled edges against the oracle, including the edges of the densest rows
+    rng = np.random.default_rng(11)
+    deg = np.diff(g.rowptr)
+    hub = int(np.argmax(deg))
+    idx = np.concatenate([rng.choice(g.nE, 60, replace=False),
+                          np.arange(g.rowptr[hub], g.rowptr[hub] + 5)])
+    assert np.array_equal(pe[idx], oracle.per_edge(g, idx, threads=16))
+    r.free()
