@@ -84,18 +84,31 @@ __global__ void __launch_bounds__(PV_THREADS) k_pv(DevGraph G, PvOut out) {
     PvSmem &sm = *reinterpret_cast<PvSmem *>(smem_raw);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = PV_THREADS / 32;
     uint32_t *err = &G.scratch->err;
-    const int64_t nA = G.nU + G.nV;
+    // anchors of the team, CTA-hash and dense classes (warp-class anchors
+    // go to k_pv_warp); a split dense anchor is taken once, at its first part
+    const uint32_t nT = G.ctr[CTR_TEAM], nC = G.ctr[CTR_CTAH], nD = G.ctr[CTR_DENSE];
+    const uint32_t nJ = nT + nC + nD;
     for (;;) {
         if (t == 0) sm.job = atomicAdd(&G.scratch->job_next[JOB_PER_VERTEX], 1u);
         __syncthreads();
-        const int64_t a = sm.job;
+        const uint32_t jb = sm.job;
         __syncthreads();
-        if (a >= nA) break;
-        const int sd = a < G.nU ? 0 : 1;
+        if (jb >= nJ) break;
+        uint32_t packed;
+        if (jb < nT) {
+            packed = G.team_list[jb].anchor;
+        } else if (jb < nT + nC) {
+            packed = G.ctah_list[jb - nT].anchor;
+        } else {
+            const DenseJob &J = G.dense_jobs[jb - nT - nC];
+            if (J.m0 != 0) continue;
+            packed = J.anchor;
+        }
+        const int sd = (int)(packed & 1u);
         const SideCSR &S = sd ? G.side[1] : G.side[0];
         const SideCSR &O = sd ? G.side[0] : G.side[1];
         unsigned long long *peS = out.pe[sd], *peO = out.pe[1 - sd];
-        const uint32_t r = (uint32_t)(sd ? a - G.nU : a);
+        const uint32_t r = packed >> 1;
         const uint64_t W = S.work[r];
         if (W == 0) continue;
         const int64_t rb = S.off[r];
@@ -206,6 +219,132 @@ __global__ void __launch_bounds__(PV_THREADS) k_pv(DevGraph G, PvOut out) {
     }
 }
 
+// Warp-class anchors (degree <= 255, at most WARP_W_MAX wedges), one per
+// warp, with the count's counter layout: the hub window in 16-bit fields
+// (S in bits 0..7, A in bits 8..15) and a 256-slot hash for the endpoints
+// below it (every endpoint when the anchor has at most WARP_SMALL_W
+// wedges). Pass 1 tallies, pass 2 walks each middle's suffix reading the
+// final tallies, then the pairs' C(S,2) + C(A,2) go to both endpoints.
+constexpr int PVW_THREADS = 256;
+constexpr uint32_t PVW_CAP = 256;
+
+struct alignas(16) PvWarpSmem {
+    uint32_t win[HUB_WINDOW / 2];
+    unsigned long long tab[PVW_CAP];
+};
+
+__global__ void __launch_bounds__(PVW_THREADS) k_pv_warp(DevGraph G, PvOut out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PvWarpSmem &sm = reinterpret_cast<PvWarpSmem *>(smem_raw)[threadIdx.x >> 5];
+    const unsigned lane = lane_id();
+    uint32_t *err = &G.scratch->err;
+    for (uint32_t i = lane; i < HUB_WINDOW / 2; i += 32) sm.win[i] = 0;
+    for (uint32_t i = lane; i < PVW_CAP; i += 32) sm.tab[i] = 0ull;
+    __syncwarp();
+    const uint32_t n = G.ctr[CTR_WARP];
+    const uint32_t gw = (blockIdx.x * PVW_THREADS + threadIdx.x) >> 5;
+    const uint32_t GW = (gridDim.x * PVW_THREADS) >> 5;
+    for (uint32_t idx = gw; idx < n; idx += GW) {
+        const AnchorRec rec = G.warp_list[idx];
+        const int sd = (int)(rec.anchor & 1u);
+        const SideCSR &S = sd ? G.side[1] : G.side[0];
+        const SideCSR &O = sd ? G.side[0] : G.side[1];
+        unsigned long long *peS = out.pe[sd], *peO = out.pe[1 - sd];
+        const uint32_t r = rec.anchor >> 1, deg = rec.deg;
+        const int64_t rb = rec.rb;
+        const uint64_t W = rec.W;
+        const uint64_t above = (uint64_t)(S.n - r - 1);
+        const bool all_hash = W <= WARP_SMALL_W;
+        const uint32_t wb = S.n > (int64_t)HUB_WINDOW ? (uint32_t)(S.n - HUB_WINDOW) : 0u;
+        const uint64_t above_nh = wb > r + 1 ? (uint64_t)wb - r - 1 : 0;
+        uint64_t need = all_hash ? (W < above ? W : above) : (rec.wnh < above_nh ? rec.wnh : above_nh);
+        uint32_t cap = 32, shift = 27;
+        while ((uint64_t)cap < 2 * need + 1 && cap < PVW_CAP) { cap <<= 1; shift--; }
+        const uint32_t mask = cap - 1;
+        uint32_t wmin = HUB_WINDOW;
+        // endpoint u (side rank) -> its window index, or HUB_WINDOW if hashed
+        auto win_index = [&](uint32_t u) -> uint32_t {
+            if (all_hash || u < wb) return HUB_WINDOW;
+            const uint32_t wi = u - wb;
+            if (wi >= HUB_WINDOW) { set_error(err, E_INTERNAL); return HUB_WINDOW; }
+            return wi;
+        };
+        // pass 1: tallies
+        for (uint32_t j = 0; j < deg; j++) {
+            const uint4 d = S.md[rb + j];
+            for (uint32_t p = d.x + lane; p < d.z; p += 32) {
+                const uint32_t x = O.adj[p];
+                const uint32_t u = x >> 1, asym = (x ^ d.w) & 1u;
+                const uint32_t wi = win_index(u);
+                if (wi < HUB_WINDOW) {
+                    wmin = wi < wmin ? wi : wmin;
+                    atomicAdd(&sm.win[wi >> 1], (1u + asym * 255u) << ((wi & 1u) << 4));
+                } else {
+                    pv_hash_add(sm.tab, shift, mask, u + 1, asym ? INC_ASYM : INC_SYM, err);
+                }
+            }
+        }
+        __syncwarp();
+        // pass 2: a middle of type t lies in cnt_t - 1 balanced butterflies of
+        // each of its pairs, and so do the edges w-v and v-u
+        for (uint32_t j = 0; j < deg; j++) {
+            const uint4 d = S.md[rb + j];
+            unsigned long long msum = 0;
+            for (uint32_t p = d.x + lane; p < d.z; p += 32) {
+                const uint32_t x = O.adj[p];
+                const uint32_t u = x >> 1, asym = (x ^ d.w) & 1u;
+                const uint32_t wi = win_index(u);
+                uint32_t ct;
+                if (wi < HUB_WINDOW) {
+                    const uint32_t c = (sm.win[wi >> 1] >> ((wi & 1u) << 4)) & 0xffffu;
+                    ct = asym ? (c >> 8) : (c & 0xffu);
+                } else {
+                    const uint32_t c = pv_hash_find(sm.tab, shift, mask, u + 1, err);
+                    ct = asym ? (c >> 16) : (c & 0xffffu);
+                }
+                const unsigned long long k = ct > 0 ? ct - 1 : 0;
+                msum += k;
+                if (peO && k) atomicAdd(&peO[p], k);  // edge v-u
+            }
+            msum = warp_sum_u64(msum);
+            if (lane == 0 && msum) {
+                const uint32_t v = S.adj[rb + j] >> 1;
+                if (out.vertex) atomicAdd(&O.pv[v], msum);
+                if (peS) atomicAdd(&peS[rb + j], msum);  // edge w-v
+            }
+        }
+        __syncwarp();
+        // pairs: C(S,2) + C(A,2) to the endpoint and (summed) to the anchor;
+        // the counters are reset as they are read
+        const uint32_t first = __reduce_min_sync(FULL, wmin) >> 1;  // word index
+        unsigned long long wsum = 0;
+        for (uint32_t q = first + lane; q < HUB_WINDOW / 2; q += 32) {
+            const uint32_t word = sm.win[q];
+            if (!word) continue;
+            sm.win[q] = 0;
+            if (!out.vertex) continue;
+#pragma unroll
+            for (uint32_t h = 0; h < 2; h++) {
+                const uint32_t c = (word >> (16 * h)) & 0xffffu;
+                const unsigned long long b = c2(c & 0xffu) + c2(c >> 8);
+                if (b) { atomicAdd(&S.pv[wb + 2 * q + h], b); wsum += b; }
+            }
+        }
+        for (uint32_t i = lane; i < cap; i += 32) {
+            const unsigned long long x = sm.tab[i];
+            if (!x) continue;
+            sm.tab[i] = 0ull;
+            if (!out.vertex) continue;
+            const uint32_t c = (uint32_t)x;
+            const unsigned long long b = c2(c & 0xffffu) + c2(c >> 16);
+            if (b) { atomicAdd(&S.pv[(uint32_t)(x >> 32) - 1u], b); wsum += b; }
+        }
+        wsum = warp_sum_u64(wsum);
+        if (lane == 0 && wsum) atomicAdd(&S.pv[r], wsum);
+        __syncwarp();
+    }
+}
+
 // per-edge counts in the caller's edge order: an input edge (u, v) is the
 // entry of v in u's U-side row and the entry of u in v's V-side row; its
 // count is the sum of the two entries' counts
@@ -235,7 +374,8 @@ __global__ void k_pv_out(SideCSR S, int64_t base, int64_t *out) {
         out[base + S.id_of_sr[r]] = (int64_t)S.pv[r];
 }
 
-int g_pv_blocks = 0, g_pv_device = -1;
+int g_pv_blocks = 0, g_pvw_blocks = 0, g_pv_device = -1;
+constexpr size_t PVW_SMEM = (PVW_THREADS / 32) * sizeof(PvWarpSmem);
 
 void pv_init() {
     int dev = 0;
@@ -247,6 +387,10 @@ void pv_init() {
         int b = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pv, PV_THREADS, sizeof(PvSmem));
         g_pv_blocks = std::max(1, b) * prop.multiProcessorCount;
+        cudaFuncSetAttribute(k_pv_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PVW_SMEM);
+        b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pv_warp, PVW_THREADS, PVW_SMEM);
+        g_pvw_blocks = std::max(1, b) * prop.multiProcessorCount;
         g_pv_device = dev;
     }
 }
@@ -261,6 +405,7 @@ void launch_per_edge(const DevGraph &g, int64_t *out_dev, unsigned long long *pe
     cudaMemsetAsync(pe_ws, 0, (size_t)g.nE * 16, s);
     cudaMemsetAsync(&g.scratch->job_next[JOB_PER_VERTEX], 0, 4, s);  // job cursor
     PvOut o{0, {peU, peV}};
+    k_pv_warp<<<g_pvw_blocks, PVW_THREADS, PVW_SMEM, s>>>(g, o); note_launch();
     k_pv<<<g_pv_blocks, PV_THREADS, sizeof(PvSmem), s>>>(g, o); note_launch();
     const int64_t blocks = std::min<int64_t>((g.nE + 255) / 256, 16384);
     k_pe_out<<<(unsigned)blocks, 256, 0, s>>>(g, peU, peV, out_dev); note_launch();
@@ -273,6 +418,7 @@ void launch_per_vertex(const DevGraph &g, int64_t *out_dev, cudaStream_t s) {
             cudaMemsetAsync(g.side[sd].pv, 0, (size_t)g.side[sd].n * 8, s);
     cudaMemsetAsync(&g.scratch->job_next[JOB_PER_VERTEX], 0, 4, s);  // job cursor
     PvOut o{1, {nullptr, nullptr}};
+    k_pv_warp<<<g_pvw_blocks, PVW_THREADS, PVW_SMEM, s>>>(g, o); note_launch();
     k_pv<<<g_pv_blocks, PV_THREADS, sizeof(PvSmem), s>>>(g, o); note_launch();
     for (int sd = 0; sd < 2; sd++) {
         const int64_t n = g.side[sd].n;
