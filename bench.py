@@ -617,7 +617,7 @@ def main():
     ap.add_argument("--batch-single-steps", type=int, default=2)
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests per rate in the serving leg (0 = skip the leg)")
-    ap.add_argument("--serve-rates", default="25,50,100,200", help="arrival rates, req/s")
+    ap.add_argument("--serve-rates", default="50,200,400,800", help="arrival rates, req/s")
     ap.add_argument("--serve-pool", type=int, default=24)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--ref-stride", type=int, default=64,

@@ -464,10 +464,15 @@ __global__ void k_classify(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
     for (int k = threadIdx.x; k < NCLS * NB; k += blockDim.x) cnt[k] = 0;
     if (threadIdx.x < 3 * NCLS) stats[threadIdx.x] = 0;
     __syncthreads();
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < S.n;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t W = S.work[r];
-        uint32_t meta = 0;
+    unsigned long long my_w[NCLS] = {}, my_m[NCLS] = {};
+    uint32_t my_a[NCLS] = {};
+    // warp-uniform trip counts (the bucket counts are aggregated per warp)
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < S.n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = base + threadIdx.x;
+        const bool in = r < S.n;
+        uint64_t W = in ? S.work[r] : 0;
+        uint32_t meta = 0, key = 0xffffffffu, nparts = 0;
         if (W > 0) {
             const uint64_t above = (uint64_t)(S.n - r - 1);
             const uint64_t wb = S.n > (int64_t)HUB_WINDOW ? (uint64_t)S.n - HUB_WINDOW : 0;
@@ -504,12 +509,30 @@ __global__ void k_classify(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
             }
             uint32_t b = bucket_of(parts > 1 ? W / parts : W);
             meta = 1u | cls << 1 | b << 3 | parts << 9;
-            atomicAdd(&cnt[cls * NB + b], parts);
-            atomicAdd(&stats[cls], (unsigned long long)W);
-            atomicAdd(&stats[NCLS + cls], (unsigned long long)(S.off[r + 1] - S.off[r]));
-            atomicAdd(&stats[2 * NCLS + cls], 1ull);
+            key = cls * NB + b;
+            nparts = parts;
+            my_w[cls] += W;
+            my_m[cls] += (unsigned long long)(S.off[r + 1] - S.off[r]);
+            my_a[cls] += 1;
         }
-        T.meta[r] = meta;
+        if (in) T.meta[r] = meta;
+        // one shared atomic per distinct bucket in the warp
+        const unsigned peers = __match_any_sync(FULL, key);
+        const uint32_t total = __reduce_add_sync(peers, nparts);
+        if (key != 0xffffffffu && (peers & ((1u << lane_id()) - 1u)) == 0)
+            atomicAdd(&cnt[key], total);
+    }
+    // per-class work: summed per thread, then per warp, then one shared atomic
+    // per warp (all threads updating the same few counters serialises)
+#pragma unroll
+    for (int c = 0; c < NCLS; c++) {
+        const unsigned long long w = warp_sum_u64(my_w[c]), m = warp_sum_u64(my_m[c]);
+        const uint32_t a = __reduce_add_sync(FULL, my_a[c]);
+        if (lane_id() == 0) {
+            if (w) atomicAdd(&stats[c], w);
+            if (m) atomicAdd(&stats[NCLS + c], m);
+            if (a) atomicAdd(&stats[2 * NCLS + c], (unsigned long long)a);
+        }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < NCLS * NB; k += blockDim.x)
