@@ -318,6 +318,14 @@ def run_ours(args, world, rank, local_rank):
         opt["count_per_edge_ms"], cpe = timed(lambda: res.count_edges())
         # every balanced butterfly has four vertices and four edges
         assert int(cpv.per_vertex.sum()) == 4 * c.balanced and int(cpe[0].sum()) == 4 * c.balanced
+        # re-queries after sign flips: few flips take the incremental walk
+        res.count()
+        frng = np.random.default_rng(7)
+        for k in (10, 1000, g.nE // 100):
+            lists = iter([frng.choice(g.nE, k, replace=False) for _ in range(4)])
+            ms, out = timed(lambda: res.count_flipped(next(lists)))
+            opt[f"count_flipped_{k}_ms"] = ms
+            opt[f"count_flipped_{k}_incremental"] = out[2]
         opt["timing"] = "host wall clock around the blocking call, best of 3, L2 flushed before"
         res.free()
 

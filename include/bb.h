@@ -135,6 +135,18 @@ BB_API bb_status bb_count(bb_graph *g, int64_t *balanced, int64_t *total, int64_
 BB_API bb_status bb_count_edges(bb_graph *g, int64_t *per_edge, int64_t *balanced_opt,
                                 int64_t *total_opt);
 
+/* Flip the signs of the listed input edges (indices into the CSR's col
+ * array; an index listed twice flips back) and return the graph's counts
+ * after the flips. When the counts before the flips are known (the graph
+ * was counted since its last plain bb_graph_flip_signs) and the butterflies
+ * through the flipped edges are cheaper to enumerate than the whole graph's
+ * wedges, only those are walked: a butterfly with an odd number of flipped
+ * edges changes balance, the others do not (incremental re-count; the paper
+ * has no counterpart beyond its edge-level extension). Otherwise the graph
+ * is recounted. *incremental_opt tells which was done. Blocking. */
+BB_API bb_status bb_count_flipped(bb_graph *g, const int64_t *edge_idx, int64_t n,
+                                  int64_t *balanced, int64_t *total, int *incremental_opt);
+
 /* Negate the sign of the listed input edges (indices into the CSR's col
  * array, host int64[n]) in the resident graph, both directions. Repeated
  * indices flip repeatedly. Later counts see the new signs. */
@@ -271,7 +283,9 @@ BB_API void bb_batch_free(bb_batch *b);
  *   until the ticket is done) into the arena, evicting the least recently
  *   used idle graphs as needed; a key in the cache is counted in place,
  *   after flipping the signs of the listed input edges (host int64
- *   indices, borrowed likewise; the flips stay). csr may be NULL when the
+ *   indices, borrowed likewise; the flips stay); a small flip set on a graph
+ *   whose counts are known is re-counted through the flipped edges only,
+ *   as in bb_count_flipped. csr may be NULL when the
  *   caller knows the key is resident (the request fails with
  *   BB_ERR_INVALID_ARG if it is not). A graph larger than the arena fails
  *   with BB_ERR_BUDGET. flags: 0, or BB_REQ_NO_CACHE to drop the graph
@@ -301,6 +315,7 @@ typedef struct {
     int64_t resident_graphs;
     uint64_t arena_bytes, arena_used, arena_largest_free;
     int64_t queued, running;
+    int64_t incremental;   /* re-queries counted through their flipped edges only */
 } bb_serve_stats;
 
 BB_API bb_status bb_ctx_serve(bb_ctx *ctx, int slots, uint64_t arena_bytes);

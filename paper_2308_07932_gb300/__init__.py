@@ -82,7 +82,7 @@ class _ServeStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "cache_hits",
                                               "uploads", "evictions", "resident_graphs")] + \
                [(n, ctypes.c_uint64) for n in ("arena_bytes", "arena_used", "arena_largest_free")] + \
-               [(n, ctypes.c_int64) for n in ("queued", "running")]
+               [(n, ctypes.c_int64) for n in ("queued", "running", "incremental")]
 
 
 REQ_NO_CACHE = 1
@@ -115,6 +115,8 @@ def lib() -> ctypes.CDLL:
             "bb_count": (S, [_VP, _I64P, _I64P, _VP]),
             "bb_graph_flip_signs": (S, [_VP, _VP, ctypes.c_int64]),
             "bb_count_edges": (S, [_VP, _VP, _I64P, _I64P]),
+            "bb_count_flipped": (S, [_VP, _VP, ctypes.c_int64, _I64P, _I64P,
+                                     ctypes.POINTER(ctypes.c_int)]),
             "bb_graph_info": (S, [_VP, _I64P, _I64P, _I64P, _I64P]),
             "bb_graph_free": (None, [_VP]),
             "bb_ctx_set_timing": (S, [_VP, ctypes.c_int]),
@@ -380,6 +382,15 @@ class Graph:
         b, t = ctypes.c_int64(), ctypes.c_int64()
         _check(lib().bb_count_edges(self._h, pe.ctypes.data, ctypes.byref(b), ctypes.byref(t)))
         return pe[:nE], b.value, t.value
+
+    def count_flipped(self, edge_idx) -> tuple[int, int, bool]:
+        """Flip the listed edges' signs and return (balanced, total,
+        incremental) after the flips (``bb_count_flipped``)."""
+        e = np.ascontiguousarray(edge_idx, dtype=np.int64)
+        b, t, inc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        _check(lib().bb_count_flipped(self._h, e.ctypes.data, e.size, ctypes.byref(b),
+                                      ctypes.byref(t), ctypes.byref(inc)))
+        return b.value, t.value, bool(inc.value)
 
     def flip(self, edge_idx):
         e = np.ascontiguousarray(edge_idx, dtype=np.int64)

@@ -11,6 +11,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <vector>
 
 #include "runtime.h"
 
@@ -287,6 +288,7 @@ void bb_ctx_destroy(bb_ctx *ctx) {
     dev_free(ctx, ctx->ws_in, ctx->ws_in_cap);
     dev_free(ctx, ctx->ws_pv, ctx->ws_pv_cap);
     dev_free(ctx, ctx->ws_pe, ctx->ws_pe_cap);
+    dev_free(ctx, ctx->ws_flip, ctx->ws_flip_cap);
     if (ctx->h_res) cudaFreeHost(ctx->h_res);
     for (int k = 0; k < NEV; k++)
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
@@ -471,6 +473,11 @@ bb_status bb_count(bb_graph *G, int64_t *balanced, int64_t *total, int64_t *per_
     if (pv_dev) launch_per_vertex(G->g, pv_dev, ctx->stream);
     BB_CUDA(cudaGetLastError(), "count launch");
     st = finish_count(ctx, G->g, ctx->stream, balanced, total, nullptr);
+    if (st == BB_OK) {
+        G->have_counts = true;
+        G->last_balanced = *balanced;
+        G->last_total = *total;
+    }
     if (st != BB_OK || !pv_dev) return st;
     BB_CUDA(cudaMemcpyAsync(per_vertex_opt, pv_dev, (size_t)(G->g.nU + G->g.nV) * 8,
                             cudaMemcpyDeviceToHost, ctx->stream), "copy per-vertex");
@@ -499,6 +506,9 @@ bb_status bb_count_edges(bb_graph *G, int64_t *per_edge, int64_t *balanced_opt,
     int64_t b = 0, t = 0;
     st = finish_count(ctx, G->g, s, &b, &t, nullptr);
     if (st != BB_OK) return st;
+    G->have_counts = true;
+    G->last_balanced = b;
+    G->last_total = t;
     if (nE > 0)
         BB_CUDA(cudaMemcpyAsync(per_edge, out_dev, (size_t)nE * 8, cudaMemcpyDeviceToHost, s),
                 "copy per-edge");
@@ -506,6 +516,93 @@ bb_status bb_count_edges(bb_graph *G, int64_t *per_edge, int64_t *balanced_opt,
     if (st != BB_OK) return st;
     if (balanced_opt) *balanced_opt = b;
     if (total_opt) *total_opt = t;
+    return BB_OK;
+}
+
+bb_status bb_count_flipped(bb_graph *G, const int64_t *edge_idx, int64_t n, int64_t *balanced,
+                           int64_t *total, int *incremental_opt) {
+    if (!G || !balanced || !total || n < 0 || (n > 0 && !edge_idx))
+        return fail(BB_ERR_INVALID_ARG, "bad argument");
+    const int64_t nE = G->g.nE;
+    for (int64_t i = 0; i < n; i++)
+        if (edge_idx[i] < 0 || edge_idx[i] >= nE)
+            return fail(BB_ERR_INVALID_ARG, "edge index %lld outside [0, %lld)",
+                        (long long)edge_idx[i], (long long)nE);
+    // An edge listed twice flips back. The incremental walk needs each
+    // flipped edge once (the edges listed an odd number of times); a recount
+    // takes the list as it is. Sets of more than nE/1024 flips are always
+    // recounted: on power-law graphs their enumeration exceeds a recount.
+    const bool small = n <= nE / 1024;
+    std::vector<int64_t> odd;
+    if (small) {
+        std::vector<int64_t> list(edge_idx, edge_idx + n);
+        std::sort(list.begin(), list.end());
+        for (size_t i = 0; i < list.size();) {
+            size_t j = i;
+            while (j < list.size() && list[j] == list[i]) j++;
+            if ((j - i) & 1) odd.push_back(list[i]);
+            i = j;
+        }
+    }
+    const int64_t m = small ? (int64_t)odd.size() : n;
+    const int64_t *flips_host = small ? odd.data() : edge_idx;
+    bb_ctx *ctx = G->ctx;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    bb_status st = set_device(ctx);
+    if (st != BB_OK) return st;
+    ctx->have_build_ev = false;
+    cudaStream_t s = ctx->stream;
+    const size_t b_list = ((size_t)(m > 0 ? m : 1) * 8 + 255) & ~(size_t)255;
+    st = ensure(ctx, &ctx->ws_flip, &ctx->ws_flip_cap, b_list + 256 + flip_ws_bytes(nE, m),
+                "flip workspace");
+    if (st != BB_OK) return st;
+    int64_t *d_list = (int64_t *)ctx->ws_flip;
+    unsigned long long *d_acc = (unsigned long long *)((char *)ctx->ws_flip + b_list);  // cost, up, down
+    void *ws = (char *)ctx->ws_flip + b_list + 256;
+    if (m > 0)
+        BB_CUDA(cudaMemcpyAsync(d_list, flips_host, (size_t)m * 8, cudaMemcpyHostToDevice, s),
+                "copy flip list");
+    // Enumeration steps (a binary search each, at random places) cost about
+    // 16 to 20 times a wedge of the full count on the 2M x 500k graph.
+    bool incremental = false;
+    if (G->have_counts && m > 0 && small) {
+        launch_flip_estimate(G->g, d_list, m, ws, d_acc, s);
+        BB_CUDA(cudaGetLastError(), "flip estimate");
+        BB_CUDA(cudaMemcpyAsync(ctx->h_res->acc, d_acc, 8, cudaMemcpyDeviceToHost, s), "copy estimate");
+        if ((st = wait_bounded(s, "flip estimate")) != BB_OK) return st;
+        incremental = ctx->h_res->acc[0] <= G->g.h_wedges / 16;
+    }
+    G->have_counts = G->have_counts && (incremental || m == 0);
+    if (incremental) {
+        launch_flip_delta(G->g, m, ws, d_acc + 1, s);
+        BB_CUDA(cudaGetLastError(), "flip delta");
+        BB_CUDA(cudaMemcpyAsync(ctx->h_res->acc + 1, d_acc + 1, 16, cudaMemcpyDeviceToHost, s),
+                "copy delta");
+    }
+    if (m > 0) {
+        launch_flip(G->g, d_list, m, s);
+        BB_CUDA(cudaGetLastError(), "sign flip");
+    }
+    if (incremental || (G->have_counts && m == 0)) {
+        if ((st = wait_bounded(s, "incremental count")) != BB_OK) return st;
+        if (incremental) {
+            const unsigned long long up = ctx->h_res->acc[1], down = ctx->h_res->acc[2];
+            const long long d3 = (long long)up - (long long)down;
+            if (d3 % 3 != 0) return fail(BB_ERR_CUDA, "internal check failed (weighted change %lld)", d3);
+            G->last_balanced += d3 / 3;
+        }
+    } else {
+        int64_t b = 0, t = 0;
+        launch_count(G->g, s, nullptr, ctx->timing ? ctx->ev + 2 : nullptr);
+        BB_CUDA(cudaGetLastError(), "count launch");
+        if ((st = finish_count(ctx, G->g, s, &b, &t, nullptr)) != BB_OK) return st;
+        G->have_counts = true;
+        G->last_balanced = b;
+        G->last_total = t;
+    }
+    *balanced = G->last_balanced;
+    *total = G->last_total;
+    if (incremental_opt) *incremental_opt = incremental ? 1 : 0;
     return BB_OK;
 }
 
@@ -520,6 +617,7 @@ bb_status bb_graph_flip_signs(bb_graph *G, const int64_t *edge_idx, int64_t n) {
     std::lock_guard<std::mutex> lk(ctx->mu);
     bb_status st = set_device(ctx);
     if (st != BB_OK) return st;
+    G->have_counts = false;
     void *d = nullptr;
     st = dev_alloc(ctx, &d, (size_t)n * 8, "flip list");
     if (st != BB_OK) return st;

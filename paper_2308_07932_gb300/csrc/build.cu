@@ -108,21 +108,36 @@ __global__ void k_global_rank(SideCSR S, const uint32_t *other_deg, int64_t n_ot
 __global__ void k_fill(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                        const int8_t *__restrict__ sign, int64_t nU, int64_t nE, SideCSR U,
                        SideCSR V, uint32_t *cursorV, uint64_t *keyU, uint64_t *keyV) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nE;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t lo = 0, hi = nU;  // last u with rowptr[u] <= e
-        while (hi - lo > 1) {
-            const int64_t m = (lo + hi) >> 1;
-            if (rowptr[m] <= e) lo = m; else hi = m;
+    // warp-uniform trip counts: lanes that share a V row take their slots
+    // in it with one atomic (hub rows would otherwise serialise on it)
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nE;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = base + threadIdx.x;
+        const bool in = e < nE;
+        uint32_t rv = 0xffffffffu, r = 0, neg = 0;
+        if (in) {
+            int64_t lo = 0, hi = nU;  // last u with rowptr[u] <= e
+            while (hi - lo > 1) {
+                const int64_t m = (lo + hi) >> 1;
+                if (rowptr[m] <= e) lo = m; else hi = m;
+            }
+            r = U.sr_of_id[lo];
+            const int64_t pu = U.off[r] + (e - rowptr[lo]);
+            const uint32_t v = (uint32_t)col[e];
+            neg = sign[e] < 0 ? 1u : 0u;
+            rv = V.sr_of_id[v];
+            keyU[pu] = ((uint64_t)((rv << 1) | neg) << 32) | (uint32_t)e;
         }
-        const uint32_t r = U.sr_of_id[lo];
-        const int64_t pu = U.off[r] + (e - rowptr[lo]);
-        const uint32_t v = (uint32_t)col[e];
-        const uint32_t neg = sign[e] < 0 ? 1u : 0u;
-        const uint32_t rv = V.sr_of_id[v];
-        keyU[pu] = ((uint64_t)((rv << 1) | neg) << 32) | (uint32_t)e;
-        const int64_t pv = V.off[rv] + atomicAdd(&cursorV[rv], 1u);
-        keyV[pv] = ((uint64_t)((r << 1) | neg) << 32) | (uint32_t)e;
+        const unsigned peers = __match_any_sync(FULL, rv);
+        const unsigned lane = lane_id();
+        const int leader = __ffs(peers) - 1;
+        uint32_t b = 0;
+        if (in && (int)lane == leader) b = atomicAdd(&cursorV[rv], (uint32_t)__popc(peers));
+        b = __shfl_sync(peers, b, leader);
+        if (in) {
+            const int64_t pv = V.off[rv] + b + __popc(peers & ((1u << lane) - 1u));
+            keyV[pv] = ((uint64_t)((r << 1) | neg) << 32) | (uint32_t)e;
+        }
     }
 }
 

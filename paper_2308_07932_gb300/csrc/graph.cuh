@@ -179,6 +179,19 @@ void launch_per_vertex(const DevGraph &g, int64_t *out_dev, cudaStream_t s);
 void launch_per_edge(const DevGraph &g, int64_t *out_dev, unsigned long long *pe_ws,
                      cudaStream_t s);
 
+// Incremental re-count under sign flips (flips.cu). The workspace of
+// flip_ws_bytes(nE, n) holds the located edges and two flag bitmaps.
+// launch_flip_estimate locates the n listed input edges (distinct), marks
+// them and writes the enumeration cost to cost_dev; launch_flip_delta then
+// writes the weighted changes to acc_dev[0] (up) and acc_dev[1] (down):
+// the balanced count changes by (up - down) / 3. Both read the signs
+// before the flips are applied (launch_flip afterwards).
+size_t flip_ws_bytes(int64_t nE, int64_t n);
+void launch_flip_estimate(const DevGraph &g, const int64_t *edges_dev, int64_t n, void *ws,
+                          unsigned long long *cost_dev, cudaStream_t s);
+void launch_flip_delta(const DevGraph &g, int64_t n, void *ws, unsigned long long *acc_dev,
+                       cudaStream_t s);
+
 // Flip the signs of listed input edges (device list of n indices).
 void launch_flip(DevGraph &g, const int64_t *edge_idx_dev, int64_t n, cudaStream_t s);
 

@@ -42,6 +42,8 @@ struct bb_ctx {
     size_t ws_pv_cap = 0;
     void *ws_pe = nullptr;     // per-edge output and entry accumulators
     size_t ws_pe_cap = 0;
+    void *ws_flip = nullptr;   // incremental re-count: edge list, records, flags
+    size_t ws_flip_cap = 0;
     bb::DevGraph oneshot;
     int64_t layout_key[3] = {-1, -1, -1};
     bb::HostResult *h_res = nullptr;  // pinned
@@ -60,6 +62,9 @@ struct bb_graph {
     size_t bytes = 0;
     void *raw = nullptr;
     size_t raw_bytes = 0;
+    // counts of the current signs, when known (the base of incremental re-counts)
+    bool have_counts = false;
+    int64_t last_balanced = 0, last_total = 0;
 };
 
 namespace bb {

@@ -36,6 +36,7 @@ struct bb_ticket_s {
     std::atomic<int> done{0};
     bb_status st = BB_OK;
     int64_t balanced = 0, total = 0;
+    bool incremental = false;  // re-counted through the flipped edges only
     std::string err;
     Clock::time_point t_submit, t_start, t_done;
 };
@@ -53,6 +54,9 @@ struct Entry {
     Block graph, raw;
     bool busy = false;
     uint64_t last_use = 0;
+    // counts of the current signs, when known (the base of incremental re-counts)
+    bool have_counts = false;
+    int64_t last_balanced = 0, last_total = 0;
 };
 
 struct Plan {
@@ -90,6 +94,18 @@ struct Engine {
 }  // namespace bb
 
 namespace {
+
+// Flip sets of at most nE/1024 distinct edges on a graph whose counts are
+// known may be re-counted incrementally (flips.cu); their arena block also
+// holds the located edges, two flag bitmaps and the change accumulators.
+bool flips_small(const Entry *e, int64_t n_flip) {
+    return e && e->have_counts && n_flip > 0 && n_flip <= e->g.nE / 1024;
+}
+
+size_t flip_block_bytes(const Entry *e, int64_t n_flip) {
+    const size_t list = Arena::round((size_t)n_flip * 8);
+    return flips_small(e, n_flip) ? list + 256 + flip_ws_bytes(e->g.nE, n_flip) : list;
+}
 
 struct RawLayout {
     size_t rowptr, col, sign, total;
@@ -175,7 +191,7 @@ bb_ticket_s *pick(Engine *E, Plan &plan) {
             Plan p;
             p.entry = e;
             if (r.n_flip > 0) {
-                p.flips.bytes = (size_t)r.n_flip * 8;
+                p.flips.bytes = flip_block_bytes(e, r.n_flip);
                 std::vector<Block *> want{&p.flips};
                 if (!alloc_all(E, want, e)) {
                     if (E->running == 0) {
@@ -255,6 +271,7 @@ bb_status count_and_wait(Slot &S, const DevGraph &g, bb_ticket_s *t) {
             "copy count status");
     BB_CUDA(cudaMemcpyAsync(&h->build_err, g.err, 4, cudaMemcpyDeviceToHost, S.s),
             "copy build status");
+    BB_CUDA(cudaMemcpyAsync(&h->wedges, g.wedges, 8, cudaMemcpyDeviceToHost, S.s), "copy wedges");
     bb_status st = wait_bounded(S.s, "served count");
     if (st != BB_OK) return st;
     if (h->build_err) return map_build_error(h->build_err);
@@ -302,13 +319,66 @@ bb_status run_managed(Engine *E, Slot &S, bb_ticket_s *t, Plan &plan) {
             if (r.flip_idx[i] < 0 || r.flip_idx[i] >= e->g.nE)
                 return fail(BB_ERR_INVALID_ARG, "edge index %lld outside [0, %lld)",
                             (long long)r.flip_idx[i], (long long)e->g.nE);
-        int64_t *d = (int64_t *)(E->arena_mem + plan.flips.off);
-        BB_CUDA(cudaMemcpyAsync(d, r.flip_idx, (size_t)r.n_flip * 8, cudaMemcpyHostToDevice, s),
-                "copy flip list");
-        launch_flip(e->g, d, r.n_flip, s);
+        char *fb = E->arena_mem + plan.flips.off;
+        int64_t *d = (int64_t *)fb;
+        if (flips_small(e, r.n_flip)) {
+            // distinct flips (an edge listed twice flips back), then the
+            // incremental walk when it is cheaper than a recount
+            std::vector<int64_t> list(r.flip_idx, r.flip_idx + r.n_flip), odd;
+            std::sort(list.begin(), list.end());
+            for (size_t i = 0; i < list.size();) {
+                size_t j = i;
+                while (j < list.size() && list[j] == list[i]) j++;
+                if ((j - i) & 1) odd.push_back(list[i]);
+                i = j;
+            }
+            const int64_t m = (int64_t)odd.size();
+            unsigned long long *acc = (unsigned long long *)(fb + Arena::round((size_t)r.n_flip * 8));
+            void *ws = (char *)acc + 256;
+            if (m > 0) {
+                BB_CUDA(cudaMemcpyAsync(d, odd.data(), (size_t)m * 8, cudaMemcpyHostToDevice, s),
+                        "copy flip list");
+                launch_flip_estimate(e->g, d, m, ws, acc, s);
+                BB_CUDA(cudaGetLastError(), "flip estimate");
+                BB_CUDA(cudaMemcpyAsync(S.h->acc, acc, 8, cudaMemcpyDeviceToHost, s), "copy estimate");
+                bb_status st = wait_bounded(s, "flip estimate");
+                if (st != BB_OK) return st;
+            }
+            if (m == 0 || S.h->acc[0] <= e->g.h_wedges / 16) {
+                if (m > 0) {
+                    launch_flip_delta(e->g, m, ws, acc + 1, s);
+                    BB_CUDA(cudaGetLastError(), "flip delta");
+                    BB_CUDA(cudaMemcpyAsync(S.h->acc + 1, acc + 1, 16, cudaMemcpyDeviceToHost, s),
+                            "copy change");
+                    launch_flip(e->g, d, m, s);
+                    BB_CUDA(cudaGetLastError(), "sign flip");
+                    bb_status st = wait_bounded(s, "incremental count");
+                    if (st != BB_OK) return st;
+                    const long long d3 = (long long)S.h->acc[1] - (long long)S.h->acc[2];
+                    if (d3 % 3 != 0) return fail(BB_ERR_CUDA, "internal check failed (weighted change %lld)", d3);
+                    e->last_balanced += d3 / 3;
+                }
+                t->balanced = e->last_balanced;
+                t->total = e->last_total;
+                t->incremental = true;
+                return BB_OK;
+            }
+            launch_flip(e->g, d, m, s);
+        } else {
+            BB_CUDA(cudaMemcpyAsync(d, r.flip_idx, (size_t)r.n_flip * 8, cudaMemcpyHostToDevice, s),
+                    "copy flip list");
+            launch_flip(e->g, d, r.n_flip, s);
+        }
         BB_CUDA(cudaGetLastError(), "sign flip");
     }
+    e->have_counts = false;
     bb_status st = count_and_wait(S, e->g, t);
+    if (st == BB_OK) {
+        e->have_counts = true;
+        e->last_balanced = t->balanced;
+        e->last_total = t->total;
+        e->g.h_wedges = S.h->wedges;  // the recount's cost, for the next flip decision
+    }
     if (st != BB_OK && plan.fresh) plan.drop = true;
     return st;
 }
@@ -349,6 +419,7 @@ void worker(Engine *E, int k) {
         E->running--;
         t->st = st;
         if (st == BB_OK) E->stats.completed++; else E->stats.failed++;
+        if (st == BB_OK && t->incremental) E->stats.incremental++;
         t->t_done = Clock::now();
         t->done.store(1, std::memory_order_release);
         E->cv.notify_all();

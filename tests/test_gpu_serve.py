@@ -192,3 +192,29 @@ def test_destroy_with_requests_in_flight(graphs, counts):
             assert e.name == "BB_ERR_BUSY"
             busy += 1
     assert ok + busy == len(tickets)
+
+
+def test_small_flip_requeries_are_incremental(graphs, counts):
+    """Re-queries flipping a handful of edges of a resident graph whose
+    counts are known take the incremental walk; every result stays exact."""
+    big = sorted(graphs, key=lambda g: g.nE)[-3:]
+    reqs, states = trace(big, 30, seed=11, requery=0.6, flip_frac=0.0)
+    # flip_frac 0 gives one flipped edge per re-query; add a few more
+    rng = np.random.default_rng(4)
+    reqs = [(k, gi, None if f is None else np.concatenate([f, rng.choice(states[i].nE, 3)]))
+            for i, (k, gi, f) in enumerate(reqs)]
+    cur, states = {}, []
+    for key, gi, f in reqs:
+        if gi is not None:
+            cur[key] = big[gi]
+        else:
+            idx, cnt = np.unique(f, return_counts=True)
+            cur[key] = flipped(cur[key], idx[cnt % 2 == 1])  # a repeated index flips back
+        states.append(cur[key])
+    want = [oracle_of(counts, s) for s in states]
+    with pkg.Context(0) as ctx:
+        ctx.serve(slots=3, arena_bytes=2048 * MB)
+        got = run_mix(ctx, big, reqs)
+        st = ctx.serve_stats()
+    assert [(o.balanced, o.total) for o in got] == want
+    assert st["incremental"] > 0 and st["failed"] == 0
