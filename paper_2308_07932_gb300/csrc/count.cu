@@ -44,7 +44,7 @@ namespace {
 constexpr int WARP_THREADS = 256;    // 8 independent warps per CTA
 constexpr int TEAM_THREADS = 128;    // one team per CTA
 constexpr int CTAH_THREADS = 512;
-constexpr int DENSE_THREADS = 1024;
+constexpr int DENSE_THREADS = 512;
 
 __device__ __forceinline__ void acc_add(CountScratch *sc, unsigned long long bal,
                                         unsigned long long tot) {

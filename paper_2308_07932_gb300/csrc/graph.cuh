@@ -22,8 +22,10 @@ namespace bb {
 // endpoints concentrate on these high-degree vertices, so team kernels keep
 // them in dense counters and hash only the rest.
 constexpr uint32_t HUB_WINDOW = 2048;
-// dense counters per CTA job: 48Ki u32 (192 KiB of shared memory)
-constexpr uint32_t DENSE_CAP = 49152;
+// dense counters per CTA job: 16Ki u32 (64 KiB of shared memory), so that
+// three 512-thread dense CTAs share an SM (one 1024-thread CTA with 48Ki
+// counters per SM was 35 % slower on the 2M x 500k graph)
+constexpr uint32_t DENSE_CAP = 16384;
 // warp class: one warp per anchor of degree <= WARP_DEG_MAX (its per-pair
 // counts then fit 8 bits) and at most WARP_W_MAX wedges. Anchors with at
 // most WARP_SMALL_W wedges hash every endpoint; larger ones keep the hub

@@ -29,10 +29,11 @@ namespace {
 
 constexpr int PV_THREADS = 512;
 constexpr uint32_t PV_HASH_CAP = 16384;   // u64 slots (128 KiB), shares memory with the counters
+constexpr uint32_t PV_DENSE_CAP = 49152;  // dense counters (192 KiB): long ranges in fewer windows
 
 struct PvSmem {
     union {
-        uint32_t cnt[DENSE_CAP];
+        uint32_t cnt[PV_DENSE_CAP];
         unsigned long long tab[PV_HASH_CAP];
     };
     unsigned long long red[PV_THREADS / 32];
@@ -115,16 +116,16 @@ __global__ void __launch_bounds__(PV_THREADS) k_pv(DevGraph G, PvOut out) {
         const uint32_t deg = (uint32_t)(S.off[r + 1] - rb);
         const uint64_t above = (uint64_t)(S.n - r - 1);
         const uint64_t dh = W < above ? W : above;
-        const bool dense = above <= DENSE_CAP || dh * 5 / 4 >= PV_HASH_CAP;
+        const bool dense = above <= PV_DENSE_CAP || dh * 5 / 4 >= PV_HASH_CAP;
         uint32_t cap = 32, shift = 27;
         if (!dense)
             while ((uint64_t)cap < dh + dh / 4 + 1) { cap <<= 1; shift--; }
         const uint32_t mask = cap - 1;
         unsigned long long wsum = 0;  // balanced butterflies containing the anchor
         const uint32_t e_lo = r + 1, e_hi = (uint32_t)S.n;
-        for (uint32_t e0 = e_lo; e0 < e_hi; e0 += dense ? DENSE_CAP : (e_hi - e_lo)) {
-            const uint32_t e1 = dense && e_hi - e0 > DENSE_CAP ? e0 + DENSE_CAP : e_hi;
-            const bool clip = dense && (e_hi - e_lo) > DENSE_CAP;
+        for (uint32_t e0 = e_lo; e0 < e_hi; e0 += dense ? PV_DENSE_CAP : (e_hi - e_lo)) {
+            const uint32_t e1 = dense && e_hi - e0 > PV_DENSE_CAP ? e0 + PV_DENSE_CAP : e_hi;
+            const bool clip = dense && (e_hi - e_lo) > PV_DENSE_CAP;
             const uint32_t len = dense ? e1 - e0 : cap;
             if (dense) for (uint32_t i = t; i < len; i += PV_THREADS) sm.cnt[i] = 0;
             else for (uint32_t i = t; i < cap; i += PV_THREADS) sm.tab[i] = 0ull;
