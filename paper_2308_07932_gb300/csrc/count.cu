@@ -28,7 +28,7 @@
 //   team  - medium anchors, one per 128-thread CTA: dense counters for the
 //           hub window (top HUB_WINDOW ranks of the side, where most
 //           endpoints fall) and a hash for the endpoints below the window;
-//   ctah  - like team with a 512-thread CTA and a 16Ki-slot hash;
+//   ctah  - like team with a 512-thread CTA and an 8Ki-slot hash;
 //   dense - heavy anchors with a short endpoint range: dense counters over
 //           the whole range (walked in windows when longer than DENSE_CAP);
 //           the heaviest are split over CTAs whose partial counts are

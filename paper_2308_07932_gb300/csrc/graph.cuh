@@ -38,8 +38,9 @@ constexpr uint32_t WARP_CAP = 256;
 // a TEAM_CAP-slot hash
 constexpr uint64_t TEAM_W_MAX = 16384;
 constexpr uint32_t TEAM_CAP = 1024;
-// CTA hash class: below-window wedges that fit a CTAH_CAP-slot hash
-constexpr uint32_t CTAH_CAP = 16384;
+// CTA hash class: below-window wedges that fit a CTAH_CAP-slot hash (64 KiB:
+// two or three CTAs per SM; 16Ki slots held one and was 75 % slower)
+constexpr uint32_t CTAH_CAP = 8192;
 // split one dense anchor over several CTAs when its wedges exceed both this
 // and 4x its endpoint range; parts are merged before the C(.,2) step
 constexpr uint64_t SPLIT_WEDGES = 65536;
