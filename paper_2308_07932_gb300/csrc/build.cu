@@ -235,12 +235,11 @@ __global__ void __launch_bounds__(WS_THREADS) k_sort_rows_warpsmem(SideCSR S, co
         __syncwarp();
         for (uint32_t k = 2; k <= P; k <<= 1) {
             for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                for (uint32_t i = lane; i < P; i += 32) {
-                    const uint32_t ixj = i ^ j;
-                    if (ixj > i) {
-                        const uint64_t a = buf[i], c = buf[ixj];
-                        if ((a > c) == ((i & k) == 0)) { buf[i] = c; buf[ixj] = a; }
-                    }
+                // compare-exchange pairs (i, i + j), i with bit j clear: P/2 of them
+                for (uint32_t q = lane; q < P / 2; q += 32) {
+                    const uint32_t i = ((q & ~(j - 1)) << 1) | (q & (j - 1));
+                    const uint64_t a = buf[i], c = buf[i | j];
+                    if ((a > c) == ((i & k) == 0)) { buf[i] = c; buf[i | j] = a; }
                 }
                 __syncwarp();
             }
@@ -272,13 +271,11 @@ __global__ void __launch_bounds__(THREADS) k_sort_rows_smem(SideCSR S, const uin
         __syncthreads();
         for (uint32_t k = 2; k <= P; k <<= 1) {
             for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                for (uint32_t i = threadIdx.x; i < P; i += THREADS) {
-                    uint32_t ixj = i ^ j;
-                    if (ixj > i) {
-                        uint64_t a = sbuf[i], c = sbuf[ixj];
-                        bool asc = (i & k) == 0;
-                        if ((a > c) == asc) { sbuf[i] = c; sbuf[ixj] = a; }
-                    }
+                // compare-exchange pairs (i, i + j), i with bit j clear: P/2 of them
+                for (uint32_t q = threadIdx.x; q < P / 2; q += THREADS) {
+                    const uint32_t i = ((q & ~(j - 1)) << 1) | (q & (j - 1));
+                    const uint64_t a = sbuf[i], c = sbuf[i | j];
+                    if ((a > c) == ((i & k) == 0)) { sbuf[i] = c; sbuf[i | j] = a; }
                 }
                 __syncthreads();
             }
