@@ -552,6 +552,9 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
         if (wnh > 0) table_geometry(wnh < above_nh ? wnh : above_nh, 32, WARP_CAP, cap, shift);
         const uint32_t mask = cap - 1;
         bool bad_any = false;
+        // 32-bit sums for the hub part: a lane walks at most W/32 + 1 <= 513
+        // wedges of the anchor, each adding at most 2 * 255
+        uint32_t b32 = 0, t32 = 0;
         lane_walk2(
             A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, sm.walk2, (int)lane, HubSeg{},
             [&](uint32_t u, uint32_t asym) {
@@ -564,14 +567,16 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
                 const uint32_t sh = (wi & 1u) << 4;
                 const uint32_t old =
                     (atomicAdd(&sm.win[wi >> 1], (1u + asym * 255u) << sh) >> sh) & 0xffffu;
-                bal += (old >> (asym << 3)) & 0xffu;
-                tot += ((old * 0x101u) >> 8) & 0xffu;  // S + A
+                b32 += (old >> (asym << 3)) & 0xffu;
+                t32 += ((old * 0x101u) >> 8) & 0xffu;  // S + A
             },
             LowSeg{},
             [&](uint32_t u, uint32_t asym) {
                 hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
             });
         if (bad_any) set_error(err, E_INTERNAL);
+        bal += b32;
+        tot += t32;
         // reset the window words an endpoint can have reached
         const uint32_t first = (A.r + 1 > wb ? A.r + 1 - wb : 0u) >> 3;  // uint4 index
         uint4 *w4 = reinterpret_cast<uint4 *>(sm.win);
