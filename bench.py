@@ -328,6 +328,19 @@ def run_ours(args, world, rank, local_rank):
             opt[f"count_flipped_{k}_incremental"] = out[2]
         opt["timing"] = "host wall clock around the blocking call, best of 3, L2 flushed before"
         res.free()
+        # the paper's baseline (BB-Base, Algorithm 1) against the bucket method,
+        # on a 1.8 M-edge graph of the same recipe (BB-Base's work is the
+        # number of butterflies, so the full graph would take seconds)
+        from paper_2308_07932_gb300 import synth
+        gb = synth.chung_lu_scaled(43, 2_000_000)
+        rb = ctx.upload(gb)
+        t_bucket, cb = timed(lambda: rb.count())
+        t_base, bb_ = timed(lambda: rb.count_base(), reps=1)
+        assert bb_ == (cb.balanced, cb.total)
+        opt["base_vs_bucket"] = {"graph": gb.name, "edges": gb.nE, "butterflies": cb.total,
+                                 "bucket_ms": t_bucket, "base_ms": t_base,
+                                 "base_over_bucket": t_base / t_bucket}
+        rb.free()
 
     # dominant wedge kernel and its roofline
     kern = {k: {"ms": statistics.mean(t["kernels"][k]["ms"] for t in timings),

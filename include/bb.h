@@ -147,6 +147,14 @@ BB_API bb_status bb_count_edges(bb_graph *g, int64_t *per_edge, int64_t *balance
 BB_API bb_status bb_count_flipped(bb_graph *g, const int64_t *edge_idx, int64_t n,
                                   int64_t *balanced, int64_t *total, int *incremental_opt);
 
+/* The same counts by the paper's baseline, BB-Base (Algorithm 1), on the
+ * GPU: the middles of each vertex pair are grouped and every pair of them
+ * is tested explicitly, so the work is the number of butterflies rather
+ * than of wedges. Kept to measure the bucket method's advantage on the same
+ * device; blocking; device workspace ~ (CTAs) x (largest anchor's wedges)
+ * bytes. */
+BB_API bb_status bb_count_base(bb_graph *g, int64_t *balanced, int64_t *total);
+
 /* Negate the sign of the listed input edges (indices into the CSR's col
  * array, host int64[n]) in the resident graph, both directions. Repeated
  * indices flip repeatedly. Later counts see the new signs. */

@@ -115,6 +115,7 @@ def lib() -> ctypes.CDLL:
             "bb_count": (S, [_VP, _I64P, _I64P, _VP]),
             "bb_graph_flip_signs": (S, [_VP, _VP, ctypes.c_int64]),
             "bb_count_edges": (S, [_VP, _VP, _I64P, _I64P]),
+            "bb_count_base": (S, [_VP, _I64P, _I64P]),
             "bb_count_flipped": (S, [_VP, _VP, ctypes.c_int64, _I64P, _I64P,
                                      ctypes.POINTER(ctypes.c_int)]),
             "bb_graph_info": (S, [_VP, _I64P, _I64P, _I64P, _I64P]),
@@ -382,6 +383,13 @@ class Graph:
         b, t = ctypes.c_int64(), ctypes.c_int64()
         _check(lib().bb_count_edges(self._h, pe.ctypes.data, ctypes.byref(b), ctypes.byref(t)))
         return pe[:nE], b.value, t.value
+
+    def count_base(self) -> tuple[int, int]:
+        """(balanced, total) by BB-Base (Algorithm 1) on the GPU, for comparison
+        with the bucket method (``bb_count_base``)."""
+        b, t = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().bb_count_base(self._h, ctypes.byref(b), ctypes.byref(t)))
+        return b.value, t.value
 
     def count_flipped(self, edge_idx) -> tuple[int, int, bool]:
         """Flip the listed edges' signs and return (balanced, total,

@@ -289,6 +289,7 @@ void bb_ctx_destroy(bb_ctx *ctx) {
     dev_free(ctx, ctx->ws_pv, ctx->ws_pv_cap);
     dev_free(ctx, ctx->ws_pe, ctx->ws_pe_cap);
     dev_free(ctx, ctx->ws_flip, ctx->ws_flip_cap);
+    dev_free(ctx, ctx->ws_base, ctx->ws_base_cap);
     if (ctx->h_res) cudaFreeHost(ctx->h_res);
     for (int k = 0; k < NEV; k++)
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
@@ -603,6 +604,41 @@ bb_status bb_count_flipped(bb_graph *G, const int64_t *edge_idx, int64_t n, int6
     *balanced = G->last_balanced;
     *total = G->last_total;
     if (incremental_opt) *incremental_opt = incremental ? 1 : 0;
+    return BB_OK;
+}
+
+bb_status bb_count_base(bb_graph *G, int64_t *balanced, int64_t *total) {
+    if (!G || !balanced || !total) return fail(BB_ERR_INVALID_ARG, "NULL argument");
+    bb_ctx *ctx = G->ctx;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    bb_status st = set_device(ctx);
+    if (st != BB_OK) return st;
+    cudaStream_t s = ctx->stream;
+    // the largest anchor's wedges bound a CTA's group buffer
+    st = ensure(ctx, &ctx->ws_base, &ctx->ws_base_cap, 256, "BB-Base workspace");
+    if (st != BB_OK) return st;
+    unsigned long long *d_acc = (unsigned long long *)ctx->ws_base;  // [0] max work, [1..2] counts
+    launch_max_work(G->g, d_acc, s);
+    BB_CUDA(cudaGetLastError(), "max work");
+    BB_CUDA(cudaMemcpyAsync(ctx->h_res->acc, d_acc, 8, cudaMemcpyDeviceToHost, s), "copy max work");
+    if ((st = wait_bounded(s, "max work")) != BB_OK) return st;
+    const uint64_t per_cta = std::max<uint64_t>(ctx->h_res->acc[0], 1);
+    const size_t need = 256 + (size_t)base_blocks() * ((per_cta + 255) / 256 * 256);
+    st = ensure(ctx, &ctx->ws_base, &ctx->ws_base_cap, need, "BB-Base workspace");
+    if (st != BB_OK) return st;
+    d_acc = (unsigned long long *)ctx->ws_base;
+    launch_base(G->g, (uint8_t *)ctx->ws_base + 256, (per_cta + 255) / 256 * 256, d_acc + 1, s);
+    BB_CUDA(cudaGetLastError(), "BB-Base");
+    BB_CUDA(cudaMemcpyAsync(ctx->h_res->acc + 1, d_acc + 1, 16, cudaMemcpyDeviceToHost, s), "copy counts");
+    BB_CUDA(cudaMemcpyAsync(&ctx->h_res->count_err, &G->g.scratch->err, 4, cudaMemcpyDeviceToHost, s),
+            "copy status");
+    if ((st = wait_bounded(s, "BB-Base")) != BB_OK) return st;
+    if (ctx->h_res->count_err)
+        return fail(BB_ERR_CUDA, "internal check failed (0x%x)", ctx->h_res->count_err);
+    if (ctx->h_res->acc[1] > (unsigned long long)LLONG_MAX || ctx->h_res->acc[2] > (unsigned long long)LLONG_MAX)
+        return fail(BB_ERR_OVERFLOW, "butterfly count exceeds int64");
+    *balanced = (int64_t)ctx->h_res->acc[1];
+    *total = (int64_t)ctx->h_res->acc[2];
     return BB_OK;
 }
 

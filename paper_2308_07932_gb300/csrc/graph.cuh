@@ -195,6 +195,15 @@ void launch_flip_estimate(const DevGraph &g, const int64_t *edges_dev, int64_t n
 void launch_flip_delta(const DevGraph &g, int64_t n, void *ws, unsigned long long *acc_dev,
                        cudaStream_t s);
 
+// BB-Base (Algorithm 1) for comparison (base.cu): explicit pair tests.
+// launch_max_work writes the largest anchor wedge count to out_dev;
+// launch_base needs base_blocks() per-CTA buffers of that many bytes and
+// writes balanced / total to acc_dev[0] / acc_dev[1].
+int base_blocks();
+void launch_max_work(const DevGraph &g, unsigned long long *out_dev, cudaStream_t s);
+void launch_base(const DevGraph &g, uint8_t *scratch, uint64_t per_cta,
+                 unsigned long long *acc_dev, cudaStream_t s);
+
 // Flip the signs of listed input edges (device list of n indices).
 void launch_flip(DevGraph &g, const int64_t *edge_idx_dev, int64_t n, cudaStream_t s);
 

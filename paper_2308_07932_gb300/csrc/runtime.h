@@ -44,6 +44,8 @@ struct bb_ctx {
     size_t ws_pe_cap = 0;
     void *ws_flip = nullptr;   // incremental re-count: edge list, records, flags
     size_t ws_flip_cap = 0;
+    void *ws_base = nullptr;   // BB-Base: per-CTA group buffers
+    size_t ws_base_cap = 0;
     bb::DevGraph oneshot;
     int64_t layout_key[3] = {-1, -1, -1};
     bb::HostResult *h_res = nullptr;  // pinned
