@@ -215,7 +215,7 @@ bb_status count_device(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int6
         ctx->layout_key[0] = nU; ctx->layout_key[1] = nV; ctx->layout_key[2] = nE;
     }
     if (ctx->timing) BB_CUDA(cudaEventRecord(ctx->ev[0], s), "event");
-    uint32_t verr = build_graph(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s);
+    uint32_t verr = build_graph(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s, &ctx->aux);
     BB_CUDA(cudaGetLastError(), "build kernels");
     if (ctx->timing) BB_CUDA(cudaEventRecord(ctx->ev[1], s), "event");
     ctx->have_build_ev = ctx->timing;
@@ -263,6 +263,10 @@ bb_status bb_ctx_create(int device, uint64_t hbm_budget_bytes, bb_ctx **out) {
     e = cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking);
     if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "cudaStreamCreate"); }
     ctx->stream = ctx->own;
+    e = cudaStreamCreateWithFlags(&ctx->aux.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->aux.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->aux.join, cudaEventDisableTiming);
+    if (e != cudaSuccess) { bb_ctx_destroy(ctx); return cuda_fail(e, "auxiliary stream"); }
     e = cudaMallocHost((void **)&ctx->h_res, sizeof(HostResult));
     if (e != cudaSuccess) {
         cudaStreamDestroy(ctx->own);
@@ -293,6 +297,9 @@ void bb_ctx_destroy(bb_ctx *ctx) {
     if (ctx->h_res) cudaFreeHost(ctx->h_res);
     for (int k = 0; k < NEV; k++)
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+    if (ctx->aux.fork) cudaEventDestroy(ctx->aux.fork);
+    if (ctx->aux.join) cudaEventDestroy(ctx->aux.join);
+    if (ctx->aux.stream) { cudaStreamSynchronize(ctx->aux.stream); cudaStreamDestroy(ctx->aux.stream); }
     if (ctx->own) cudaStreamDestroy(ctx->own);
     delete ctx;
 }
@@ -423,7 +430,7 @@ static bb_status upload_impl(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs
     G->g.rowptr = rp; G->g.col = cl; G->g.sign = sg;
     cudaMemsetAsync(G->g.gpart, 0, (size_t)G->g.gpart_cap * 4, s);
     cudaMemsetAsync(G->g.gdone, 0, MAX_SPLIT_JOBS * 4, s);
-    uint32_t verr = build_graph(G->g, rp, cl, sg, ctx->ws_temp, s);
+    uint32_t verr = build_graph(G->g, rp, cl, sg, ctx->ws_temp, s, &ctx->aux);
     if (verr) { bb_graph_free(G); return map_build_error(verr); }
     e = cudaMemcpyAsync(&ctx->h_res->build_err, G->g.err, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&ctx->h_res->wedges, G->g.wedges, 8, cudaMemcpyDeviceToHost, s);

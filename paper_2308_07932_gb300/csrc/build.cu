@@ -699,7 +699,7 @@ void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_m
 }
 
 uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
-                     void *temp_mem, cudaStream_t s) {
+                     void *temp_mem, cudaStream_t s, const BuildAux *aux) {
     const int64_t nU = g.nU, nV = g.nV, nE = g.nE;
     const int64_t nmax = std::max<int64_t>(std::max(nU, nV), 1);
     Carver c{(char *)temp_mem};
@@ -760,13 +760,33 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
     if (nU > 0 && nE > 0)
         k_fill<<<grid_for(nE, BT, 32768), BT, 0, s>>>(rowptr, col, sign, nU, nE, g.side[0],
                                                      g.side[1], cursorV, keys[0], keys[1]); note_launch();
+    // bd[k]: first rank with degree > ROW_LIMS[k]; bd[NLIMS] = n
+    for (int sd = 0; sd < 2; sd++)
+        if (ns[sd] > 0 && nE > 0) {
+            k_row_bounds<<<1, 32, 0, s>>>(g.side[sd].deg, ns[sd], bounds + sd * 16); note_launch();
+        }
+    // rows above 2048 entries: per-row radix sort (faster there than bitonic);
+    // on the auxiliary stream when there is one, beside the other row sorts
+    // (the longest rows' sorts would otherwise leave most SMs idle at the end)
+    cudaStream_t rs = aux ? aux->stream : s;
+    if (aux) {
+        cudaEventRecord(aux->fork, s);
+        cudaStreamWaitEvent(rs, aux->fork, 0);
+    }
+    for (int sd = 0; sd < 2; sd++) {
+        if (ns[sd] == 0 || nE == 0) continue;
+        const int64_t n_other = ns[1 - sd];
+        int key_bits = 1;
+        while (key_bits < 32 && ((uint64_t)1 << key_bits) < (uint64_t)(2 * n_other + 2)) key_bits++;
+        k_sort_rows_radix<<<1024, RR_THREADS, 0, rs>>>(g.side[sd], keys[sd], bufC, eid[sd], rowid[sd],
+                                                        bounds + sd * 16, 7, NLIMS, key_bits, g.err); note_launch();
+    }
+    if (aux) cudaEventRecord(aux->join, rs);
     for (int sd = 0; sd < 2; sd++) {
         int64_t n = ns[sd];
         if (n == 0 || nE == 0) continue;
         SideCSR &S = g.side[sd];
         int64_t *bd = bounds + sd * 16;
-        // bd[k]: first rank with degree > ROW_LIMS[k]; bd[NLIMS] = n
-        k_row_bounds<<<1, 32, 0, s>>>(S.deg, n, bd); note_launch();
         uint64_t *ky = keys[sd];
         k_rows_single<<<grid_for(n, BT, 4096), BT, 0, s>>>(S, ky, eid[sd], rowid[sd], bd); note_launch();
         k_sort_rows_sub<2><<<grid_for(n * 2, BT, 8192), BT, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 0, g.err); note_launch();
@@ -776,13 +796,8 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
         k_sort_rows_sub<32><<<grid_for(n * 32, BT, 8192), BT, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 4, g.err); note_launch();
         k_sort_rows_warpsmem<<<1024, WS_THREADS, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 5, g.err); note_launch();
         k_sort_rows_smem<2048, 256><<<2048, 256, 2048 * 8, s>>>(S, ky, eid[sd], rowid[sd], bd, 6, g.err); note_launch();
-        int64_t n_other = ns[1 - sd];
-        int key_bits = 1;
-        while (key_bits < 32 && ((uint64_t)1 << key_bits) < (uint64_t)(2 * n_other + 2)) key_bits++;
-        // rows above 2048 entries: per-row radix sort (faster there than bitonic)
-        k_sort_rows_radix<<<1024, RR_THREADS, 0, s>>>(S, ky, bufC, eid[sd], rowid[sd], bd, 7, NLIMS,
-                                                       key_bits, g.err); note_launch();
     }
+    if (aux) cudaStreamWaitEvent(s, aux->join, 0);
     for (int sd = 0; sd < 2; sd++) {
         if (ns[sd] == 0) continue;
         k_lo<<<grid_for(ns[sd], BT, 8192), BT, 0, s>>>(g.side[sd], g.side[1 - sd]); note_launch();

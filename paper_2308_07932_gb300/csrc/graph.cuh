@@ -128,11 +128,18 @@ BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE);
 // Carve the graph's arrays out of `graph_mem` (graph_bytes long).
 void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_mem);
 
+// An auxiliary stream and two events the build may fork work onto (it is
+// joined back to s before the build's last kernels).
+struct BuildAux {
+    cudaStream_t stream;
+    cudaEvent_t fork, join;
+};
+
 // Build from device CSR (rowptr/col/sign on the device). Returns 0 or the
-// error bits. Blocking only on
-// the validation check and at the end.
+// error bits. Blocking only on the validation check. aux may be null (all
+// work on s).
 uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
-                     void *temp_mem, cudaStream_t s);
+                     void *temp_mem, cudaStream_t s, const BuildAux *aux = nullptr);
 
 // Count balanced/total butterflies of a built graph on stream s. Writes the
 // 128-bit sums to g.scratch->acc (device); per_vertex may be null. When ev

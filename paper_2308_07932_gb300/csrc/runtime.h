@@ -31,6 +31,7 @@ struct bb_ctx {
     uint64_t budget = 0;
     uint64_t used = 0;
     cudaStream_t own = nullptr, stream = nullptr;
+    bb::BuildAux aux{};  // the build's auxiliary stream and fork/join events
     // one-shot workspace
     void *ws_graph = nullptr;
     size_t ws_graph_cap = 0;

@@ -69,6 +69,7 @@ struct Plan {
 
 struct Slot {
     cudaStream_t s = nullptr;
+    BuildAux aux{};           // the build's auxiliary stream and events
     HostResult *h = nullptr;  // pinned
     std::thread th;
 };
@@ -307,7 +308,7 @@ bb_status run_managed(Engine *E, Slot &S, bb_ticket_s *t, Plan &plan) {
         e->g.sign = sg;
         BB_CUDA(cudaMemsetAsync(e->g.gpart, 0, (size_t)e->g.gpart_cap * 4, s), "zero merge buffer");
         BB_CUDA(cudaMemsetAsync(e->g.gdone, 0, MAX_SPLIT_JOBS * 4, s), "zero merge counters");
-        const uint32_t verr = build_graph(e->g, rp, cl, sg, E->arena_mem + plan.temp.off, s);
+        const uint32_t verr = build_graph(e->g, rp, cl, sg, E->arena_mem + plan.temp.off, s, &S.aux);
         BB_CUDA(cudaGetLastError(), "build kernels");
         if (verr) {
             plan.drop = true;
@@ -439,6 +440,9 @@ void destroy_engine(Engine *E) {
     cudaSetDevice(E->device);
     for (Slot &S : E->slots) {
         if (S.s) { cudaStreamSynchronize(S.s); cudaStreamDestroy(S.s); }
+        if (S.aux.stream) { cudaStreamSynchronize(S.aux.stream); cudaStreamDestroy(S.aux.stream); }
+        if (S.aux.fork) cudaEventDestroy(S.aux.fork);
+        if (S.aux.join) cudaEventDestroy(S.aux.join);
         if (S.h) cudaFreeHost(S.h);
     }
     for (auto &kv : E->cache) delete kv.second;
@@ -462,6 +466,9 @@ bb_status start_engine(bb_ctx *ctx, int slots, uint64_t arena_bytes) {
     E->slots.resize(slots);
     for (Slot &S : E->slots) {
         cudaError_t e = cudaStreamCreateWithFlags(&S.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S.aux.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.aux.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.aux.join, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost((void **)&S.h, sizeof(HostResult));
         if (e != cudaSuccess) {
             destroy_engine(E);
