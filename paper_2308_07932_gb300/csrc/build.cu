@@ -362,27 +362,23 @@ __global__ void __launch_bounds__(RR_THREADS) k_sort_rows_radix(SideCSR S, uint6
     }
 }
 
-// lo(x): neighbours of x with lower global priority (a prefix of its row)
-__global__ void k_lo(SideCSR S, SideCSR O) {
+// Per row of a side, as absolute positions in its adjacency: the row's
+// start and end, lo (the first neighbour of higher global priority than the
+// row's vertex; the neighbours below it form a prefix) and the first
+// neighbour inside the other side's hub window (side ranks >= window_base).
+// One 16-byte record per row, read once per entry by k_md_work.
+__global__ void k_row_info(SideCSR S, SideCSR O, uint32_t window_base, uint4 *info) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < S.n;
          r += (int64_t)gridDim.x * blockDim.x) {
-        int64_t lo = S.off[r], hi = S.off[r + 1], b = lo;
-        uint32_t g = S.grank[r];
+        const int64_t b = S.off[r], e = S.off[r + 1];
+        const uint32_t g = S.grank[r];
+        int64_t lo = b, hi = e;
         while (lo < hi) {
-            int64_t m = (lo + hi) >> 1;
+            const int64_t m = (lo + hi) >> 1;
             if (O.grank[S.adj[m] >> 1] < g) lo = m + 1; else hi = m;
         }
-        S.lo[r] = (uint32_t)(lo - b);
-    }
-}
-
-// hstart(v): first index in v's row of a neighbour inside the hub window of
-// the neighbours' side (side ranks >= window_base)
-__global__ void k_hstart(SideCSR S, uint32_t window_base) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < S.n;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        int64_t b = S.off[r];
-        S.hstart[r] = (uint32_t)(lower_bound_u32(S.adj, b, S.off[r + 1], window_base << 1) - b);
+        const int64_t h = lower_bound_u32(S.adj, b, e, window_base << 1);
+        info[r] = make_uint4((uint32_t)b, (uint32_t)e, (uint32_t)lo, (uint32_t)h);
     }
 }
 
@@ -395,13 +391,16 @@ __global__ void k_epos(const uint32_t *eid, int64_t nE, uint32_t *epos) {
 // ------------------------------------------------- 4. suffixes and work
 // For the entry w -> v at position p of anchor w's row: the wedge suffix of
 // v's row holds the neighbours ranked above max(v, w). If v outranks w that
-// is v's own upper part (from lo(v)); otherwise it starts right after w's
-// position in v's row (w and the suffix are on the same side). One thread
-// per entry; the per-row sums of suffix lengths (wedges) and of their parts
-// below the hub window are reduced per warp segment, then added per row.
-__global__ void k_md_work(SideCSR S, SideCSR O, const uint32_t *__restrict__ eid_s,
-                          const uint32_t *__restrict__ epos_o, const uint32_t *__restrict__ row_s,
-                          int64_t nE, unsigned long long *wedges) {
+// is v's own upper part, from lo(v); otherwise it starts right after w's
+// position in v's row (w and the suffix are on the same side). w lies below
+// lo(v) exactly when v outranks w, so the start is max(lo(v), pos_v(w) + 1).
+// One thread per entry; the per-row sums of suffix lengths (wedges) and of
+// their parts below the hub window are reduced per warp segment, then added
+// per row.
+__global__ void k_md_work(SideCSR S, const uint4 *__restrict__ info_o,
+                          const uint32_t *__restrict__ eid_s, const uint32_t *__restrict__ epos_o,
+                          const uint32_t *__restrict__ row_s, int64_t nE,
+                          unsigned long long *wedges) {
     __shared__ unsigned long long block_sum;
     if (threadIdx.x == 0) block_sum = 0;
     __syncthreads();
@@ -418,15 +417,12 @@ __global__ void k_md_work(SideCSR S, SideCSR O, const uint32_t *__restrict__ eid
         if (valid) {
             r = row_s[p];
             const uint32_t ent = S.adj[p];
-            const uint32_t v = ent >> 1;
-            const int64_t ob = O.off[v], oe = O.off[v + 1];
-            uint32_t st;
-            if (O.grank[v] > S.grank[r]) st = O.lo[v];
-            else st = (uint32_t)(epos_o[eid_s[p]] - ob) + 1u;
-            const uint32_t hst = O.hstart[v];
-            const uint32_t hs = hst > st ? hst : st;
-            S.md[p] = make_uint4((uint32_t)(ob + st), (uint32_t)(ob + hs), (uint32_t)oe, ent & 1u);
-            len = (uint32_t)(oe - ob) - st;
+            const uint4 vi = info_o[ent >> 1];  // v's row: start, end, lo, hub start
+            const uint32_t pw = epos_o[eid_s[p]];
+            const uint32_t st = vi.z > pw + 1u ? vi.z : pw + 1u;
+            const uint32_t hs = vi.w > st ? vi.w : st;
+            S.md[p] = make_uint4(st, hs, vi.y, ent & 1u);
+            len = vi.y - st;
             nh = hs - st;
         }
         // segmented sums over runs of equal r within the warp
@@ -632,7 +628,7 @@ struct Carver {
 
 size_t side_bytes(int64_t n, int64_t nE) {
     return align256((size_t)(n + 1) * 8) + align256((size_t)nE * 4) + align256((size_t)nE * 16) +
-           6 * align256((size_t)(n > 0 ? n : 1) * 4) + 3 * align256((size_t)(n > 0 ? n : 1) * 8);
+           5 * align256((size_t)(n > 0 ? n : 1) * 4) + 3 * align256((size_t)(n > 0 ? n : 1) * 8);
 }
 
 }  // namespace
@@ -658,6 +654,7 @@ BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE) {
     t += align256(std::max(radix_temp_bytes(nmax), scan_temp_bytes(nmax + 1)));
     t += 2 * align256((size_t)nmax * 4 + 4) * 2;                             // classify meta/grp
     t += 2 * align256(NCLS * NB * 4) + align256(64 * 8);                     // buckets, bounds
+    t += align256((size_t)(nU + 1) * 16) + align256((size_t)(nV + 1) * 16);  // row records
     return {g, t};
 }
 
@@ -677,7 +674,6 @@ void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_m
         S.grank = c.take<uint32_t>(n1);
         S.deg = c.take<uint32_t>(n1);
         S.lo = c.take<uint32_t>(n1);
-        S.hstart = c.take<uint32_t>(n1);
         S.work = c.take<uint64_t>(n1);
         S.work_nh = c.take<uint64_t>(n1);
         S.pv = c.take<unsigned long long>(n1);
@@ -720,6 +716,7 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
     T.bucket_cnt = c.take<uint32_t>(NCLS * NB);
     T.bucket_base = c.take<uint32_t>(NCLS * NB);
     int64_t *bounds = c.take<int64_t>(32);
+    uint4 *rinfo[2] = {c.take<uint4>(nU + 1), c.take<uint4>(nV + 1)};  // per-row records
 
     cudaMemsetAsync(g.err, 0, 4, s);
     cudaMemsetAsync(g.ctr, 0, NCTR * 4, s);
@@ -800,10 +797,10 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
     if (aux) cudaStreamWaitEvent(s, aux->join, 0);
     for (int sd = 0; sd < 2; sd++) {
         if (ns[sd] == 0) continue;
-        k_lo<<<grid_for(ns[sd], BT, 8192), BT, 0, s>>>(g.side[sd], g.side[1 - sd]); note_launch();
         int64_t n_other = ns[1 - sd];
         uint32_t wb = n_other > (int64_t)HUB_WINDOW ? (uint32_t)(n_other - HUB_WINDOW) : 0u;
-        k_hstart<<<grid_for(ns[sd], BT, 8192), BT, 0, s>>>(g.side[sd], wb); note_launch();
+        k_row_info<<<grid_for(ns[sd], BT, 8192), BT, 0, s>>>(g.side[sd], g.side[1 - sd], wb,
+                                                            rinfo[sd]); note_launch();
     }
 
     // 4. twin positions, suffix starts, work per anchor
@@ -815,7 +812,7 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
             if (ns[sd] == 0) continue;
             cudaMemsetAsync(g.side[sd].work, 0, (size_t)ns[sd] * 8, s);
             cudaMemsetAsync(g.side[sd].work_nh, 0, (size_t)ns[sd] * 8, s);
-            k_md_work<<<grid_for(nE, BT, 8192), BT, 0, s>>>(g.side[sd], g.side[1 - sd], eid[sd],
+            k_md_work<<<grid_for(nE, BT, 8192), BT, 0, s>>>(g.side[sd], rinfo[1 - sd], eid[sd],
                                                            epos[1 - sd], rowid[sd], nE,
                                                            g.wedges); note_launch();
         }

@@ -47,9 +47,7 @@ struct SideCSR {
     uint32_t *sr_of_id;   // [n]   input id -> side rank
     uint32_t *grank;      // [n]   side rank -> global priority rank
     uint32_t *deg;        // [n]   side rank -> degree
-    uint32_t *lo;         // [n]   side rank -> neighbours of lower priority
-    uint32_t *hstart;     // [n]   side rank -> first index in its row of a neighbour in
-                          //       the other side's hub window (top HUB_WINDOW ranks)
+    uint32_t *lo;         // [n]   scratch of the build (degree keys of the rank sort)
     uint64_t *work;       // [n]   side rank -> wedges anchored at this vertex
     uint64_t *work_nh;    // [n]   of those, wedges whose endpoint lies below the hub window
     unsigned long long *pv;  // [n] balanced butterflies containing each vertex (when asked)
