@@ -633,8 +633,6 @@ size_t side_bytes(int64_t n, int64_t nE) {
 
 }  // namespace
 
-void build_init() {}
-
 BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE) {
     int64_t n = nU + nV;
     int64_t nmax = std::max<int64_t>(std::max(nU, nV), 1);

@@ -986,7 +986,7 @@ void init_cfg() {
 
 }  // namespace
 
-void count_init() { init_cfg(); build_init(); }
+void count_init() { init_cfg(); }
 
 void launch_count(const DevGraph &g, cudaStream_t s, int64_t *per_vertex_dev, cudaEvent_t *ev) {
     (void)per_vertex_dev;

@@ -84,11 +84,12 @@ enum Ctr : uint32_t {
 // per-count scratch (zeroed before each count)
 struct CountScratch {
     unsigned long long acc[4];   // balanced lo/hi, total lo/hi (128-bit sums)
-    uint32_t job_next[5];        // dynamic job cursors: one per class, then per-vertex
+    uint32_t job_next[6];        // dynamic job cursors: one per class, then the per-vertex walks
     uint32_t err;
     uint32_t pad[2];
 };
 constexpr int JOB_PER_VERTEX = 4;
+constexpr int JOB_PV_TEAM = 5;
 
 struct DevGraph {
     int64_t nU = 0, nV = 0, nE = 0;
@@ -214,8 +215,7 @@ void launch_base(const DevGraph &g, uint8_t *scratch, uint64_t per_cta,
 // Flip the signs of listed input edges (device list of n indices).
 void launch_flip(DevGraph &g, const int64_t *edge_idx_dev, int64_t n, cudaStream_t s);
 
-// One-time per-device kernel attributes (shared-memory opt-ins).
-void build_init();
+// One-time per-device kernel attributes (shared-memory opt-ins, grids).
 void count_init();
 
 // Sets the calling thread's bb_last_error() message; returns st.

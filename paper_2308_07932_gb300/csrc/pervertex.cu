@@ -18,8 +18,10 @@
 // adjacency entry of each side and summed per input edge at the end.
 //
 // This runs only when per-vertex or per-edge counts are requested, after
-// the regular count; its walk is simple (one warp per middle) rather than
-// fast.
+// the regular count. Warp-class anchors are walked one per warp (k_pv_warp),
+// the others one per CTA, one warp per middle (k_pv): with a single
+// 512-thread CTA per SM the coalesced reads of a warp per middle beat a
+// lane walker here.
 #include <algorithm>
 #include "graph.cuh"
 
@@ -27,16 +29,25 @@ namespace bb {
 
 namespace {
 
+// Two instances of k_pv: dense-class and CTA-hash anchors in 512-thread
+// CTAs over 192 KiB of counters (one CTA per SM), and team-class anchors,
+// whose below-window endpoints fit a TEAM_CAP-slot hash by construction, in
+// 128-thread CTAs over 16 KiB (several CTAs per SM).
 constexpr int PV_THREADS = 512;
-constexpr uint32_t PV_HASH_CAP = 16384;   // u64 slots (128 KiB), shares memory with the counters
 constexpr uint32_t PV_DENSE_CAP = 49152;  // dense counters (192 KiB): long ranges in fewer windows
+constexpr int PVT_THREADS = 128;
+constexpr uint32_t PVT_WORDS = HUB_WINDOW + 2 * TEAM_CAP;  // hub window + TEAM_CAP hash slots
 
+constexpr uint32_t pow2_floor(uint32_t x) {
+    uint32_t p = 1;
+    while (p <= x / 2) p <<= 1;
+    return p;
+}
+
+template <int TH, uint32_t WORDS>
 struct PvSmem {
-    union {
-        uint32_t cnt[PV_DENSE_CAP];
-        unsigned long long tab[PV_HASH_CAP];
-    };
-    unsigned long long red[PV_THREADS / 32];
+    uint32_t cnt[WORDS];  // dense counters, or the hub window then the hash
+    unsigned long long red[TH / 32];
     uint32_t job;
 };
 
@@ -80,30 +91,34 @@ struct PvOut {
     unsigned long long *pe[2];
 };
 
-__global__ void __launch_bounds__(PV_THREADS) k_pv(DevGraph G, PvOut out) {
+template <int TH, uint32_t WORDS, bool TEAM>
+__global__ void __launch_bounds__(TH) k_pv(DevGraph G, PvOut out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PvSmem &sm = *reinterpret_cast<PvSmem *>(smem_raw);
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = PV_THREADS / 32;
+    PvSmem<TH, WORDS> &sm = *reinterpret_cast<PvSmem<TH, WORDS> *>(smem_raw);
+    // hash slots after the window: the largest power of two that fits
+    constexpr uint32_t HYB_CAP = pow2_floor((WORDS - HUB_WINDOW) / 2);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = TH / 32;
     uint32_t *err = &G.scratch->err;
-    // anchors of the team, CTA-hash and dense classes (warp-class anchors
-    // go to k_pv_warp); a split dense anchor is taken once, at its first part
+    // team anchors, or the dense and CTA-hash classes (warp-class anchors go
+    // to k_pv_warp); a split dense anchor is taken once, at its first part
     const uint32_t nT = G.ctr[CTR_TEAM], nC = G.ctr[CTR_CTAH], nD = G.ctr[CTR_DENSE];
-    const uint32_t nJ = nT + nC + nD;
+    const uint32_t nJ = TEAM ? nT : nD + nC;
     for (;;) {
-        if (t == 0) sm.job = atomicAdd(&G.scratch->job_next[JOB_PER_VERTEX], 1u);
+        if (t == 0) sm.job = atomicAdd(&G.scratch->job_next[TEAM ? JOB_PV_TEAM : JOB_PER_VERTEX], 1u);
         __syncthreads();
         const uint32_t jb = sm.job;
         __syncthreads();
         if (jb >= nJ) break;
+        // heaviest first: dense jobs, then CTA-hash anchors
         uint32_t packed;
-        if (jb < nT) {
+        if (TEAM) {
             packed = G.team_list[jb].anchor;
-        } else if (jb < nT + nC) {
-            packed = G.ctah_list[jb - nT].anchor;
-        } else {
-            const DenseJob &J = G.dense_jobs[jb - nT - nC];
+        } else if (jb < nD) {
+            const DenseJob &J = G.dense_jobs[jb];
             if (J.m0 != 0) continue;
             packed = J.anchor;
+        } else {
+            packed = G.ctah_list[jb - nD].anchor;
         }
         const int sd = (int)(packed & 1u);
         const SideCSR &S = sd ? G.side[1] : G.side[0];
@@ -114,21 +129,37 @@ __global__ void __launch_bounds__(PV_THREADS) k_pv(DevGraph G, PvOut out) {
         if (W == 0) continue;
         const int64_t rb = S.off[r];
         const uint32_t deg = (uint32_t)(S.off[r + 1] - rb);
-        const uint64_t above = (uint64_t)(S.n - r - 1);
-        const uint64_t dh = W < above ? W : above;
-        const bool dense = above <= PV_DENSE_CAP || dh * 5 / 4 >= PV_HASH_CAP;
+        const uint32_t ns = (uint32_t)S.n;
+        // hybrid layout: the endpoints in the hub window (the top HUB_WINDOW
+        // ranks, those above the anchor) in dense counters, the ones below
+        // it in a hash sized by their count; dense layout (when that hash
+        // would not fit): counters over the whole endpoint range, walked in
+        // windows of the counter capacity when it is longer
+        const uint32_t wb = ns > HUB_WINDOW ? ns - HUB_WINDOW : 0u;
+        const uint32_t wlo = wb > r + 1 ? wb : r + 1;  // first endpoint in the window
+        const uint32_t wlen = ns - wlo;
+        const uint64_t above_nh = (uint64_t)(wlo - (r + 1));
+        const uint64_t wnh = S.work_nh[r];
+        const uint64_t need = (wnh < above_nh ? wnh : above_nh) * 5 / 4 + 1;
+        const bool hybrid = need <= HYB_CAP;
+        if (TEAM && !hybrid) {  // impossible for a team-class anchor
+            set_error(err, E_INTERNAL);
+            continue;
+        }
         uint32_t cap = 32, shift = 27;
-        if (!dense)
-            while ((uint64_t)cap < dh + dh / 4 + 1) { cap <<= 1; shift--; }
+        if (hybrid)
+            while ((uint64_t)cap < need) { cap <<= 1; shift--; }
         const uint32_t mask = cap - 1;
+        unsigned long long *tab = reinterpret_cast<unsigned long long *>(sm.cnt + HUB_WINDOW);
         unsigned long long wsum = 0;  // balanced butterflies containing the anchor
-        const uint32_t e_lo = r + 1, e_hi = (uint32_t)S.n;
-        for (uint32_t e0 = e_lo; e0 < e_hi; e0 += dense ? PV_DENSE_CAP : (e_hi - e_lo)) {
-            const uint32_t e1 = dense && e_hi - e0 > PV_DENSE_CAP ? e0 + PV_DENSE_CAP : e_hi;
-            const bool clip = dense && (e_hi - e_lo) > PV_DENSE_CAP;
-            const uint32_t len = dense ? e1 - e0 : cap;
-            if (dense) for (uint32_t i = t; i < len; i += PV_THREADS) sm.cnt[i] = 0;
-            else for (uint32_t i = t; i < cap; i += PV_THREADS) sm.tab[i] = 0ull;
+        const uint32_t e_lo = r + 1, e_hi = ns;
+        for (uint32_t e0 = e_lo; e0 < e_hi; e0 += hybrid ? (e_hi - e_lo) : WORDS) {
+            const uint32_t e1 = !hybrid && e_hi - e0 > WORDS ? e0 + WORDS : e_hi;
+            const bool clip = !hybrid && (e_hi - e_lo) > WORDS;
+            const uint32_t len = hybrid ? wlen : e1 - e0;
+            for (uint32_t i = t; i < len; i += TH) sm.cnt[i] = 0;
+            if (hybrid)
+                for (uint32_t i = t; i < cap; i += TH) tab[i] = 0ull;
             __syncthreads();
             // segment of middle j's row: the wedge suffix, clipped to [e0, e1)
             auto segment = [&](uint32_t j, int64_t &st, int64_t &en, uint32_t &sw, uint32_t &v) {
@@ -140,7 +171,14 @@ __global__ void __launch_bounds__(PV_THREADS) k_pv(DevGraph G, PvOut out) {
                     en = lower_bound_u32(O.adj, st, en, e1 << 1);
                 }
             };
-            // pass 1: tally
+            // counter index of endpoint u (>= len: in the hash)
+            auto index = [&](uint32_t u) -> uint32_t {
+                if (hybrid) return u >= wlo ? u - wlo : 0xffffffffu;
+                const uint32_t idx = u - e0;
+                if (idx >= len) set_error(err, E_INTERNAL);
+                return idx;
+            };
+            // pass 1: tally (one warp per middle, coalesced reads of its suffix)
             for (uint32_t j = warp; j < deg; j += nwarps) {
                 int64_t st, en; uint32_t sw, v;
                 segment(j, st, en, sw, v);
@@ -148,12 +186,9 @@ __global__ void __launch_bounds__(PV_THREADS) k_pv(DevGraph G, PvOut out) {
                     const uint32_t x = O.adj[p];
                     const uint32_t u = x >> 1;
                     const uint32_t inc = ((x ^ sw) & 1u) ? INC_ASYM : INC_SYM;
-                    if (dense) {
-                        const uint32_t idx = u - e0;
-                        if (idx < len) atomicAdd(&sm.cnt[idx], inc); else set_error(err, E_INTERNAL);
-                    } else {
-                        pv_hash_add(sm.tab, shift, mask, u + 1, inc, err);
-                    }
+                    const uint32_t idx = index(u);
+                    if (idx < len) atomicAdd(&sm.cnt[idx], inc);
+                    else if (hybrid) pv_hash_add(tab, shift, mask, u + 1, inc, err);
                 }
             }
             __syncthreads();
@@ -166,13 +201,10 @@ __global__ void __launch_bounds__(PV_THREADS) k_pv(DevGraph G, PvOut out) {
                 for (int64_t p = st + lane; p < en; p += 32) {
                     const uint32_t x = O.adj[p];
                     const uint32_t u = x >> 1;
+                    const uint32_t idx = index(u);
                     uint32_t c = 0;
-                    if (dense) {
-                        const uint32_t idx = u - e0;
-                        if (idx < len) c = sm.cnt[idx];
-                    } else {
-                        c = pv_hash_find(sm.tab, shift, mask, u + 1, err);
-                    }
+                    if (idx < len) c = sm.cnt[idx];
+                    else if (hybrid) c = pv_hash_find(tab, shift, mask, u + 1, err);
                     const uint32_t ct = ((x ^ sw) & 1u) ? (c >> 16) : (c & 0xffffu);
                     const unsigned long long k = ct > 0 ? ct - 1 : 0;
                     msum += k;
@@ -185,26 +217,25 @@ __global__ void __launch_bounds__(PV_THREADS) k_pv(DevGraph G, PvOut out) {
                 }
             }
             __syncthreads();
-            if (!out.vertex) {
-                if (!dense) break;
-                continue;
-            }
+            if (!out.vertex) continue;
             // each pair's balanced butterflies contain both of its endpoints
-            for (uint32_t i = t; i < len; i += PV_THREADS) {
-                uint32_t c, u;
-                if (dense) { c = sm.cnt[i]; u = e0 + i; }
-                else {
-                    const unsigned long long x = sm.tab[i];
-                    c = (uint32_t)x; u = (uint32_t)(x >> 32) - 1u;
-                    if (x == 0ull) c = 0;
-                }
+            const uint32_t ubase = hybrid ? wlo : e0;
+            for (uint32_t i = t; i < len; i += TH) {
+                const uint32_t c = sm.cnt[i];
                 if (c) {
                     const unsigned long long b = c2(c & 0xffffu) + c2(c >> 16);
-                    if (b) { atomicAdd(&S.pv[u], b); wsum += b; }
+                    if (b) { atomicAdd(&S.pv[ubase + i], b); wsum += b; }
                 }
             }
+            if (hybrid)
+                for (uint32_t i = t; i < cap; i += TH) {
+                    const unsigned long long x = tab[i];
+                    if (!x) continue;
+                    const uint32_t c = (uint32_t)x;
+                    const unsigned long long b = c2(c & 0xffffu) + c2(c >> 16);
+                    if (b) { atomicAdd(&S.pv[(uint32_t)(x >> 32) - 1u], b); wsum += b; }
+                }
             __syncthreads();
-            if (!dense) break;
         }
         if (out.vertex) {
             wsum = warp_sum_u64(wsum);
@@ -375,8 +406,20 @@ __global__ void k_pv_out(SideCSR S, int64_t base, int64_t *out) {
         out[base + S.id_of_sr[r]] = (int64_t)S.pv[r];
 }
 
-int g_pv_blocks = 0, g_pvw_blocks = 0, g_pv_device = -1;
+int g_pv_blocks = 0, g_pvt_blocks = 0, g_pvw_blocks = 0, g_pv_device = -1;
 constexpr size_t PVW_SMEM = (PVW_THREADS / 32) * sizeof(PvWarpSmem);
+constexpr size_t PV_SMEM = sizeof(PvSmem<PV_THREADS, PV_DENSE_CAP>);
+constexpr size_t PVT_SMEM = sizeof(PvSmem<PVT_THREADS, PVT_WORDS>);
+auto *const k_pv_big = k_pv<PV_THREADS, PV_DENSE_CAP, false>;
+auto *const k_pv_team = k_pv<PVT_THREADS, PVT_WORDS, true>;
+
+template <typename K>
+int pv_blocks(K kernel, int threads, size_t smem, int sms) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem);
+    return std::max(1, b) * sms;
+}
 
 void pv_init() {
     int dev = 0;
@@ -384,16 +427,22 @@ void pv_init() {
     if (g_pv_device != dev) {
         cudaDeviceProp prop;
         cudaGetDeviceProperties(&prop, dev);
-        cudaFuncSetAttribute(k_pv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PvSmem));
-        int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pv, PV_THREADS, sizeof(PvSmem));
-        g_pv_blocks = std::max(1, b) * prop.multiProcessorCount;
-        cudaFuncSetAttribute(k_pv_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PVW_SMEM);
-        b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pv_warp, PVW_THREADS, PVW_SMEM);
-        g_pvw_blocks = std::max(1, b) * prop.multiProcessorCount;
+        const int sms = prop.multiProcessorCount;
+        g_pv_blocks = pv_blocks(k_pv_big, PV_THREADS, PV_SMEM, sms);
+        g_pvt_blocks = pv_blocks(k_pv_team, PVT_THREADS, PVT_SMEM, sms);
+        g_pvw_blocks = pv_blocks(k_pv_warp, PVW_THREADS, PVW_SMEM, sms);
         g_pv_device = dev;
     }
+}
+
+// the three per-vertex walks: warp-class, team-class, then dense and
+// CTA-hash anchors (each kernel drains its own job cursor)
+void launch_pv_kernels(const DevGraph &g, const PvOut &o, cudaStream_t s) {
+    cudaMemsetAsync(&g.scratch->job_next[JOB_PV_TEAM], 0, 4, s);
+    cudaMemsetAsync(&g.scratch->job_next[JOB_PER_VERTEX], 0, 4, s);
+    k_pv_warp<<<g_pvw_blocks, PVW_THREADS, PVW_SMEM, s>>>(g, o); note_launch();
+    k_pv_team<<<g_pvt_blocks, PVT_THREADS, PVT_SMEM, s>>>(g, o); note_launch();
+    k_pv_big<<<g_pv_blocks, PV_THREADS, PV_SMEM, s>>>(g, o); note_launch();
 }
 
 }  // namespace
@@ -404,10 +453,8 @@ void launch_per_edge(const DevGraph &g, int64_t *out_dev, unsigned long long *pe
     if (g.nE == 0) return;
     unsigned long long *peU = pe_ws, *peV = pe_ws + g.nE;
     cudaMemsetAsync(pe_ws, 0, (size_t)g.nE * 16, s);
-    cudaMemsetAsync(&g.scratch->job_next[JOB_PER_VERTEX], 0, 4, s);  // job cursor
     PvOut o{0, {peU, peV}};
-    k_pv_warp<<<g_pvw_blocks, PVW_THREADS, PVW_SMEM, s>>>(g, o); note_launch();
-    k_pv<<<g_pv_blocks, PV_THREADS, sizeof(PvSmem), s>>>(g, o); note_launch();
+    launch_pv_kernels(g, o, s);
     const int64_t blocks = std::min<int64_t>((g.nE + 255) / 256, 16384);
     k_pe_out<<<(unsigned)blocks, 256, 0, s>>>(g, peU, peV, out_dev); note_launch();
 }
@@ -417,10 +464,8 @@ void launch_per_vertex(const DevGraph &g, int64_t *out_dev, cudaStream_t s) {
     for (int sd = 0; sd < 2; sd++)
         if (g.side[sd].n > 0)
             cudaMemsetAsync(g.side[sd].pv, 0, (size_t)g.side[sd].n * 8, s);
-    cudaMemsetAsync(&g.scratch->job_next[JOB_PER_VERTEX], 0, 4, s);  // job cursor
     PvOut o{1, {nullptr, nullptr}};
-    k_pv_warp<<<g_pvw_blocks, PVW_THREADS, PVW_SMEM, s>>>(g, o); note_launch();
-    k_pv<<<g_pv_blocks, PV_THREADS, sizeof(PvSmem), s>>>(g, o); note_launch();
+    launch_pv_kernels(g, o, s);
     for (int sd = 0; sd < 2; sd++) {
         const int64_t n = g.side[sd].n;
         if (n == 0) continue;
