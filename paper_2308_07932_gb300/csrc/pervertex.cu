@@ -30,11 +30,12 @@ namespace bb {
 namespace {
 
 // Two instances of k_pv: dense-class and CTA-hash anchors in 512-thread
-// CTAs over 192 KiB of counters (one CTA per SM), and team-class anchors,
+// CTAs over 96 KiB of counters (two CTAs per SM; the hybrid hash then holds
+// 8,192 slots, enough for every CTA-hash anchor), and team-class anchors,
 // whose below-window endpoints fit a TEAM_CAP-slot hash by construction, in
 // 128-thread CTAs over 16 KiB (several CTAs per SM).
 constexpr int PV_THREADS = 512;
-constexpr uint32_t PV_DENSE_CAP = 49152;  // dense counters (192 KiB): long ranges in fewer windows
+constexpr uint32_t PV_DENSE_CAP = 24576;  // dense counters (96 KiB)
 constexpr int PVT_THREADS = 128;
 constexpr uint32_t PVT_WORDS = HUB_WINDOW + 2 * TEAM_CAP;  // hub window + TEAM_CAP hash slots
 
@@ -43,6 +44,11 @@ constexpr uint32_t pow2_floor(uint32_t x) {
     while (p <= x / 2) p <<= 1;
     return p;
 }
+
+// every CTA-hash anchor (below-window endpoints < CTAH_CAP / 2) fits the
+// heavy instance's hybrid hash at load <= 0.8
+static_assert(pow2_floor((PV_DENSE_CAP - HUB_WINDOW) / 2) >= CTAH_CAP / 2 * 5 / 4 + 1,
+              "CTA-hash anchors would fall back to dense windows");
 
 template <int TH, uint32_t WORDS>
 struct PvSmem {
