@@ -527,6 +527,7 @@ struct alignas(16) WarpSmem {
 
 // per-warp copies are laid out back to back and reset with 16-byte stores
 static_assert(sizeof(WarpSmem) % 16 == 0, "WarpSmem must keep 16-byte alignment");
+static_assert((HUB_WINDOW & (HUB_WINDOW - 1)) == 0, "hub window indexes are masked");
 static_assert(offsetof(WarpSmem, tab) % 16 == 0, "table needs 16-byte alignment");
 
 // one warp-class anchor, walked by one warp
@@ -551,30 +552,31 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
         const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
         if (wnh > 0) table_geometry(wnh < above_nh ? wnh : above_nh, 32, WARP_CAP, cap, shift);
         const uint32_t mask = cap - 1;
-        bool bad_any = false;
+        uint32_t bad_off = 0;
         // 32-bit sums for the hub part: a lane walks at most W/32 + 1 <= 513
         // wedges of the anchor, each adding at most 2 * 255
         uint32_t b32 = 0, t32 = 0;
         lane_walk2(
             A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, sm.walk2, (int)lane, HubSeg{},
             [&](uint32_t u, uint32_t asym) {
-                // S in bits 0..7 and A in bits 8..15 of the endpoint's 16-bit
-                // half-word (both <= the degree <= 255, so S + A fits 8 bits)
-                uint32_t wi = u - wb;
-                const bool bad = wi >= HUB_WINDOW;  // checked, not branched on
-                bad_any |= bad;
-                wi = bad ? 0u : wi;
+                // S in byte 0 and A in byte 1 of the endpoint's 16-bit half
+                // of a word (both <= the degree <= 255). The increment is a
+                // single set bit; as a byte mask for dp4a it picks the
+                // tally's own previous value out of the returned word, and
+                // 0x0101 at the half picks S + A.
+                const uint32_t wi = u - wb;
+                bad_off |= wi;  // any index >= HUB_WINDOW sets a high bit
                 const uint32_t sh = (wi & 1u) << 4;
-                const uint32_t old =
-                    (atomicAdd(&sm.win[wi >> 1], (1u + asym * 255u) << sh) >> sh) & 0xffffu;
-                b32 += (old >> (asym << 3)) & 0xffu;
-                t32 += ((old * 0x101u) >> 8) & 0xffu;  // S + A
+                const uint32_t inc = 1u << (sh | (asym << 3));
+                const uint32_t old = atomicAdd(&sm.win[(wi >> 1) & (HUB_WINDOW / 2 - 1)], inc);
+                b32 = __dp4a(old, inc, b32);
+                t32 = __dp4a(old, 0x0101u << sh, t32);
             },
             LowSeg{},
             [&](uint32_t u, uint32_t asym) {
                 hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
             });
-        if (bad_any) set_error(err, E_INTERNAL);
+        if (bad_off >= HUB_WINDOW) set_error(err, E_INTERNAL);
         bal += b32;
         tot += t32;
         // reset the window words an endpoint can have reached
