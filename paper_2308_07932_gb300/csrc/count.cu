@@ -133,7 +133,8 @@ constexpr uint32_t WALK_ITEM = 256;
 // the anchor side's descriptors smd; the middles' rows are in oadj) as a
 // team of TS threads (t = thread index in the team). seg(md, st, len) picks
 // the segment [st, st+len) of a middle's row from its descriptor;
-// add(u_side_rank, asymmetric) is called once per wedge.
+// add(entry, sign bit of the anchor's edge to the middle) is called once per
+// wedge (entry = endpoint side rank << 1 | sign of the middle-endpoint edge).
 //
 // Per chunk of TS middles the team scans the segment lengths and compacts
 // the non-empty segments (their ends, incl[], are the chunk's wedge
@@ -252,7 +253,7 @@ __device__ __forceinline__ void team_walk(const uint4 *__restrict__ smd,
                     if (ok[u]) xv[u] = oadj[addr[u]];
 #pragma unroll
                 for (int u = 0; u < UNROLL; u++)
-                    if (ok[u]) add(xv[u] >> 1, (xv[u] ^ swq[u]) & 1u);
+                    if (ok[u]) add(xv[u], swq[u]);
             }
         }
         team_sync<TS>();
@@ -308,12 +309,12 @@ __device__ __forceinline__ void lane_range(const uint32_t *__restrict__ oadj, co
 #pragma unroll
         for (int u = 0; u < U; u++) xv[u] = oadj[pa[u]];
 #pragma unroll
-        for (int u = 0; u < U; u++) add(xv[u] >> 1, (xv[u] ^ sq[u]) & 1u);
+        for (int u = 0; u < U; u++) add(xv[u], sq[u]);
     }
     for (; i < b; i++) {
         if (p == pend) next_segment();
         const uint32_t x = oadj[p++];
-        add(x >> 1, (x ^ cs) & 1u);
+        add(x, cs);
     }
 }
 
@@ -542,12 +543,13 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
         table_geometry(W < above ? W : above, 32, WARP_CAP, cap, shift);
         const uint32_t mask = cap - 1;
         lane_walk<32>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, FullSeg{},
-                      [&](uint32_t u, uint32_t asym) {
-                          hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
+                      [&](uint32_t x, uint32_t sw) {
+                          hash_wedge(sm.tab, shift, mask, x >> 1, (x ^ sw) & 1u, err, bal, tot);
                       });
     } else {
         const int64_t ns = A.ns;
         const uint32_t wb = ns > (int64_t)HUB_WINDOW ? (uint32_t)(ns - HUB_WINDOW) : 0u;
+        const uint32_t wb2 = wb << 1;  // the window base as an entry (side ranks < 2^31)
         const uint64_t wnh = A.wnh;
         const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
         if (wnh > 0) table_geometry(wnh < above_nh ? wnh : above_nh, 32, WARP_CAP, cap, shift);
@@ -558,25 +560,27 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
         uint32_t b32 = 0, t32 = 0;
         lane_walk2(
             A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, sm.walk2, (int)lane, HubSeg{},
-            [&](uint32_t u, uint32_t asym) {
+            [&](uint32_t x, uint32_t sw) {
                 // S in byte 0 and A in byte 1 of the endpoint's 16-bit half
-                // of a word (both <= the degree <= 255). The increment is a
-                // single set bit; as a byte mask for dp4a it picks the
-                // tally's own previous value out of the returned word, and
-                // 0x0101 at the half picks S + A.
-                const uint32_t wi = u - wb;
-                bad_off |= wi;  // any index >= HUB_WINDOW sets a high bit
-                const uint32_t sh = (wi & 1u) << 4;
-                const uint32_t inc = 1u << (sh | (asym << 3));
-                const uint32_t old = atomicAdd(&sm.win[(wi >> 1) & (HUB_WINDOW / 2 - 1)], inc);
+                // of a word (both <= the degree <= 255). The entry less
+                // twice the window base is 2 * (window index) + sign: bit 1
+                // picks the half and bit 0 xor the anchor edge's sign the
+                // byte. The increment is that byte's lowest bit; as a byte
+                // mask for dp4a it picks the tally's own previous value out
+                // of the returned word, and 0x0101 at the half picks S + A.
+                const uint32_t xi = x - wb2;
+                bad_off |= xi;  // any entry outside the window sets a high bit
+                const uint32_t sh = ((xi ^ sw) & 3u) << 3;
+                const uint32_t inc = 1u << sh;
+                const uint32_t old = atomicAdd(&sm.win[(xi >> 2) & (HUB_WINDOW / 2 - 1)], inc);
                 b32 = __dp4a(old, inc, b32);
-                t32 = __dp4a(old, 0x0101u << sh, t32);
+                t32 = __dp4a(old, 0x0101u << (sh & 16u), t32);
             },
             LowSeg{},
-            [&](uint32_t u, uint32_t asym) {
-                hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
+            [&](uint32_t x, uint32_t sw) {
+                hash_wedge(sm.tab, shift, mask, x >> 1, (x ^ sw) & 1u, err, bal, tot);
             });
-        if (bad_off >= HUB_WINDOW) set_error(err, E_INTERNAL);
+        if (bad_off >= 2 * HUB_WINDOW) set_error(err, E_INTERNAL);
         bal += b32;
         tot += t32;
         // reset the window words an endpoint can have reached
@@ -644,13 +648,27 @@ __device__ __forceinline__ void hybrid_anchor(const DevGraph &G, HybSmem<TS, HCA
     const uint64_t W = A.W, wnh = A.wnh;
     const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
     if (W > wnh) {  // endpoints inside the hub window
+        // Team anchors (at most TEAM_W_MAX wedges, each adding at most
+        // 2 * 65535) sum the hub part in 32 bits: dp2a takes the previous
+        // S or A (16-bit halves of the returned word) or their sum.
+        constexpr bool narrow = TS == TEAM_THREADS;
+        static_assert(!narrow || TEAM_W_MAX * 2 * 65535 < (1ull << 32), "32-bit team sums");
+        uint32_t b32 = 0, t32 = 0;
         lane_walk<TS>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, HubSeg{},
-                      [&](uint32_t u, uint32_t asym) {
-                          const uint32_t idx = u - wb;
+                      [&](uint32_t x, uint32_t sw) {
+                          const uint32_t asym = (x ^ sw) & 1u;
+                          const uint32_t idx = (x >> 1) - wb;
                           if (idx >= HUB_WINDOW) { set_error(err, E_INTERNAL); return; }
                           const uint32_t old = atomicAdd(&sm.win[idx], asym ? INC_ASYM : INC_SYM);
-                          wedge_terms(old & 0xffffu, old >> 16, asym, bal, tot);
+                          if constexpr (narrow) {
+                              b32 = __dp2a_lo(old, 1u << (asym << 3), b32);
+                              t32 = __dp2a_lo(old, 0x0101u, t32);
+                          } else {
+                              wedge_terms(old & 0xffffu, old >> 16, asym, bal, tot);
+                          }
                       });
+        bal += b32;
+        tot += t32;
     }
     uint32_t cap = 0;
     if (wnh > 0) {  // endpoints below the window
@@ -658,8 +676,8 @@ __device__ __forceinline__ void hybrid_anchor(const DevGraph &G, HybSmem<TS, HCA
         table_geometry(wnh < above_nh ? wnh : above_nh, 32, HCAP, cap, shift);
         const uint32_t mask = cap - 1;
         lane_walk<TS>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, LowSeg{},
-                      [&](uint32_t u, uint32_t asym) {
-                          hash_wedge(sm.tab, shift, mask, u, asym, err, bal, tot);
+                      [&](uint32_t x, uint32_t sw) {
+                          hash_wedge(sm.tab, shift, mask, x >> 1, (x ^ sw) & 1u, err, bal, tot);
                       });
     }
     __syncthreads();
@@ -726,8 +744,9 @@ __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, cons
         const uint32_t len = e1 - e0;
         for (uint32_t i = t; i < len; i += DENSE_THREADS) sm.cnt[i] = 0;
         __syncthreads();
-        auto add = [&](uint32_t u, uint32_t asym) {
-            const uint32_t idx = u - e0;
+        auto add = [&](uint32_t x, uint32_t sw) {
+            const uint32_t asym = (x ^ sw) & 1u;
+            const uint32_t idx = (x >> 1) - e0;
             if (idx >= len) { set_error(&sc->err, E_INTERNAL); return; }
             const uint32_t old = atomicAdd(&sm.cnt[idx], asym ? INC_ASYM : INC_SYM);
             wedge_terms(old & 0xffffu, old >> 16, asym, bal, tot);
