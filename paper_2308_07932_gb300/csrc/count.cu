@@ -452,6 +452,17 @@ __device__ __forceinline__ void hash_wedge(unsigned long long *tab, uint32_t shi
     wedge_terms(old & 0xffffu, old >> 16, asym, bal, tot);
 }
 
+// the same with 32-bit running sums (anchors whose sums provably fit):
+// dp2a takes the previous S or A (16-bit halves of the slot's count) or both
+__device__ __forceinline__ void hash_wedge32(unsigned long long *tab, uint32_t shift,
+                                             uint32_t mask, uint32_t x, uint32_t sw,
+                                             uint32_t *err, uint32_t &b32, uint32_t &t32) {
+    const uint32_t asym = (x ^ sw) & 1u;
+    const uint32_t old = hash_add(tab, shift, mask, (x >> 1) + 1, asym ? INC_ASYM : INC_SYM, err);
+    b32 = __dp2a_lo(old, 1u << (asym << 3), b32);
+    t32 = __dp2a_lo(old, 0x0101u, t32);
+}
+
 // zero the first `cap` slots of a table (cap a multiple of 2) as a team
 template <int TS>
 __device__ __forceinline__ void clear_table(unsigned long long *tab, uint32_t cap, int t) {
@@ -539,12 +550,15 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
     const Anchor A = load_anchor(G, rec);
     const uint64_t W = A.W, above = (uint64_t)(A.ns - A.r - 1);
     uint32_t cap = 0, shift = 0;
+    // 32-bit sums: a lane walks at most W/32 + 1 <= 513 wedges of each
+    // family of the anchor, each adding at most 2 * 255
+    uint32_t b32 = 0, t32 = 0;
     if (W <= WARP_SMALL_W) {  // hash every endpoint
         table_geometry(W < above ? W : above, 32, WARP_CAP, cap, shift);
         const uint32_t mask = cap - 1;
         lane_walk<32>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, FullSeg{},
                       [&](uint32_t x, uint32_t sw) {
-                          hash_wedge(sm.tab, shift, mask, x >> 1, (x ^ sw) & 1u, err, bal, tot);
+                          hash_wedge32(sm.tab, shift, mask, x, sw, err, b32, t32);
                       });
     } else {
         const int64_t ns = A.ns;
@@ -555,9 +569,6 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
         if (wnh > 0) table_geometry(wnh < above_nh ? wnh : above_nh, 32, WARP_CAP, cap, shift);
         const uint32_t mask = cap - 1;
         uint32_t bad_off = 0;
-        // 32-bit sums for the hub part: a lane walks at most W/32 + 1 <= 513
-        // wedges of the anchor, each adding at most 2 * 255
-        uint32_t b32 = 0, t32 = 0;
         lane_walk2(
             A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, sm.walk2, (int)lane, HubSeg{},
             [&](uint32_t x, uint32_t sw) {
@@ -578,17 +589,17 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
             },
             LowSeg{},
             [&](uint32_t x, uint32_t sw) {
-                hash_wedge(sm.tab, shift, mask, x >> 1, (x ^ sw) & 1u, err, bal, tot);
+                hash_wedge32(sm.tab, shift, mask, x, sw, err, b32, t32);
             });
         if (bad_off >= 2 * HUB_WINDOW) set_error(err, E_INTERNAL);
-        bal += b32;
-        tot += t32;
         // reset the window words an endpoint can have reached
         const uint32_t first = (A.r + 1 > wb ? A.r + 1 - wb : 0u) >> 3;  // uint4 index
         uint4 *w4 = reinterpret_cast<uint4 *>(sm.win);
         for (uint32_t q = first + lane; q < HUB_WINDOW / 8; q += 32)
             w4[q] = make_uint4(0u, 0u, 0u, 0u);
     }
+    bal += b32;
+    tot += t32;
     clear_table<32>(sm.tab, cap, (int)lane);
     __syncwarp();
 }
