@@ -542,7 +542,14 @@ static_assert(sizeof(WarpSmem) % 16 == 0, "WarpSmem must keep 16-byte alignment"
 static_assert((HUB_WINDOW & (HUB_WINDOW - 1)) == 0, "hub window indexes are masked");
 static_assert(offsetof(WarpSmem, tab) % 16 == 0, "table needs 16-byte alignment");
 
-// one warp-class anchor, walked by one warp
+// anchors with at least this many wedges walk eight wedges per lane step
+// (more loads in flight) in the single-graph kernel
+constexpr uint64_t WARP_WIDE_W = 2048;
+
+// one warp-class anchor, walked by one warp; WIDE: large anchors take the
+// eight-wedge lane steps (the batch kernel, whose mix is mostly small
+// anchors, keeps four: the second walker instance slows it)
+template <bool WIDE>
 __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, const AnchorRec &rec,
                                             unsigned lane, unsigned long long &bal,
                                             unsigned long long &tot) {
@@ -569,28 +576,31 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
         if (wnh > 0) table_geometry(wnh < above_nh ? wnh : above_nh, 32, WARP_CAP, cap, shift);
         const uint32_t mask = cap - 1;
         uint32_t bad_off = 0;
-        lane_walk2(
-            A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, sm.walk2, (int)lane, HubSeg{},
-            [&](uint32_t x, uint32_t sw) {
-                // S in byte 0 and A in byte 1 of the endpoint's 16-bit half
-                // of a word (both <= the degree <= 255). The entry less
-                // twice the window base is 2 * (window index) + sign: bit 1
-                // picks the half and bit 0 xor the anchor edge's sign the
-                // byte. The increment is that byte's lowest bit; as a byte
-                // mask for dp4a it picks the tally's own previous value out
-                // of the returned word, and 0x0101 at the half picks S + A.
-                const uint32_t xi = x - wb2;
-                bad_off |= xi;  // any entry outside the window sets a high bit
-                const uint32_t sh = ((xi ^ sw) & 3u) << 3;
-                const uint32_t inc = 1u << sh;
-                const uint32_t old = atomicAdd(&sm.win[(xi >> 2) & (HUB_WINDOW / 2 - 1)], inc);
-                b32 = __dp4a(old, inc, b32);
-                t32 = __dp4a(old, 0x0101u << (sh & 16u), t32);
-            },
-            LowSeg{},
-            [&](uint32_t x, uint32_t sw) {
-                hash_wedge32(sm.tab, shift, mask, x, sw, err, b32, t32);
-            });
+        auto hub_add = [&](uint32_t x, uint32_t sw) {
+            // S in byte 0 and A in byte 1 of the endpoint's 16-bit half of a
+            // word (both <= the degree <= 255). The entry less twice the
+            // window base is 2 * (window index) + sign: bit 1 picks the half
+            // and bit 0 xor the anchor edge's sign the byte. The increment is
+            // that byte's lowest bit; as a byte mask for dp4a it picks the
+            // tally's own previous value out of the returned word, and
+            // 0x0101 at the half picks S + A.
+            const uint32_t xi = x - wb2;
+            bad_off |= xi;  // any entry outside the window sets a high bit
+            const uint32_t sh = ((xi ^ sw) & 3u) << 3;
+            const uint32_t inc = 1u << sh;
+            const uint32_t old = atomicAdd(&sm.win[(xi >> 2) & (HUB_WINDOW / 2 - 1)], inc);
+            b32 = __dp4a(old, inc, b32);
+            t32 = __dp4a(old, 0x0101u << (sh & 16u), t32);
+        };
+        auto low_add = [&](uint32_t x, uint32_t sw) {
+            hash_wedge32(sm.tab, shift, mask, x, sw, err, b32, t32);
+        };
+        if (WIDE && W >= WARP_WIDE_W)
+            lane_walk2<8>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, sm.walk2, (int)lane, HubSeg{},
+                          hub_add, LowSeg{}, low_add);
+        else
+            lane_walk2<4>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, sm.walk2, (int)lane, HubSeg{},
+                          hub_add, LowSeg{}, low_add);
         if (bad_off >= 2 * HUB_WINDOW) set_error(err, E_INTERNAL);
         // reset the window words an endpoint can have reached
         const uint32_t first = (A.r + 1 > wb ? A.r + 1 - wb : 0u) >> 3;  // uint4 index
@@ -612,7 +622,7 @@ __device__ __forceinline__ WarpSmem &warp_smem_init(unsigned char *smem_raw, uns
     return sm;
 }
 
-__global__ void __launch_bounds__(WARP_THREADS, 4) k_warp(DevGraph G) {
+__global__ void __launch_bounds__(WARP_THREADS, 3) k_warp(DevGraph G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const unsigned lane = lane_id();
     WarpSmem &sm = warp_smem_init(smem_raw, lane);
@@ -621,7 +631,7 @@ __global__ void __launch_bounds__(WARP_THREADS, 4) k_warp(DevGraph G) {
     const uint32_t GW = (gridDim.x * WARP_THREADS) >> 5;
     unsigned long long bal = 0, tot = 0;
     for (uint32_t idx = gw; idx < n; idx += GW) {
-        warp_anchor(G, sm, G.warp_list[idx], lane, bal, tot);
+        warp_anchor<true>(G, sm, G.warp_list[idx], lane, bal, tot);
         spill_if_large(G.scratch, bal, tot);
     }
     flush_warp(G.scratch, bal, tot);
@@ -870,7 +880,7 @@ __global__ void __launch_bounds__(WARP_THREADS, 4) k_warp_batch(BatchArgs B) {
                 do { gi++; gbeg = gend; gend = p[gi + 1]; } while (it >= gend);
             }
             const DevGraph &G = B.graphs[gi];
-            warp_anchor(G, sm, G.warp_list[it - gbeg], lane, bal, tot);
+            warp_anchor<false>(G, sm, G.warp_list[it - gbeg], lane, bal, tot);
         }
         bal = warp_sum_u64(bal); tot = warp_sum_u64(tot);
         if (lane == 0) acc_add(B.graphs[gi].scratch, bal, tot);
