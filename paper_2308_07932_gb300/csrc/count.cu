@@ -668,6 +668,9 @@ __device__ __forceinline__ void hybrid_anchor(const DevGraph &G, HybSmem<TS, HCA
     const uint32_t wb = ns > (int64_t)HUB_WINDOW ? (uint32_t)(ns - HUB_WINDOW) : 0u;
     const uint64_t W = A.W, wnh = A.wnh;
     const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
+    // lane steps: four wedges for team anchors (more register pressure
+    // costs them occupancy), eight for the CTA-hash class
+    constexpr int LU = TS == TEAM_THREADS ? 4 : 8;
     if (W > wnh) {  // endpoints inside the hub window
         // Team anchors (at most TEAM_W_MAX wedges, each adding at most
         // 2 * 65535) sum the hub part in 32 bits: dp2a takes the previous
@@ -675,7 +678,7 @@ __device__ __forceinline__ void hybrid_anchor(const DevGraph &G, HybSmem<TS, HCA
         constexpr bool narrow = TS == TEAM_THREADS;
         static_assert(!narrow || TEAM_W_MAX * 2 * 65535 < (1ull << 32), "32-bit team sums");
         uint32_t b32 = 0, t32 = 0;
-        lane_walk<TS>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, HubSeg{},
+        lane_walk<TS, LU>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, HubSeg{},
                       [&](uint32_t x, uint32_t sw) {
                           const uint32_t asym = (x ^ sw) & 1u;
                           const uint32_t idx = (x >> 1) - wb;
@@ -696,7 +699,7 @@ __device__ __forceinline__ void hybrid_anchor(const DevGraph &G, HybSmem<TS, HCA
         uint32_t shift;
         table_geometry(wnh < above_nh ? wnh : above_nh, 32, HCAP, cap, shift);
         const uint32_t mask = cap - 1;
-        lane_walk<TS>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, LowSeg{},
+        lane_walk<TS, LU>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, LowSeg{},
                       [&](uint32_t x, uint32_t sw) {
                           hash_wedge(sm.tab, shift, mask, x >> 1, (x ^ sw) & 1u, err, bal, tot);
                       });
