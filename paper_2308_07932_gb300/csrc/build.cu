@@ -692,30 +692,54 @@ void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_m
     g.scratch = c.take<CountScratch>(1);
 }
 
-uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
-                     void *temp_mem, cudaStream_t s, const BuildAux *aux) {
+namespace {
+
+// The build's temporaries, carved from the caller's block in one fixed
+// order (so the two build stages below see the same layout).
+struct BuildTemp {
+    uint32_t *deg_in[2], *eid[2], *rowid[2], *cursorV;
+    uint64_t *bufA, *bufB, *bufC, *keys[2];
+    uint32_t *ralt_k, *ralt_v;
+    void *ptemp;
+    uint32_t *meta[2], *grp[2];
+    ClassifyTemp T;
+    int64_t *bounds;
+    uint4 *rinfo[2];
+};
+
+BuildTemp carve_temp(const DevGraph &g, void *temp_mem) {
     const int64_t nU = g.nU, nV = g.nV, nE = g.nE;
     const int64_t nmax = std::max<int64_t>(std::max(nU, nV), 1);
     Carver c{(char *)temp_mem};
-    uint32_t *deg_in[2] = {c.take<uint32_t>(nU + 1), c.take<uint32_t>(nV + 1)};
-    uint32_t *eid[2] = {c.take<uint32_t>(nE + 1), c.take<uint32_t>(nE + 1)};
-    uint32_t *rowid[2] = {c.take<uint32_t>(nE + 1), c.take<uint32_t>(nE + 1)};
-    uint32_t *cursorV = c.take<uint32_t>(nV + 1);
-    uint64_t *bufA = c.take<uint64_t>(nE + 1);   // U-side row keys, later twin positions
-    uint64_t *bufB = c.take<uint64_t>(nE + 1);   // V-side row keys
-    uint64_t *bufC = c.take<uint64_t>(nE + 1);   // radix sort alternate buffer
-    uint64_t *keys[2] = {bufA, bufB};
-    uint32_t *ralt_k = c.take<uint32_t>(nmax + 1);
-    uint32_t *ralt_v = c.take<uint32_t>(nmax + 1);
-    void *ptemp = c.take<char>(std::max(radix_temp_bytes(nmax), scan_temp_bytes(nmax + 1)));
-    ClassifyTemp T;
-    uint32_t *meta[2] = {c.take<uint32_t>(nmax + 1), c.take<uint32_t>(nmax + 1)};
-    uint32_t *grp[2] = {c.take<uint32_t>(nmax + 1), c.take<uint32_t>(nmax + 1)};
-    T.bucket_cnt = c.take<uint32_t>(NCLS * NB);
-    T.bucket_base = c.take<uint32_t>(NCLS * NB);
-    int64_t *bounds = c.take<int64_t>(32);
-    uint4 *rinfo[2] = {c.take<uint4>(nU + 1), c.take<uint4>(nV + 1)};  // per-row records
+    BuildTemp t;
+    t.deg_in[0] = c.take<uint32_t>(nU + 1); t.deg_in[1] = c.take<uint32_t>(nV + 1);
+    t.eid[0] = c.take<uint32_t>(nE + 1); t.eid[1] = c.take<uint32_t>(nE + 1);
+    t.rowid[0] = c.take<uint32_t>(nE + 1); t.rowid[1] = c.take<uint32_t>(nE + 1);
+    t.cursorV = c.take<uint32_t>(nV + 1);
+    t.bufA = c.take<uint64_t>(nE + 1);   // U-side row keys, later twin positions
+    t.bufB = c.take<uint64_t>(nE + 1);   // V-side row keys
+    t.bufC = c.take<uint64_t>(nE + 1);   // radix sort alternate buffer
+    t.keys[0] = t.bufA; t.keys[1] = t.bufB;
+    t.ralt_k = c.take<uint32_t>(nmax + 1);
+    t.ralt_v = c.take<uint32_t>(nmax + 1);
+    t.ptemp = c.take<char>(std::max(radix_temp_bytes(nmax), scan_temp_bytes(nmax + 1)));
+    t.meta[0] = c.take<uint32_t>(nmax + 1); t.meta[1] = c.take<uint32_t>(nmax + 1);
+    t.grp[0] = c.take<uint32_t>(nmax + 1); t.grp[1] = c.take<uint32_t>(nmax + 1);
+    t.T.bucket_cnt = c.take<uint32_t>(NCLS * NB);
+    t.T.bucket_base = c.take<uint32_t>(NCLS * NB);
+    t.bounds = c.take<int64_t>(32);
+    t.rinfo[0] = c.take<uint4>(nU + 1); t.rinfo[1] = c.take<uint4>(nV + 1);  // per-row records
+    return t;
+}
 
+}  // namespace
+
+uint32_t build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
+                        void *temp_mem, cudaStream_t s) {
+    const int64_t nU = g.nU, nV = g.nV, nE = g.nE;
+    BuildTemp bt = carve_temp(g, temp_mem);
+    uint32_t **deg_in = bt.deg_in, *cursorV = bt.cursorV;
+    ClassifyTemp &T = bt.T;
     cudaMemsetAsync(g.err, 0, 4, s);
     cudaMemsetAsync(g.ctr, 0, NCTR * 4, s);
     cudaMemsetAsync(g.wedges, 0, 8, s);
@@ -733,6 +757,21 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
     cudaStreamSynchronize(s);
     if (herr) return herr;
 
+    return 0;
+}
+
+void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
+                void *temp_mem, cudaStream_t s, const BuildAux *aux) {
+    const int64_t nU = g.nU, nV = g.nV, nE = g.nE;
+    BuildTemp bt = carve_temp(g, temp_mem);
+    uint32_t **deg_in = bt.deg_in, **eid = bt.eid, **rowid = bt.rowid, *cursorV = bt.cursorV;
+    uint64_t *bufA = bt.bufA, *bufC = bt.bufC, **keys = bt.keys;
+    uint32_t *ralt_k = bt.ralt_k, *ralt_v = bt.ralt_v;
+    void *ptemp = bt.ptemp;
+    uint32_t **meta = bt.meta, **grp = bt.grp;
+    ClassifyTemp &T = bt.T;
+    int64_t *bounds = bt.bounds;
+    uint4 **rinfo = bt.rinfo;
     // 2. side ranks by (degree, id), then the global priority rank
     int64_t ns[2] = {nU, nV};
     for (int sd = 0; sd < 2; sd++) {
@@ -837,6 +876,13 @@ uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, con
         T.grp = grp[sd];
         k_emit<<<grid_for(ns[sd], BT, 2048), BT, 0, s>>>(g.side[sd], sd, T, g); note_launch();
     }
+}
+
+uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
+                     void *temp_mem, cudaStream_t s, const BuildAux *aux) {
+    const uint32_t e = build_validate(g, rowptr, col, sign, temp_mem, s);
+    if (e) return e;
+    build_rest(g, rowptr, col, sign, temp_mem, s, aux);
     return 0;
 }
 

@@ -1037,15 +1037,15 @@ void launch_count(const DevGraph &g, cudaStream_t s, int64_t *per_vertex_dev, cu
     (void)per_vertex_dev;
     init_cfg();
     cudaMemsetAsync(g.scratch, 0, sizeof(CountScratch), s);
-    if (ev) cudaEventRecord(ev[0], s);
+    if (ev) record_timing_event(ev[0], s);
     k_dense<<<g_cfg.dense_blocks, DENSE_THREADS, DENSE_SMEM, s>>>(g); note_launch();
-    if (ev) cudaEventRecord(ev[1], s);
+    if (ev) record_timing_event(ev[1], s);
     k_ctah<<<g_cfg.ctah_blocks, CTAH_THREADS, CTAH_SMEM, s>>>(g); note_launch();
-    if (ev) cudaEventRecord(ev[2], s);
+    if (ev) record_timing_event(ev[2], s);
     k_team<<<g_cfg.team_blocks, TEAM_THREADS, TEAM_SMEM, s>>>(g); note_launch();
-    if (ev) cudaEventRecord(ev[3], s);
+    if (ev) record_timing_event(ev[3], s);
     k_warp<<<g_cfg.warp_blocks, WARP_THREADS, WARP_SMEM, s>>>(g); note_launch();
-    if (ev) cudaEventRecord(ev[4], s);
+    if (ev) record_timing_event(ev[4], s);
 }
 
 int batch_max_blocks(int cls) {

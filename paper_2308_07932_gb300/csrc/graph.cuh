@@ -138,9 +138,15 @@ struct BuildAux {
 
 // Build from device CSR (rowptr/col/sign on the device). Returns 0 or the
 // error bits. Blocking only on the validation check. aux may be null (all
-// work on s).
+// work on s). The two stages separately: build_validate (resets, input
+// checks and degrees; blocks to read the check) and build_rest (everything
+// after, no host synchronisation: it can be captured in a CUDA graph).
 uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
                      void *temp_mem, cudaStream_t s, const BuildAux *aux = nullptr);
+uint32_t build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
+                        void *temp_mem, cudaStream_t s);
+void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
+                void *temp_mem, cudaStream_t s, const BuildAux *aux);
 
 // Count balanced/total butterflies of a built graph on stream s. Writes the
 // 128-bit sums to g.scratch->acc (device); per_vertex may be null. When ev
@@ -217,6 +223,17 @@ void launch_flip(DevGraph &g, const int64_t *edge_idx_dev, int64_t n, cudaStream
 
 // One-time per-device kernel attributes (shared-memory opt-ins, grids).
 void count_init();
+
+// Records a timing event on s; while s is being captured into a CUDA graph
+// the record is made an external one (an event record node that fires at
+// each replay, not a dependency inside the capture).
+inline void record_timing_event(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, s);
+}
 
 // Sets the calling thread's bb_last_error() message; returns st.
 bb_status report_error(bb_status st, const char *msg);

@@ -49,6 +49,12 @@ struct bb_ctx {
     size_t ws_base_cap = 0;
     bb::DevGraph oneshot;
     int64_t layout_key[3] = {-1, -1, -1};
+    // the one-shot path's work after validation, captured as a CUDA graph
+    // for one shape and set of buffers (key) and replayed while they repeat
+    cudaGraphExec_t step_exec = nullptr;
+    const void *step_key[9] = {};   // key of step_exec
+    const void *step_last[9] = {};  // key of the previous call (capture when it repeats)
+    uint64_t step_launches = 0;     // kernels in the captured graph
     bb::HostResult *h_res = nullptr;  // pinned
     std::mutex mu;
     bool timing = false;
@@ -86,8 +92,10 @@ bb_status map_build_error(uint32_t e);
 bb_status check_csr(const bb_csr *csr, const int8_t *signs);
 // stops the context's serving engine (waits for running requests)
 void engine_stop(bb_ctx *ctx);
-// adds launches made by replaying a captured CUDA graph to bb_launch_count
+// adds launches made by replaying a captured CUDA graph to bb_launch_count;
+// retract_launches takes back those counted while capturing (not run then)
 void note_launches(uint64_t n);
+void retract_launches(uint64_t n);
 uint64_t launches();
 
 }  // namespace bb
