@@ -326,10 +326,8 @@ bb_status bb_ctx_create(int device, uint64_t hbm_budget_bytes, bb_ctx **out) {
     e = cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking);
     if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "cudaStreamCreate"); }
     ctx->stream = ctx->own;
-    e = cudaStreamCreateWithFlags(&ctx->aux.stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->aux.fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->aux.join, cudaEventDisableTiming);
-    if (e != cudaSuccess) { bb_ctx_destroy(ctx); return cuda_fail(e, "auxiliary stream"); }
+    e = aux_create(ctx->aux);
+    if (e != cudaSuccess) { bb_ctx_destroy(ctx); return cuda_fail(e, "auxiliary streams"); }
     e = cudaMallocHost((void **)&ctx->h_res, sizeof(HostResult));
     if (e != cudaSuccess) { bb_ctx_destroy(ctx); return cuda_fail(e, "cudaMallocHost"); }
     for (int k = 0; k < NEV; k++) {
@@ -357,9 +355,7 @@ void bb_ctx_destroy(bb_ctx *ctx) {
     if (ctx->h_res) cudaFreeHost(ctx->h_res);
     for (int k = 0; k < NEV; k++)
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
-    if (ctx->aux.fork) cudaEventDestroy(ctx->aux.fork);
-    if (ctx->aux.join) cudaEventDestroy(ctx->aux.join);
-    if (ctx->aux.stream) { cudaStreamSynchronize(ctx->aux.stream); cudaStreamDestroy(ctx->aux.stream); }
+    aux_destroy(ctx->aux);
     if (ctx->own) cudaStreamDestroy(ctx->own);
     delete ctx;
 }

@@ -806,6 +806,7 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
     if (aux) {
         cudaEventRecord(aux->fork, s);
         cudaStreamWaitEvent(rs, aux->fork, 0);
+        cudaStreamWaitEvent(aux->stream2, aux->fork, 0);
     }
     for (int sd = 0; sd < 2; sd++) {
         if (ns[sd] == 0 || nE == 0) continue;
@@ -816,22 +817,28 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
                                                         bounds + sd * 16, 7, NLIMS, key_bits, g.err); note_launch();
     }
     if (aux) cudaEventRecord(aux->join, rs);
+    // the shorter rows: U side on s, V side on the second auxiliary stream
     for (int sd = 0; sd < 2; sd++) {
         int64_t n = ns[sd];
         if (n == 0 || nE == 0) continue;
         SideCSR &S = g.side[sd];
         int64_t *bd = bounds + sd * 16;
         uint64_t *ky = keys[sd];
-        k_rows_single<<<grid_for(n, BT, 4096), BT, 0, s>>>(S, ky, eid[sd], rowid[sd], bd); note_launch();
-        k_sort_rows_sub<2><<<grid_for(n * 2, BT, 8192), BT, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 0, g.err); note_launch();
-        k_sort_rows_sub<4><<<grid_for(n * 4, BT, 8192), BT, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 1, g.err); note_launch();
-        k_sort_rows_sub<8><<<grid_for(n * 8, BT, 8192), BT, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 2, g.err); note_launch();
-        k_sort_rows_sub<16><<<grid_for(n * 16, BT, 8192), BT, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 3, g.err); note_launch();
-        k_sort_rows_sub<32><<<grid_for(n * 32, BT, 8192), BT, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 4, g.err); note_launch();
-        k_sort_rows_warpsmem<<<1024, WS_THREADS, 0, s>>>(S, ky, eid[sd], rowid[sd], bd, 5, g.err); note_launch();
-        k_sort_rows_smem<2048, 256><<<2048, 256, 2048 * 8, s>>>(S, ky, eid[sd], rowid[sd], bd, 6, g.err); note_launch();
+        const cudaStream_t ss = (aux && sd == 1) ? aux->stream2 : s;
+        k_rows_single<<<grid_for(n, BT, 4096), BT, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd); note_launch();
+        k_sort_rows_sub<2><<<grid_for(n * 2, BT, 8192), BT, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 0, g.err); note_launch();
+        k_sort_rows_sub<4><<<grid_for(n * 4, BT, 8192), BT, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 1, g.err); note_launch();
+        k_sort_rows_sub<8><<<grid_for(n * 8, BT, 8192), BT, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 2, g.err); note_launch();
+        k_sort_rows_sub<16><<<grid_for(n * 16, BT, 8192), BT, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 3, g.err); note_launch();
+        k_sort_rows_sub<32><<<grid_for(n * 32, BT, 8192), BT, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 4, g.err); note_launch();
+        k_sort_rows_warpsmem<<<1024, WS_THREADS, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 5, g.err); note_launch();
+        k_sort_rows_smem<2048, 256><<<2048, 256, 2048 * 8, ss>>>(S, ky, eid[sd], rowid[sd], bd, 6, g.err); note_launch();
     }
-    if (aux) cudaStreamWaitEvent(s, aux->join, 0);
+    if (aux) {
+        cudaEventRecord(aux->join2, aux->stream2);
+        cudaStreamWaitEvent(s, aux->join, 0);
+        cudaStreamWaitEvent(s, aux->join2, 0);
+    }
     for (int sd = 0; sd < 2; sd++) {
         if (ns[sd] == 0) continue;
         int64_t n_other = ns[1 - sd];
@@ -849,9 +856,23 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
             if (ns[sd] == 0) continue;
             cudaMemsetAsync(g.side[sd].work, 0, (size_t)ns[sd] * 8, s);
             cudaMemsetAsync(g.side[sd].work_nh, 0, (size_t)ns[sd] * 8, s);
-            k_md_work<<<grid_for(nE, BT, 8192), BT, 0, s>>>(g.side[sd], rinfo[1 - sd], eid[sd],
-                                                           epos[1 - sd], rowid[sd], nE,
-                                                           g.wedges); note_launch();
+        }
+        // the two sides' descriptor passes side by side (V on the second
+        // auxiliary stream when there is one)
+        if (aux) {
+            cudaEventRecord(aux->fork, s);
+            cudaStreamWaitEvent(aux->stream2, aux->fork, 0);
+        }
+        for (int sd = 0; sd < 2; sd++) {
+            if (ns[sd] == 0) continue;
+            const cudaStream_t ss = (aux && sd == 1) ? aux->stream2 : s;
+            k_md_work<<<grid_for(nE, BT, 8192), BT, 0, ss>>>(g.side[sd], rinfo[1 - sd], eid[sd],
+                                                            epos[1 - sd], rowid[sd], nE,
+                                                            g.wedges); note_launch();
+        }
+        if (aux) {
+            cudaEventRecord(aux->join2, aux->stream2);
+            cudaStreamWaitEvent(s, aux->join2, 0);
         }
     } else {
         for (int sd = 0; sd < 2; sd++)
@@ -876,6 +897,22 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
         T.grp = grp[sd];
         k_emit<<<grid_for(ns[sd], BT, 2048), BT, 0, s>>>(g.side[sd], sd, T, g); note_launch();
     }
+}
+
+cudaError_t aux_create(BuildAux &a) {
+    cudaError_t e = cudaStreamCreateWithFlags(&a.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&a.stream2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.join2, cudaEventDisableTiming);
+    return e;
+}
+
+void aux_destroy(BuildAux &a) {
+    for (cudaStream_t *st : {&a.stream, &a.stream2})
+        if (*st) { cudaStreamSynchronize(*st); cudaStreamDestroy(*st); *st = nullptr; }
+    for (cudaEvent_t *ev : {&a.fork, &a.join, &a.join2})
+        if (*ev) { cudaEventDestroy(*ev); *ev = nullptr; }
 }
 
 uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,

@@ -129,12 +129,15 @@ BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE);
 // Carve the graph's arrays out of `graph_mem` (graph_bytes long).
 void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_mem);
 
-// An auxiliary stream and two events the build may fork work onto (it is
-// joined back to s before the build's last kernels).
+// Two auxiliary streams and their events the build may fork work onto (both
+// are joined back to s before the build's later stages): the long-row radix
+// sorts run on `stream`, the V side's shorter-row sorts on `stream2`.
 struct BuildAux {
-    cudaStream_t stream;
-    cudaEvent_t fork, join;
+    cudaStream_t stream = nullptr, stream2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
 };
+cudaError_t aux_create(BuildAux &a);   // non-blocking streams, timing-free events
+void aux_destroy(BuildAux &a);         // waits for both streams; safe on a partial create
 
 // Build from device CSR (rowptr/col/sign on the device). Returns 0 or the
 // error bits. Blocking only on the validation check. aux may be null (all

@@ -440,9 +440,7 @@ void destroy_engine(Engine *E) {
     cudaSetDevice(E->device);
     for (Slot &S : E->slots) {
         if (S.s) { cudaStreamSynchronize(S.s); cudaStreamDestroy(S.s); }
-        if (S.aux.stream) { cudaStreamSynchronize(S.aux.stream); cudaStreamDestroy(S.aux.stream); }
-        if (S.aux.fork) cudaEventDestroy(S.aux.fork);
-        if (S.aux.join) cudaEventDestroy(S.aux.join);
+        aux_destroy(S.aux);
         if (S.h) cudaFreeHost(S.h);
     }
     for (auto &kv : E->cache) delete kv.second;
@@ -466,9 +464,7 @@ bb_status start_engine(bb_ctx *ctx, int slots, uint64_t arena_bytes) {
     E->slots.resize(slots);
     for (Slot &S : E->slots) {
         cudaError_t e = cudaStreamCreateWithFlags(&S.s, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S.aux.stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.aux.fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.aux.join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = aux_create(S.aux);
         if (e == cudaSuccess) e = cudaMallocHost((void **)&S.h, sizeof(HostResult));
         if (e != cudaSuccess) {
             destroy_engine(E);
