@@ -127,7 +127,7 @@ struct alignas(16) WalkSmem {
 };
 
 // wedges per work item when a team's warps share a chunk dynamically
-constexpr uint32_t WALK_ITEM = 256;
+constexpr uint32_t WALK_ITEM = 512;
 
 // Walk the wedges of one anchor's middles [m0, m1) (its row starts at rb in
 // the anchor side's descriptors smd; the middles' rows are in oadj) as a
@@ -138,7 +138,7 @@ constexpr uint32_t WALK_ITEM = 256;
 //
 // Per chunk of TS middles the team scans the segment lengths and compacts
 // the non-empty segments (their ends, incl[], are the chunk's wedge
-// prefix); its warps then take 256-wedge slices of the chunk in turn (a
+// prefix); its warps then take WALK_ITEM-wedge slices of the chunk in turn (a
 // lone warp takes the whole chunk). A warp walks its slice flat, 32
 // consecutive wedges per step, lane l taking wedge base + l (coalesced
 // loads). The step's wedges lie in at most 32 consecutive segments from
@@ -192,7 +192,7 @@ __device__ __forceinline__ void team_walk(const uint4 *__restrict__ smd,
         if (t == TS - 1) { sm.tot[0] = x; sm.tot[1] = nzi; sm.item_next = 0; }
         team_sync<TS>();
         const uint32_t T = sm.tot[0], NZ = sm.tot[1];
-        // a warp takes the whole chunk when alone, else 256-wedge items in turn
+        // a warp takes the whole chunk when alone, else WALK_ITEM-wedge items in turn
         for (uint32_t item = 0;; item++) {
             uint32_t a, b;
             if constexpr (NW == 1) {
