@@ -106,7 +106,13 @@ BB_API uint64_t bb_ctx_device_bytes(const bb_ctx *ctx);
  *   memory of the context's device; the buffers are only read (written for
  *   per_vertex_opt) on the context's stream, during the call.
  * wedges_opt: NULL or receives the number of wedges aggregated.
- * The workspace grows to the largest graph seen and is reused. */
+ * The workspace grows to the largest graph seen and is reused. A call that
+ * repeats the previous call's sizes and buffers (and timing setting)
+ * replays the work after input validation from a CUDA graph captured at
+ * the first repeat; the buffers' contents are read afresh by every call,
+ * so results are those of the current inputs. The context's stream must
+ * then be one that can be captured (not the legacy default stream, for
+ * which every call launches directly). */
 BB_API bb_status bb_count_csr(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int64_t *balanced,
                        int64_t *total, int64_t *per_vertex_opt, int64_t *wedges_opt);
 BB_API bb_status bb_count_csr_device(bb_ctx *ctx, const bb_csr *csr_dev, const int8_t *signs_dev,
