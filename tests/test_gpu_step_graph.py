@@ -90,3 +90,21 @@ def test_invalid_input_after_replay_is_rejected(ctx):
         ctx.count_tensors(g.nV, rp, cl, sg2)
     c = ctx.count_tensors(g.nV, rp, cl, sg)
     assert (c.balanced, c.total) == want
+
+
+def test_repeated_degenerate_graphs(ctx):
+    """Repeats of empty and tiny graphs (host path: the staging buffers
+    repeat, so the second call captures and later calls replay)."""
+    cases = [
+        (synth.SignedBipartite(3, 4, np.zeros(4, np.int64), np.zeros(0, np.int32),
+                               np.zeros(0, np.int8)), (0, 0)),
+        (synth.SignedBipartite(0, 5, np.zeros(1, np.int64), np.zeros(0, np.int32),
+                               np.zeros(0, np.int8)), (0, 0)),
+        (synth.from_edges(1, 60, [0] * 60, list(range(60)), [1] * 60), (0, 0)),
+        (synth.from_edges(2, 2, [0, 0, 1, 1], [0, 1, 0, 1], [1, 1, 1, -1]), (0, 1)),
+        (synth.from_edges(2, 2, [0, 0, 1, 1], [0, 1, 0, 1], [1, -1, -1, 1]), (1, 1)),
+    ]
+    for g, want in cases:
+        for _ in range(4):
+            c = ctx.count(g)
+            assert (c.balanced, c.total) == want, g.name
