@@ -253,9 +253,10 @@ bool replay_step(bb_ctx *ctx, DevGraph &g, const bb_csr *csr, const int8_t *sign
     return true;
 }
 
-// one-shot path on device-resident inputs
+// one-shot path on device-resident inputs (`in`: still being copied)
 bb_status count_device(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int64_t *balanced,
-                       int64_t *total, int64_t *pv_dev, int64_t *wedges_opt) {
+                       int64_t *total, int64_t *pv_dev, int64_t *wedges_opt,
+                       const StagedInput *in = nullptr) {
     const int64_t nU = csr->nU, nV = csr->nV, nE = csr->nE;
     BuildSizes bs = build_sizes(nU, nV, nE);
     bb_status st = ensure(ctx, &ctx->ws_graph, &ctx->ws_graph_cap, bs.graph_bytes, "graph workspace");
@@ -274,7 +275,7 @@ bb_status count_device(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int6
         ctx->layout_key[0] = nU; ctx->layout_key[1] = nV; ctx->layout_key[2] = nE;
     }
     if (ctx->timing) BB_CUDA(cudaEventRecord(ctx->ev[0], s), "event");
-    uint32_t verr = build_validate(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s);
+    uint32_t verr = build_validate(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s, in);
     BB_CUDA(cudaGetLastError(), "validation kernels");
     if (verr) {
         ctx->layout_key[0] = -1;  // leave the merge buffers to be re-zeroed
@@ -334,6 +335,10 @@ bb_status bb_ctx_create(int device, uint64_t hbm_budget_bytes, bb_ctx **out) {
         e = cudaEventCreate(&ctx->ev[k]);
         if (e != cudaSuccess) { bb_ctx_destroy(ctx); return cuda_fail(e, "cudaEventCreate"); }
     }
+    for (cudaEvent_t &ev : ctx->in_ev) {
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) { bb_ctx_destroy(ctx); return cuda_fail(e, "cudaEventCreate"); }
+    }
     count_init();
     *out = ctx;
     return BB_OK;
@@ -355,6 +360,8 @@ void bb_ctx_destroy(bb_ctx *ctx) {
     if (ctx->h_res) cudaFreeHost(ctx->h_res);
     for (int k = 0; k < NEV; k++)
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+    for (cudaEvent_t ev : ctx->in_ev)
+        if (ev) cudaEventDestroy(ev);
     aux_destroy(ctx->aux);
     if (ctx->own) cudaStreamDestroy(ctx->own);
     delete ctx;
@@ -419,13 +426,27 @@ bb_status bb_count_csr(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int6
     d.col = (const int32_t *)(p + b_row);
     const int8_t *dsg = (const int8_t *)(p + b_row + b_col);
     cudaStream_t s = ctx->stream;
+    // copies on the second auxiliary stream (the staging buffers are free:
+    // the previous call has finished), in edge chunks of at least 2^21
+    // whose checks start as each chunk lands
+    cudaStream_t cs = ctx->aux.stream2;
+    StagedInput in;
+    in.chunks = nE > 0 ? (int)std::min<int64_t>(StagedInput::MAX_CHUNKS / 2, (nE >> 21) + 1) : 0;
+    for (int c = 0; c <= in.chunks; c++) in.lo[c] = nE * c / std::max(in.chunks, 1);
     BB_CUDA(cudaMemcpyAsync((void *)d.rowptr, csr->rowptr, (size_t)(nU + 1) * 8,
-                            cudaMemcpyHostToDevice, s), "copy rowptr");
-    if (nE > 0) {
-        BB_CUDA(cudaMemcpyAsync((void *)d.col, csr->col, (size_t)nE * 4, cudaMemcpyHostToDevice, s),
-                "copy col");
-        BB_CUDA(cudaMemcpyAsync((void *)dsg, signs, (size_t)nE, cudaMemcpyHostToDevice, s),
-                "copy signs");
+                            cudaMemcpyHostToDevice, cs), "copy rowptr");
+    BB_CUDA(cudaEventRecord(ctx->in_ev[0], cs), "input event");
+    in.rowptr_ready = ctx->in_ev[0];
+    for (int c = 0; c < in.chunks; c++) {
+        const int64_t lo = in.lo[c], n = in.lo[c + 1] - lo;
+        if (n > 0) {
+            BB_CUDA(cudaMemcpyAsync((void *)(d.col + lo), csr->col + lo, (size_t)n * 4,
+                                    cudaMemcpyHostToDevice, cs), "copy col");
+            BB_CUDA(cudaMemcpyAsync((void *)(dsg + lo), signs + lo, (size_t)n,
+                                    cudaMemcpyHostToDevice, cs), "copy signs");
+        }
+        BB_CUDA(cudaEventRecord(ctx->in_ev[1 + c], cs), "input event");
+        in.ready[c] = ctx->in_ev[1 + c];
     }
     int64_t *pv_dev = nullptr;
     if (per_vertex_opt) {
@@ -434,7 +455,7 @@ bb_status bb_count_csr(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int6
         if (st != BB_OK) return st;
         pv_dev = ctx->ws_pv;
     }
-    st = count_device(ctx, &d, dsg, balanced, total, pv_dev, wedges_opt);
+    st = count_device(ctx, &d, dsg, balanced, total, pv_dev, wedges_opt, &in);
     if (st != BB_OK) return st;
     if (per_vertex_opt) {
         BB_CUDA(cudaMemcpyAsync(per_vertex_opt, pv_dev, (size_t)(csr->nU + csr->nV) * 8,

@@ -735,7 +735,7 @@ BuildTemp carve_temp(const DevGraph &g, void *temp_mem) {
 }  // namespace
 
 uint32_t build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
-                        void *temp_mem, cudaStream_t s) {
+                        void *temp_mem, cudaStream_t s, const StagedInput *in) {
     const int64_t nU = g.nU, nV = g.nV, nE = g.nE;
     BuildTemp bt = carve_temp(g, temp_mem);
     uint32_t **deg_in = bt.deg_in, *cursorV = bt.cursorV;
@@ -749,8 +749,20 @@ uint32_t build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col, 
     cudaMemsetAsync(T.bucket_cnt, 0, NCLS * NB * 4, s);
 
     // 1. validate + degrees
+    if (in) cudaStreamWaitEvent(s, in->rowptr_ready, 0);
     if (nU > 0) k_validate_rows<<<grid_for(nU, BT, 8192), BT, 0, s>>>(rowptr, nU, nE, deg_in[0], g.err); note_launch();
-    if (nE > 0) k_validate_edges<<<grid_for(nE, BT, 16384), BT, 0, s>>>(col, sign, nE, nV, deg_in[1], g.err); note_launch();
+    if (nE > 0 && in && in->chunks > 0) {
+        for (int c = 0; c < in->chunks; c++) {
+            const int64_t lo = in->lo[c], n = in->lo[c + 1] - lo;
+            cudaStreamWaitEvent(s, in->ready[c], 0);
+            if (n > 0) {
+                k_validate_edges<<<grid_for(n, BT, 16384), BT, 0, s>>>(col + lo, sign + lo, n, nV,
+                                                                      deg_in[1], g.err); note_launch();
+            }
+        }
+    } else if (nE > 0) {
+        k_validate_edges<<<grid_for(nE, BT, 16384), BT, 0, s>>>(col, sign, nE, nV, deg_in[1], g.err); note_launch();
+    }
     if (nV > 0) k_check_degree<<<grid_for(nV, BT, 8192), BT, 0, s>>>(deg_in[1], nV, g.err); note_launch();
     uint32_t herr = 0;
     cudaMemcpyAsync(&herr, g.err, 4, cudaMemcpyDeviceToHost, s);

@@ -146,8 +146,18 @@ void aux_destroy(BuildAux &a);         // waits for both streams; safe on a part
 // after, no host synchronisation: it can be captured in a CUDA graph).
 uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
                      void *temp_mem, cudaStream_t s, const BuildAux *aux = nullptr);
+// Inputs still arriving (host-to-device copies on another stream): the
+// validation waits on each part's event before checking it, so the checks
+// of early edge chunks overlap the copies of later ones.
+struct StagedInput {
+    static constexpr int MAX_CHUNKS = 8;
+    int chunks = 0;                         // edge chunks
+    int64_t lo[MAX_CHUNKS + 1] = {};        // chunk c: edges [lo[c], lo[c+1])
+    cudaEvent_t rowptr_ready = nullptr;
+    cudaEvent_t ready[MAX_CHUNKS] = {};
+};
 uint32_t build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
-                        void *temp_mem, cudaStream_t s);
+                        void *temp_mem, cudaStream_t s, const StagedInput *in = nullptr);
 void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
                 void *temp_mem, cudaStream_t s, const BuildAux *aux);
 

@@ -56,6 +56,9 @@ struct bb_ctx {
     const void *step_last[9] = {};  // key of the previous call (capture when it repeats)
     uint64_t step_launches = 0;     // kernels in the captured graph
     bb::HostResult *h_res = nullptr;  // pinned
+    // host inputs: rowptr and edge-chunk copy events (copies run on the
+    // second auxiliary stream while the first chunks are checked)
+    cudaEvent_t in_ev[1 + bb::StagedInput::MAX_CHUNKS] = {};
     std::mutex mu;
     bool timing = false;
     cudaEvent_t ev[bb::NEV] = {};
