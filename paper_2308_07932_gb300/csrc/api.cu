@@ -257,6 +257,7 @@ bool replay_step(bb_ctx *ctx, DevGraph &g, const bb_csr *csr, const int8_t *sign
 bb_status count_device(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int64_t *balanced,
                        int64_t *total, int64_t *pv_dev, int64_t *wedges_opt,
                        const StagedInput *in = nullptr) {
+    Range range("bb count (device inputs)");
     const int64_t nU = csr->nU, nV = csr->nV, nE = csr->nE;
     BuildSizes bs = build_sizes(nU, nV, nE);
     bb_status st = ensure(ctx, &ctx->ws_graph, &ctx->ws_graph_cap, bs.graph_bytes, "graph workspace");
@@ -275,12 +276,17 @@ bb_status count_device(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int6
         ctx->layout_key[0] = nU; ctx->layout_key[1] = nV; ctx->layout_key[2] = nE;
     }
     if (ctx->timing) BB_CUDA(cudaEventRecord(ctx->ev[0], s), "event");
-    uint32_t verr = build_validate(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s, in);
+    uint32_t verr;
+    {
+        Range r("validate");
+        verr = build_validate(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s, in);
+    }
     BB_CUDA(cudaGetLastError(), "validation kernels");
     if (verr) {
         ctx->layout_key[0] = -1;  // leave the merge buffers to be re-zeroed
         return map_build_error(verr);
     }
+    Range r_rest("build and count");
     if (pv_dev || !replay_step(ctx, g, csr, signs)) {
         build_rest(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s, &ctx->aux);
         BB_CUDA(cudaGetLastError(), "build kernels");
@@ -414,6 +420,7 @@ bb_status bb_count_csr(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int6
     if (st != BB_OK) return st;
     std::lock_guard<std::mutex> lk(ctx->mu);
     if ((st = set_device(ctx)) != BB_OK) return st;
+    Range range("bb count (host inputs)");
     const int64_t nU = csr->nU, nE = csr->nE;
     size_t b_row = ((size_t)(nU + 1) * 8 + 255) & ~(size_t)255;
     size_t b_col = ((size_t)nE * 4 + 255) & ~(size_t)255;
@@ -468,6 +475,7 @@ bb_status bb_count_csr(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int6
 // ------------------------------------------------------- resident graphs
 static bb_status upload_impl(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, bool on_device,
                              bb_graph **out) {
+    bb::Range range_("bb graph upload");
     if (!ctx || !out) return fail(BB_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     bb_status st = check_csr(csr, signs);
@@ -541,6 +549,7 @@ bb_status bb_graph_upload_device(bb_ctx *ctx, const bb_csr *csr_dev, const int8_
 }
 
 bb_status bb_count(bb_graph *G, int64_t *balanced, int64_t *total, int64_t *per_vertex_opt) {
+    bb::Range range_("bb count (resident graph)");
     if (!G || !balanced || !total) return fail(BB_ERR_INVALID_ARG, "NULL argument");
     bb_ctx *ctx = G->ctx;
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -571,6 +580,7 @@ bb_status bb_count(bb_graph *G, int64_t *balanced, int64_t *total, int64_t *per_
 
 bb_status bb_count_edges(bb_graph *G, int64_t *per_edge, int64_t *balanced_opt,
                          int64_t *total_opt) {
+    bb::Range range_("bb count per edge");
     if (!G || !per_edge) return fail(BB_ERR_INVALID_ARG, "NULL argument");
     bb_ctx *ctx = G->ctx;
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -606,6 +616,7 @@ bb_status bb_count_edges(bb_graph *G, int64_t *per_edge, int64_t *balanced_opt,
 
 bb_status bb_count_flipped(bb_graph *G, const int64_t *edge_idx, int64_t n, int64_t *balanced,
                            int64_t *total, int *incremental_opt) {
+    bb::Range range_("bb count flipped");
     if (!G || !balanced || !total || n < 0 || (n > 0 && !edge_idx))
         return fail(BB_ERR_INVALID_ARG, "bad argument");
     const int64_t nE = G->g.nE;
@@ -692,6 +703,7 @@ bb_status bb_count_flipped(bb_graph *G, const int64_t *edge_idx, int64_t n, int6
 }
 
 bb_status bb_count_base(bb_graph *G, int64_t *balanced, int64_t *total) {
+    bb::Range range_("bb count base (Algorithm 1)");
     if (!G || !balanced || !total) return fail(BB_ERR_INVALID_ARG, "NULL argument");
     bb_ctx *ctx = G->ctx;
     std::lock_guard<std::mutex> lk(ctx->mu);

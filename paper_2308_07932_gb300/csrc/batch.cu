@@ -181,6 +181,7 @@ bb_status bb_batch_create(bb_ctx *ctx, bb_graph *const *graphs, int64_t n, bb_ba
 }
 
 bb_status bb_batch_count(bb_batch *b, int64_t *balanced, int64_t *total, bb_status *status_opt) {
+    bb::Range range_("bb batch count");
     if (!b || !balanced || !total) return fail(BB_ERR_INVALID_ARG, "NULL argument");
     bb_ctx *ctx = b->ctx;
     std::lock_guard<std::mutex> lk(ctx->mu);

@@ -2,6 +2,7 @@
 // and the helpers the ABI's translation units share: error reporting,
 // bounded waits and budgeted device allocation.
 #pragma once
+#include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 #include <mutex>
 
@@ -101,6 +102,17 @@ void note_launches(uint64_t n);
 void retract_launches(uint64_t n);
 uint64_t launches();
 
+}  // namespace bb
+
+// Named host ranges for timeline profilers (NVTX; header-only, a no-op
+// unless a profiler is attached): one per public call and build stage.
+namespace bb {
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 }  // namespace bb
 
 #define BB_CUDA(call, what)                                      \

@@ -286,6 +286,7 @@ bb_status count_and_wait(Slot &S, const DevGraph &g, bb_ticket_s *t) {
 }
 
 bb_status run_managed(Engine *E, Slot &S, bb_ticket_s *t, Plan &plan) {
+    bb::Range range_("bb served request");
     Entry *e = plan.entry;
     const bb_request &r = t->req;
     cudaStream_t s = S.s;
