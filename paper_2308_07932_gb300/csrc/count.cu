@@ -13,12 +13,12 @@
 // to the total, which is exact in any order and needs no pass over the
 // counters afterwards, only their reset.
 //
-// Work is spread by walkers: a team (a warp, or a whole CTA) loads a chunk
-// of the anchor's middles, scans their suffix lengths and compacts the
-// non-empty ones. The dense class's team_walk then steps through the
-// chunk's wedges 32 at a time per warp (coalesced, one segment lookup per
-// step); the other classes' lane_walk gives each thread an equal contiguous
-// share of the chunk's wedges to stream through.
+// Work is spread by the quad walker: a team (a warp, or a whole CTA) loads a
+// chunk of the anchor's middles, takes each middle's segment of the other
+// side's adjacency, counts the aligned 16-byte quads that hold it and
+// compacts the non-empty segments. Every thread then takes an equal share
+// of the chunk's quads and streams through them, one 16-byte load per four
+// entries, with the entries outside their segment predicated off.
 //
 // Counters, per class (all in shared memory; S in bits 0..15, A in bits
 // 16..31 of a u32, both bounded by the anchor's degree):
@@ -78,13 +78,6 @@ __device__ __forceinline__ void flush_warp(CountScratch *sc, unsigned long long 
     if (lane_id() == 0) acc_add(sc, bal, tot);
 }
 
-// contribution of one wedge given its pair's counts before it
-__device__ __forceinline__ void wedge_terms(uint32_t oldS, uint32_t oldA, uint32_t asym,
-                                            unsigned long long &bal, unsigned long long &tot) {
-    bal += asym ? oldA : oldS;
-    tot += oldS + oldA;
-}
-
 // block-wide sum of two u64 values, result valid in thread 0
 template <int THREADS>
 __device__ __forceinline__ void block_sum2(unsigned long long &a, unsigned long long &b) {
@@ -108,214 +101,34 @@ __device__ __forceinline__ void team_sync() {
     else __syncthreads();   // teams of more than one warp are whole CTAs
 }
 
-// A chunk of middles, compacted to those with a non-empty segment: the
-// first entry of the segment in the other side's adjacency (absolute index,
-// below 2^32 because nE is), and the wedges of the chunk before this middle
-// (below 2^31) with the sign bit of the anchor's edge in bit 31.
-struct Desc {
-    uint32_t st;
-    uint32_t excl_sw;
+// A chunk of middles, compacted to those with a non-empty segment, for the
+// quad walker: the segment as a word range [st, en) of the middle side's
+// adjacency (absolute, below 2^32 because nE is), the aligned 16-byte quads
+// of the chunk before this segment (below 2^31) with the sign bit of the
+// anchor's edge in bit 31, and the quads up to and including it.
+struct alignas(16) QSeg {
+    uint32_t st, en, excl_sw, incl;
 };
 
 template <int TS>
 struct alignas(16) WalkSmem {
-    Desc desc[TS];
-    uint32_t incl[TS];
-    unsigned long long warp_part[TS / 32];  // per warp: wedges (low half), segments (high half)
+    QSeg seg[TS];
+    unsigned long long warp_part[TS / 32];  // per warp: quads (low half), segments (high half)
     uint32_t tot[2];
-    uint32_t item_next;               // next work item of the chunk (teams of several warps)
+};
+// a lone warp scans with shuffles only
+template <>
+struct alignas(16) WalkSmem<32> {
+    QSeg seg[32];
 };
 
-// wedges per work item when a team's warps share a chunk dynamically
-constexpr uint32_t WALK_ITEM = 512;
+constexpr uint32_t EXMASK = 0x7fffffffu;
 
-// Walk the wedges of one anchor's middles [m0, m1) (its row starts at rb in
-// the anchor side's descriptors smd; the middles' rows are in oadj) as a
-// team of TS threads (t = thread index in the team). seg(md, st, len) picks
-// the segment [st, st+len) of a middle's row from its descriptor;
-// add(entry, sign bit of the anchor's edge to the middle) is called once per
-// wedge (entry = endpoint side rank << 1 | sign of the middle-endpoint edge).
-//
-// Per chunk of TS middles the team scans the segment lengths and compacts
-// the non-empty segments (their ends, incl[], are the chunk's wedge
-// prefix); its warps then take WALK_ITEM-wedge slices of the chunk in turn (a
-// lone warp takes the whole chunk). A warp walks its slice flat, 32
-// consecutive wedges per step, lane l taking wedge base + l (coalesced
-// loads). The step's wedges lie in at most 32 consecutive segments from
-// `cur`, the segment of the step's first wedge: each lane reads one of
-// their ends, the ends that fall inside the step form a bitmask, and a lane's
-// segment is cur plus the ends at or before its wedge. When the whole step
-// lies in segment cur (long segments) that reduces to one broadcast read.
-template <int TS, int UNROLL = 4, typename Seg, typename Add>
-__device__ __forceinline__ void team_walk(const uint4 *__restrict__ smd,
-                                          const uint32_t *__restrict__ oadj, int64_t rb,
-                                          uint32_t m0, uint32_t m1, WalkSmem<TS> &sm, int t,
-                                          Seg &&seg, Add &&add) {
-    constexpr int NW = TS / 32;
-    constexpr uint32_t EXMASK = 0x7fffffffu;
-    const int lane = t & 31, w = t >> 5;
-    const unsigned upto = (2u << lane) - 1u;   // bits 0..lane
-    for (uint32_t mc = m0; mc < m1; mc += TS) {
-        const uint32_t j = mc + (uint32_t)t;
-        long long st = 0;
-        uint32_t len = 0, sw = 0;
-        if (j < m1) {
-            const uint4 d = smd[rb + j];
-            sw = d.w;
-            seg(d, st, len);
-        }
-        // inclusive team scan of the lengths; compacted index from a ballot
-        uint32_t x = len;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, x, d);
-            if (lane >= d) x += y;
-        }
-        const unsigned nzb = __ballot_sync(FULL, len > 0);
-        uint32_t nzi = __popc(nzb & upto);
-        if constexpr (NW > 1) {
-            if (lane == 31) sm.warp_part[w] = x | ((unsigned long long)__popc(nzb) << 32);
-            team_sync<TS>();
-            uint32_t add_x = 0, add_n = 0;
-            for (int k = 0; k < w; k++) {
-                const unsigned long long v = sm.warp_part[k];
-                add_x += (uint32_t)v;
-                add_n += (uint32_t)(v >> 32);
-            }
-            x += add_x;
-            nzi += add_n;
-        }
-        if (len > 0) {
-            sm.desc[nzi - 1] = Desc{(uint32_t)st, (x - len) | (sw << 31)};
-            sm.incl[nzi - 1] = x;
-        }
-        if (t == TS - 1) { sm.tot[0] = x; sm.tot[1] = nzi; sm.item_next = 0; }
-        team_sync<TS>();
-        const uint32_t T = sm.tot[0], NZ = sm.tot[1];
-        // a warp takes the whole chunk when alone, else WALK_ITEM-wedge items in turn
-        for (uint32_t item = 0;; item++) {
-            uint32_t a, b;
-            if constexpr (NW == 1) {
-                if (item > 0) break;
-                a = 0; b = T;
-            } else {
-                uint32_t it = 0;
-                if (lane == 0) it = atomicAdd(&sm.item_next, 1u);
-                it = __shfl_sync(FULL, it, 0);
-                a = it * WALK_ITEM;
-                if (a >= T) break;
-                b = T - a > WALK_ITEM ? a + WALK_ITEM : T;
-            }
-            // segment holding wedge a: the first whose end is past a
-            uint32_t cur = 0;
-            if (a > 0) {
-                uint32_t hi = NZ;
-                while (cur < hi) {
-                    const uint32_t mid = (cur + hi) >> 1;
-                    if (sm.incl[mid] <= a) cur = mid + 1; else hi = mid;
-                }
-            }
-            for (uint32_t base = a; base < b; base += 32u * UNROLL) {
-                uint32_t addr[UNROLL], swq[UNROLL];
-                bool ok[UNROLL];
-#pragma unroll
-                for (int u = 0; u < UNROLL; u++) {
-                    const uint32_t bq = base + 32u * u;
-                    ok[u] = false;
-                    addr[u] = 0;
-                    swq[u] = 0;
-                    if (bq < b) {
-                        const uint32_t ecur = sm.incl[cur];
-                        uint32_t sg, nxt;
-                        if (ecur >= bq + 32u) {  // the whole step is in segment cur
-                            sg = cur;
-                            nxt = ecur == bq + 32u ? cur + 1 : cur;
-                        } else {
-                            const uint32_t jj = cur + (uint32_t)lane;
-                            const uint32_t p = (jj < NZ ? sm.incl[jj] : 0xffffffffu) - bq;  // >= 1
-                            const unsigned M = __reduce_or_sync(FULL, p < 32u ? (1u << p) : 0u);
-                            sg = cur + __popc(M & upto);
-                            nxt = cur + __popc(__ballot_sync(FULL, p <= 32u));
-                        }
-                        const uint32_t q = bq + (uint32_t)lane;
-                        if (q < b) {
-                            const Desc dd = sm.desc[sg];
-                            ok[u] = true;
-                            addr[u] = dd.st + (q - (dd.excl_sw & EXMASK));
-                            swq[u] = dd.excl_sw >> 31;
-                        }
-                        cur = nxt;
-                    }
-                }
-                uint32_t xv[UNROLL];
-#pragma unroll
-                for (int u = 0; u < UNROLL; u++)
-                    if (ok[u]) xv[u] = oadj[addr[u]];
-#pragma unroll
-                for (int u = 0; u < UNROLL; u++)
-                    if (ok[u]) add(xv[u], swq[u]);
-            }
-        }
-        team_sync<TS>();
-    }
-}
-
-// Lane walker. After the same chunk scan and compaction, each thread takes
-// an equal contiguous part [a, b) of the chunk's flat wedge range and
-// streams through it, stepping to the next segment when one ends: no
-// per-step segment search, and the threads of a team get equal wedge
-// counts. Used where anchors are small or medium (warp, team and CTA-hash
-// classes); the dense class keeps team_walk's coalesced steps.
-template <int U, typename Add>
-__device__ __forceinline__ void lane_range(const uint32_t *__restrict__ oadj, const Desc *desc,
-                                           const uint32_t *incl, uint32_t NZ, uint32_t a,
-                                           uint32_t b, Add &&add) {
-    constexpr uint32_t EXMASK = 0x7fffffffu;
-    if (a >= b) return;
-    uint32_t k = 0, hi = NZ;  // segment holding wedge a
-    while (k < hi) {
-        const uint32_t mid = (k + hi) >> 1;
-        if (incl[mid] <= a) k = mid + 1; else hi = mid;
-    }
-    Desc d = desc[k];
-    uint32_t ex = d.excl_sw & EXMASK;
-    uint32_t p = d.st + (a - ex);
-    uint32_t pend = d.st + (incl[k] - ex);
-    uint32_t cs = d.excl_sw >> 31;
-    auto next_segment = [&]() {
-        k++;
-        d = desc[k];
-        ex = d.excl_sw & EXMASK;
-        p = d.st;
-        pend = d.st + (incl[k] - ex);
-        cs = d.excl_sw >> 31;
-    };
-    uint32_t i = a;
-    for (; i + U <= b; i += U) {
-        uint32_t pa[U], sq[U];
-        if (pend - p >= U) {  // the U wedges lie in the current segment
-#pragma unroll
-            for (int u = 0; u < U; u++) { pa[u] = p + u; sq[u] = cs; }
-            p += U;
-        } else {
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                if (p == pend) next_segment();
-                pa[u] = p++;
-                sq[u] = cs;
-            }
-        }
-        uint32_t xv[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) xv[u] = oadj[pa[u]];
-#pragma unroll
-        for (int u = 0; u < U; u++) add(xv[u], sq[u]);
-    }
-    for (; i < b; i++) {
-        if (p == pend) next_segment();
-        const uint32_t x = oadj[p++];
-        add(x, cs);
-    }
+// aligned quads (four-entry, 16-byte blocks) that hold the words [st, st + len)
+__device__ __forceinline__ uint32_t quads_of(uint32_t st, uint32_t len) {
+    if (len == 0) return 0u;
+    const uint32_t en = st + len;
+    return (en >> 2) + ((en & 3u) != 0u) - (st >> 2);
 }
 
 // equal share t of n among TS threads
@@ -324,67 +137,172 @@ __device__ __forceinline__ uint32_t share(uint32_t n, uint32_t t) {
     return (uint32_t)((unsigned long long)n * t / TS);
 }
 
-template <int TS, int U = 4, typename Seg, typename Add>
-__device__ __forceinline__ void lane_walk(const uint4 *__restrict__ smd,
-                                          const uint32_t *__restrict__ oadj, int64_t rb,
-                                          uint32_t m0, uint32_t m1, WalkSmem<TS> &sm, int t,
-                                          Seg &&seg, Add &&add) {
-    constexpr int NW = TS / 32;
-    const int lane = t & 31, w = t >> 5;
-    const unsigned upto = (2u << lane) - 1u;
-    for (uint32_t mc = m0; mc < m1; mc += TS) {
-        const uint32_t j = mc + (uint32_t)t;
-        long long st = 0;
-        uint32_t len = 0, sw = 0;
-        if (j < m1) {
-            const uint4 d = smd[rb + j];
-            sw = d.w;
-            seg(d, st, len);
-        }
-        uint32_t x = len;
+// Quad walker, per thread: the quads [a, b) of a compacted chunk (NZ
+// segments). Every step loads whole aligned quads of the middle side's
+// adjacency (one 16-byte load for four entries) and calls add(entry, sign
+// bit of the anchor's edge) for each entry of the quad inside its segment.
+// A quad holds at least one entry of its segment, so it lies inside the
+// adjacency's 16-byte-padded allocation. Threads get equal quad counts, so
+// a team's lanes run the same number of steps; entries outside a segment
+// (its first and last quad) are predicated off.
+template <int U, typename Add>
+__device__ __forceinline__ void quad_range(const uint4 *__restrict__ oadj4, const QSeg *seg,
+                                           uint32_t NZ, uint32_t a, uint32_t b, Add &&add) {
+    if (a >= b) return;
+    uint32_t k = 0, hi = NZ;  // segment holding quad a: the first whose end is past a
+    while (k < hi) {
+        const uint32_t mid = (k + hi) >> 1;
+        if (seg[mid].incl <= a) k = mid + 1; else hi = mid;
+    }
+    QSeg d = seg[k];
+    uint32_t q = (d.st >> 2) + (a - (d.excl_sw & EXMASK));
+    uint32_t qn = d.incl - a;  // quads left in this segment
+    for (uint32_t i = a; i < b; i += U) {
+        uint32_t qa[U], lo[U], hi4[U], sw[U];
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, x, d);
-            if (lane >= d) x += y;
-        }
-        const unsigned nzb = __ballot_sync(FULL, len > 0);
-        uint32_t nzi = __popc(nzb & upto);
-        if constexpr (NW > 1) {
-            if (lane == 31) sm.warp_part[w] = x | ((unsigned long long)__popc(nzb) << 32);
-            team_sync<TS>();
-            uint32_t add_x = 0, add_n = 0;
-            for (int k = 0; k < w; k++) {
-                const unsigned long long v = sm.warp_part[k];
-                add_x += (uint32_t)v;
-                add_n += (uint32_t)(v >> 32);
+        for (int u = 0; u < U; u++) {
+            lo[u] = 4u;  // an empty step: no entry passes lo <= j < hi4
+            hi4[u] = 0u;
+            qa[u] = 0u;
+            sw[u] = 0u;
+            if (i + u < b) {
+                if (qn == 0) {
+                    k++;
+                    d = seg[k];
+                    q = d.st >> 2;
+                    qn = d.incl - (d.excl_sw & EXMASK);
+                }
+                const uint32_t w0 = q << 2;
+                qa[u] = q;
+                lo[u] = d.st > w0 ? d.st - w0 : 0u;
+                hi4[u] = d.en - w0 < 4u ? d.en - w0 : 4u;
+                sw[u] = d.excl_sw >> 31;
+                q++;
+                qn--;
             }
-            x += add_x;
-            nzi += add_n;
         }
-        if (len > 0) {
-            sm.desc[nzi - 1] = Desc{(uint32_t)st, (x - len) | (sw << 31)};
-            sm.incl[nzi - 1] = x;
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            v[u] = hi4[u] ? __ldg(oadj4 + qa[u]) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (lo[u] == 0u) add(v[u].x, sw[u]);
+            if (lo[u] <= 1u && hi4[u] >= 2u) add(v[u].y, sw[u]);
+            if (lo[u] <= 2u && hi4[u] >= 3u) add(v[u].z, sw[u]);
+            if (hi4[u] == 4u) add(v[u].w, sw[u]);
         }
+    }
+}
+
+// the same over [a, b) in sub-ranges of at most `span` quads, calling
+// flush() after each (callers whose per-thread running sums must be
+// bounded between flushes)
+template <int U, typename Add, typename Flush>
+__device__ __forceinline__ void quad_range_flushed(const uint4 *__restrict__ oadj4,
+                                                   const QSeg *seg, uint32_t NZ, uint32_t a,
+                                                   uint32_t b, uint32_t span, Add &&add,
+                                                   Flush &&flush) {
+    for (uint32_t s = a; s < b;) {
+        const uint32_t e = b - s > span ? s + span : b;
+        quad_range<U>(oadj4, seg, NZ, s, e, add);
+        flush();
+        s = e;
+    }
+}
+
+// One chunk of up to TS middles (j = this thread's middle, valid below m1):
+// reads each middle's descriptor, takes its segment, and compacts the
+// non-empty segments into sm.seg with their quad prefix. T = the chunk's
+// quads, NZ = its segments (the same in every thread of the team).
+template <int TS, typename Seg>
+__device__ __forceinline__ void chunk_scan(const uint4 *__restrict__ smd, int64_t rb, uint32_t j,
+                                           uint32_t m1, WalkSmem<TS> &sm, int t, Seg &&seg,
+                                           uint32_t &T, uint32_t &NZ) {
+    const int lane = t & 31, w = t >> 5;
+    long long st = 0;
+    uint32_t len = 0, sw = 0;
+    if (j < m1) {
+        const uint4 d = smd[rb + j];
+        sw = d.w;
+        seg(d, st, len);
+    }
+    const uint32_t nq = quads_of((uint32_t)st, len);
+    uint32_t x = warp_incl_scan(nq);
+    const unsigned nzb = __ballot_sync(FULL, nq > 0);
+    uint32_t nzi = __popc(nzb & ((2u << lane) - 1u));
+    if constexpr (TS > 32) {
+        if (lane == 31) sm.warp_part[w] = x | ((unsigned long long)__popc(nzb) << 32);
+        team_sync<TS>();
+        uint32_t add_x = 0, add_n = 0;
+        for (int k = 0; k < w; k++) {
+            const unsigned long long v = sm.warp_part[k];
+            add_x += (uint32_t)v;
+            add_n += (uint32_t)(v >> 32);
+        }
+        x += add_x;
+        nzi += add_n;
+    }
+    if (nq > 0) sm.seg[nzi - 1] = QSeg{(uint32_t)st, (uint32_t)st + len, (x - nq) | (sw << 31), x};
+    if constexpr (TS == 32) {
+        T = __shfl_sync(FULL, x, 31);
+        NZ = __popc(nzb);
+        __syncwarp();
+    } else {
         if (t == TS - 1) { sm.tot[0] = x; sm.tot[1] = nzi; }
         team_sync<TS>();
-        const uint32_t T = sm.tot[0], NZ = sm.tot[1];
-        lane_range<U>(oadj, sm.desc, sm.incl, NZ, share<TS>(T, t), share<TS>(T, t + 1), add);
+        T = sm.tot[0];
+        NZ = sm.tot[1];
+    }
+}
+
+// Walk the wedges of one anchor's middles [m0, m1) (its row starts at rb in
+// the anchor side's descriptors smd; the middles' rows are in oadj) as a
+// team of TS threads (t = thread index in the team): per chunk of TS
+// middles, a chunk scan and then each thread's equal share of the chunk's
+// quads. seg(md, st, len) picks the segment [st, st+len) of a middle's row
+// from its descriptor; add(entry, sign bit of the anchor's edge to the
+// middle) is called once per wedge (entry = endpoint side rank << 1 | sign
+// of the middle-endpoint edge). flush() follows every `span` quads of a
+// thread.
+template <int TS, int U, typename Seg, typename Add, typename Flush>
+__device__ __forceinline__ void quad_walk(const uint4 *__restrict__ smd,
+                                          const uint32_t *__restrict__ oadj, int64_t rb,
+                                          uint32_t m0, uint32_t m1, WalkSmem<TS> &sm, int t,
+                                          uint32_t span, Seg &&seg, Add &&add, Flush &&flush) {
+    const uint4 *oadj4 = reinterpret_cast<const uint4 *>(oadj);
+    for (uint32_t mc = m0; mc < m1; mc += TS) {
+        uint32_t T, NZ;
+        chunk_scan<TS>(smd, rb, mc + (uint32_t)t, m1, sm, t, seg, T, NZ);
+        quad_range_flushed<U>(oadj4, sm.seg, NZ, share<TS>(T, t), share<TS>(T, t + 1), span, add,
+                              flush);
         team_sync<TS>();
     }
 }
 
-// One warp, two segment families of the same middles (the hub-window part
-// and the part below it) from one chunk scan: each lane walks its share of
-// the first family with addA, then its share of the second with addB.
-template <int U = 4, typename SegA, typename AddA, typename SegB, typename AddB>
-__device__ __forceinline__ void lane_walk2(const uint4 *__restrict__ smd,
-                                           const uint32_t *__restrict__ oadj, int64_t rb,
-                                           uint32_t m0, uint32_t m1, WalkSmem<32> &sa,
-                                           WalkSmem<32> &sb, int lane, SegA &&sega, AddA &&adda,
-                                           SegB &&segb, AddB &&addb) {
+// One warp walks two segment families of an anchor's middles (the
+// hub-window part and the part below it) from one chunk scan per 32
+// middles, in rounds. A round of the first family covers 32 consecutive
+// quads of the chunk's compacted quad range, lane l taking quad r + l, so
+// the lanes of a round read consecutive quads of a segment (coalesced
+// 16-byte loads); a round of the second family covers 32 consecutive
+// wedges, one per lane. A lane finds the segment of its quad or wedge from
+// the bitmask of the segments that start inside the round (one warp
+// OR-reduction): it is the last segment starting at or before its
+// position. quada(v, vm, sw) takes a loaded quad (vm: its entries inside
+// the segment, bit j for entry j; the quad is only read when vm != 0) and
+// oneb(x, sw) one wedge of the second family; sw is the sign bit of the
+// anchor's edge to the middle.
+template <typename SegA, typename QuadA, typename SegB, typename OneB>
+__device__ __forceinline__ void warp_rounds(const uint4 *__restrict__ smd,
+                                            const uint32_t *__restrict__ oadj, int64_t rb,
+                                            uint32_t m0, uint32_t m1, WalkSmem<32> &sa,
+                                            WalkSmem<32> &sb, unsigned lane, SegA &&sega,
+                                            QuadA &&quada, SegB &&segb, OneB &&oneb) {
+    const uint4 *oadj4 = reinterpret_cast<const uint4 *>(oadj);
     const unsigned upto = (2u << lane) - 1u;
     for (uint32_t mc = m0; mc < m1; mc += 32) {
-        const uint32_t j = mc + (uint32_t)lane;
+        const uint32_t j = mc + lane;
         long long sta = 0, stb = 0;
         uint32_t la = 0, lb = 0, sw = 0;
         if (j < m1) {
@@ -393,33 +311,60 @@ __device__ __forceinline__ void lane_walk2(const uint4 *__restrict__ smd,
             sega(d, sta, la);
             segb(d, stb, lb);
         }
-        unsigned long long x = (unsigned long long)la | ((unsigned long long)lb << 32);
+        const uint32_t qa = quads_of((uint32_t)sta, la);
+        unsigned long long x = (unsigned long long)qa | ((unsigned long long)lb << 32);
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const unsigned long long y = __shfl_up_sync(FULL, x, d);
-            if (lane >= d) x += y;
+            if (lane >= (unsigned)d) x += y;
         }
         const uint32_t xa = (uint32_t)x, xb = (uint32_t)(x >> 32);
-        const unsigned nza = __ballot_sync(FULL, la > 0), nzb = __ballot_sync(FULL, lb > 0);
-        if (la > 0) {
-            const uint32_t i = __popc(nza & upto) - 1;
-            sa.desc[i] = Desc{(uint32_t)sta, (xa - la) | (sw << 31)};
-            sa.incl[i] = xa;
-        }
-        if (lb > 0) {
-            const uint32_t i = __popc(nzb & upto) - 1;
-            sb.desc[i] = Desc{(uint32_t)stb, (xb - lb) | (sw << 31)};
-            sb.incl[i] = xb;
-        }
+        const uint32_t ea = xa - qa, eb = xb - lb;  // first quad / wedge of this lane's segments
+        const unsigned nza = __ballot_sync(FULL, qa > 0), nzb = __ballot_sync(FULL, lb > 0);
+        if (qa > 0)
+            sa.seg[__popc(nza & upto) - 1] =
+                QSeg{(uint32_t)sta, (uint32_t)sta + la, ea | (sw << 31), xa};
+        if (lb > 0)
+            sb.seg[__popc(nzb & upto) - 1] =
+                QSeg{(uint32_t)stb, (uint32_t)stb + lb, eb | (sw << 31), xb};
         const uint32_t TA = __shfl_sync(FULL, xa, 31), TB = __shfl_sync(FULL, xb, 31);
         __syncwarp();
-        lane_range<U>(oadj, sa.desc, sa.incl, __popc(nza), share<32>(TA, lane),
-                      share<32>(TA, lane + 1), adda);
-        lane_range<U>(oadj, sb.desc, sb.incl, __popc(nzb), share<32>(TB, lane),
-                      share<32>(TB, lane + 1), addb);
+        uint32_t base = 0;  // segments starting before this round
+        for (uint32_t r = 0; r < TA; r += 32) {
+            const uint32_t s = ea - r;
+            const unsigned M = __reduce_or_sync(FULL, (qa > 0 && s < 32u) ? 1u << s : 0u);
+            const uint32_t k = base + __popc(M & upto) - 1u;
+            base += __popc(M);
+            const uint32_t q = r + lane;
+            if (q < TA) {
+                const QSeg d = sa.seg[k];
+                const uint32_t qq = (d.st >> 2) + (q - (d.excl_sw & EXMASK));
+                const uint32_t w0 = qq << 2;
+                const uint32_t lo = d.st > w0 ? d.st - w0 : 0u;
+                const uint32_t hi = d.en - w0 < 4u ? d.en - w0 : 4u;
+                quada(__ldg(oadj4 + qq), (0xfu >> (4u - hi)) & (0xfu << lo), d.excl_sw >> 31);
+            }
+        }
+        base = 0;
+        for (uint32_t r = 0; r < TB; r += 32) {
+            const uint32_t s = eb - r;
+            const unsigned M = __reduce_or_sync(FULL, (lb > 0 && s < 32u) ? 1u << s : 0u);
+            const uint32_t k = base + __popc(M & upto) - 1u;
+            base += __popc(M);
+            const uint32_t p = r + lane;
+            if (p < TB) {
+                const QSeg d = sb.seg[k];
+                oneb(oadj[d.st + (p - (d.excl_sw & EXMASK))], d.excl_sw >> 31);
+            }
+        }
         __syncwarp();
     }
 }
+
+struct NoFlush {
+    __device__ void operator()() const {}
+};
+constexpr uint32_t NO_SPAN = 0xffffffffu;
 
 // insert-or-increment in a shared-memory table of 2^(32-shift) u64 slots;
 // returns the packed (S | A << 16) count the key held before
@@ -444,16 +389,8 @@ __device__ __forceinline__ uint32_t hash_add(unsigned long long *tab, uint32_t s
     return 0u;
 }
 
-// hash add plus the wedge's contribution
-__device__ __forceinline__ void hash_wedge(unsigned long long *tab, uint32_t shift, uint32_t mask,
-                                           uint32_t u, uint32_t asym, uint32_t *err,
-                                           unsigned long long &bal, unsigned long long &tot) {
-    const uint32_t old = hash_add(tab, shift, mask, u + 1, asym ? INC_ASYM : INC_SYM, err);
-    wedge_terms(old & 0xffffu, old >> 16, asym, bal, tot);
-}
-
-// the same with 32-bit running sums (anchors whose sums provably fit):
-// dp2a takes the previous S or A (16-bit halves of the slot's count) or both
+// hash add plus the wedge's contribution to 32-bit running sums (callers
+// bound them): dp2a takes the previous S or A (16-bit halves of the slot's count) or both
 __device__ __forceinline__ void hash_wedge32(unsigned long long *tab, uint32_t shift,
                                              uint32_t mask, uint32_t x, uint32_t sw,
                                              uint32_t *err, uint32_t &b32, uint32_t &t32) {
@@ -542,14 +479,7 @@ static_assert(sizeof(WarpSmem) % 16 == 0, "WarpSmem must keep 16-byte alignment"
 static_assert((HUB_WINDOW & (HUB_WINDOW - 1)) == 0, "hub window indexes are masked");
 static_assert(offsetof(WarpSmem, tab) % 16 == 0, "table needs 16-byte alignment");
 
-// anchors with at least this many wedges walk eight wedges per lane step
-// (more loads in flight) in the single-graph kernel
-constexpr uint64_t WARP_WIDE_W = 2048;
-
-// one warp-class anchor, walked by one warp; WIDE: large anchors take the
-// eight-wedge lane steps (the batch kernel, whose mix is mostly small
-// anchors, keeps four: the second walker instance slows it)
-template <bool WIDE>
+// one warp-class anchor, walked by one warp
 __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, const AnchorRec &rec,
                                             unsigned lane, unsigned long long &bal,
                                             unsigned long long &tot) {
@@ -557,16 +487,19 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
     const Anchor A = load_anchor(G, rec);
     const uint64_t W = A.W, above = (uint64_t)(A.ns - A.r - 1);
     uint32_t cap = 0, shift = 0;
-    // 32-bit sums: a lane walks at most W/32 + 1 <= 513 wedges of each
-    // family of the anchor, each adding at most 2 * 255
+    // 32-bit sums: an anchor has at most WARP_W_MAX wedges, each adding less
+    // than 2^8 (tallies are bounded by the degree, at most WARP_DEG_MAX)
+    static_assert(WARP_W_MAX * 2 * WARP_DEG_MAX < (1ull << 32), "32-bit warp sums");
     uint32_t b32 = 0, t32 = 0;
+    auto none = [](const uint4 &, long long &st, uint32_t &len) { st = 0; len = 0; };
+    auto no_quad = [](const uint4 &, uint32_t, uint32_t) {};
     if (W <= WARP_SMALL_W) {  // hash every endpoint
         table_geometry(W < above ? W : above, 32, WARP_CAP, cap, shift);
         const uint32_t mask = cap - 1;
-        lane_walk<32>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, (int)lane, FullSeg{},
-                      [&](uint32_t x, uint32_t sw) {
-                          hash_wedge32(sm.tab, shift, mask, x, sw, err, b32, t32);
-                      });
+        warp_rounds(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, sm.walk2, lane, none, no_quad,
+                    FullSeg{}, [&](uint32_t x, uint32_t sw) {
+                        hash_wedge32(sm.tab, shift, mask, x, sw, err, b32, t32);
+                    });
     } else {
         const int64_t ns = A.ns;
         const uint32_t wb = ns > (int64_t)HUB_WINDOW ? (uint32_t)(ns - HUB_WINDOW) : 0u;
@@ -576,31 +509,32 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
         if (wnh > 0) table_geometry(wnh < above_nh ? wnh : above_nh, 32, WARP_CAP, cap, shift);
         const uint32_t mask = cap - 1;
         uint32_t bad_off = 0;
-        auto hub_add = [&](uint32_t x, uint32_t sw) {
-            // S in byte 0 and A in byte 1 of the endpoint's 16-bit half of a
-            // word (both <= the degree <= 255). The entry less twice the
-            // window base is 2 * (window index) + sign: bit 1 picks the half
-            // and bit 0 xor the anchor edge's sign the byte. The increment is
-            // that byte's lowest bit; as a byte mask for dp4a it picks the
-            // tally's own previous value out of the returned word, and
-            // 0x0101 at the half picks S + A.
+        // S in byte 0 and A in byte 1 of the endpoint's 16-bit half of a word
+        // (both <= the degree <= 255). The entry less twice the window base
+        // is 2 * (window index) + sign: bit 1 picks the half and bit 0 xor
+        // the anchor edge's sign the byte. The increment is that byte's
+        // lowest bit (zero for an entry outside the segment, vb = 0); as a
+        // byte mask for dp4a it picks the tally's own previous value out of
+        // the returned word, and 0x0101 at the half picks S + A.
+        auto hub_one = [&](uint32_t x, uint32_t vb, uint32_t sw) {
             const uint32_t xi = x - wb2;
-            bad_off |= xi;  // any entry outside the window sets a high bit
+            bad_off |= xi & (0u - vb);  // an entry outside the window sets a high bit
             const uint32_t sh = ((xi ^ sw) & 3u) << 3;
-            const uint32_t inc = 1u << sh;
+            const uint32_t inc = vb << sh;
             const uint32_t old = atomicAdd(&sm.win[(xi >> 2) & (HUB_WINDOW / 2 - 1)], inc);
             b32 = __dp4a(old, inc, b32);
-            t32 = __dp4a(old, 0x0101u << (sh & 16u), t32);
+            t32 = __dp4a(old, (vb * 0x0101u) << (sh & 16u), t32);
         };
-        auto low_add = [&](uint32_t x, uint32_t sw) {
-            hash_wedge32(sm.tab, shift, mask, x, sw, err, b32, t32);
-        };
-        if (WIDE && W >= WARP_WIDE_W)
-            lane_walk2<8>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, sm.walk2, (int)lane, HubSeg{},
-                          hub_add, LowSeg{}, low_add);
-        else
-            lane_walk2<4>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, sm.walk2, (int)lane, HubSeg{},
-                          hub_add, LowSeg{}, low_add);
+        warp_rounds(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, sm.walk2, lane, HubSeg{},
+                    [&](const uint4 &v, uint32_t vm, uint32_t sw) {
+                        hub_one(v.x, vm & 1u, sw);
+                        hub_one(v.y, (vm >> 1) & 1u, sw);
+                        hub_one(v.z, (vm >> 2) & 1u, sw);
+                        hub_one(v.w, vm >> 3, sw);
+                    },
+                    LowSeg{}, [&](uint32_t x, uint32_t sw) {
+                        hash_wedge32(sm.tab, shift, mask, x, sw, err, b32, t32);
+                    });
         if (bad_off >= 2 * HUB_WINDOW) set_error(err, E_INTERNAL);
         // reset the window words an endpoint can have reached
         const uint32_t first = (A.r + 1 > wb ? A.r + 1 - wb : 0u) >> 3;  // uint4 index
@@ -622,7 +556,7 @@ __device__ __forceinline__ WarpSmem &warp_smem_init(unsigned char *smem_raw, uns
     return sm;
 }
 
-__global__ void __launch_bounds__(WARP_THREADS, 3) k_warp(DevGraph G) {
+__global__ void __launch_bounds__(WARP_THREADS, 4) k_warp(DevGraph G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const unsigned lane = lane_id();
     WarpSmem &sm = warp_smem_init(smem_raw, lane);
@@ -631,7 +565,7 @@ __global__ void __launch_bounds__(WARP_THREADS, 3) k_warp(DevGraph G) {
     const uint32_t GW = (gridDim.x * WARP_THREADS) >> 5;
     unsigned long long bal = 0, tot = 0;
     for (uint32_t idx = gw; idx < n; idx += GW) {
-        warp_anchor<true>(G, sm, G.warp_list[idx], lane, bal, tot);
+        warp_anchor(G, sm, G.warp_list[idx], lane, bal, tot);
         spill_if_large(G.scratch, bal, tot);
     }
     flush_warp(G.scratch, bal, tot);
@@ -656,6 +590,13 @@ __device__ __forceinline__ HybSmem<TS, HCAP> &hybrid_smem_init(unsigned char *sm
     return sm;
 }
 
+// Running sums in 32 bits: a wedge adds its pair's previous tallies, which
+// are at most the anchor's degree (<= MAX_DEGREE), so SUM_SPAN quads of one
+// thread (four wedges each) cannot wrap a u32 before the walker flushes
+// them into the 64-bit sums.
+constexpr uint32_t SUM_SPAN = 8192;
+static_assert((unsigned long long)SUM_SPAN * 4 * MAX_DEGREE < (1ull << 32), "32-bit span sums");
+
 // one team/CTA-hash anchor, walked by the whole CTA
 template <int TS, uint32_t HCAP>
 __device__ __forceinline__ void hybrid_anchor(const DevGraph &G, HybSmem<TS, HCAP> &sm,
@@ -668,41 +609,38 @@ __device__ __forceinline__ void hybrid_anchor(const DevGraph &G, HybSmem<TS, HCA
     const uint32_t wb = ns > (int64_t)HUB_WINDOW ? (uint32_t)(ns - HUB_WINDOW) : 0u;
     const uint64_t W = A.W, wnh = A.wnh;
     const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
-    // lane steps: four wedges for team anchors (more register pressure
-    // costs them occupancy), eight for the CTA-hash class
-    constexpr int LU = TS == TEAM_THREADS ? 4 : 8;
-    if (W > wnh) {  // endpoints inside the hub window
-        // Team anchors (at most TEAM_W_MAX wedges, each adding at most
-        // 2 * 65535) sum the hub part in 32 bits: dp2a takes the previous
-        // S or A (16-bit halves of the returned word) or their sum.
-        constexpr bool narrow = TS == TEAM_THREADS;
-        static_assert(!narrow || TEAM_W_MAX * 2 * 65535 < (1ull << 32), "32-bit team sums");
-        uint32_t b32 = 0, t32 = 0;
-        lane_walk<TS, LU>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, HubSeg{},
-                      [&](uint32_t x, uint32_t sw) {
-                          const uint32_t asym = (x ^ sw) & 1u;
-                          const uint32_t idx = (x >> 1) - wb;
-                          if (idx >= HUB_WINDOW) { set_error(err, E_INTERNAL); return; }
-                          const uint32_t old = atomicAdd(&sm.win[idx], asym ? INC_ASYM : INC_SYM);
-                          if constexpr (narrow) {
-                              b32 = __dp2a_lo(old, 1u << (asym << 3), b32);
-                              t32 = __dp2a_lo(old, 0x0101u, t32);
-                          } else {
-                              wedge_terms(old & 0xffffu, old >> 16, asym, bal, tot);
-                          }
-                      });
+    constexpr int QU = TS == TEAM_THREADS ? 1 : 2;  // quads per walker step
+    uint32_t b32 = 0, t32 = 0;
+    auto flush = [&]() {
         bal += b32;
         tot += t32;
+        b32 = t32 = 0;
+    };
+    if (W > wnh) {  // endpoints inside the hub window
+        // dp2a takes the previous S or A (16-bit halves of the returned
+        // word) or their sum
+        quad_walk<TS, QU>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, SUM_SPAN, HubSeg{},
+                          [&](uint32_t x, uint32_t sw) {
+                              const uint32_t asym = (x ^ sw) & 1u;
+                              const uint32_t idx = (x >> 1) - wb;
+                              if (idx >= HUB_WINDOW) { set_error(err, E_INTERNAL); return; }
+                              const uint32_t old =
+                                  atomicAdd(&sm.win[idx], asym ? INC_ASYM : INC_SYM);
+                              b32 = __dp2a_lo(old, 1u << (asym << 3), b32);
+                              t32 = __dp2a_lo(old, 0x0101u, t32);
+                          },
+                          flush);
     }
     uint32_t cap = 0;
     if (wnh > 0) {  // endpoints below the window
         uint32_t shift;
         table_geometry(wnh < above_nh ? wnh : above_nh, 32, HCAP, cap, shift);
         const uint32_t mask = cap - 1;
-        lane_walk<TS, LU>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, LowSeg{},
-                      [&](uint32_t x, uint32_t sw) {
-                          hash_wedge(sm.tab, shift, mask, x >> 1, (x ^ sw) & 1u, err, bal, tot);
-                      });
+        quad_walk<TS, QU>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, SUM_SPAN, LowSeg{},
+                          [&](uint32_t x, uint32_t sw) {
+                              hash_wedge32(sm.tab, shift, mask, x, sw, err, b32, t32);
+                          },
+                          flush);
     }
     __syncthreads();
     if (W > wnh) {
@@ -742,6 +680,8 @@ __global__ void __launch_bounds__(CTAH_THREADS) k_ctah(DevGraph G) {
 }
 
 // ------------------------------------------------------------ dense class
+constexpr int DENSE_U = 2;  // quads per walker step
+
 struct alignas(16) DenseSmem {
     uint32_t cnt[DENSE_CAP];
     WalkSmem<DENSE_THREADS> walk;
@@ -768,24 +708,32 @@ __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, cons
         const uint32_t len = e1 - e0;
         for (uint32_t i = t; i < len; i += DENSE_THREADS) sm.cnt[i] = 0;
         __syncthreads();
+        uint32_t b32 = 0, t32 = 0;
         auto add = [&](uint32_t x, uint32_t sw) {
             const uint32_t asym = (x ^ sw) & 1u;
             const uint32_t idx = (x >> 1) - e0;
             if (idx >= len) { set_error(&sc->err, E_INTERNAL); return; }
             const uint32_t old = atomicAdd(&sm.cnt[idx], asym ? INC_ASYM : INC_SYM);
-            wedge_terms(old & 0xffffu, old >> 16, asym, bal, tot);
+            b32 = __dp2a_lo(old, 1u << (asym << 3), b32);
+            t32 = __dp2a_lo(old, 0x0101u, t32);
+        };
+        auto flush = [&]() {
+            bal += b32;
+            tot += t32;
+            b32 = t32 = 0;
         };
         if (windows) {
-            team_walk<DENSE_THREADS>(
-                A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t,
+            quad_walk<DENSE_THREADS, DENSE_U>(
+                A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t, SUM_SPAN,
                 [&](const uint4 &d, long long &st, uint32_t &l) {
                     const long long s0 = lower_bound_u32(A.oadj, d.x, d.z, e0 << 1);
                     st = s0;
                     l = (uint32_t)(lower_bound_u32(A.oadj, s0, d.z, e1 << 1) - s0);
                 },
-                add);
+                add, flush);
         } else {
-            team_walk<DENSE_THREADS>(A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t, FullSeg{}, add);
+            quad_walk<DENSE_THREADS, DENSE_U>(A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t,
+                                              SUM_SPAN, FullSeg{}, add, flush);
         }
         if (J.group != NO_GROUP) {
             // merge this part's counts into the group's global counters; a
@@ -821,7 +769,7 @@ __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, cons
     }
 }
 
-__global__ void __launch_bounds__(DENSE_THREADS) k_dense(DevGraph G) {
+__global__ void __launch_bounds__(DENSE_THREADS, 3) k_dense(DevGraph G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DenseSmem &sm = *reinterpret_cast<DenseSmem *>(smem_raw);
     const uint32_t njobs = G.ctr[CTR_DENSE];
@@ -883,7 +831,7 @@ __global__ void __launch_bounds__(WARP_THREADS, 4) k_warp_batch(BatchArgs B) {
                 do { gi++; gbeg = gend; gend = p[gi + 1]; } while (it >= gend);
             }
             const DevGraph &G = B.graphs[gi];
-            warp_anchor<false>(G, sm, G.warp_list[it - gbeg], lane, bal, tot);
+            warp_anchor(G, sm, G.warp_list[it - gbeg], lane, bal, tot);
         }
         bal = warp_sum_u64(bal); tot = warp_sum_u64(tot);
         if (lane == 0) acc_add(B.graphs[gi].scratch, bal, tot);
