@@ -311,14 +311,12 @@ __device__ __forceinline__ void warp_rounds(const uint4 *__restrict__ smd,
             sega(d, sta, la);
             segb(d, stb, lb);
         }
+        // one scan of both families' sizes in 16-bit halves: an anchor of
+        // the warp class has at most WARP_W_MAX wedges, so neither sum wraps
+        static_assert(WARP_W_MAX < 0xffff, "packed warp chunk scan");
         const uint32_t qa = quads_of((uint32_t)sta, la);
-        unsigned long long x = (unsigned long long)qa | ((unsigned long long)lb << 32);
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const unsigned long long y = __shfl_up_sync(FULL, x, d);
-            if (lane >= (unsigned)d) x += y;
-        }
-        const uint32_t xa = (uint32_t)x, xb = (uint32_t)(x >> 32);
+        const uint32_t x = warp_incl_scan(qa | (lb << 16));
+        const uint32_t xa = x & 0xffffu, xb = x >> 16;
         const uint32_t ea = xa - qa, eb = xb - lb;  // first quad / wedge of this lane's segments
         const unsigned nza = __ballot_sync(FULL, qa > 0), nzb = __ballot_sync(FULL, lb > 0);
         if (qa > 0)
@@ -329,28 +327,62 @@ __device__ __forceinline__ void warp_rounds(const uint4 *__restrict__ smd,
                 QSeg{(uint32_t)stb, (uint32_t)stb + lb, eb | (sw << 31), xb};
         const uint32_t TA = __shfl_sync(FULL, xa, 31), TB = __shfl_sync(FULL, xb, 31);
         __syncwarp();
-        uint32_t base = 0;  // segments starting before this round
-        for (uint32_t r = 0; r < TA; r += 32) {
+        // The second family's first round is loaded before the first
+        // family's rounds run, and each round of the first family loads its
+        // quads one round ahead: a warp keeps two loads in flight instead of
+        // waiting out one memory round trip per round.
+        uint32_t xb0 = 0, swb0 = 0, baseb = 0;
+        bool hb0 = false;
+        if (TB > 0) {
+            const unsigned M = __reduce_or_sync(FULL, (lb > 0 && eb < 32u) ? 1u << eb : 0u);
+            const uint32_t k = __popc(M & upto) - 1u;
+            baseb = __popc(M);
+            if (lane < TB) {
+                const QSeg d = sb.seg[k];
+                xb0 = oadj[d.st + (lane - (d.excl_sw & EXMASK))];
+                swb0 = d.excl_sw >> 31;
+                hb0 = true;
+            }
+        }
+        uint32_t base = 0;  // segments of the first family starting before the next round
+        // quad of lane `lane` in the round starting at quad r: loads it and
+        // sets vm (0 past the chunk's quads) and sw
+        auto locate = [&](uint32_t r, uint4 &v, uint32_t &vm, uint32_t &swq) {
             const uint32_t s = ea - r;
             const unsigned M = __reduce_or_sync(FULL, (qa > 0 && s < 32u) ? 1u << s : 0u);
             const uint32_t k = base + __popc(M & upto) - 1u;
             base += __popc(M);
             const uint32_t q = r + lane;
+            vm = 0u;
             if (q < TA) {
                 const QSeg d = sa.seg[k];
                 const uint32_t qq = (d.st >> 2) + (q - (d.excl_sw & EXMASK));
                 const uint32_t w0 = qq << 2;
                 const uint32_t lo = d.st > w0 ? d.st - w0 : 0u;
                 const uint32_t hi = d.en - w0 < 4u ? d.en - w0 : 4u;
-                quada(__ldg(oadj4 + qq), (0xfu >> (4u - hi)) & (0xfu << lo), d.excl_sw >> 31);
+                vm = (0xfu >> (4u - hi)) & (0xfu << lo);
+                swq = d.excl_sw >> 31;
+                v = __ldg(oadj4 + qq);
             }
+        };
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t vm = 0u, swq = 0u;
+        if (TA > 0) locate(0, v, vm, swq);
+        for (uint32_t r = 0; r < TA; r += 32) {
+            uint4 vn = make_uint4(0u, 0u, 0u, 0u);
+            uint32_t vmn = 0u, swn = 0u;
+            if (r + 32 < TA) locate(r + 32, vn, vmn, swn);
+            if (vm) quada(v, vm, swq);
+            v = vn;
+            vm = vmn;
+            swq = swn;
         }
-        base = 0;
-        for (uint32_t r = 0; r < TB; r += 32) {
+        if (hb0) oneb(xb0, swb0);
+        for (uint32_t r = 32; r < TB; r += 32) {
             const uint32_t s = eb - r;
             const unsigned M = __reduce_or_sync(FULL, (lb > 0 && s < 32u) ? 1u << s : 0u);
-            const uint32_t k = base + __popc(M & upto) - 1u;
-            base += __popc(M);
+            const uint32_t k = baseb + __popc(M & upto) - 1u;
+            baseb += __popc(M);
             const uint32_t p = r + lane;
             if (p < TB) {
                 const QSeg d = sb.seg[k];
@@ -361,24 +393,22 @@ __device__ __forceinline__ void warp_rounds(const uint4 *__restrict__ smd,
     }
 }
 
-struct NoFlush {
-    __device__ void operator()() const {}
-};
-constexpr uint32_t NO_SPAN = 0xffffffffu;
-
-// insert-or-increment in a shared-memory table of 2^(32-shift) u64 slots;
-// returns the packed (S | A << 16) count the key held before
+// Open-addressing tables in shared memory of 2^(32-shift) u64 slots: the
+// key (endpoint + 1; 0 = empty) in the high half and the packed tallies
+// (S | A << 16) in the low half. hash_add inserts or finds the key and adds
+// inc to its tallies (an insert sets key and first tally in one
+// compare-and-swap); it returns the tallies the key held before.
 __device__ __forceinline__ uint32_t hash_add(unsigned long long *tab, uint32_t shift,
                                              uint32_t mask, uint32_t key, uint32_t inc,
                                              uint32_t *err) {
     uint32_t h = hash_slot(key, shift);
     for (uint32_t probe = 0; probe <= mask; probe++) {
-        unsigned long long cur = *((volatile unsigned long long *)&tab[h]);
-        uint32_t k = (uint32_t)(cur >> 32);
+        const unsigned long long cur = *((volatile unsigned long long *)&tab[h]);
+        const uint32_t k = (uint32_t)(cur >> 32);
         if (k == key) return (uint32_t)atomicAdd(&tab[h], (unsigned long long)inc);
         if (k == 0) {
-            unsigned long long want = ((unsigned long long)key << 32) | inc;
-            unsigned long long old = atomicCAS(&tab[h], 0ull, want);
+            const unsigned long long want = ((unsigned long long)key << 32) | inc;
+            const unsigned long long old = atomicCAS(&tab[h], 0ull, want);
             if (old == 0ull) return 0u;
             if ((uint32_t)(old >> 32) == key)
                 return (uint32_t)atomicAdd(&tab[h], (unsigned long long)inc);
@@ -389,15 +419,19 @@ __device__ __forceinline__ uint32_t hash_add(unsigned long long *tab, uint32_t s
     return 0u;
 }
 
-// hash add plus the wedge's contribution to 32-bit running sums (callers
-// bound them): dp2a takes the previous S or A (16-bit halves of the slot's count) or both
+// Running sums of one thread, per wedge: own += the previous value of the
+// wedge's own tally, other += the previous value of the pair's other tally.
+// Over all wedges own is the balanced count (C(S,2) + C(A,2) per pair) and
+// own + other the total (C(S+A,2)). dp2a picks a 16-bit half of the packed
+// tallies by a byte mask: 1 for S, 0x100 for A.
 __device__ __forceinline__ void hash_wedge32(unsigned long long *tab, uint32_t shift,
                                              uint32_t mask, uint32_t x, uint32_t sw,
-                                             uint32_t *err, uint32_t &b32, uint32_t &t32) {
+                                             uint32_t *err, uint32_t &own, uint32_t &other) {
     const uint32_t asym = (x ^ sw) & 1u;
     const uint32_t old = hash_add(tab, shift, mask, (x >> 1) + 1, asym ? INC_ASYM : INC_SYM, err);
-    b32 = __dp2a_lo(old, 1u << (asym << 3), b32);
-    t32 = __dp2a_lo(old, 0x0101u, t32);
+    const uint32_t pick = 1u << (asym << 3);
+    own = __dp2a_lo(old, pick, own);
+    other = __dp2a_lo(old, pick ^ 0x0101u, other);
 }
 
 // zero the first `cap` slots of a table (cap a multiple of 2) as a team
@@ -467,7 +501,13 @@ struct LowSeg {
 // ------------------------------------------------------------ warp class
 // Per warp: the hub window as 16-bit counters, two per word (S in the low
 // byte, A in the high byte; both <= the anchor's degree <= 255), a small
-// hash for endpoints below the window, and the walker's chunk.
+// hash for endpoints below the window, and the walker's chunks.
+//
+// The hub window holds the top HUB_WINDOW side ranks; a rank's counter is
+// at rank mod HUB_WINDOW, one to one on any HUB_WINDOW consecutive ranks.
+// With entry x = rank << 1 | sign: the counter's word is at byte offset
+// x & (2 HUB_WINDOW - 4), its half is bit 1 of x, and bit 0 of x xor the
+// anchor edge's sign picks the byte (S or A).
 struct alignas(16) WarpSmem {
     uint32_t win[HUB_WINDOW / 2];
     unsigned long long tab[WARP_CAP];
@@ -488,9 +528,9 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
     const uint64_t W = A.W, above = (uint64_t)(A.ns - A.r - 1);
     uint32_t cap = 0, shift = 0;
     // 32-bit sums: an anchor has at most WARP_W_MAX wedges, each adding less
-    // than 2^8 (tallies are bounded by the degree, at most WARP_DEG_MAX)
-    static_assert(WARP_W_MAX * 2 * WARP_DEG_MAX < (1ull << 32), "32-bit warp sums");
-    uint32_t b32 = 0, t32 = 0;
+    // than 2^8 to each sum (tallies are bounded by the degree <= WARP_DEG_MAX)
+    static_assert(WARP_W_MAX * WARP_DEG_MAX < (1ull << 32), "32-bit warp sums");
+    uint32_t own = 0, other = 0;
     auto none = [](const uint4 &, long long &st, uint32_t &len) { st = 0; len = 0; };
     auto no_quad = [](const uint4 &, uint32_t, uint32_t) {};
     if (W <= WARP_SMALL_W) {  // hash every endpoint
@@ -498,32 +538,28 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
         const uint32_t mask = cap - 1;
         warp_rounds(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, sm.walk2, lane, none, no_quad,
                     FullSeg{}, [&](uint32_t x, uint32_t sw) {
-                        hash_wedge32(sm.tab, shift, mask, x, sw, err, b32, t32);
+                        hash_wedge32(sm.tab, shift, mask, x, sw, err, own, other);
                     });
     } else {
         const int64_t ns = A.ns;
         const uint32_t wb = ns > (int64_t)HUB_WINDOW ? (uint32_t)(ns - HUB_WINDOW) : 0u;
-        const uint32_t wb2 = wb << 1;  // the window base as an entry (side ranks < 2^31)
         const uint64_t wnh = A.wnh;
         const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
         if (wnh > 0) table_geometry(wnh < above_nh ? wnh : above_nh, 32, WARP_CAP, cap, shift);
         const uint32_t mask = cap - 1;
-        uint32_t bad_off = 0;
-        // S in byte 0 and A in byte 1 of the endpoint's 16-bit half of a word
-        // (both <= the degree <= 255). The entry less twice the window base
-        // is 2 * (window index) + sign: bit 1 picks the half and bit 0 xor
-        // the anchor edge's sign the byte. The increment is that byte's
-        // lowest bit (zero for an entry outside the segment, vb = 0); as a
-        // byte mask for dp4a it picks the tally's own previous value out of
-        // the returned word, and 0x0101 at the half picks S + A.
+        char *win = reinterpret_cast<char *>(sm.win);
+        // one hub-window wedge (vb = 1) or an entry of the quad outside the
+        // segment (vb = 0: adds 0 and picks nothing); the increment is the
+        // tally byte's lowest bit, and as a dp4a byte mask it picks that
+        // tally's previous value out of the returned word (the other
+        // tally's byte for `other`)
         auto hub_one = [&](uint32_t x, uint32_t vb, uint32_t sw) {
-            const uint32_t xi = x - wb2;
-            bad_off |= xi & (0u - vb);  // an entry outside the window sets a high bit
-            const uint32_t sh = ((xi ^ sw) & 3u) << 3;
+            const uint32_t sh = ((x ^ sw) & 3u) << 3;
             const uint32_t inc = vb << sh;
-            const uint32_t old = atomicAdd(&sm.win[(xi >> 2) & (HUB_WINDOW / 2 - 1)], inc);
-            b32 = __dp4a(old, inc, b32);
-            t32 = __dp4a(old, (vb * 0x0101u) << (sh & 16u), t32);
+            const uint32_t old =
+                atomicAdd(reinterpret_cast<uint32_t *>(win + (x & (2u * HUB_WINDOW - 4u))), inc);
+            own = __dp4a(old, inc, own);
+            other = __dp4a(old, __byte_perm(inc, 0u, 0x2301u), other);  // the half's other byte
         };
         warp_rounds(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, sm.walk2, lane, HubSeg{},
                     [&](const uint4 &v, uint32_t vm, uint32_t sw) {
@@ -533,17 +569,13 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
                         hub_one(v.w, vm >> 3, sw);
                     },
                     LowSeg{}, [&](uint32_t x, uint32_t sw) {
-                        hash_wedge32(sm.tab, shift, mask, x, sw, err, b32, t32);
+                        hash_wedge32(sm.tab, shift, mask, x, sw, err, own, other);
                     });
-        if (bad_off >= 2 * HUB_WINDOW) set_error(err, E_INTERNAL);
-        // reset the window words an endpoint can have reached
-        const uint32_t first = (A.r + 1 > wb ? A.r + 1 - wb : 0u) >> 3;  // uint4 index
         uint4 *w4 = reinterpret_cast<uint4 *>(sm.win);
-        for (uint32_t q = first + lane; q < HUB_WINDOW / 8; q += 32)
-            w4[q] = make_uint4(0u, 0u, 0u, 0u);
+        for (uint32_t q = lane; q < HUB_WINDOW / 8; q += 32) w4[q] = make_uint4(0u, 0u, 0u, 0u);
     }
-    bal += b32;
-    tot += t32;
+    bal += own;
+    tot += (unsigned long long)own + other;
     clear_table<32>(sm.tab, cap, (int)lane);
     __syncwarp();
 }
@@ -564,18 +596,26 @@ __global__ void __launch_bounds__(WARP_THREADS, 4) k_warp(DevGraph G) {
     const uint32_t gw = (blockIdx.x * WARP_THREADS + threadIdx.x) >> 5;
     const uint32_t GW = (gridDim.x * WARP_THREADS) >> 5;
     unsigned long long bal = 0, tot = 0;
+    // the next anchor's record is loaded while this one is walked
+    AnchorRec cur;
+    if (gw < n) cur = G.warp_list[gw];
     for (uint32_t idx = gw; idx < n; idx += GW) {
-        warp_anchor(G, sm, G.warp_list[idx], lane, bal, tot);
+        AnchorRec nxt;
+        if (idx + GW < n) nxt = G.warp_list[idx + GW];
+        warp_anchor(G, sm, cur, lane, bal, tot);
         spill_if_large(G.scratch, bal, tot);
+        cur = nxt;
     }
     flush_warp(G.scratch, bal, tot);
 }
 
 // ------------------------------------------------- team and CTA-hash classes
+// Per CTA: the hub window as 32-bit counters (S | A << 16), a hash for
+// endpoints below the window, and the walker's chunk.
 template <int TS, uint32_t HCAP>
 struct alignas(16) HybSmem {
-    uint32_t win[HUB_WINDOW];          // hub window counters
-    unsigned long long tab[HCAP];      // hash for endpoints below the window
+    uint32_t win[HUB_WINDOW];             // hub window counters
+    unsigned long long tab[HCAP];         // hash for endpoints below the window
     WalkSmem<TS> walk;
     uint32_t job;
 };
@@ -610,15 +650,15 @@ __device__ __forceinline__ void hybrid_anchor(const DevGraph &G, HybSmem<TS, HCA
     const uint64_t W = A.W, wnh = A.wnh;
     const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
     constexpr int QU = TS == TEAM_THREADS ? 1 : 2;  // quads per walker step
-    uint32_t b32 = 0, t32 = 0;
+    // hub walk: hb = the wedges' own previous tallies, ht = both previous
+    // tallies; hash walk: own and other as in hash_wedge32
+    uint32_t hb = 0, ht = 0, own = 0, other = 0;
     auto flush = [&]() {
-        bal += b32;
-        tot += t32;
-        b32 = t32 = 0;
+        bal += (unsigned long long)hb + own;
+        tot += (unsigned long long)ht + own + other;
+        hb = ht = own = other = 0;
     };
     if (W > wnh) {  // endpoints inside the hub window
-        // dp2a takes the previous S or A (16-bit halves of the returned
-        // word) or their sum
         quad_walk<TS, QU>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, SUM_SPAN, HubSeg{},
                           [&](uint32_t x, uint32_t sw) {
                               const uint32_t asym = (x ^ sw) & 1u;
@@ -626,8 +666,8 @@ __device__ __forceinline__ void hybrid_anchor(const DevGraph &G, HybSmem<TS, HCA
                               if (idx >= HUB_WINDOW) { set_error(err, E_INTERNAL); return; }
                               const uint32_t old =
                                   atomicAdd(&sm.win[idx], asym ? INC_ASYM : INC_SYM);
-                              b32 = __dp2a_lo(old, 1u << (asym << 3), b32);
-                              t32 = __dp2a_lo(old, 0x0101u, t32);
+                              hb = __dp2a_lo(old, 1u << (asym << 3), hb);
+                              ht = __dp2a_lo(old, 0x0101u, ht);
                           },
                           flush);
     }
@@ -638,16 +678,14 @@ __device__ __forceinline__ void hybrid_anchor(const DevGraph &G, HybSmem<TS, HCA
         const uint32_t mask = cap - 1;
         quad_walk<TS, QU>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, SUM_SPAN, LowSeg{},
                           [&](uint32_t x, uint32_t sw) {
-                              hash_wedge32(sm.tab, shift, mask, x, sw, err, b32, t32);
+                              hash_wedge32(sm.tab, shift, mask, x, sw, err, own, other);
                           },
                           flush);
     }
     __syncthreads();
     if (W > wnh) {
-        const uint32_t first = (A.r + 1 > wb ? A.r + 1 - wb : 0u) >> 2;  // uint4 index
         uint4 *w4 = reinterpret_cast<uint4 *>(sm.win);
-        for (uint32_t q = first + t; q < HUB_WINDOW / 4; q += TS)
-            w4[q] = make_uint4(0u, 0u, 0u, 0u);
+        for (uint32_t q = t; q < HUB_WINDOW / 4; q += TS) w4[q] = make_uint4(0u, 0u, 0u, 0u);
     }
     clear_table<TS>(sm.tab, cap, t);
 }
@@ -708,6 +746,7 @@ __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, cons
         const uint32_t len = e1 - e0;
         for (uint32_t i = t; i < len; i += DENSE_THREADS) sm.cnt[i] = 0;
         __syncthreads();
+        // b32: the wedges' own previous tallies; t32: both previous tallies
         uint32_t b32 = 0, t32 = 0;
         auto add = [&](uint32_t x, uint32_t sw) {
             const uint32_t asym = (x ^ sw) & 1u;
