@@ -139,13 +139,16 @@ __device__ __forceinline__ uint32_t share(uint32_t n, uint32_t t) {
 
 // Quad walker, per thread: the quads [a, b) of a compacted chunk (NZ
 // segments). Every step loads whole aligned quads of the middle side's
-// adjacency (one 16-byte load for four entries) and calls add(entry, sign
-// bit of the anchor's edge) for each entry of the quad inside its segment.
-// A quad holds at least one entry of its segment, so it lies inside the
-// adjacency's 16-byte-padded allocation. Threads get equal quad counts, so
-// a team's lanes run the same number of steps; entries outside a segment
-// (its first and last quad) are predicated off.
-template <int U, typename Add>
+// adjacency (one 16-byte load for four entries). A quad holds at least one
+// entry of its segment, so it lies inside the adjacency's 16-byte-padded
+// allocation. Threads get equal quad counts, so a team's lanes run the same
+// number of steps. Entries outside a segment (in its first and last quad)
+// are skipped: with BF, add(entry, vb, sign bit of the anchor's edge) is
+// called for every entry with vb = 1 inside the segment and 0 outside
+// (branch-free; add must then change nothing), otherwise add(entry, sign)
+// is called for the entries inside only. Which form compiles to fewer
+// instructions depends on the class (measured per class).
+template <int U, bool BF, typename Add>
 __device__ __forceinline__ void quad_range(const uint4 *__restrict__ oadj4, const QSeg *seg,
                                            uint32_t NZ, uint32_t a, uint32_t b, Add &&add) {
     if (a >= b) return;
@@ -187,10 +190,17 @@ __device__ __forceinline__ void quad_range(const uint4 *__restrict__ oadj4, cons
             v[u] = hi4[u] ? __ldg(oadj4 + qa[u]) : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
         for (int u = 0; u < U; u++) {
-            if (lo[u] == 0u) add(v[u].x, sw[u]);
-            if (lo[u] <= 1u && hi4[u] >= 2u) add(v[u].y, sw[u]);
-            if (lo[u] <= 2u && hi4[u] >= 3u) add(v[u].z, sw[u]);
-            if (hi4[u] == 4u) add(v[u].w, sw[u]);
+            if constexpr (BF) {
+                add(v[u].x, (uint32_t)(lo[u] == 0u), sw[u]);
+                add(v[u].y, (uint32_t)(lo[u] <= 1u && hi4[u] >= 2u), sw[u]);
+                add(v[u].z, (uint32_t)(lo[u] <= 2u && hi4[u] >= 3u), sw[u]);
+                add(v[u].w, (uint32_t)(hi4[u] == 4u), sw[u]);
+            } else {
+                if (lo[u] == 0u) add(v[u].x, sw[u]);
+                if (lo[u] <= 1u && hi4[u] >= 2u) add(v[u].y, sw[u]);
+                if (lo[u] <= 2u && hi4[u] >= 3u) add(v[u].z, sw[u]);
+                if (hi4[u] == 4u) add(v[u].w, sw[u]);
+            }
         }
     }
 }
@@ -198,14 +208,14 @@ __device__ __forceinline__ void quad_range(const uint4 *__restrict__ oadj4, cons
 // the same over [a, b) in sub-ranges of at most `span` quads, calling
 // flush() after each (callers whose per-thread running sums must be
 // bounded between flushes)
-template <int U, typename Add, typename Flush>
+template <int U, bool BF, typename Add, typename Flush>
 __device__ __forceinline__ void quad_range_flushed(const uint4 *__restrict__ oadj4,
                                                    const QSeg *seg, uint32_t NZ, uint32_t a,
                                                    uint32_t b, uint32_t span, Add &&add,
                                                    Flush &&flush) {
     for (uint32_t s = a; s < b;) {
         const uint32_t e = b - s > span ? s + span : b;
-        quad_range<U>(oadj4, seg, NZ, s, e, add);
+        quad_range<U, BF>(oadj4, seg, NZ, s, e, add);
         flush();
         s = e;
     }
@@ -213,9 +223,10 @@ __device__ __forceinline__ void quad_range_flushed(const uint4 *__restrict__ oad
 
 // One chunk of up to TS middles (j = this thread's middle, valid below m1):
 // reads each middle's descriptor, takes its segment, and compacts the
-// non-empty segments into sm.seg with their quad prefix. T = the chunk's
-// quads, NZ = its segments (the same in every thread of the team).
-template <int TS, typename Seg>
+// non-empty segments into sm.seg with their prefix in quads (QUADS) or in
+// wedges. T = the chunk's quads or wedges, NZ = its segments (the same in
+// every thread of the team).
+template <int TS, bool QUADS = true, typename Seg>
 __device__ __forceinline__ void chunk_scan(const uint4 *__restrict__ smd, int64_t rb, uint32_t j,
                                            uint32_t m1, WalkSmem<TS> &sm, int t, Seg &&seg,
                                            uint32_t &T, uint32_t &NZ) {
@@ -227,7 +238,7 @@ __device__ __forceinline__ void chunk_scan(const uint4 *__restrict__ smd, int64_
         sw = d.w;
         seg(d, st, len);
     }
-    const uint32_t nq = quads_of((uint32_t)st, len);
+    const uint32_t nq = QUADS ? quads_of((uint32_t)st, len) : len;
     uint32_t x = warp_incl_scan(nq);
     const unsigned nzb = __ballot_sync(FULL, nq > 0);
     uint32_t nzi = __popc(nzb & ((2u << lane) - 1u));
@@ -261,11 +272,10 @@ __device__ __forceinline__ void chunk_scan(const uint4 *__restrict__ smd, int64_
 // team of TS threads (t = thread index in the team): per chunk of TS
 // middles, a chunk scan and then each thread's equal share of the chunk's
 // quads. seg(md, st, len) picks the segment [st, st+len) of a middle's row
-// from its descriptor; add(entry, sign bit of the anchor's edge to the
-// middle) is called once per wedge (entry = endpoint side rank << 1 | sign
-// of the middle-endpoint edge). flush() follows every `span` quads of a
-// thread.
-template <int TS, int U, typename Seg, typename Add, typename Flush>
+// from its descriptor; add is called as in quad_range, once per wedge
+// (entry = endpoint side rank << 1 | sign of the middle-endpoint edge).
+// flush() follows every `span` quads of a thread.
+template <int TS, int U, bool BF, typename Seg, typename Add, typename Flush>
 __device__ __forceinline__ void quad_walk(const uint4 *__restrict__ smd,
                                           const uint32_t *__restrict__ oadj, int64_t rb,
                                           uint32_t m0, uint32_t m1, WalkSmem<TS> &sm, int t,
@@ -274,8 +284,67 @@ __device__ __forceinline__ void quad_walk(const uint4 *__restrict__ smd,
     for (uint32_t mc = m0; mc < m1; mc += TS) {
         uint32_t T, NZ;
         chunk_scan<TS>(smd, rb, mc + (uint32_t)t, m1, sm, t, seg, T, NZ);
-        quad_range_flushed<U>(oadj4, sm.seg, NZ, share<TS>(T, t), share<TS>(T, t + 1), span, add,
-                              flush);
+        quad_range_flushed<U, BF>(oadj4, sm.seg, NZ, share<TS>(T, t), share<TS>(T, t + 1), span,
+                                  add, flush);
+        team_sync<TS>();
+    }
+}
+
+// Wedge walker, per thread: the wedges [a, b) of a compacted chunk whose
+// prefix is in wedges, U loads in flight per step, one(entry, sign bit of
+// the anchor's edge) per wedge. For segment families whose per-wedge work
+// is a loop (hash probes): one call site, no predicated quad entries.
+template <int U, typename One>
+__device__ __forceinline__ void wedge_range(const uint32_t *__restrict__ oadj, const QSeg *seg,
+                                            uint32_t NZ, uint32_t a, uint32_t b, One &&one) {
+    if (a >= b) return;
+    uint32_t k = 0, hi = NZ;  // segment holding wedge a
+    while (k < hi) {
+        const uint32_t mid = (k + hi) >> 1;
+        if (seg[mid].incl <= a) k = mid + 1; else hi = mid;
+    }
+    QSeg d = seg[k];
+    uint32_t p = d.st + (a - (d.excl_sw & EXMASK));
+    for (uint32_t i = a; i < b; i += U) {
+        uint32_t pa[U], sq[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            pa[u] = 0xffffffffu;
+            sq[u] = 0u;
+            if (i + u < b) {
+                if (p == d.en) {
+                    k++;
+                    d = seg[k];
+                    p = d.st;
+                }
+                pa[u] = p++;
+                sq[u] = d.excl_sw >> 31;
+            }
+        }
+        uint32_t xv[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) xv[u] = pa[u] != 0xffffffffu ? __ldg(oadj + pa[u]) : 0u;
+        for (int u = 0; u < U; u++)
+            if (pa[u] != 0xffffffffu) one(xv[u], sq[u]);
+    }
+}
+
+// quad_walk's counterpart over wedges (wedge_range per thread)
+template <int TS, int U, typename Seg, typename One, typename Flush>
+__device__ __forceinline__ void wedge_walk(const uint4 *__restrict__ smd,
+                                           const uint32_t *__restrict__ oadj, int64_t rb,
+                                           uint32_t m0, uint32_t m1, WalkSmem<TS> &sm, int t,
+                                           uint32_t span, Seg &&seg, One &&one, Flush &&flush) {
+    for (uint32_t mc = m0; mc < m1; mc += TS) {
+        uint32_t T, NZ;
+        chunk_scan<TS, false>(smd, rb, mc + (uint32_t)t, m1, sm, t, seg, T, NZ);
+        const uint32_t a = share<TS>(T, t), b = share<TS>(T, t + 1);
+        for (uint32_t s0 = a; s0 < b;) {
+            const uint32_t e = b - s0 > span ? s0 + span : b;
+            wedge_range<U>(oadj, sm.seg, NZ, s0, e, one);
+            flush();
+            s0 = e;
+        }
         team_sync<TS>();
     }
 }
@@ -610,8 +679,8 @@ __global__ void __launch_bounds__(WARP_THREADS, 4) k_warp(DevGraph G) {
 }
 
 // ------------------------------------------------- team and CTA-hash classes
-// Per CTA: the hub window as 32-bit counters (S | A << 16), a hash for
-// endpoints below the window, and the walker's chunk.
+// Per CTA: the hub window as 32-bit counters (S | A << 16) at rank mod
+// HUB_WINDOW, a hash for endpoints below the window, and the walker's chunk.
 template <int TS, uint32_t HCAP>
 struct alignas(16) HybSmem {
     uint32_t win[HUB_WINDOW];             // hub window counters
@@ -659,24 +728,26 @@ __device__ __forceinline__ void hybrid_anchor(const DevGraph &G, HybSmem<TS, HCA
         hb = ht = own = other = 0;
     };
     if (W > wnh) {  // endpoints inside the hub window
-        quad_walk<TS, QU>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, SUM_SPAN, HubSeg{},
-                          [&](uint32_t x, uint32_t sw) {
-                              const uint32_t asym = (x ^ sw) & 1u;
-                              const uint32_t idx = (x >> 1) - wb;
-                              if (idx >= HUB_WINDOW) { set_error(err, E_INTERNAL); return; }
-                              const uint32_t old =
-                                  atomicAdd(&sm.win[idx], asym ? INC_ASYM : INC_SYM);
-                              hb = __dp2a_lo(old, 1u << (asym << 3), hb);
-                              ht = __dp2a_lo(old, 0x0101u, ht);
-                          },
-                          flush);
+        // counter of a rank at rank mod HUB_WINDOW (one to one on the
+        // window's consecutive ranks); an entry outside its segment (vb = 0)
+        // adds 0 and picks nothing
+        quad_walk<TS, QU, true>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, SUM_SPAN, HubSeg{},
+                                [&](uint32_t x, uint32_t vb, uint32_t sw) {
+                                    const uint32_t asym = (x ^ sw) & 1u;
+                                    const uint32_t old =
+                                        atomicAdd(&sm.win[(x >> 1) & (HUB_WINDOW - 1)],
+                                                  vb << (asym << 4));
+                                    hb = __dp2a_lo(old, vb << (asym << 3), hb);
+                                    ht = __dp2a_lo(old, vb * 0x0101u, ht);
+                                },
+                                flush);
     }
     uint32_t cap = 0;
     if (wnh > 0) {  // endpoints below the window
         uint32_t shift;
         table_geometry(wnh < above_nh ? wnh : above_nh, 32, HCAP, cap, shift);
         const uint32_t mask = cap - 1;
-        quad_walk<TS, QU>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, SUM_SPAN, LowSeg{},
+        wedge_walk<TS, 2>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, 4 * SUM_SPAN, LowSeg{},
                           [&](uint32_t x, uint32_t sw) {
                               hash_wedge32(sm.tab, shift, mask, x, sw, err, own, other);
                           },
@@ -762,7 +833,7 @@ __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, cons
             b32 = t32 = 0;
         };
         if (windows) {
-            quad_walk<DENSE_THREADS, DENSE_U>(
+            quad_walk<DENSE_THREADS, DENSE_U, false>(
                 A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t, SUM_SPAN,
                 [&](const uint4 &d, long long &st, uint32_t &l) {
                     const long long s0 = lower_bound_u32(A.oadj, d.x, d.z, e0 << 1);
@@ -771,8 +842,8 @@ __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, cons
                 },
                 add, flush);
         } else {
-            quad_walk<DENSE_THREADS, DENSE_U>(A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t,
-                                              SUM_SPAN, FullSeg{}, add, flush);
+            quad_walk<DENSE_THREADS, DENSE_U, false>(A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t,
+                                                     SUM_SPAN, FullSeg{}, add, flush);
         }
         if (J.group != NO_GROUP) {
             // merge this part's counts into the group's global counters; a
