@@ -290,6 +290,84 @@ __device__ __forceinline__ void quad_walk(const uint4 *__restrict__ smd,
     }
 }
 
+// Team walker in coalesced rounds. After the chunk scan each warp of the
+// team takes an equal part [A, B) of the chunk's quads and walks it in
+// rounds of 32 consecutive quads, lane l taking quad r + l (a round reads
+// up to 512 consecutive bytes of a segment). The segments that start inside
+// a round are found from the next 32 compacted segments, one per lane, whose
+// starts form a bitmask (one warp OR-reduction); a lane's segment is the
+// last one starting at or before its quad. Each round's quads are loaded one
+// round ahead. add is called as in quad_range (BF chooses the form);
+// flush() follows every `span` rounds of a warp and the end of its part.
+template <int TS, bool BF, typename Seg, typename Add, typename Flush>
+__device__ __forceinline__ void team_rounds(const uint4 *__restrict__ smd,
+                                            const uint32_t *__restrict__ oadj, int64_t rb,
+                                            uint32_t m0, uint32_t m1, WalkSmem<TS> &sm, int t,
+                                            uint32_t span, Seg &&seg, Add &&add, Flush &&flush) {
+    constexpr uint32_t NW = TS / 32;
+    const uint4 *oadj4 = reinterpret_cast<const uint4 *>(oadj);
+    const uint32_t lane = (uint32_t)t & 31u, w = (uint32_t)t >> 5;
+    const unsigned upto = (2u << lane) - 1u;
+    for (uint32_t mc = m0; mc < m1; mc += TS) {
+        uint32_t T, NZ;
+        chunk_scan<TS>(smd, rb, mc + (uint32_t)t, m1, sm, t, seg, T, NZ);
+        const uint32_t A = share<NW>(T, w), B = share<NW>(T, w + 1);
+        if (A < B) {
+            uint32_t kb = 0, hi = NZ;  // segment holding quad A
+            while (kb < hi) {
+                const uint32_t mid = (kb + hi) >> 1;
+                if (sm.seg[mid].incl <= A) kb = mid + 1; else hi = mid;
+            }
+            kb++;  // next segment to start
+            // lane's quad of the round at r: loads it, sets vm (0 past B) and sw
+            auto locate = [&](uint32_t r, uint4 &v, uint32_t &vm, uint32_t &swq) {
+                const uint32_t c = kb + lane;
+                const uint32_t s = c < NZ ? (sm.seg[c].excl_sw & EXMASK) - r : 32u;
+                const unsigned M = __reduce_or_sync(FULL, s < 32u ? 1u << s : 0u);
+                const uint32_t k = kb - 1u + __popc(M & upto);
+                kb += __popc(M);
+                const uint32_t q = r + lane;
+                vm = 0u;
+                if (q < B) {
+                    const QSeg d = sm.seg[k];
+                    const uint32_t qq = (d.st >> 2) + (q - (d.excl_sw & EXMASK));
+                    const uint32_t w0 = qq << 2;
+                    const uint32_t lo = d.st > w0 ? d.st - w0 : 0u;
+                    const uint32_t hq = d.en - w0 < 4u ? d.en - w0 : 4u;
+                    vm = (0xfu >> (4u - hq)) & (0xfu << lo);
+                    swq = d.excl_sw >> 31;
+                    v = __ldg(oadj4 + qq);
+                }
+            };
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            uint32_t vm = 0u, swq = 0u, rounds = 0u;
+            locate(A, v, vm, swq);
+            for (uint32_t r = A; r < B; r += 32) {
+                uint4 vn = make_uint4(0u, 0u, 0u, 0u);
+                uint32_t vmn = 0u, swn = 0u;
+                if (r + 32 < B) locate(r + 32, vn, vmn, swn);
+                if constexpr (BF) {
+                    add(v.x, vm & 1u, swq);
+                    add(v.y, (vm >> 1) & 1u, swq);
+                    add(v.z, (vm >> 2) & 1u, swq);
+                    add(v.w, vm >> 3, swq);
+                } else {
+                    if (vm & 1u) add(v.x, swq);
+                    if (vm & 2u) add(v.y, swq);
+                    if (vm & 4u) add(v.z, swq);
+                    if (vm & 8u) add(v.w, swq);
+                }
+                v = vn;
+                vm = vmn;
+                swq = swn;
+                if (++rounds == span) { flush(); rounds = 0u; }
+            }
+            flush();
+        }
+        team_sync<TS>();
+    }
+}
+
 // Wedge walker, per thread: the wedges [a, b) of a compacted chunk whose
 // prefix is in wedges, U loads in flight per step, one(entry, sign bit of
 // the anchor's edge) per wedge. For segment families whose per-wedge work
@@ -718,9 +796,11 @@ __device__ __forceinline__ void hybrid_anchor(const DevGraph &G, HybSmem<TS, HCA
     const uint32_t wb = ns > (int64_t)HUB_WINDOW ? (uint32_t)(ns - HUB_WINDOW) : 0u;
     const uint64_t W = A.W, wnh = A.wnh;
     const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
-    constexpr int QU = TS == TEAM_THREADS ? 1 : 2;  // quads per walker step
     // hub walk: hb = the wedges' own previous tallies, ht = both previous
     // tallies; hash walk: own and other as in hash_wedge32
+    // quads per thread step (per-thread quad shares measured faster than
+    // warp rounds for these classes)
+    constexpr int QU = TS == TEAM_THREADS ? 1 : 2;
     uint32_t hb = 0, ht = 0, own = 0, other = 0;
     auto flush = [&]() {
         bal += (unsigned long long)hb + own;
@@ -789,8 +869,6 @@ __global__ void __launch_bounds__(CTAH_THREADS) k_ctah(DevGraph G) {
 }
 
 // ------------------------------------------------------------ dense class
-constexpr int DENSE_U = 2;  // quads per walker step
-
 struct alignas(16) DenseSmem {
     uint32_t cnt[DENSE_CAP];
     WalkSmem<DENSE_THREADS> walk;
@@ -802,7 +880,6 @@ struct alignas(16) DenseSmem {
 __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, const DenseJob &J,
                                           unsigned long long &bal, unsigned long long &tot) {
     const int t = threadIdx.x;
-    CountScratch *sc = G.scratch;
     const bool sv = J.anchor & 1u;
     const SideCSR &S = sv ? G.side[1] : G.side[0];
     AnchorRec rec;
@@ -817,15 +894,17 @@ __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, cons
         const uint32_t len = e1 - e0;
         for (uint32_t i = t; i < len; i += DENSE_THREADS) sm.cnt[i] = 0;
         __syncthreads();
-        // b32: the wedges' own previous tallies; t32: both previous tallies
+        // b32: the wedges' own previous tallies; t32: both previous tallies.
+        // The segments hold only endpoints in [e0, e1): the mask keeps a
+        // counter index inside the array whatever the entry; an entry
+        // outside its segment (vb = 0) adds 0 and picks nothing.
         uint32_t b32 = 0, t32 = 0;
-        auto add = [&](uint32_t x, uint32_t sw) {
+        auto add = [&](uint32_t x, uint32_t vb, uint32_t sw) {
             const uint32_t asym = (x ^ sw) & 1u;
-            const uint32_t idx = (x >> 1) - e0;
-            if (idx >= len) { set_error(&sc->err, E_INTERNAL); return; }
-            const uint32_t old = atomicAdd(&sm.cnt[idx], asym ? INC_ASYM : INC_SYM);
-            b32 = __dp2a_lo(old, 1u << (asym << 3), b32);
-            t32 = __dp2a_lo(old, 0x0101u, t32);
+            const uint32_t idx = ((x >> 1) - e0) & (DENSE_CAP - 1);
+            const uint32_t old = atomicAdd(&sm.cnt[idx], vb << (asym << 4));
+            b32 = __dp2a_lo(old, vb << (asym << 3), b32);
+            t32 = __dp2a_lo(old, vb * 0x0101u, t32);
         };
         auto flush = [&]() {
             bal += b32;
@@ -833,7 +912,7 @@ __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, cons
             b32 = t32 = 0;
         };
         if (windows) {
-            quad_walk<DENSE_THREADS, DENSE_U, false>(
+            team_rounds<DENSE_THREADS, true>(
                 A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t, SUM_SPAN,
                 [&](const uint4 &d, long long &st, uint32_t &l) {
                     const long long s0 = lower_bound_u32(A.oadj, d.x, d.z, e0 << 1);
@@ -842,8 +921,8 @@ __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, cons
                 },
                 add, flush);
         } else {
-            quad_walk<DENSE_THREADS, DENSE_U, false>(A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t,
-                                                     SUM_SPAN, FullSeg{}, add, flush);
+            team_rounds<DENSE_THREADS, true>(A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t,
+                                             SUM_SPAN, FullSeg{}, add, flush);
         }
         if (J.group != NO_GROUP) {
             // merge this part's counts into the group's global counters; a
