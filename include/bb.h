@@ -21,8 +21,10 @@
  *   rowptr[nU] = nE. col: int32[nE], V ids in [0, nV); a row may be in any
  *   order but must not repeat a V id (E is a set). signs: int8[nE], each +1
  *   or -1, aligned with col.
- * Limits: nU + nV < 2^31, every vertex degree <= 65535 (counts per vertex
- *   pair are held in 16-bit fields), nE < 2^32.
+ * Limits: nU + nV < 2^31, nE < 2^32 - 1 (so every degree and every
+ *   per-pair wedge count is below 2^32). Counts per vertex pair are held in
+ *   16-bit fields for anchors of degree <= 65535 and in 32-bit fields for
+ *   the few of higher degree.
  *
  * Errors: every call returns a bb_status. On error no output is written and
  * bb_last_error() (thread-local) describes the failure. Device-side input
@@ -191,13 +193,15 @@ BB_API void bb_graph_free(bb_graph *g);
  * carved out of one device array of BB_NOALLOC_SCRATCH_BYTES that the
  * library reserves on every GPU it is loaded on until the process exits.
  * A graph whose workspace does not fit is rejected with BB_ERR_TOO_LARGE
- * (roughly 1M edges fit). The first call on a device looks the array's
- * device address up (a one-time set-up); make that first call before any
- * stream capture. Work is queued on `stream` (NULL = the legacy default
- * stream) and the call returns when it is done. All calls share the array
- * and it keeps the last call's contents: the call clears what must start
- * at zero itself, and two calls whose work overlaps on the GPU (another
- * thread, another stream) race and give wrong results. */
+ * (roughly 1M edges fit). Every call looks the array's device address up
+ * on the current device; the first call on a device may load the
+ * library's device code, so make it before any stream capture. Work is
+ * queued on `stream` (NULL = the legacy default stream) and the call
+ * returns when it is done; its waits honour bb_set_wait_timeout
+ * (BB_ERR_TIMEOUT). All calls share the array and it keeps the last call's
+ * contents: the call clears what must start at zero itself, and two calls
+ * whose work overlaps on the GPU (another thread, another stream) race and
+ * give wrong results. */
 #define BB_NOALLOC_SCRATCH_BYTES (128u << 20)
 BB_API bb_status bb_count_csr_device_noalloc(const bb_csr *csr_dev, const int8_t *signs_dev,
                                              void *stream, int64_t *balanced, int64_t *total,
@@ -344,9 +348,21 @@ BB_API bb_status bb_ctx_serve_stats(bb_ctx *ctx, bb_serve_stats *out);
 /* Process-wide limit, in seconds, on how long a blocking call waits for its
  * device work (default 600). When it runs out the call returns
  * BB_ERR_TIMEOUT and its outputs are untouched; the work it queued still
- * runs, and later calls on the same context's stream run after it.
+ * runs, and later calls on the same context's stream run after it (their
+ * waits, including the input validation, honour the same limit). The
+ * release calls (bb_ctx_destroy, bb_graph_free, bb_batch_free) wait for the
+ * object's queued work within the limit too; when it runs out they return
+ * without freeing the object's device memory (it stays allocated, rather
+ * than being freed under running work).
  * BB_ERR_INVALID_ARG unless 0 < seconds <= 86400. */
 BB_API bb_status bb_set_wait_timeout(double seconds);
+
+/* Failure injection for tests (no paper counterpart): the nth device
+ * allocation the library makes from now on (workspaces, resident graphs,
+ * batches, the serving arena; nth >= 1) fails once with BB_ERR_OOM as if
+ * cudaMalloc had failed, so that callers can check how they recover.
+ * 0 disarms it; BB_ERR_INVALID_ARG for nth < 0. Process-wide. */
+BB_API bb_status bb_set_alloc_failure(int64_t nth);
 
 /* Measurement probe: shared-memory atomic adds per second on `device`, each
  * a u32 atomicAdd whose previous value is used (the wedge kernels' inner

@@ -139,6 +139,7 @@ def lib() -> ctypes.CDLL:
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
             "bb_ctx_serve_stats": (S, [_VP, ctypes.POINTER(_ServeStats)]),
             "bb_set_wait_timeout": (S, [ctypes.c_double]),
+            "bb_set_alloc_failure": (S, [ctypes.c_int64]),
             "bb_probe_shared_atomics": (S, [ctypes.c_int, ctypes.c_uint32,
                                             ctypes.POINTER(ctypes.c_double)]),
             "bb_graph_bytes": (S, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
@@ -493,6 +494,12 @@ def request_bytes(g) -> int:
 def set_wait_timeout(seconds: float):
     """Limit on how long blocking calls wait for device work (process-wide)."""
     _check(lib().bb_set_wait_timeout(seconds))
+
+
+def set_alloc_failure(nth: int):
+    """Makes the nth device allocation of the library from now on fail once
+    with BB_ERR_OOM (``bb_set_alloc_failure``; 0 disarms). For tests."""
+    _check(lib().bb_set_alloc_failure(nth))
 
 
 def probe_shared_atomics(device: int = 0, window: int = 2048) -> float:

@@ -69,6 +69,23 @@ bb_status bb::wait_bounded(cudaStream_t s, const char *what) {
     return BB_OK;
 }
 
+// The same bound without creating anything (no event): polls the stream
+// until it is idle. For paths that must not create CUDA objects.
+bb_status bb::wait_stream_bounded(cudaStream_t s, const char *what) {
+    auto t0 = std::chrono::steady_clock::now();
+    int spins = 0;
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery(s);
+        if (e == cudaSuccess) return BB_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(e, what);
+        const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        const double limit = g_timeout_s.load(std::memory_order_relaxed);
+        if (dt > limit)
+            return fail(BB_ERR_TIMEOUT, "%s: device work did not finish within %g s", what, limit);
+        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
 bb_status bb::check_csr(const bb_csr *csr, const int8_t *signs) {
     if (!csr) return fail(BB_ERR_INVALID_ARG, "csr is NULL");
     if (csr->nU < 0 || csr->nV < 0 || csr->nE < 0)
@@ -78,7 +95,7 @@ bb_status bb::check_csr(const bb_csr *csr, const int8_t *signs) {
         return fail(BB_ERR_TOO_LARGE, "nU + nV = %lld must be below 2^31",
                     (long long)(csr->nU + csr->nV));
     if (csr->nE >= ((int64_t)1 << 32) - 1)
-        return fail(BB_ERR_TOO_LARGE, "nE = %lld must be below 2^32", (long long)csr->nE);
+        return fail(BB_ERR_TOO_LARGE, "nE = %lld must be below 2^32 - 1", (long long)csr->nE);
     if (csr->nU == 0 && csr->nE != 0)
         return fail(BB_ERR_INVALID_ARG, "nE must be 0 when nU is 0");
     if (!csr->rowptr) return fail(BB_ERR_INVALID_ARG, "rowptr is NULL");
@@ -92,7 +109,6 @@ bb_status bb::map_build_error(uint32_t e) {
     if (e & E_COL) return fail(BB_ERR_INVALID_ARG, "a column id is outside [0, nV)");
     if (e & E_SIGN) return fail(BB_ERR_INVALID_ARG, "a sign is not +1 or -1");
     if (e & E_DUP) return fail(BB_ERR_INVALID_ARG, "an edge is listed twice");
-    if (e & E_DEGREE) return fail(BB_ERR_TOO_LARGE, "a vertex degree exceeds %u", MAX_DEGREE);
     if (e) return fail(BB_ERR_CUDA, "internal device check failed (0x%x)", e);
     return BB_OK;
 }
@@ -100,11 +116,26 @@ bb_status bb::map_build_error(uint32_t e) {
 // lets other translation units of the library set bb_last_error()
 bb_status bb::report_error(bb_status st, const char *msg) { return fail(st, "%s", msg); }
 
+namespace {
+// allocations left until the injected failure (0 = none armed)
+std::atomic<int64_t> g_alloc_fail_in{0};
+}
+
 bb_status bb::dev_alloc(bb_ctx *ctx, void **p, size_t bytes, const char *what) {
     if (bytes == 0) bytes = 256;
     if (ctx->used + bytes > ctx->budget)
         return fail(BB_ERR_BUDGET, "%s: %zu bytes would exceed the budget (%llu of %llu used)",
                     what, bytes, (unsigned long long)ctx->used, (unsigned long long)ctx->budget);
+    for (int64_t k = g_alloc_fail_in.load(); k > 0;) {
+        if (g_alloc_fail_in.compare_exchange_weak(k, k - 1)) {
+            if (k == 1) {
+                *p = nullptr;
+                return fail(BB_ERR_OOM, "%s: cudaMalloc(%zu) failed (injected failure)", what,
+                            bytes);
+            }
+            break;
+        }
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -133,7 +164,9 @@ namespace {
 // grow-only workspace buffer
 bb_status ensure(bb_ctx *ctx, void **buf, size_t *cap, size_t need, const char *what) {
     if (*cap >= need && *buf) return BB_OK;
-    BB_CUDA(cudaStreamSynchronize(ctx->stream), "workspace sync");
+    // the old buffer may still be in use by queued work
+    bb_status ws = wait_bounded(ctx->stream, "workspace sync");
+    if (ws != BB_OK) return ws;
     dev_free(ctx, *buf, *cap);
     *buf = nullptr;
     *cap = 0;
@@ -203,9 +236,11 @@ bb_status finish_count(bb_ctx *ctx, const DevGraph &g, cudaStream_t s, int64_t *
 // when the call is not a repeat or the stream cannot be captured; the
 // caller launches directly then.
 bool replay_step(bb_ctx *ctx, DevGraph &g, const bb_csr *csr, const int8_t *signs) {
-    const void *key[9] = {(const void *)(intptr_t)csr->nU, (const void *)(intptr_t)csr->nV,
-                          (const void *)(intptr_t)csr->nE, csr->rowptr, csr->col, signs,
-                          ctx->ws_temp, ctx->ws_graph, (const void *)(intptr_t)ctx->timing};
+    // the degree sort's key width depends on the inputs' largest degree
+    const void *key[10] = {(const void *)(intptr_t)csr->nU, (const void *)(intptr_t)csr->nV,
+                           (const void *)(intptr_t)csr->nE, csr->rowptr, csr->col, signs,
+                           ctx->ws_temp, ctx->ws_graph, (const void *)(intptr_t)ctx->timing,
+                           (const void *)(intptr_t)g.deg_bits};
     static_assert(sizeof(key) == sizeof(ctx->step_key), "step key size");
     static_assert(sizeof(key) == sizeof(ctx->step_last), "step key size");
     cudaStream_t s = ctx->stream;
@@ -276,12 +311,15 @@ bb_status count_device(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int6
         ctx->layout_key[0] = nU; ctx->layout_key[1] = nV; ctx->layout_key[2] = nE;
     }
     if (ctx->timing) BB_CUDA(cudaEventRecord(ctx->ev[0], s), "event");
-    uint32_t verr;
+    uint32_t verr = 0;
     {
         Range r("validate");
-        verr = build_validate(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s, in);
+        st = build_validate(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s, in, &verr);
     }
-    BB_CUDA(cudaGetLastError(), "validation kernels");
+    if (st != BB_OK) {
+        ctx->layout_key[0] = -1;
+        return st;
+    }
     if (verr) {
         ctx->layout_key[0] = -1;  // leave the merge buffers to be re-zeroed
         return map_build_error(verr);
@@ -354,7 +392,12 @@ void bb_ctx_destroy(bb_ctx *ctx) {
     if (!ctx) return;
     engine_stop(ctx);
     cudaSetDevice(ctx->device);
-    cudaStreamSynchronize(ctx->stream);
+    if (wait_bounded(ctx->stream, "context destroy") != BB_OK) {
+        // work still running after the wait limit: leave its memory and
+        // streams in place (leaked) rather than hang the caller
+        delete ctx;
+        return;
+    }
     if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
     dev_free(ctx, ctx->ws_graph, ctx->ws_graph_cap);
     dev_free(ctx, ctx->ws_temp, ctx->ws_temp_cap);
@@ -391,6 +434,12 @@ bb_status bb_set_wait_timeout(double seconds) {
     if (!(seconds > 0.0 && seconds <= 86400.0))
         return fail(BB_ERR_INVALID_ARG, "timeout %g s outside (0, 86400]", seconds);
     g_timeout_s.store(seconds, std::memory_order_relaxed);
+    return BB_OK;
+}
+
+bb_status bb_set_alloc_failure(int64_t nth) {
+    if (nth < 0) return fail(BB_ERR_INVALID_ARG, "nth must be >= 0");
+    g_alloc_fail_in.store(nth);
     return BB_OK;
 }
 
@@ -515,7 +564,9 @@ static bb_status upload_impl(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs
     G->g.rowptr = rp; G->g.col = cl; G->g.sign = sg;
     cudaMemsetAsync(G->g.gpart, 0, (size_t)G->g.gpart_cap * 4, s);
     cudaMemsetAsync(G->g.gdone, 0, MAX_SPLIT_JOBS * 4, s);
-    uint32_t verr = build_graph(G->g, rp, cl, sg, ctx->ws_temp, s, &ctx->aux);
+    uint32_t verr = 0;
+    st = build_graph(G->g, rp, cl, sg, ctx->ws_temp, s, &ctx->aux, &verr);
+    if (st != BB_OK) { bb_graph_free(G); return st; }
     if (verr) { bb_graph_free(G); return map_build_error(verr); }
     e = cudaMemcpyAsync(&ctx->h_res->build_err, G->g.err, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&ctx->h_res->wedges, G->g.wedges, 8, cudaMemcpyDeviceToHost, s);
@@ -787,7 +838,10 @@ void bb_graph_free(bb_graph *G) {
     if (!G) return;
     bb_ctx *ctx = G->ctx;
     cudaSetDevice(ctx->device);
-    cudaStreamSynchronize(ctx->stream);
+    if (wait_bounded(ctx->stream, "graph free") != BB_OK) {
+        delete G;  // its device memory may still be read: leaked, not freed
+        return;
+    }
     dev_free(ctx, G->mem, G->bytes);
     dev_free(ctx, G->raw, G->raw_bytes);
     delete G;

@@ -11,6 +11,7 @@
 // memory), and pass 3 walks every pair of every group. The work is the
 // number of butterflies instead of the number of wedges.
 #include <algorithm>
+#include <mutex>
 
 #include "graph.cuh"
 
@@ -216,23 +217,28 @@ __global__ void k_max_work(SideCSR S, unsigned long long *out) {
     if (lane_id() == 0 && m) atomicMax(out, m);
 }
 
-int g_base_blocks = 0, g_base_device = -1;
+// grid of k_base, once per device (any thread may count on any device)
+constexpr int MAX_DEVICES = 64;
+int g_base_blocks[MAX_DEVICES];
+std::once_flag g_base_once[MAX_DEVICES];
 
 }  // namespace
 
 int base_blocks() {
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (g_base_device != dev) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    std::call_once(g_base_once[dev], [dev]() {
         cudaDeviceProp prop;
         cudaGetDeviceProperties(&prop, dev);
         cudaFuncSetAttribute(k_base, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BaseSmem));
         int b = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_base, BASE_THREADS, sizeof(BaseSmem));
-        g_base_blocks = std::max(1, b) * prop.multiProcessorCount;
-        g_base_device = dev;
-    }
-    return g_base_blocks;
+        g_base_blocks[dev] = std::max(1, b) * prop.multiProcessorCount;
+    });
+    return g_base_blocks[dev];
 }
 
 void launch_max_work(const DevGraph &g, unsigned long long *out_dev, cudaStream_t s) {

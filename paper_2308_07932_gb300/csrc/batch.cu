@@ -329,10 +329,18 @@ void bb_batch_free(bb_batch *b) {
     if (!b) return;
     bb_ctx *ctx = b->ctx;
     cudaSetDevice(ctx->device);
-    cudaStreamSynchronize(ctx->stream);
+    // work still running after the wait limit: its memory is left (leaked)
+    // rather than freed under it
+    bool idle = wait_bounded(ctx->stream, "batch free") == BB_OK;
+    for (int k = 0; k < NCLS - 1 && idle; k++)
+        if (b->side[k]) idle = wait_bounded(b->side[k], "batch free") == BB_OK;
+    if (!idle) {
+        delete b;
+        return;
+    }
     drop_exec(b);
     for (int k = 0; k < NCLS - 1; k++)
-        if (b->side[k]) { cudaStreamSynchronize(b->side[k]); cudaStreamDestroy(b->side[k]); }
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
     for (int k = 0; k < NCLS; k++)
         if (b->ev[k]) cudaEventDestroy(b->ev[k]);
     if (b->h_out) cudaFreeHost(b->h_out);

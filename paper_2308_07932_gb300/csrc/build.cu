@@ -31,19 +31,29 @@ inline unsigned grid_for(int64_t n, int threads, int64_t cap = 1 << 20) {
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // ------------------------------------------------------------ 1. validate
+// largest of the warp's values into *maxdeg (all lanes of the warp call it)
+__device__ __forceinline__ void warp_max_to(uint32_t v, uint32_t *maxdeg) {
+    v = __reduce_max_sync(FULL, v);
+    if (lane_id() == 0 && v) atomicMax(maxdeg, v);
+}
+
+// rows: rowptr monotone within [0, nE]; U degrees (a degree fits 32 bits
+// because nE < 2^32) and their maximum
 __global__ void k_validate_rows(const int64_t *rowptr, int64_t nU, int64_t nE, uint32_t *degU,
-                                uint32_t *err) {
+                                uint32_t *err, uint32_t *maxdeg) {
+    uint32_t mx = 0;
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nU;
          u += (int64_t)gridDim.x * blockDim.x) {
         int64_t a = rowptr[u], b = rowptr[u + 1];
         uint32_t d = 0;
         if (a < 0 || b < a || b > nE) set_error(err, E_ROWPTR);
-        else if (b - a > (int64_t)MAX_DEGREE) { set_error(err, E_DEGREE); d = 0; }
         else d = (uint32_t)(b - a);
         degU[u] = d;
+        mx = d > mx ? d : mx;
         if (u == 0 && a != 0) set_error(err, E_ROWPTR);
         if (u == nU - 1 && b != nE) set_error(err, E_ROWPTR);
     }
+    warp_max_to(mx, maxdeg);
 }
 
 __global__ void k_validate_edges(const int32_t *col, const int8_t *sign, int64_t nE, int64_t nV,
@@ -58,10 +68,13 @@ __global__ void k_validate_edges(const int32_t *col, const int8_t *sign, int64_t
     }
 }
 
-__global__ void k_check_degree(const uint32_t *deg, int64_t n, uint32_t *err) {
+// largest V degree
+__global__ void k_max_degree(const uint32_t *deg, int64_t n, uint32_t *maxdeg) {
+    uint32_t mx = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        if (deg[i] > MAX_DEGREE) set_error(err, E_DEGREE);
+        mx = deg[i] > mx ? deg[i] : mx;
+    warp_max_to(mx, maxdeg);
 }
 
 __global__ void k_iota(uint32_t *a, int64_t n) {
@@ -457,7 +470,8 @@ __global__ void k_md_work(SideCSR S, const uint4 *__restrict__ info_o,
 constexpr int NB = 64;  // log2 work buckets
 
 struct ClassifyTemp {
-    uint32_t *meta;         // per anchor: cls | bucket << 2 | parts << 8 (0 = no work)
+    uint32_t *meta;         // per anchor: 1 | cls << 1 | bucket << 3 | parts << 9 | wide << 31
+                            // (0 = no work)
     uint32_t *grp;          // per anchor: split group id
     uint32_t *bucket_cnt;   // [NCLS][NB]
     uint32_t *bucket_base;  // [NCLS][NB]
@@ -489,16 +503,21 @@ __global__ void k_classify(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
             const uint64_t dnh = wnh < above_nh ? wnh : above_nh;
             const uint64_t dh = W < above ? W : above;
             const uint32_t deg = (uint32_t)(S.off[r + 1] - S.off[r]);
+            // an anchor of degree above MAX_DEGREE needs 32-bit tally fields:
+            // a wide dense job; every other class packs them in 16 bits. The
+            // hash classes also keep their wedge prefixes below 2^31.
+            const bool wide = deg > MAX_DEGREE;
             uint32_t cls;
-            if (deg <= WARP_DEG_MAX && W <= WARP_W_MAX &&
+            if (wide) cls = CLS_DENSE;
+            else if (deg <= WARP_DEG_MAX && W <= WARP_W_MAX &&
                 (W <= WARP_SMALL_W ? dh * 5 / 4 < WARP_CAP : dnh * 5 / 4 < WARP_CAP))
                 cls = CLS_WARP;
             else if (W <= TEAM_W_MAX && dnh * 5 / 4 < TEAM_CAP) cls = CLS_TEAM;
             else if (above <= DENSE_CAP) cls = CLS_DENSE;
-            else if (dnh * 2 < CTAH_CAP) cls = CLS_CTAH;
+            else if (dnh * 2 < CTAH_CAP && wnh < (1ull << 31)) cls = CLS_CTAH;
             else cls = CLS_DENSE;  // endpoint range walked in DENSE_CAP windows
             uint32_t parts = 1;
-            if (cls == CLS_DENSE && above <= DENSE_CAP && above > 0) {
+            if (cls == CLS_DENSE && !wide && above <= DENSE_CAP && above > 0) {
                 uint64_t unit = SPLIT_WEDGES > 4 * above ? SPLIT_WEDGES : 4 * above;
                 uint64_t k = W / unit;
                 uint32_t deg = (uint32_t)(S.off[r + 1] - S.off[r]);
@@ -516,7 +535,7 @@ __global__ void k_classify(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
                 }
             }
             uint32_t b = bucket_of(parts > 1 ? W / parts : W);
-            meta = 1u | cls << 1 | b << 3 | parts << 9;
+            meta = 1u | cls << 1 | b << 3 | parts << 9 | (wide ? 1u << 31 : 0u);
             key = cls * NB + b;
             nparts = parts;
             my_w[cls] += W;
@@ -575,7 +594,7 @@ __global__ void k_emit(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
         uint32_t local = 0, key = 0, parts = 0;
         if (meta) {
             uint32_t cls = (meta >> 1) & 3u, b = (meta >> 3) & 63u;
-            parts = meta >> 9;
+            parts = (meta >> 9) & 0xffu;
             key = cls * NB + b;
             local = atomicAdd(&cnt[key], parts);
         }
@@ -602,7 +621,7 @@ __global__ void k_emit(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
                                   : cls == CLS_TEAM ? G.team_list : G.ctah_list;
                 list[pos] = rec;
             } else {
-                uint32_t grp = parts > 1 ? T.grp[r] : NO_GROUP;
+                uint32_t grp = (meta >> 31) ? WIDE_JOB : parts > 1 ? T.grp[r] : NO_GROUP;
                 for (uint32_t i = 0; i < parts; i++) {
                     uint32_t m0 = (uint32_t)((uint64_t)deg * i / parts);
                     uint32_t m1 = (uint32_t)((uint64_t)deg * (i + 1) / parts);
@@ -734,8 +753,8 @@ BuildTemp carve_temp(const DevGraph &g, void *temp_mem) {
 
 }  // namespace
 
-uint32_t build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
-                        void *temp_mem, cudaStream_t s, const StagedInput *in) {
+bb_status build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
+                         void *temp_mem, cudaStream_t s, const StagedInput *in, uint32_t *verr) {
     const int64_t nU = g.nU, nV = g.nV, nE = g.nE;
     BuildTemp bt = carve_temp(g, temp_mem);
     uint32_t **deg_in = bt.deg_in, *cursorV = bt.cursorV;
@@ -750,7 +769,7 @@ uint32_t build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col, 
 
     // 1. validate + degrees
     if (in) cudaStreamWaitEvent(s, in->rowptr_ready, 0);
-    if (nU > 0) k_validate_rows<<<grid_for(nU, BT, 8192), BT, 0, s>>>(rowptr, nU, nE, deg_in[0], g.err); note_launch();
+    if (nU > 0) k_validate_rows<<<grid_for(nU, BT, 8192), BT, 0, s>>>(rowptr, nU, nE, deg_in[0], g.err, g.ctr + CTR_MAXDEG); note_launch();
     if (nE > 0 && in && in->chunks > 0) {
         for (int c = 0; c < in->chunks; c++) {
             const int64_t lo = in->lo[c], n = in->lo[c + 1] - lo;
@@ -763,13 +782,21 @@ uint32_t build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col, 
     } else if (nE > 0) {
         k_validate_edges<<<grid_for(nE, BT, 16384), BT, 0, s>>>(col, sign, nE, nV, deg_in[1], g.err); note_launch();
     }
-    if (nV > 0) k_check_degree<<<grid_for(nV, BT, 8192), BT, 0, s>>>(deg_in[1], nV, g.err); note_launch();
-    uint32_t herr = 0;
-    cudaMemcpyAsync(&herr, g.err, 4, cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    if (herr) return herr;
-
-    return 0;
+    if (nV > 0) k_max_degree<<<grid_for(nV, BT, 8192), BT, 0, s>>>(deg_in[1], nV, g.ctr + CTR_MAXDEG); note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return report_error(BB_ERR_CUDA, cudaGetErrorString(e));
+    // the one host wait of a build: bounded, creating nothing; the two words
+    // are then copied from the idle stream (to pageable memory)
+    bb_status st = wait_stream_bounded(s, "input validation");
+    if (st != BB_OK) return st;
+    uint32_t herr = 0, hmax = 0;
+    e = cudaMemcpyAsync(&herr, g.err, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hmax, g.ctr + CTR_MAXDEG, 4, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return report_error(BB_ERR_CUDA, cudaGetErrorString(e));
+    *verr = herr;
+    g.h_maxdeg = hmax;
+    g.deg_bits = hmax < (1u << 16) ? 16 : hmax < (1u << 24) ? 24 : 32;
+    return BB_OK;
 }
 
 void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
@@ -793,7 +820,7 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
         // sort ids by degree (stable => ties by id): reuse id_of_sr / deg as buffers
         k_iota<<<grid_for(n, BT, 8192), BT, 0, s>>>(S.sr_of_id, n); note_launch();
         cudaMemcpyAsync(S.lo, deg_in[sd], (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
-        radix_sort_pairs_u32(S.lo, S.sr_of_id, ralt_k, ralt_v, n, 16, ptemp, s);
+        radix_sort_pairs_u32(S.lo, S.sr_of_id, ralt_k, ralt_v, n, g.deg_bits, ptemp, s);
         cudaMemcpyAsync(ralt_v, S.sr_of_id, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
         k_side_rank<<<grid_for(n, BT, 8192), BT, 0, s>>>(ralt_v, S.lo, n, S); note_launch();
     }
@@ -922,17 +949,21 @@ cudaError_t aux_create(BuildAux &a) {
 
 void aux_destroy(BuildAux &a) {
     for (cudaStream_t *st : {&a.stream, &a.stream2})
-        if (*st) { cudaStreamSynchronize(*st); cudaStreamDestroy(*st); *st = nullptr; }
+        if (*st) {
+            // work still running after the wait limit keeps its stream (leaked)
+            if (wait_bounded(*st, "auxiliary stream") == BB_OK) cudaStreamDestroy(*st);
+            *st = nullptr;
+        }
     for (cudaEvent_t *ev : {&a.fork, &a.join, &a.join2})
         if (*ev) { cudaEventDestroy(*ev); *ev = nullptr; }
 }
 
-uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
-                     void *temp_mem, cudaStream_t s, const BuildAux *aux) {
-    const uint32_t e = build_validate(g, rowptr, col, sign, temp_mem, s);
-    if (e) return e;
+bb_status build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
+                      void *temp_mem, cudaStream_t s, const BuildAux *aux, uint32_t *verr) {
+    const bb_status st = build_validate(g, rowptr, col, sign, temp_mem, s, nullptr, verr);
+    if (st != BB_OK || *verr) return st;
     build_rest(g, rowptr, col, sign, temp_mem, s, aux);
-    return 0;
+    return BB_OK;
 }
 
 }  // namespace bb

@@ -19,13 +19,15 @@ enum : uint32_t {
     E_SIGN = 4u,        // sign not +1 / -1
     E_DUP = 8u,         // an edge listed twice
     E_PROBE = 16u,      // hash probe bound exceeded (must not happen)
-    E_DEGREE = 32u,     // a degree above the supported limit
     E_INTERNAL = 64u,   // an internal bound check failed
 };
 
 // Counter fields: per (anchor, endpoint) pair the symmetric-wedge count S in
 // bits 0..15 and the asymmetric-wedge count A in bits 16..31. Both are at
-// most the anchor's degree, which the build checks against this limit.
+// most the anchor's degree (the anchor is the pair's lower-priority vertex,
+// Def. 4, so its degree is the smaller one), which fits 16 bits up to
+// MAX_DEGREE; anchors of higher degree are counted with 32-bit fields
+// (wide dense jobs).
 constexpr uint32_t MAX_DEGREE = 65535;
 constexpr uint32_t INC_SYM = 1u;
 constexpr uint32_t INC_ASYM = 1u << 16;

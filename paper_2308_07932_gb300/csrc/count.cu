@@ -33,8 +33,11 @@
 //           the whole range (walked in windows when longer than DENSE_CAP);
 //           the heaviest are split over CTAs whose partial counts are
 //           merged in global memory, adding the pairs formed across parts.
+//           Anchors of degree above MAX_DEGREE are wide jobs: 32-bit S and
+//           A fields (u64 counters), one CTA each.
 #include <algorithm>
 #include <cstddef>
+#include <mutex>
 #include "graph.cuh"
 
 namespace bb {
@@ -958,6 +961,58 @@ __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, cons
     }
 }
 
+// One wide job (group WIDE_JOB): an anchor of degree above MAX_DEGREE,
+// walked whole by the CTA with 64-bit counters, S in the low and A in the
+// high half (each at most the degree < 2^32), over windows of DENSE_CAP / 2
+// endpoints in the same shared memory. Each wedge adds the previous values
+// of its own tally (balanced) and of both tallies (total) to 64-bit sums,
+// which go to the grid accumulator before they could reach 2^53.
+__device__ __noinline__ void dense_job_wide(const DevGraph &G, DenseSmem &sm, const DenseJob &J,
+                                            unsigned long long &bal, unsigned long long &tot) {
+    constexpr uint32_t CAP = DENSE_CAP / 2;
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(sm.cnt);
+    const int t = threadIdx.x;
+    const SideCSR &S = (J.anchor & 1u) ? G.side[1] : G.side[0];
+    AnchorRec rec;
+    rec.anchor = J.anchor;
+    rec.rb = (uint32_t)S.off[J.anchor >> 1];
+    rec.deg = 0; rec.W = 0; rec.wnh = 0;
+    const Anchor A = load_anchor(G, rec);
+    const uint32_t e_lo = A.r + 1, e_hi = (uint32_t)A.ns;
+    const bool windows = (e_hi - e_lo) > CAP;
+    for (uint32_t e0 = e_lo; e0 < e_hi; e0 += CAP) {
+        const uint32_t e1 = e_hi - e0 > CAP ? e0 + CAP : e_hi;
+        for (uint32_t i = t; i < e1 - e0; i += DENSE_THREADS) cnt[i] = 0ull;
+        __syncthreads();
+        auto add = [&](uint32_t x, uint32_t vb, uint32_t sw) {
+            const uint32_t asym = (x ^ sw) & 1u;
+            const uint32_t idx = ((x >> 1) - e0) & (CAP - 1);
+            const unsigned long long old =
+                atomicAdd(&cnt[idx], (unsigned long long)vb << (asym << 5));
+            const unsigned long long oS = old & 0xffffffffull, oA = old >> 32;
+            if (vb) {
+                bal += asym ? oA : oS;
+                tot += oS + oA;
+            }
+        };
+        auto flush = [&]() { spill_if_large(G.scratch, bal, tot); };
+        if (windows) {
+            team_rounds<DENSE_THREADS, true>(
+                A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t, 1024,
+                [&](const uint4 &d, long long &st, uint32_t &l) {
+                    const long long s0 = lower_bound_u32(A.oadj, d.x, d.z, e0 << 1);
+                    st = s0;
+                    l = (uint32_t)(lower_bound_u32(A.oadj, s0, d.z, e1 << 1) - s0);
+                },
+                add, flush);
+        } else {
+            team_rounds<DENSE_THREADS, true>(A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t, 1024,
+                                             FullSeg{}, add, flush);
+        }
+        __syncthreads();  // the next window rewrites the counters
+    }
+}
+
 __global__ void __launch_bounds__(DENSE_THREADS, 3) k_dense(DevGraph G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DenseSmem &sm = *reinterpret_cast<DenseSmem *>(smem_raw);
@@ -969,7 +1024,9 @@ __global__ void __launch_bounds__(DENSE_THREADS, 3) k_dense(DevGraph G) {
         const uint32_t jid = sm.job;
         __syncthreads();
         if (jid >= njobs) break;
-        dense_job(G, sm, G.dense_jobs[jid], bal, tot);
+        const DenseJob J = G.dense_jobs[jid];
+        if (J.group == WIDE_JOB) dense_job_wide(G, sm, J, bal, tot);
+        else dense_job(G, sm, J, bal, tot);
         spill_if_large(G.scratch, bal, tot);
     }
     flush_warp(G.scratch, bal, tot);
@@ -1071,7 +1128,10 @@ __global__ void __launch_bounds__(DENSE_THREADS) k_dense_batch(BatchArgs B) {
         const uint32_t gi = batch_graph_of(p, B.n, it);
         const DevGraph &G = B.graphs[gi];
         unsigned long long bal = 0, tot = 0;
-        dense_job(G, sm, G.dense_jobs[it - p[gi]], bal, tot);
+        const DenseJob J = G.dense_jobs[it - p[gi]];
+        if (J.group == WIDE_JOB) dense_job_wide(G, sm, J, bal, tot);
+        else dense_job(G, sm, J, bal, tot);
+        spill_if_large(G.scratch, bal, tot);
         block_sum2<DENSE_THREADS>(bal, tot);
         if (threadIdx.x == 0) acc_add(G.scratch, bal, tot);
     }
@@ -1136,9 +1196,6 @@ struct LaunchCfg {
     int sms = 0;
 };
 
-LaunchCfg g_cfg;
-int g_cfg_device = -1;
-
 template <typename K>
 int blocks_for(K kernel, int threads, size_t smem, int sms) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1147,23 +1204,34 @@ int blocks_for(K kernel, int threads, size_t smem, int sms) {
     return std::max(1, b) * sms;
 }
 
-void init_cfg() {
+// Grids and shared-memory opt-ins, once per device (any thread may count on
+// any device; the first launch on a device sets its entry up).
+constexpr int MAX_DEVICES = 64;
+LaunchCfg g_cfg[MAX_DEVICES];
+std::once_flag g_cfg_once[MAX_DEVICES];
+
+const LaunchCfg &init_cfg() {
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (g_cfg_device == dev) return;
-    cudaDeviceProp prop;
-    cudaGetDeviceProperties(&prop, dev);
-    const int sms = prop.multiProcessorCount;
-    g_cfg.sms = sms;
-    g_cfg.warp_blocks = blocks_for(k_warp, WARP_THREADS, WARP_SMEM, sms);
-    g_cfg.team_blocks = blocks_for(k_team, TEAM_THREADS, TEAM_SMEM, sms);
-    g_cfg.ctah_blocks = blocks_for(k_ctah, CTAH_THREADS, CTAH_SMEM, sms);
-    g_cfg.dense_blocks = blocks_for(k_dense, DENSE_THREADS, DENSE_SMEM, sms);
-    g_cfg.batch_blocks[CLS_WARP] = blocks_for(k_warp_batch, WARP_THREADS, WARP_SMEM, sms);
-    g_cfg.batch_blocks[CLS_TEAM] = blocks_for(k_team_batch, TEAM_THREADS, TEAM_SMEM, sms);
-    g_cfg.batch_blocks[CLS_CTAH] = blocks_for(k_ctah_batch, CTAH_THREADS, CTAH_SMEM, sms);
-    g_cfg.batch_blocks[CLS_DENSE] = blocks_for(k_dense_batch, DENSE_THREADS, DENSE_SMEM, sms);
-    g_cfg_device = dev;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    std::call_once(g_cfg_once[dev], [dev]() {
+        LaunchCfg &c = g_cfg[dev];
+        cudaDeviceProp prop;
+        cudaGetDeviceProperties(&prop, dev);
+        const int sms = prop.multiProcessorCount;
+        c.sms = sms;
+        c.warp_blocks = blocks_for(k_warp, WARP_THREADS, WARP_SMEM, sms);
+        c.team_blocks = blocks_for(k_team, TEAM_THREADS, TEAM_SMEM, sms);
+        c.ctah_blocks = blocks_for(k_ctah, CTAH_THREADS, CTAH_SMEM, sms);
+        c.dense_blocks = blocks_for(k_dense, DENSE_THREADS, DENSE_SMEM, sms);
+        c.batch_blocks[CLS_WARP] = blocks_for(k_warp_batch, WARP_THREADS, WARP_SMEM, sms);
+        c.batch_blocks[CLS_TEAM] = blocks_for(k_team_batch, TEAM_THREADS, TEAM_SMEM, sms);
+        c.batch_blocks[CLS_CTAH] = blocks_for(k_ctah_batch, CTAH_THREADS, CTAH_SMEM, sms);
+        c.batch_blocks[CLS_DENSE] = blocks_for(k_dense_batch, DENSE_THREADS, DENSE_SMEM, sms);
+    });
+    return g_cfg[dev];
 }
 
 }  // namespace
@@ -1172,27 +1240,24 @@ void count_init() { init_cfg(); }
 
 void launch_count(const DevGraph &g, cudaStream_t s, int64_t *per_vertex_dev, cudaEvent_t *ev) {
     (void)per_vertex_dev;
-    init_cfg();
+    const LaunchCfg &cfg = init_cfg();
     cudaMemsetAsync(g.scratch, 0, sizeof(CountScratch), s);
     if (ev) record_timing_event(ev[0], s);
-    k_dense<<<g_cfg.dense_blocks, DENSE_THREADS, DENSE_SMEM, s>>>(g); note_launch();
+    k_dense<<<cfg.dense_blocks, DENSE_THREADS, DENSE_SMEM, s>>>(g); note_launch();
     if (ev) record_timing_event(ev[1], s);
-    k_ctah<<<g_cfg.ctah_blocks, CTAH_THREADS, CTAH_SMEM, s>>>(g); note_launch();
+    k_ctah<<<cfg.ctah_blocks, CTAH_THREADS, CTAH_SMEM, s>>>(g); note_launch();
     if (ev) record_timing_event(ev[2], s);
-    k_team<<<g_cfg.team_blocks, TEAM_THREADS, TEAM_SMEM, s>>>(g); note_launch();
+    k_team<<<cfg.team_blocks, TEAM_THREADS, TEAM_SMEM, s>>>(g); note_launch();
     if (ev) record_timing_event(ev[3], s);
-    k_warp<<<g_cfg.warp_blocks, WARP_THREADS, WARP_SMEM, s>>>(g); note_launch();
+    k_warp<<<cfg.warp_blocks, WARP_THREADS, WARP_SMEM, s>>>(g); note_launch();
     if (ev) record_timing_event(ev[4], s);
 }
 
-int batch_max_blocks(int cls) {
-    init_cfg();
-    return g_cfg.batch_blocks[cls];
-}
+int batch_max_blocks(int cls) { return init_cfg().batch_blocks[cls]; }
 
 void launch_count_batch(const BatchLaunch &L, const BatchTune &T, cudaStream_t s,
                         const cudaStream_t *side, const cudaEvent_t *ev, const cudaEvent_t *tev) {
-    init_cfg();
+    const LaunchCfg &cfg = init_cfg();
     BatchArgs B;
     B.graphs = L.graphs;
     B.prefix = L.prefix;
@@ -1218,8 +1283,8 @@ void launch_count_batch(const BatchLaunch &L, const BatchTune &T, cudaStream_t s
         // with concurrency the first class stays on s, the others go to side streams
         cudaStream_t cs = conc && used > 0 ? side[used - 1] : s;
         used++;
-        int blocks = std::max(1, (int)(g_cfg.batch_blocks[c] * T.grid_frac[c] + 0.5f));
-        blocks = std::min(blocks, g_cfg.batch_blocks[c]);
+        int blocks = std::max(1, (int)(cfg.batch_blocks[c] * T.grid_frac[c] + 0.5f));
+        blocks = std::min(blocks, cfg.batch_blocks[c]);
         if (c == CLS_WARP) {
             const uint64_t warps = ((uint64_t)L.items[c] + B.warp_chunk - 1) / B.warp_chunk;
             blocks = (int)std::min<uint64_t>(blocks, (warps + WARP_THREADS / 32 - 1) / (WARP_THREADS / 32));

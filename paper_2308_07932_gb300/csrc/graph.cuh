@@ -62,6 +62,9 @@ struct alignas(16) AnchorRec {
 // NO_GROUP). A job whose anchor has more than DENSE_CAP vertices above it
 // walks the endpoint range in DENSE_CAP windows.
 constexpr uint32_t NO_GROUP = 0xffffffffu;
+// group of a wide job: an anchor of degree above MAX_DEGREE, walked whole
+// by one CTA with 32-bit tally fields (never split)
+constexpr uint32_t WIDE_JOB = 0xfffffffeu;
 struct DenseJob {
     uint32_t anchor;
     uint32_t m0, m1;
@@ -78,7 +81,7 @@ struct SplitGroup {
 // counters written by the classifier
 enum Ctr : uint32_t {
     CTR_WARP = 0, CTR_TEAM = 1, CTR_CTAH = 2, CTR_DENSE = 3, CTR_GROUPS = 4, CTR_GPART = 5,
-    CTR_SPLITJOBS = 6, NCTR = 8
+    CTR_SPLITJOBS = 6, CTR_MAXDEG = 7, NCTR = 8
 };
 
 // per-count scratch (zeroed before each count)
@@ -116,6 +119,8 @@ struct DevGraph {
     // host copies after the build
     uint32_t h_ctr[NCTR] = {};
     uint64_t h_wedges = 0;
+    uint32_t h_maxdeg = 0;   // largest vertex degree (read back by build_validate)
+    int deg_bits = 16;       // key bits of the degree sort (16, 24 or 32, from h_maxdeg)
     unsigned long long h_cls_stats[3 * NCLS] = {};  // resident graphs: copy of cls_stats
 };
 
@@ -137,15 +142,24 @@ struct BuildAux {
     cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
 };
 cudaError_t aux_create(BuildAux &a);   // non-blocking streams, timing-free events
-void aux_destroy(BuildAux &a);         // waits for both streams; safe on a partial create
+void aux_destroy(BuildAux &a);         // waits (bounded) for both streams; safe on a partial create
 
-// Build from device CSR (rowptr/col/sign on the device). Returns 0 or the
-// error bits. Blocking only on the validation check. aux may be null (all
-// work on s). The two stages separately: build_validate (resets, input
-// checks and degrees; blocks to read the check) and build_rest (everything
-// after, no host synchronisation: it can be captured in a CUDA graph).
-uint32_t build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
-                     void *temp_mem, cudaStream_t s, const BuildAux *aux = nullptr);
+// Waits for the work queued so far on s (BB_ERR_TIMEOUT after the
+// library's wait limit, bb_set_wait_timeout). wait_stream_bounded waits
+// until s is idle instead and creates no CUDA object (for paths that must
+// not).
+bb_status wait_bounded(cudaStream_t s, const char *what);
+bb_status wait_stream_bounded(cudaStream_t s, const char *what);
+
+// Build from device CSR (rowptr/col/sign on the device). Sets *verr to 0 or
+// the input-check error bits; returns BB_OK, or the failure of the one wait
+// (on the validation check). aux may be null (all work on s). The two
+// stages separately: build_validate (resets, input checks and degrees;
+// waits for the check, bounded, and reads back its error bits and the
+// largest degree) and build_rest (everything after, no host
+// synchronisation: it can be captured in a CUDA graph).
+bb_status build_graph(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
+                      void *temp_mem, cudaStream_t s, const BuildAux *aux, uint32_t *verr);
 // Inputs still arriving (host-to-device copies on another stream): the
 // validation waits on each part's event before checking it, so the checks
 // of early edge chunks overlap the copies of later ones.
@@ -156,8 +170,8 @@ struct StagedInput {
     cudaEvent_t rowptr_ready = nullptr;
     cudaEvent_t ready[MAX_CHUNKS] = {};
 };
-uint32_t build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
-                        void *temp_mem, cudaStream_t s, const StagedInput *in = nullptr);
+bb_status build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
+                         void *temp_mem, cudaStream_t s, const StagedInput *in, uint32_t *verr);
 void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
                 void *temp_mem, cudaStream_t s, const BuildAux *aux);
 

@@ -3,15 +3,14 @@
 // file-scope device array instead of allocated memory.
 //
 // The array is reserved in every GPU that loads the library, for the life of
-// the process. Its device address is looked up once per device (on the first
-// call made with that device current) and cached. All calls on a device
-// share the array: the merge counters that must start at zero are cleared on
-// every call, everything else is rewritten by the build; two calls whose
-// work overlaps on the GPU race on it.
-#include <chrono>
+// the process. Host code cannot use the array's name as a device address, so
+// every call looks the address up (cudaGetSymbolAddress, with the caller's
+// device current; cheap once the library's device code is loaded, and right
+// again after a device reset between calls). All calls on a device share the
+// array: the merge counters that must start at zero are cleared on every
+// call, everything else is rewritten by the build; two calls whose work
+// overlaps on the GPU race on it.
 #include <cstdio>
-#include <mutex>
-#include <thread>
 
 #include "graph.cuh"
 
@@ -23,9 +22,17 @@ constexpr size_t SCRATCH_BYTES = BB_NOALLOC_SCRATCH_BYTES;
 
 static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
 
-constexpr int MAX_DEVICES = 64;
-std::mutex g_mu;
-void *g_scratch_addr[MAX_DEVICES] = {};
+// device address of g_scratch on the current device
+bb_status scratch_address(void **out) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return report_error(BB_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
+    }
+    *out = p;
+    return BB_OK;
+}
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -35,47 +42,12 @@ bb_status err(bb_status st, const char *fmt, long long a = 0, long long b = 0) {
     return report_error(st, buf);
 }
 
-// device address of g_scratch on the current device (looked up once)
-bb_status scratch_address(int dev, void **out) {
-    if (dev < 0 || dev >= MAX_DEVICES) return err(BB_ERR_NO_DEVICE, "device %lld out of range", dev);
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return report_error(BB_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
-        }
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
-    return BB_OK;
-}
-
 bb_status map_error(uint32_t e) {
     if (e & E_ROWPTR) return report_error(BB_ERR_INVALID_ARG, "rowptr is not a valid CSR row pointer");
     if (e & E_COL) return report_error(BB_ERR_INVALID_ARG, "a column id is outside [0, nV)");
     if (e & E_SIGN) return report_error(BB_ERR_INVALID_ARG, "a sign is not +1 or -1");
     if (e & E_DUP) return report_error(BB_ERR_INVALID_ARG, "an edge is listed twice");
-    if (e & E_DEGREE) return report_error(BB_ERR_TOO_LARGE, "a vertex degree exceeds 65535");
     return err(BB_ERR_CUDA, "internal device check failed (0x%llx)", e);
-}
-
-// waits for the stream without an event (creating one is not needed here)
-bb_status wait_stream(cudaStream_t s) {
-    auto t0 = std::chrono::steady_clock::now();
-    int spins = 0;
-    for (;;) {
-        cudaError_t e = cudaStreamQuery(s);
-        if (e == cudaSuccess) return BB_OK;
-        if (e != cudaErrorNotReady) {
-            cudaGetLastError();
-            return report_error(BB_ERR_CUDA, cudaGetErrorString(e));
-        }
-        if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > 600.0)
-            return report_error(BB_ERR_TIMEOUT, "device work did not finish within 600 s");
-        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
-    }
 }
 
 struct Result {
@@ -105,9 +77,12 @@ extern "C" bb_status bb_count_csr_device_noalloc(const bb_csr *csr_dev, const in
                    (long long)need, (long long)SCRATCH_BYTES);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) { cudaGetLastError(); return report_error(BB_ERR_NO_DEVICE, "no current device"); }
+    if (e != cudaSuccess || dev < 0) {
+        cudaGetLastError();
+        return report_error(BB_ERR_NO_DEVICE, "no current device");
+    }
     void *base = nullptr;
-    bb_status st = scratch_address(dev, &base);
+    bb_status st = scratch_address(&base);
     if (st != BB_OK) return st;
     count_init();
     cudaStream_t s = (cudaStream_t)stream;
@@ -117,18 +92,22 @@ extern "C" bb_status bb_count_csr_device_noalloc(const bb_csr *csr_dev, const in
     // the split-merge counters must start at zero; the array keeps the last call's bytes
     cudaMemsetAsync(g.gpart, 0, (size_t)g.gpart_cap * 4, s);
     cudaMemsetAsync(g.gdone, 0, (size_t)MAX_SPLIT_JOBS * 4, s);
-    const uint32_t verr = build_graph(g, csr_dev->rowptr, csr_dev->col, signs_dev, temp, s);
+    uint32_t verr = 0;
+    st = build_graph(g, csr_dev->rowptr, csr_dev->col, signs_dev, temp, s, nullptr, &verr);
+    if (st != BB_OK) return st;
     if ((e = cudaGetLastError()) != cudaSuccess) return report_error(BB_ERR_CUDA, cudaGetErrorString(e));
     if (verr) return map_error(verr);
     launch_count(g, s, nullptr, nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return report_error(BB_ERR_CUDA, cudaGetErrorString(e));
+    // the bounded wait comes first (the library's wait limit); the small
+    // copies to pageable host memory then complete at once on the idle stream
+    if ((st = wait_stream_bounded(s, "allocation-free count")) != BB_OK) return st;
     Result h;
-    cudaMemcpyAsync(h.acc, g.scratch->acc, sizeof(h.acc), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(&h.count_err, &g.scratch->err, 4, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(&h.build_err, g.err, 4, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(&h.wedges, g.wedges, 8, cudaMemcpyDeviceToHost, s);
-    if ((st = wait_stream(s)) != BB_OK) return st;
-    if ((e = cudaGetLastError()) != cudaSuccess) return report_error(BB_ERR_CUDA, cudaGetErrorString(e));
+    e = cudaMemcpyAsync(h.acc, g.scratch->acc, sizeof(h.acc), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h.count_err, &g.scratch->err, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h.build_err, g.err, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h.wedges, g.wedges, 8, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) { cudaGetLastError(); return report_error(BB_ERR_CUDA, cudaGetErrorString(e)); }
     if (h.build_err) return map_error(h.build_err);
     if (h.count_err) return err(BB_ERR_CUDA, "internal count check failed (0x%llx)", h.count_err);
     if (h.acc[1] || h.acc[3] || h.acc[0] > 0x7fffffffffffffffull || h.acc[2] > 0x7fffffffffffffffull)

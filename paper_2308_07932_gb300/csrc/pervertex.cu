@@ -23,6 +23,7 @@
 // 512-thread CTA per SM the coalesced reads of a warp per middle beat a
 // lane walker here.
 #include <algorithm>
+#include <mutex>
 #include "graph.cuh"
 
 namespace bb {
@@ -147,7 +148,14 @@ __global__ void __launch_bounds__(TH) k_pv(DevGraph G, PvOut out) {
         const uint64_t above_nh = (uint64_t)(wlo - (r + 1));
         const uint64_t wnh = S.work_nh[r];
         const uint64_t need = (wnh < above_nh ? wnh : above_nh) * 5 / 4 + 1;
-        const bool hybrid = need <= HYB_CAP;
+        // an anchor of degree above MAX_DEGREE (wide) needs 32-bit S and A:
+        // dense windows of half the length, S in the first half of the
+        // counters and A in the second (pass 2 reads only final tallies, so
+        // two separate arrays suffice)
+        const bool wide = deg > MAX_DEGREE;
+        const bool hybrid = !wide && need <= HYB_CAP;
+        constexpr uint32_t HALF = WORDS / 2;
+        const uint32_t span = wide ? HALF : WORDS;
         if (TEAM && !hybrid) {  // impossible for a team-class anchor
             set_error(err, E_INTERNAL);
             continue;
@@ -159,11 +167,13 @@ __global__ void __launch_bounds__(TH) k_pv(DevGraph G, PvOut out) {
         unsigned long long *tab = reinterpret_cast<unsigned long long *>(sm.cnt + HUB_WINDOW);
         unsigned long long wsum = 0;  // balanced butterflies containing the anchor
         const uint32_t e_lo = r + 1, e_hi = ns;
-        for (uint32_t e0 = e_lo; e0 < e_hi; e0 += hybrid ? (e_hi - e_lo) : WORDS) {
-            const uint32_t e1 = !hybrid && e_hi - e0 > WORDS ? e0 + WORDS : e_hi;
-            const bool clip = !hybrid && (e_hi - e_lo) > WORDS;
+        for (uint32_t e0 = e_lo; e0 < e_hi; e0 += hybrid ? (e_hi - e_lo) : span) {
+            const uint32_t e1 = !hybrid && e_hi - e0 > span ? e0 + span : e_hi;
+            const bool clip = !hybrid && (e_hi - e_lo) > span;
             const uint32_t len = hybrid ? wlen : e1 - e0;
             for (uint32_t i = t; i < len; i += TH) sm.cnt[i] = 0;
+            if (wide)
+                for (uint32_t i = t; i < len; i += TH) sm.cnt[HALF + i] = 0;
             if (hybrid)
                 for (uint32_t i = t; i < cap; i += TH) tab[i] = 0ull;
             __syncthreads();
@@ -191,9 +201,11 @@ __global__ void __launch_bounds__(TH) k_pv(DevGraph G, PvOut out) {
                 for (int64_t p = st + lane; p < en; p += 32) {
                     const uint32_t x = O.adj[p];
                     const uint32_t u = x >> 1;
-                    const uint32_t inc = ((x ^ sw) & 1u) ? INC_ASYM : INC_SYM;
+                    const uint32_t asym = (x ^ sw) & 1u;
+                    const uint32_t inc = asym ? INC_ASYM : INC_SYM;
                     const uint32_t idx = index(u);
-                    if (idx < len) atomicAdd(&sm.cnt[idx], inc);
+                    if (wide) { if (idx < len) atomicAdd(&sm.cnt[asym * HALF + idx], 1u); }
+                    else if (idx < len) atomicAdd(&sm.cnt[idx], inc);
                     else if (hybrid) pv_hash_add(tab, shift, mask, u + 1, inc, err);
                 }
             }
@@ -208,10 +220,14 @@ __global__ void __launch_bounds__(TH) k_pv(DevGraph G, PvOut out) {
                     const uint32_t x = O.adj[p];
                     const uint32_t u = x >> 1;
                     const uint32_t idx = index(u);
-                    uint32_t c = 0;
-                    if (idx < len) c = sm.cnt[idx];
-                    else if (hybrid) c = pv_hash_find(tab, shift, mask, u + 1, err);
-                    const uint32_t ct = ((x ^ sw) & 1u) ? (c >> 16) : (c & 0xffffu);
+                    uint32_t c = 0, ct;
+                    if (wide) {
+                        ct = idx < len ? sm.cnt[((x ^ sw) & 1u) * HALF + idx] : 0u;
+                    } else {
+                        if (idx < len) c = sm.cnt[idx];
+                        else if (hybrid) c = pv_hash_find(tab, shift, mask, u + 1, err);
+                        ct = ((x ^ sw) & 1u) ? (c >> 16) : (c & 0xffffu);
+                    }
                     const unsigned long long k = ct > 0 ? ct - 1 : 0;
                     msum += k;
                     if (peO && k) atomicAdd(&peO[p], k);   // edge v-u
@@ -228,10 +244,9 @@ __global__ void __launch_bounds__(TH) k_pv(DevGraph G, PvOut out) {
             const uint32_t ubase = hybrid ? wlo : e0;
             for (uint32_t i = t; i < len; i += TH) {
                 const uint32_t c = sm.cnt[i];
-                if (c) {
-                    const unsigned long long b = c2(c & 0xffffu) + c2(c >> 16);
-                    if (b) { atomicAdd(&S.pv[ubase + i], b); wsum += b; }
-                }
+                const unsigned long long b =
+                    wide ? c2(c) + c2(sm.cnt[HALF + i]) : c2(c & 0xffffu) + c2(c >> 16);
+                if (b) { atomicAdd(&S.pv[ubase + i], b); wsum += b; }
             }
             if (hybrid)
                 for (uint32_t i = t; i < cap; i += TH) {
@@ -412,7 +427,14 @@ __global__ void k_pv_out(SideCSR S, int64_t base, int64_t *out) {
         out[base + S.id_of_sr[r]] = (int64_t)S.pv[r];
 }
 
-int g_pv_blocks = 0, g_pvt_blocks = 0, g_pvw_blocks = 0, g_pv_device = -1;
+// grids of the three per-vertex kernels, once per device (any thread may
+// count on any device)
+struct PvCfg {
+    int pv = 0, pvt = 0, pvw = 0;
+};
+constexpr int MAX_DEVICES = 64;
+PvCfg g_pv_cfg[MAX_DEVICES];
+std::once_flag g_pv_once[MAX_DEVICES];
 constexpr size_t PVW_SMEM = (PVW_THREADS / 32) * sizeof(PvWarpSmem);
 constexpr size_t PV_SMEM = sizeof(PvSmem<PV_THREADS, PV_DENSE_CAP>);
 constexpr size_t PVT_SMEM = sizeof(PvSmem<PVT_THREADS, PVT_WORDS>);
@@ -427,28 +449,33 @@ int pv_blocks(K kernel, int threads, size_t smem, int sms) {
     return std::max(1, b) * sms;
 }
 
-void pv_init() {
+const PvCfg &pv_init() {
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (g_pv_device != dev) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    std::call_once(g_pv_once[dev], [dev]() {
         cudaDeviceProp prop;
         cudaGetDeviceProperties(&prop, dev);
         const int sms = prop.multiProcessorCount;
-        g_pv_blocks = pv_blocks(k_pv_big, PV_THREADS, PV_SMEM, sms);
-        g_pvt_blocks = pv_blocks(k_pv_team, PVT_THREADS, PVT_SMEM, sms);
-        g_pvw_blocks = pv_blocks(k_pv_warp, PVW_THREADS, PVW_SMEM, sms);
-        g_pv_device = dev;
-    }
+        PvCfg &c = g_pv_cfg[dev];
+        c.pv = pv_blocks(k_pv_big, PV_THREADS, PV_SMEM, sms);
+        c.pvt = pv_blocks(k_pv_team, PVT_THREADS, PVT_SMEM, sms);
+        c.pvw = pv_blocks(k_pv_warp, PVW_THREADS, PVW_SMEM, sms);
+    });
+    return g_pv_cfg[dev];
 }
 
 // the three per-vertex walks: warp-class, team-class, then dense and
 // CTA-hash anchors (each kernel drains its own job cursor)
 void launch_pv_kernels(const DevGraph &g, const PvOut &o, cudaStream_t s) {
+    const PvCfg &c = pv_init();
     cudaMemsetAsync(&g.scratch->job_next[JOB_PV_TEAM], 0, 4, s);
     cudaMemsetAsync(&g.scratch->job_next[JOB_PER_VERTEX], 0, 4, s);
-    k_pv_warp<<<g_pvw_blocks, PVW_THREADS, PVW_SMEM, s>>>(g, o); note_launch();
-    k_pv_team<<<g_pvt_blocks, PVT_THREADS, PVT_SMEM, s>>>(g, o); note_launch();
-    k_pv_big<<<g_pv_blocks, PV_THREADS, PV_SMEM, s>>>(g, o); note_launch();
+    k_pv_warp<<<c.pvw, PVW_THREADS, PVW_SMEM, s>>>(g, o); note_launch();
+    k_pv_team<<<c.pvt, PVT_THREADS, PVT_SMEM, s>>>(g, o); note_launch();
+    k_pv_big<<<c.pv, PV_THREADS, PV_SMEM, s>>>(g, o); note_launch();
 }
 
 }  // namespace

@@ -73,7 +73,8 @@ extern "C" bb_status bb_probe_shared_atomics(int device, uint32_t window, double
         if (rep > 0 && (best == 0 || ms < best)) best = ms;
     }
     if (sink) cudaFreeAsync(sink, s);
-    cudaStreamSynchronize(s);
+    const bb_status ws = wait_bounded(s, "atomic probe");
+    if (ws != BB_OK) return ws;  // the stream and events stay (leaked) while work runs
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaStreamDestroy(s);

@@ -53,8 +53,8 @@ struct bb_ctx {
     // the one-shot path's work after validation, captured as a CUDA graph
     // for one shape and set of buffers (key) and replayed while they repeat
     cudaGraphExec_t step_exec = nullptr;
-    const void *step_key[9] = {};   // key of step_exec
-    const void *step_last[9] = {};  // key of the previous call (capture when it repeats)
+    const void *step_key[10] = {};   // key of step_exec
+    const void *step_last[10] = {};  // key of the previous call (capture when it repeats)
     uint64_t step_launches = 0;     // kernels in the captured graph
     bb::HostResult *h_res = nullptr;  // pinned
     // host inputs: rowptr and edge-chunk copy events (copies run on the

@@ -309,7 +309,13 @@ bb_status run_managed(Engine *E, Slot &S, bb_ticket_s *t, Plan &plan) {
         e->g.sign = sg;
         BB_CUDA(cudaMemsetAsync(e->g.gpart, 0, (size_t)e->g.gpart_cap * 4, s), "zero merge buffer");
         BB_CUDA(cudaMemsetAsync(e->g.gdone, 0, MAX_SPLIT_JOBS * 4, s), "zero merge counters");
-        const uint32_t verr = build_graph(e->g, rp, cl, sg, E->arena_mem + plan.temp.off, s, &S.aux);
+        uint32_t verr = 0;
+        const bb_status bst =
+            build_graph(e->g, rp, cl, sg, E->arena_mem + plan.temp.off, s, &S.aux, &verr);
+        if (bst != BB_OK) {
+            plan.drop = true;
+            return bst;
+        }
         BB_CUDA(cudaGetLastError(), "build kernels");
         if (verr) {
             plan.drop = true;
@@ -440,7 +446,8 @@ void destroy_engine(Engine *E) {
         if (S.th.joinable()) S.th.join();
     cudaSetDevice(E->device);
     for (Slot &S : E->slots) {
-        if (S.s) { cudaStreamSynchronize(S.s); cudaStreamDestroy(S.s); }
+        // a slot's work still running after the wait limit keeps its stream
+        if (S.s && wait_bounded(S.s, "serving slot") == BB_OK) cudaStreamDestroy(S.s);
         aux_destroy(S.aux);
         if (S.h) cudaFreeHost(S.h);
     }

@@ -1,8 +1,13 @@
 """Failure handling without faulting the GPU: a blocking call whose device
 work outlasts the wait limit returns BB_ERR_TIMEOUT (the limit is made
-tiny; the work itself is ordinary and finishes), the context and the
-serving engine stay usable afterwards, and results are right again once
-the limit is restored."""
+tiny; the work itself is ordinary and finishes), later calls honour the
+same limit while that work drains, the context and the serving engine stay
+usable afterwards, and results are right again once the limit is restored
+(nothing outside the library waits for the device in between). A device
+allocation failure is injected on the host (bb_set_alloc_failure) and
+surfaces as BB_ERR_OOM, after which the same objects count right."""
+import time
+
 import pytest
 
 import oracle
@@ -19,9 +24,7 @@ def big():
 
 
 def restore():
-    import torch
-    pkg.set_wait_timeout(600.0)
-    torch.cuda.synchronize()   # the timed-out work drains on its own
+    pkg.set_wait_timeout(600.0)   # the timed-out work drains on its own
 
 
 def test_blocking_count_times_out_then_recovers(big):
@@ -54,3 +57,62 @@ def test_served_request_times_out_then_recovers(big):
         assert (o.balanced, o.total) == want
         st = ctx.serve_stats()
         assert st["failed"] == 1 and st["completed"] == 1
+
+
+def test_second_call_after_timeout_is_bounded_too(big):
+    g, want = big
+    with pkg.Context(0) as ctx:
+        try:
+            pkg.set_wait_timeout(1e-4)
+            for _ in range(2):   # the second call finds the first one's work queued
+                t0 = time.perf_counter()
+                with pytest.raises(pkg.BBError) as ei:
+                    ctx.count(g)
+                assert ei.value.name == "BB_ERR_TIMEOUT"
+                assert time.perf_counter() - t0 < 5.0
+        finally:
+            restore()
+        c = ctx.count(g)
+        assert (c.balanced, c.total) == want
+
+
+def test_injected_allocation_failure_count_and_upload(big):
+    g, want = big
+    with pkg.Context(0) as ctx:
+        try:
+            # the first workspace request (with headroom) fails; the library
+            # retries at the exact size and the count goes through
+            pkg.set_alloc_failure(1)
+            c = ctx.count(g)
+            assert (c.balanced, c.total) == want
+        finally:
+            pkg.set_alloc_failure(0)
+        for nth in (1, 2):   # an upload allocates the input copy, then the graph
+            try:
+                pkg.set_alloc_failure(nth)
+                with pytest.raises(pkg.BBError) as ei:
+                    ctx.upload(g)
+                assert ei.value.name == "BB_ERR_OOM"
+            finally:
+                pkg.set_alloc_failure(0)
+        res = ctx.upload(g)
+        try:
+            r = res.count()
+            assert (r.balanced, r.total) == want
+        finally:
+            res.free()
+
+
+def test_injected_allocation_failure_serving_engine(big):
+    g, want = big
+    with pkg.Context(0) as ctx:
+        try:
+            pkg.set_alloc_failure(1)   # the arena reservation fails
+            with pytest.raises(pkg.BBError) as ei:
+                ctx.serve(slots=2, arena_bytes=2 << 30)
+            assert ei.value.name == "BB_ERR_OOM"
+        finally:
+            pkg.set_alloc_failure(0)
+        ctx.serve(slots=2, arena_bytes=2 << 30)
+        o = ctx.submit_request(3, g).wait()
+        assert (o.balanced, o.total) == want

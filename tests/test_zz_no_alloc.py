@@ -1,8 +1,9 @@
 """The allocation-free entry point, for callers that cannot ask for device
 memory when they count (their memory belongs to another allocator, or they
-must not allocate once running). It must give the same counts as the
-regular device entry point, call after call, and turn away graphs whose
-workspace does not fit its fixed array.
+must not allocate once running). It must give the oracle's counts and the
+regular device entry point's, call after call, allocate nothing while
+doing so, recover from a rejected input, honour the wait limit, and turn
+away graphs whose workspace does not fit its fixed array.
 
 This file is collected last so that a run stopping at its first failure has
 already run every other test."""
@@ -11,10 +12,13 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import paper_2308_07932_gb300 as pkg
 from paper_2308_07932_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+
+OK, INVALID_ARG, TOO_LARGE, TIMEOUT = 0, 1, 2, 5
 
 
 def entry_point():
@@ -34,33 +38,106 @@ def device_graph(torch, g):
     return rp, cl, sg
 
 
-def test_matches_regular_entry_point_twice_in_a_row():
+def call(f, g, bufs, stream):
+    """One call on device buffers; returns (status, balanced, total, wedges)."""
+    rp, cl, sg = bufs
+    csr = pkg._Csr(g.nU, g.nV, g.nE, rp.data_ptr(), cl.data_ptr())
+    b, t, w = ctypes.c_int64(-1), ctypes.c_int64(-1), ctypes.c_int64(-1)
+    st = f(ctypes.byref(csr), sg.data_ptr(), stream, ctypes.byref(b), ctypes.byref(t),
+           ctypes.byref(w))
+    return st, b.value, t.value, w.value
+
+
+GRAPHS = [lambda: synth.uniform_2k_1k(), lambda: synth.chung_lu_scaled(41, 200_000),
+          lambda: synth.vote(5, 60, 8_000, 0.4, 2, 0.55, 0.8),
+          lambda: synth.chung_lu_scaled(47, 600_000)]
+
+
+def test_matches_oracle_and_regular_entry_point_twice_in_a_row():
     torch = pytest.importorskip("torch")
     f = entry_point()
-    graphs = [synth.uniform_2k_1k(), synth.chung_lu_scaled(41, 200_000),
-              synth.vote(5, 60, 8_000, 0.4, 2, 0.55, 0.8), synth.chung_lu_scaled(47, 600_000)]
+    stream = torch.cuda.current_stream().cuda_stream
     with pkg.Context(0) as ctx:
-        for g in graphs:
-            rp, cl, sg = device_graph(torch, g)
-            want = ctx.count_device(g.nU, g.nV, g.nE, rp.data_ptr(), cl.data_ptr(), sg.data_ptr())
-            csr = pkg._Csr(g.nU, g.nV, g.nE, rp.data_ptr(), cl.data_ptr())
-            stream = torch.cuda.current_stream().cuda_stream
+        for make in GRAPHS:
+            g = make()
+            want = oracle.count(g, threads=8)
+            bufs = device_graph(torch, g)
+            reg = ctx.count_device(g.nU, g.nV, g.nE, *(x.data_ptr() for x in bufs))
+            assert (reg.balanced, reg.total) == want, g.name
             for _ in range(2):
-                b, t, w = ctypes.c_int64(-1), ctypes.c_int64(-1), ctypes.c_int64(-1)
-                st = f(ctypes.byref(csr), sg.data_ptr(), stream, ctypes.byref(b), ctypes.byref(t),
-                       ctypes.byref(w))
-                assert st == 0, pkg.lib().bb_last_error()
-                assert (b.value, t.value, w.value) == (want.balanced, want.total, want.wedges)
+                st, b, t, w = call(f, g, bufs, stream)
+                assert st == OK, pkg.lib().bb_last_error()
+                assert (b, t, w) == (reg.balanced, reg.total, reg.wedges), g.name
+
+
+def test_calls_allocate_nothing():
+    torch = pytest.importorskip("torch")
+    f = entry_point()
+    stream = torch.cuda.current_stream().cuda_stream
+    graphs = [make() for make in GRAPHS]
+    bufs = [device_graph(torch, g) for g in graphs]
+    want = [oracle.count(g, threads=8) for g in graphs]
+    # first calls: every kernel the graphs need has run (and been loaded) once
+    for g, bb in zip(graphs, bufs):
+        assert call(f, g, bb, stream)[0] == OK
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    allocs0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    for _ in range(2):
+        for g, bb, w in zip(graphs, bufs, want):
+            st, b, t, _ = call(f, g, bb, stream)
+            assert st == OK and (b, t) == w, pkg.lib().bb_last_error()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == allocs0
+
+
+def test_rejected_input_then_valid_and_empty_graph():
+    torch = pytest.importorskip("torch")
+    f = entry_point()
+    stream = torch.cuda.current_stream().cuda_stream
+    g = synth.chung_lu_scaled(41, 200_000)
+    bad_sign = g.sign.copy()
+    bad_sign[g.nE // 2] = 0
+    bad = synth.SignedBipartite(g.nU, g.nV, g.rowptr, g.col, bad_sign, "bad sign")
+    bad_col = g.col.copy()
+    bad_col[7] = g.nV
+    bad2 = synth.SignedBipartite(g.nU, g.nV, g.rowptr, bad_col, g.sign, "bad column")
+    for b in (bad, bad2):
+        st, bal, tot, _ = call(f, b, device_graph(torch, b), stream)
+        assert st == INVALID_ARG and (bal, tot) == (-1, -1)
+    # the shared array still holds the rejected call's state; a valid graph
+    # counts right after it
+    st, bal, tot, _ = call(f, g, device_graph(torch, g), stream)
+    assert st == OK and (bal, tot) == oracle.count(g, threads=8)
+    empty = synth.from_edges(5, 3, [], [], [], "empty")
+    st, bal, tot, w = call(f, empty, device_graph(torch, empty), stream)
+    assert (st, bal, tot, w) == (OK, 0, 0, 0)
+
+
+def test_honours_the_wait_limit():
+    torch = pytest.importorskip("torch")
+    f = entry_point()
+    stream = torch.cuda.current_stream().cuda_stream
+    g = synth.chung_lu_scaled(47, 600_000)
+    bufs = device_graph(torch, g)
+    try:
+        pkg.set_wait_timeout(1e-4)
+        st, b, t, _ = call(f, g, bufs, stream)
+        assert st == TIMEOUT and (b, t) == (-1, -1)
+    finally:
+        pkg.set_wait_timeout(600.0)
+    # the timed-out call's work runs first on the stream; this one counts right
+    st, b, t, _ = call(f, g, bufs, stream)
+    assert st == OK and (b, t) == oracle.count(g, threads=8)
 
 
 def test_rejects_graphs_beyond_its_array():
     torch = pytest.importorskip("torch")
     f = entry_point()
     g = synth.chung_lu_scaled(3, 4_000_000)
-    rp, cl, sg = device_graph(torch, g)
-    csr = pkg._Csr(g.nU, g.nV, g.nE, rp.data_ptr(), cl.data_ptr())
-    b, t = ctypes.c_int64(-1), ctypes.c_int64(-1)
-    st = f(ctypes.byref(csr), sg.data_ptr(), None, ctypes.byref(b), ctypes.byref(t), None)
-    assert st == 2  # BB_ERR_TOO_LARGE
+    bufs = device_graph(torch, g)
+    st, b, t, _ = call(f, g, bufs, None)
+    assert st == TOO_LARGE
     assert b"workspace" in pkg.lib().bb_last_error()
-    assert (b.value, t.value) == (-1, -1)
+    assert (b, t) == (-1, -1)
