@@ -143,6 +143,14 @@ def oracle_rate(g, wedges: int, stride: int, offset: int, threads: int):
     return wedges / t_full, t_call, desc
 
 
+def workload_config(name: str, g, wedges: int, world: int) -> dict:
+    """The workload as both arms report it (identical keys and values)."""
+    return {"workload": name, "nU": g.nU, "nV": g.nV, "nE": g.nE, "wedges": wedges,
+            "inputs": "CSR resident in device memory when a timed GPU step starts",
+            "l2": f"flushed before every timed GPU step ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -164,8 +172,7 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "nU": g.nU, "nV": g.nV, "nE": g.nE,
-                   "wedges": wedges},
+        "config": workload_config(args.workload, g, wedges, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"per step: {desc}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -343,9 +350,7 @@ def run_ours(args, world, rank, local_rank):
         rb.free()
 
     # dominant wedge kernel and its roofline
-    kern = {k: {"ms": statistics.mean(t["kernels"][k]["ms"] for t in timings),
-                **{f: timings[-1]["kernels"][k][f] for f in ("wedges", "middles", "anchors")}}
-            for k in pkg.KERNELS}
+    kern = kernel_table(pkg, timings)
     build_ms = statistics.mean(t["build_ms"] for t in timings)
     count_ms = statistics.mean(t["count_ms"] for t in timings)
     top = max(kern, key=lambda k: kern[k]["ms"])
@@ -360,12 +365,8 @@ def run_ours(args, world, rank, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic",
-        "config": {
-            "workload": args.workload, "nU": g.nU, "nV": g.nV, "nE": g.nE, "wedges": c.wedges,
-            "balanced": c.balanced, "total": c.total, "inputs": "device-resident CSR",
-            "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
-            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-        },
+        "config": workload_config(args.workload, g, c.wedges, world),
+        "counts": {"balanced": c.balanced, "total": c.total},
         "phases_ms": {"build": build_ms, "count": count_ms,
                       **{k: v["ms"] for k, v in kern.items()}},
         "kernels": kern,
@@ -385,6 +386,9 @@ def run_ours(args, world, rank, local_rank):
         "clocks": clocks,
         "optional_outputs": opt,
     }
+    if rank == 0 and world == 1 and not args.no_extra_workloads:
+        line["workloads"] = {w: run_workload_leg(args, w, local_rank)
+                             for w in EXTRA_WORKLOADS if w != args.workload}
     if rank == 0 and world == 1 and args.batch_graphs > 0:
         line["batch"] = run_batch_leg(args, local_rank)
     if rank == 0 and world == 1 and args.serve_requests > 0:
@@ -399,6 +403,103 @@ def run_ours(args, world, rank, local_rank):
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------ the other single graphs
+EXTRA_WORKLOADS = ["vote_500x50000_p0.4_b2", "uniform_2000x1000_e20000_p0.7"]
+
+
+def kernel_table(pkg, timings):
+    """Per wedge kernel: mean CUDA-event time over the timed steps and its
+    work (wedges, middles, anchors)."""
+    return {k: {"ms": statistics.mean(t["kernels"][k]["ms"] for t in timings),
+                **{f: timings[-1]["kernels"][k][f] for f in ("wedges", "middles", "anchors")}}
+            for k in pkg.KERNELS}
+
+
+def run_workload_leg(args, name: str, dev_index: int) -> dict:
+    """One more single-graph configuration, measured like the headline: the
+    whole path through bb_count_csr_device on the device-resident graph (L2
+    flushed before each step, CUDA events), the dominant kernel's roofline,
+    the same through bb_count_csr from pinned host buffers (e2e), and the
+    oracle on the host cores. The 500 x 50k vote graph stands in for the
+    dense vote-like datasets; the 2k x 1k uniform graph is launch-bound, so
+    its figure is the latency of one call."""
+    import torch
+    import paper_2308_07932_gb300 as pkg
+
+    g = make_graph(name)
+    dev = torch.device("cuda", dev_index)
+    t_rp, t_cl, t_sg = (torch.from_numpy(a).to(dev) for a in (g.rowptr, g.col, g.sign))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = pkg.Context(dev_index)
+    ctx.set_stream(stream.cuda_stream)
+    ctx.set_timing(True)
+    torch.cuda.synchronize()
+
+    def step():
+        return ctx.count_device(g.nU, g.nV, g.nE, t_rp.data_ptr(), t_cl.data_ptr(),
+                                t_sg.data_ptr())
+
+    for _ in range(max(3, args.warmup)):
+        c = step()
+    steps = max(5, args.extra_steps)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    timings = []
+    with ClockSampler(dev_index) as clk:
+        for k in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            c = step()
+            ev[k][1].record(stream)
+            timings.append(ctx.last_timing())
+        torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ms_step = statistics.mean(ms)
+    kern = kernel_table(pkg, timings)
+    top = max(kern, key=lambda k: kern[k]["ms"])
+    peak, peak_kind = load_peaks()
+    ach = algorithmic_bytes(kern[top]) / (kern[top]["ms"] / 1e3) / 1e9
+    # end to end from pinned host buffers
+    h = [torch.from_numpy(a).pin_memory() for a in (g.rowptr, g.col, g.sign)]
+    ctx.set_timing(False)
+    for _ in range(2):
+        ctx.count_host_ptrs(g.nU, g.nV, g.nE, *(x.data_ptr() for x in h))
+    e2e = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        ce = ctx.count_host_ptrs(g.nU, g.nV, g.nE, *(x.data_ptr() for x in h))
+        e2e.append(time.perf_counter() - t0)
+    assert (ce.balanced, ce.total) == (c.balanced, c.total)
+    ctx.close()
+    e2e_s = statistics.mean(e2e)
+    cores = os.cpu_count() or 1
+    rate, secs, desc = oracle_rate(g, c.wedges, args.cpu_stride if g.nE > 1e6 else 1, 0, cores)
+    return {
+        "metric": METRIC, "unit": UNIT, "value": c.wedges / (ms_step / 1e3),
+        "ms_per_step": ms_step, "steps": steps,
+        "latency_ms": {"device_median": statistics.median(ms),
+                       "e2e_median": 1e3 * statistics.median(e2e)},
+        "config": workload_config(name, g, c.wedges, 1),
+        "counts": {"balanced": c.balanced, "total": c.total},
+        "phases_ms": {"build": statistics.mean(t["build_ms"] for t in timings),
+                      "count": statistics.mean(t["count_ms"] for t in timings),
+                      **{k: v["ms"] for k, v in kern.items()}},
+        "kernels": kern,
+        "roofline": {"bound": "hbm", "kernel": top, "achieved": ach, "peak": peak,
+                     "unit": "GB/s", "frac": ach / peak, "peak_kind": peak_kind,
+                     "algorithmic_bytes": algorithmic_bytes(kern[top]),
+                     "traffic": traffic_for(top, name)},
+        "e2e": {"value": c.wedges / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": g.rowptr.nbytes + g.col.nbytes + g.sign.nbytes,
+                "d2h_bytes_per_step": 52},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": desc, "seconds": secs},
+        "clocks": clk.summary(),
+    }
 
 
 # ------------------------------------------------------- batched counting
@@ -528,7 +629,10 @@ def run_serve_leg(args, dev_index: int) -> dict:
     re-queries of a resident graph with 1% of its edge signs flipped, a
     120 GiB HBM budget. Served = the engine (4 slots, managed cache in a
     120 GiB arena); plain = per request upload + count + free, one at a
-    time. Latency = arrival to result; both paths must agree on every count."""
+    time. Every request (flip lists included) is generated before the trace
+    starts, and each path is warmed up on graphs outside the trace. Latency
+    = arrival to the moment the client holds the result, on the client's
+    clock for both paths; both paths must agree on every count."""
     import paper_2308_07932_gb300 as pkg
     from concurrent.futures import ThreadPoolExecutor
     from paper_2308_07932_gb300 import synth
@@ -536,22 +640,43 @@ def run_serve_leg(args, dev_index: int) -> dict:
     t0 = time.perf_counter()
     with ThreadPoolExecutor(min(32, os.cpu_count() or 4)) as ex:
         pool = list(ex.map(synth.serving_graph, range(args.serve_pool)))
+        warm = list(ex.map(synth.serving_graph, range(10_000, 10_004)))
     gen_s = time.perf_counter() - t0
     rates = [float(x) for x in args.serve_rates.split(",")]
     out = {"pool_graphs": len(pool), "pool_edges": int(sum(g.nE for g in pool)),
            "requests_per_rate": args.serve_requests, "slots": args.serve_slots,
-           "budget_bytes": SERVE_BUDGET, "setup_s": {"generate": gen_s}, "rates": []}
-
-    def host_graph(state, key, gidx):
-        g = pool[gidx]
-        return synth.SignedBipartite(g.nU, g.nV, g.rowptr, g.col, state.get(key, g.sign), g.name)
+           "budget_bytes": SERVE_BUDGET, "setup_s": {"generate": gen_s},
+           "latency": "arrival to result held by the client, client clock, both paths",
+           "warmup": f"{len(warm)} graphs outside the trace through each path before it",
+           "rates": []}
 
     for ri, rate in enumerate(rates):
-        reqs = serve_trace(args.serve_requests, rate, len(pool), seed=100 + ri)
+        trace = serve_trace(args.serve_requests, rate, len(pool), seed=100 + ri)
+        # resolve every request before the clock starts: graph, flip list and
+        # the key's signs before and after it. A re-query carries the CSR with
+        # the signs before its flips: the engine ignores it while the key is
+        # resident and uploads it when the key was evicted meanwhile.
+        key_graph, state, reqs = {}, {}, []
+        for at, key, gidx, u in trace:
+            if gidx is not None:
+                key_graph[key] = gidx
+                state[key] = pool[gidx].sign
+                reqs.append((at, key, gidx, None, pool[gidx], pool[gidx]))
+            else:
+                g0 = pool[key_graph[key]]
+                fl = flip_list(g0.nE, 0.01, u)
+                pre = state[key]
+                post = pre.copy()
+                post[fl] = -post[fl]
+                state[key] = post
+                mk = lambda sg: synth.SignedBipartite(g0.nU, g0.nV, g0.rowptr, g0.col, sg, g0.name)  # noqa: E731
+                reqs.append((at, key, key_graph[key], fl, mk(pre), mk(post)))
+        del state
         # ---- served
         ctx = pkg.Context(dev_index, budget_bytes=SERVE_BUDGET + (4 << 30))
         ctx.serve(slots=args.serve_slots, arena_bytes=SERVE_BUDGET)
-        key_graph = {}
+        for k, g in enumerate(warm):
+            ctx.submit_request(1_000_000 + k, g).wait()
         lat, got, pending = [0.0] * len(reqs), [None] * len(reqs), []
         start = time.perf_counter()
         i = 0
@@ -560,23 +685,18 @@ def run_serve_leg(args, dev_index: int) -> dict:
                 now = time.perf_counter() - start
                 busy = False
                 while i < len(reqs) and reqs[i][0] <= now:
-                    at, key, gidx, u = reqs[i]
-                    late = (time.perf_counter() - start) - at
-                    if gidx is not None:
-                        key_graph[key] = gidx
-                        tk = ctx.submit_request(key, pool[gidx])
-                    else:
-                        tk = ctx.submit_request(key, None, flip_list(pool[key_graph[key]].nE, 0.01, u))
-                    pending.append((i, tk, late))
+                    at, key, gidx, fl, pre, _ = reqs[i]
+                    tk = ctx.submit_request(key, pre, fl)
+                    pending.append((i, tk))
                     i += 1
                     busy = True
                 still = []
-                for j, tk, late in pending:
+                for j, tk in pending:
                     r = tk.poll()
                     if r is None:
-                        still.append((j, tk, late))
+                        still.append((j, tk))
                     else:
-                        lat[j] = late * 1e3 + r.queue_ms + r.run_ms
+                        lat[j] = (time.perf_counter() - start - reqs[j][0]) * 1e3
                         got[j] = (r.balanced, r.total)
                         busy = True
                 pending = still
@@ -587,22 +707,17 @@ def run_serve_leg(args, dev_index: int) -> dict:
         ctx.close()
         # ---- plain: upload + count + free per request, one at a time
         ctx = pkg.Context(dev_index, budget_bytes=SERVE_BUDGET)
-        state, plat, pgot = {}, [0.0] * len(reqs), [None] * len(reqs)
-        key_graph = {}
+        for g in warm:
+            gr = ctx.upload(g)
+            gr.count()
+            gr.free()
+        plat, pgot = [0.0] * len(reqs), [None] * len(reqs)
         start = time.perf_counter()
-        for j, (at, key, gidx, u) in enumerate(reqs):
+        for j, (at, key, gidx, fl, _, post) in enumerate(reqs):
             now = time.perf_counter() - start
             if now < at:
                 time.sleep(at - now)
-            if gidx is not None:
-                key_graph[key] = gidx
-            else:
-                g0 = pool[key_graph[key]]
-                idx = flip_list(g0.nE, 0.01, u)
-                s = state.get(key, g0.sign).copy()
-                s[idx] = -s[idx]
-                state[key] = s
-            gr = ctx.upload(host_graph(state, key, key_graph[key]))
+            gr = ctx.upload(post)
             c = gr.count()
             gr.free()
             pgot[j] = (c.balanced, c.total)
@@ -613,11 +728,11 @@ def run_serve_leg(args, dev_index: int) -> dict:
         out["rates"].append({
             "rate_req_s": rate,
             "served": {"graphs_per_s": len(reqs) / served_s, "p50_ms": pctl(lat, 50),
-                       "p99_ms": pctl(lat, 99), "cache_hits": stats["cache_hits"],
-                       "uploads": stats["uploads"], "evictions": stats["evictions"],
-                       "clocks": clk.summary()},
+                       "p99_ms": pctl(lat, 99), "max_ms": max(lat),
+                       "cache_hits": stats["cache_hits"], "uploads": stats["uploads"],
+                       "evictions": stats["evictions"], "clocks": clk.summary()},
             "plain": {"graphs_per_s": len(reqs) / plain_s, "p50_ms": pctl(plat, 50),
-                      "p99_ms": pctl(plat, 99)},
+                      "p99_ms": pctl(plat, 99), "max_ms": max(plat)},
         })
     return out
 
@@ -632,11 +747,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-stride", type=int, default=8,
                     help="oracle sample: every k-th endpoint vertex")
+    ap.add_argument("--no-extra-workloads", action="store_true",
+                    help="skip the vote 500x50k and uniform 2k x 1k legs")
+    ap.add_argument("--extra-steps", type=int, default=20,
+                    help="timed steps of each extra single-graph leg")
     ap.add_argument("--batch-graphs", type=int, default=BATCH_GRAPHS,
                     help="graphs in the batched leg (0 = skip the leg)")
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--batch-single-steps", type=int, default=2)
-    ap.add_argument("--serve-requests", type=int, default=200,
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests per rate in the serving leg (0 = skip the leg)")
     ap.add_argument("--serve-rates", default="50,200,400,800", help="arrival rates, req/s")
     ap.add_argument("--serve-pool", type=int, default=24)

@@ -173,9 +173,16 @@ bool alloc_all(Engine *E, std::vector<Block *> want, const Entry *keep) {
     }
 }
 
-// oldest admissible request, with its plan (caller holds the lock)
+// oldest admissible request, with its plan (caller holds the lock). A key
+// whose earlier request is still queued is not admitted again (same-key
+// requests run in arrival order).
 bb_ticket_s *pick(Engine *E, Plan &plan) {
     bool memory_blocked = false;
+    std::vector<uint64_t> waiting;  // keys with an earlier request left in the queue
+    auto skip = [&](uint64_t key) { waiting.push_back(key); };
+    auto is_waiting = [&](uint64_t key) {
+        return std::find(waiting.begin(), waiting.end(), key) != waiting.end();
+    };
     for (auto it = E->queue.begin(); it != E->queue.end();) {
         bb_ticket_s *t = *it;
         if (!t->managed) {
@@ -185,10 +192,11 @@ bb_ticket_s *pick(Engine *E, Plan &plan) {
             return t;
         }
         const bb_request &r = t->req;
+        if (is_waiting(r.key)) { ++it; continue; }
         auto ce = E->cache.find(r.key);
         if (ce != E->cache.end()) {
             Entry *e = ce->second;
-            if (e->busy) { ++it; continue; }
+            if (e->busy) { skip(r.key); ++it; continue; }
             Plan p;
             p.entry = e;
             if (r.n_flip > 0) {
@@ -200,6 +208,7 @@ bb_ticket_s *pick(Engine *E, Plan &plan) {
                         it = E->queue.erase(it);
                         continue;
                     }
+                    skip(r.key);
                     ++it;
                     continue;
                 }
@@ -215,7 +224,7 @@ bb_ticket_s *pick(Engine *E, Plan &plan) {
             it = E->queue.erase(it);
             continue;
         }
-        if (memory_blocked) { ++it; continue; }  // no overtaking for new memory
+        if (memory_blocked) { skip(r.key); ++it; continue; }  // no overtaking for new memory
         const BuildSizes bs = build_sizes(r.csr->nU, r.csr->nV, r.csr->nE);
         Plan p;
         p.fresh = true;
@@ -243,6 +252,7 @@ bb_ticket_s *pick(Engine *E, Plan &plan) {
                 continue;
             }
             memory_blocked = true;  // wait for running requests to release memory
+            skip(r.key);
             ++it;
             continue;
         }
