@@ -114,43 +114,84 @@ __global__ void k_global_rank(SideCSR S, const uint32_t *other_deg, int64_t n_ot
 }
 
 // --------------------------------------------------------------- 3. rows
-// One thread per input edge e (its row u found by binary search in rowptr):
-// the U-side entry keeps the input position within u's row; the V-side
-// entry takes the next free slot of v's row. Each entry is written as one
-// key (packed entry << 32 | input edge id) for the row sorts.
-__global__ void k_fill(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                       const int8_t *__restrict__ sign, int64_t nU, int64_t nE, SideCSR U,
-                       SideCSR V, uint32_t *cursorV, uint64_t *keyU, uint64_t *keyV) {
+// One thread per input edge e: the U-side entry keeps the input position
+// within its row u; the V-side entry takes the next free slot of v's row.
+// Each entry is written as one key (packed entry << 32 | input edge id) for
+// the row sorts. A block takes FILL_EDGES consecutive edges per step and
+// stages the slice of rowptr that covers them in shared memory (when it
+// spans at most FILL_ROWS rows), so that a thread finds its row u with a
+// search in shared memory rather than in global memory.
+constexpr int FILL_THREADS = 256;
+constexpr int FILL_EDGES = 2048;
+constexpr int FILL_ROWS = 2048;
+
+// last u in [lo, hi) with rp[u] <= e (rp[lo] <= e)
+template <typename P>
+__device__ __forceinline__ int64_t row_of(const P *rp, int64_t lo, int64_t hi, int64_t e) {
+    while (hi - lo > 1) {
+        const int64_t m = (lo + hi) >> 1;
+        if (rp[m] <= e) lo = m; else hi = m;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(FILL_THREADS) k_fill(
+    const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+    const int8_t *__restrict__ sign, int64_t nU, int64_t nE, SideCSR U, SideCSR V,
+    uint32_t *cursorV, uint64_t *keyU, uint64_t *keyV) {
+    __shared__ int64_t rp[FILL_ROWS + 1];
+    __shared__ int64_t row0, nrows;
     // warp-uniform trip counts: lanes that share a V row take their slots
     // in it with one atomic (hub rows would otherwise serialise on it)
-    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nE;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = base + threadIdx.x;
-        const bool in = e < nE;
-        uint32_t rv = 0xffffffffu, r = 0, neg = 0;
-        if (in) {
-            int64_t lo = 0, hi = nU;  // last u with rowptr[u] <= e
-            while (hi - lo > 1) {
-                const int64_t m = (lo + hi) >> 1;
-                if (rowptr[m] <= e) lo = m; else hi = m;
+    for (int64_t e0 = blockIdx.x * (int64_t)FILL_EDGES; e0 < nE;
+         e0 += (int64_t)gridDim.x * FILL_EDGES) {
+        const int64_t e1 = nE - e0 > FILL_EDGES ? e0 + FILL_EDGES : nE;
+        if (threadIdx.x == 0) {
+            const int64_t u0 = row_of(rowptr, 0, nU, e0);
+            const int64_t u1 = row_of(rowptr, u0, nU, e1 - 1);
+            row0 = u0;
+            nrows = u1 - u0 + 1;
+        }
+        __syncthreads();
+        const int64_t u0 = row0, nr = nrows;
+        const bool staged = nr <= FILL_ROWS;
+        if (staged)
+            for (int64_t i = threadIdx.x; i <= nr && u0 + i <= nU; i += FILL_THREADS)
+                rp[i] = rowptr[u0 + i];
+        __syncthreads();
+        for (int64_t eb = e0; eb < e1; eb += FILL_THREADS) {
+            const int64_t e = eb + threadIdx.x;
+            const bool in = e < e1;
+            uint32_t rv = 0xffffffffu, r = 0, neg = 0;
+            if (in) {
+                int64_t u, ru;
+                if (staged) {
+                    const int64_t k = row_of(rp, 0, nr, e);
+                    u = u0 + k;
+                    ru = rp[k];
+                } else {
+                    u = row_of(rowptr, u0, u0 + nr, e);
+                    ru = rowptr[u];
+                }
+                r = U.sr_of_id[u];
+                const int64_t pu = U.off[r] + (e - ru);
+                const uint32_t v = (uint32_t)col[e];
+                neg = sign[e] < 0 ? 1u : 0u;
+                rv = V.sr_of_id[v];
+                keyU[pu] = ((uint64_t)((rv << 1) | neg) << 32) | (uint32_t)e;
             }
-            r = U.sr_of_id[lo];
-            const int64_t pu = U.off[r] + (e - rowptr[lo]);
-            const uint32_t v = (uint32_t)col[e];
-            neg = sign[e] < 0 ? 1u : 0u;
-            rv = V.sr_of_id[v];
-            keyU[pu] = ((uint64_t)((rv << 1) | neg) << 32) | (uint32_t)e;
+            const unsigned peers = __match_any_sync(FULL, rv);
+            const unsigned lane = lane_id();
+            const int leader = __ffs(peers) - 1;
+            uint32_t b = 0;
+            if (in && (int)lane == leader) b = atomicAdd(&cursorV[rv], (uint32_t)__popc(peers));
+            b = __shfl_sync(peers, b, leader);
+            if (in) {
+                const int64_t pv = V.off[rv] + b + __popc(peers & ((1u << lane) - 1u));
+                keyV[pv] = ((uint64_t)((r << 1) | neg) << 32) | (uint32_t)e;
+            }
         }
-        const unsigned peers = __match_any_sync(FULL, rv);
-        const unsigned lane = lane_id();
-        const int leader = __ffs(peers) - 1;
-        uint32_t b = 0;
-        if (in && (int)lane == leader) b = atomicAdd(&cursorV[rv], (uint32_t)__popc(peers));
-        b = __shfl_sync(peers, b, leader);
-        if (in) {
-            const int64_t pv = V.off[rv] + b + __popc(peers & ((1u << lane) - 1u));
-            keyV[pv] = ((uint64_t)((r << 1) | neg) << 32) | (uint32_t)e;
-        }
+        __syncthreads();  // rp is rewritten by the next step
     }
 }
 
@@ -831,8 +872,8 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
     for (int sd = 0; sd < 2; sd++)
         scan_exclusive_u32_to_i64(g.side[sd].deg, g.side[sd].off, ns[sd], ptemp, s);
     if (nU > 0 && nE > 0)
-        k_fill<<<grid_for(nE, BT, 32768), BT, 0, s>>>(rowptr, col, sign, nU, nE, g.side[0],
-                                                     g.side[1], cursorV, keys[0], keys[1]); note_launch();
+        k_fill<<<grid_for(nE, FILL_EDGES, 4096), FILL_THREADS, 0, s>>>(
+            rowptr, col, sign, nU, nE, g.side[0], g.side[1], cursorV, keys[0], keys[1]); note_launch();
     // bd[k]: first rank with degree > ROW_LIMS[k]; bd[NLIMS] = n
     for (int sd = 0; sd < 2; sd++)
         if (ns[sd] > 0 && nE > 0) {

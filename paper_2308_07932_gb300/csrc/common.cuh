@@ -20,6 +20,7 @@ enum : uint32_t {
     E_DUP = 8u,         // an edge listed twice
     E_PROBE = 16u,      // hash probe bound exceeded (must not happen)
     E_INTERNAL = 64u,   // an internal bound check failed
+    E_WAIT = 128u,      // a bounded device-side wait gave up (reported as a timeout)
 };
 
 // Counter fields: per (anchor, endpoint) pair the symmetric-wedge count S in

@@ -371,6 +371,183 @@ __device__ __forceinline__ void team_rounds(const uint4 *__restrict__ smd,
     }
 }
 
+// ------------------------------------------- bulk-copy staging (async proxy)
+// Shared-memory mbarriers and non-multicast bulk copies from this GPU's
+// global memory into the CTA's own shared memory (PTX cp.async.bulk with
+// mbarrier::complete_tx).
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p;\n"
+        "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "  selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bytes (a multiple of 16, 16-byte aligned source and destination)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Bounded wait for phase `parity` of an mbarrier: false after MBAR_SPINS
+// tries (try_wait itself blocks for a short time per try), so a copy that
+// never lands turns into an error status instead of a hang.
+constexpr uint32_t MBAR_SPINS = 1u << 22;
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < MBAR_SPINS; i++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Per warp: S stages of one round (32 quads) each, each lane's entry mask
+// and sign for its quad of the stage, and the stages' mbarriers.
+template <int S>
+struct alignas(16) StageRing {
+    uint4 q[S][32];
+    uint32_t meta[S][32];
+    unsigned long long bar[S];
+};
+
+// team_rounds with the adjacency staged in shared memory by bulk copies:
+// the round at r is copied S - 1 rounds ahead of its use. Per round, the
+// lane at the head of each run of lanes in one segment copies that run's
+// quads (contiguous in the middle's row, 16-byte aligned) into the stage in
+// one cp.async.bulk; lane 0 arms the stage's mbarrier with the round's
+// bytes. A lane then reads its quad from the stage. `ring` is this warp's
+// ring; its mbarriers are initialised once per kernel (stage_ring_init).
+template <int S>
+__device__ __forceinline__ void stage_ring_init(StageRing<S> &ring, unsigned lane) {
+    if (lane == 0) {
+        for (int k = 0; k < S; k++) mbar_init(smem_addr(&ring.bar[k]), 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+}
+
+// Per-warp state of the staged walker across jobs: the parity of each
+// stage's next phase, and whether the warp may still copy (a wait that gave
+// up turns it off for the rest of the kernel: its copies are drained, its
+// later rounds skipped, the error word set).
+struct StageState {
+    uint32_t phase = 0;
+    bool ok = true;
+};
+
+template <int TS, int S, typename Seg, typename Add, typename Flush>
+__device__ __forceinline__ void team_rounds_bulk(const uint4 *__restrict__ smd,
+                                                 const uint32_t *__restrict__ oadj, int64_t rb,
+                                                 uint32_t m0, uint32_t m1, WalkSmem<TS> &sm,
+                                                 StageRing<S> &ring, StageState &ss, int t,
+                                                 uint32_t span, uint32_t *err, Seg &&seg,
+                                                 Add &&add, Flush &&flush) {
+    constexpr uint32_t NW = TS / 32;
+    const uint4 *oadj4 = reinterpret_cast<const uint4 *>(oadj);
+    const uint32_t lane = (uint32_t)t & 31u, w = (uint32_t)t >> 5;
+    const unsigned upto = (2u << lane) - 1u;
+    for (uint32_t mc = m0; mc < m1; mc += TS) {
+        uint32_t T, NZ;
+        chunk_scan<TS>(smd, rb, mc + (uint32_t)t, m1, sm, t, seg, T, NZ);
+        const uint32_t A = share<NW>(T, w), B = share<NW>(T, w + 1);
+        if (A < B && ss.ok) {
+            uint32_t kb = 0, hi = NZ;  // segment holding quad A
+            while (kb < hi) {
+                const uint32_t mid = (kb + hi) >> 1;
+                if (sm.seg[mid].incl <= A) kb = mid + 1; else hi = mid;
+            }
+            kb++;
+            const uint32_t nrounds = (B - A + 31) / 32;
+            // issues round j (quads A + 32 j ..) into stage j % S
+            auto issue = [&](uint32_t j) {
+                const uint32_t r = A + 32 * j, st = j % S;
+                const uint32_t c = kb + lane;
+                const uint32_t s0 = c < NZ ? (sm.seg[c].excl_sw & EXMASK) - r : 32u;
+                const unsigned M = __reduce_or_sync(FULL, s0 < 32u ? 1u << s0 : 0u);
+                const uint32_t k = kb - 1u + __popc(M & upto);
+                kb += __popc(M);
+                const uint32_t q = r + lane;
+                const uint32_t nv = B - r < 32u ? B - r : 32u;  // valid lanes this round
+                uint32_t vm = 0u, swq = 0u, qq = 0u;
+                if (q < B) {
+                    const QSeg d = sm.seg[k];
+                    qq = (d.st >> 2) + (q - (d.excl_sw & EXMASK));
+                    const uint32_t w0 = qq << 2;
+                    const uint32_t lo = d.st > w0 ? d.st - w0 : 0u;
+                    const uint32_t hq = d.en - w0 < 4u ? d.en - w0 : 4u;
+                    vm = (0xfu >> (4u - hq)) & (0xfu << lo);
+                    swq = d.excl_sw >> 31;
+                }
+                ring.meta[st][lane] = vm | swq << 4;
+                const uint32_t bar = smem_addr(&ring.bar[st]);
+                fence_proxy_async();  // this stage's last reads before the new copy
+                if (lane == 0) mbar_arrive_expect_tx(bar, nv * 16u);
+                __syncwarp();
+                // a run starts at lane 0 and at every segment start in the round
+                const unsigned heads = (M | 1u) & ((nv == 32u) ? FULL : ((1u << nv) - 1u));
+                if (q < B && ((heads >> lane) & 1u)) {
+                    const unsigned later = heads & ~upto;  // heads after this lane
+                    const uint32_t end = later ? (uint32_t)(__ffs(later) - 1) : nv;
+                    bulk_g2s(smem_addr(&ring.q[st][lane]), oadj4 + qq, (end - lane) * 16u, bar);
+                }
+            };
+            uint32_t issued = nrounds < (uint32_t)(S - 1) ? nrounds : (uint32_t)(S - 1);
+            for (uint32_t j = 0; j < issued; j++) issue(j);
+            uint32_t rounds = 0u;
+            for (uint32_t j = 0; j < nrounds; j++) {
+                if (issued < nrounds) issue(issued++);
+                const uint32_t st = j % S;
+                // all lanes take the same branch (one lane's wait may give up
+                // while another's sees the phase complete)
+                const bool landed = mbar_wait(smem_addr(&ring.bar[st]), (ss.phase >> st) & 1u);
+                if (!__all_sync(FULL, landed)) {
+                    // give up: drain every copy issued and not yet consumed
+                    // (again bounded), then stop copying for good
+                    set_error(err, E_WAIT);
+                    for (uint32_t i = j; i < issued; i++)
+                        mbar_wait(smem_addr(&ring.bar[i % S]), (ss.phase >> (i % S)) & 1u);
+                    ss.ok = false;
+                    break;
+                }
+                ss.phase ^= 1u << st;
+                const uint32_t meta = ring.meta[st][lane];
+                const uint32_t vm = meta & 0xfu, swq = meta >> 4;
+                if (vm) {
+                    const uint4 v = ring.q[st][lane];
+                    add(v.x, vm & 1u, swq);
+                    add(v.y, (vm >> 1) & 1u, swq);
+                    add(v.z, (vm >> 2) & 1u, swq);
+                    add(v.w, vm >> 3, swq);
+                }
+                __syncwarp();
+                if (++rounds == span) { flush(); rounds = 0u; }
+            }
+            flush();
+        }
+        team_sync<TS>();
+    }
+}
+
 // Wedge walker, per thread: the wedges [a, b) of a compacted chunk whose
 // prefix is in wedges, U loads in flight per step, one(entry, sign bit of
 // the anchor's edge) per wedge. For segment families whose per-wedge work
@@ -872,16 +1049,24 @@ __global__ void __launch_bounds__(CTAH_THREADS) k_ctah(DevGraph G) {
 }
 
 // ------------------------------------------------------------ dense class
+// Dense CTAs stage the middles' rows in shared memory by bulk copies
+// (DENSE_STAGES rounds per warp in flight) when DENSE_STAGED is set;
+// otherwise each lane loads its quads itself, one round ahead.
+constexpr bool DENSE_STAGED = false;
+constexpr int DENSE_STAGES = 4;
+
 struct alignas(16) DenseSmem {
     uint32_t cnt[DENSE_CAP];
     WalkSmem<DENSE_THREADS> walk;
+    StageRing<DENSE_STAGES> ring[DENSE_STAGED ? DENSE_THREADS / 32 : 1];
     uint32_t job, last;
 };
 
 // one dense job (an anchor, or one middle slice of a split anchor), walked
 // by the whole CTA; adds each thread's part of its sums to bal and tot
 __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, const DenseJob &J,
-                                          unsigned long long &bal, unsigned long long &tot) {
+                                          StageState &ss, unsigned long long &bal,
+                                          unsigned long long &tot) {
     const int t = threadIdx.x;
     const bool sv = J.anchor & 1u;
     const SideCSR &S = sv ? G.side[1] : G.side[0];
@@ -914,18 +1099,29 @@ __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, cons
             tot += t32;
             b32 = t32 = 0;
         };
-        if (windows) {
-            team_rounds<DENSE_THREADS, true>(
-                A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t, SUM_SPAN,
-                [&](const uint4 &d, long long &st, uint32_t &l) {
-                    const long long s0 = lower_bound_u32(A.oadj, d.x, d.z, e0 << 1);
-                    st = s0;
-                    l = (uint32_t)(lower_bound_u32(A.oadj, s0, d.z, e1 << 1) - s0);
-                },
-                add, flush);
+        auto clipped = [&](const uint4 &d, long long &st, uint32_t &l) {
+            const long long s0 = lower_bound_u32(A.oadj, d.x, d.z, e0 << 1);
+            st = s0;
+            l = (uint32_t)(lower_bound_u32(A.oadj, s0, d.z, e1 << 1) - s0);
+        };
+        if constexpr (DENSE_STAGED) {
+            StageRing<DENSE_STAGES> &ring = sm.ring[t >> 5];
+            if (windows)
+                team_rounds_bulk<DENSE_THREADS, DENSE_STAGES>(A.smd, A.oadj, A.rb, J.m0, J.m1,
+                                                              sm.walk, ring, ss, t, SUM_SPAN,
+                                                              &G.scratch->err, clipped, add, flush);
+            else
+                team_rounds_bulk<DENSE_THREADS, DENSE_STAGES>(A.smd, A.oadj, A.rb, J.m0, J.m1,
+                                                              sm.walk, ring, ss, t, SUM_SPAN,
+                                                              &G.scratch->err, FullSeg{}, add,
+                                                              flush);
         } else {
-            team_rounds<DENSE_THREADS, true>(A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t,
-                                             SUM_SPAN, FullSeg{}, add, flush);
+            if (windows)
+                team_rounds<DENSE_THREADS, true>(A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t,
+                                                 SUM_SPAN, clipped, add, flush);
+            else
+                team_rounds<DENSE_THREADS, true>(A.smd, A.oadj, A.rb, J.m0, J.m1, sm.walk, t,
+                                                 SUM_SPAN, FullSeg{}, add, flush);
         }
         if (J.group != NO_GROUP) {
             // merge this part's counts into the group's global counters; a
@@ -1013,10 +1209,12 @@ __device__ __noinline__ void dense_job_wide(const DevGraph &G, DenseSmem &sm, co
     }
 }
 
-__global__ void __launch_bounds__(DENSE_THREADS, 3) k_dense(DevGraph G) {
+__global__ void __launch_bounds__(DENSE_THREADS, DENSE_STAGED ? 2 : 3) k_dense(DevGraph G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DenseSmem &sm = *reinterpret_cast<DenseSmem *>(smem_raw);
     const uint32_t njobs = G.ctr[CTR_DENSE];
+    StageState ss;
+    if constexpr (DENSE_STAGED) stage_ring_init(sm.ring[threadIdx.x >> 5], lane_id());
     unsigned long long bal = 0, tot = 0;  // summed over all jobs of this CTA
     for (;;) {
         if (threadIdx.x == 0) sm.job = atomicAdd(&G.scratch->job_next[CLS_DENSE], 1u);
@@ -1026,7 +1224,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 3) k_dense(DevGraph G) {
         if (jid >= njobs) break;
         const DenseJob J = G.dense_jobs[jid];
         if (J.group == WIDE_JOB) dense_job_wide(G, sm, J, bal, tot);
-        else dense_job(G, sm, J, bal, tot);
+        else dense_job(G, sm, J, ss, bal, tot);
         spill_if_large(G.scratch, bal, tot);
     }
     flush_warp(G.scratch, bal, tot);
@@ -1117,6 +1315,8 @@ __global__ void __launch_bounds__(CTAH_THREADS) k_ctah_batch(BatchArgs B) {
 __global__ void __launch_bounds__(DENSE_THREADS) k_dense_batch(BatchArgs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DenseSmem &sm = *reinterpret_cast<DenseSmem *>(smem_raw);
+    StageState ss;
+    if constexpr (DENSE_STAGED) stage_ring_init(sm.ring[threadIdx.x >> 5], lane_id());
     const uint32_t *p = B.prefix + (size_t)CLS_DENSE * (B.n + 1);
     const uint32_t total = p[B.n];
     for (;;) {
@@ -1130,7 +1330,7 @@ __global__ void __launch_bounds__(DENSE_THREADS) k_dense_batch(BatchArgs B) {
         unsigned long long bal = 0, tot = 0;
         const DenseJob J = G.dense_jobs[it - p[gi]];
         if (J.group == WIDE_JOB) dense_job_wide(G, sm, J, bal, tot);
-        else dense_job(G, sm, J, bal, tot);
+        else dense_job(G, sm, J, ss, bal, tot);
         spill_if_large(G.scratch, bal, tot);
         block_sum2<DENSE_THREADS>(bal, tot);
         if (threadIdx.x == 0) acc_add(G.scratch, bal, tot);
