@@ -228,6 +228,38 @@ typedef struct {
 BB_API bb_status bb_ctx_set_timing(bb_ctx *ctx, int enable);
 BB_API bb_status bb_ctx_last_timing(const bb_ctx *ctx, bb_timing *out);
 
+/* ------------------------------------------------------ bucket shapes
+ * The work classes of a graph's anchors (Algorithm 2's per-start work,
+ * bucketed by wedge count and endpoint range; this library's division of
+ * the paper's bucket loop into kernels) have runtime bounds, none of which
+ * changes a count:
+ *   warp_w_max:   warp-class anchors have at most this many wedges
+ *                 (1..16384, default 16384; degree <= 255 is fixed);
+ *   warp_small_w: warp-class anchors with at most this many wedges keep
+ *                 every endpoint in a hash instead of the hub window
+ *                 (0..warp_w_max, default 32);
+ *   team_w_max:   team-class anchors have at most this many wedges
+ *                 (1..16384, default 16384);
+ *   split_wedges: a dense anchor is split over CTAs into parts of at least
+ *                 this many wedges (1024..2^30, default 65536).
+ * dense_staged (0/1, default 0): the dense-class walker stages the
+ * middles' rows in shared memory by bulk copies instead of loading them
+ * directly.
+ * bb_ctx_set_shape: used by the context's later one-shot counts and
+ *   uploads (shape NULL = the defaults). BB_ERR_INVALID_ARG outside the
+ *   ranges above.
+ * bb_graph_set_shape: re-classifies a resident graph (its rows are kept;
+ *   blocking; uses the context's build workspace). */
+typedef struct {
+    uint32_t warp_w_max;
+    uint32_t warp_small_w;
+    uint32_t team_w_max;
+    uint32_t split_wedges;
+} bb_class_shape;
+
+BB_API bb_status bb_ctx_set_shape(bb_ctx *ctx, const bb_class_shape *shape, int dense_staged);
+BB_API bb_status bb_graph_set_shape(bb_graph *g, const bb_class_shape *shape, int dense_staged);
+
 /* ------------------------------------------------------------- batches
  * Many resident graphs counted together: every graph's wedge work goes
  * into one shared work queue per work class (dense-counter, CTA-hash, team
@@ -257,15 +289,22 @@ BB_API bb_status bb_ctx_last_timing(const bb_ctx *ctx, bb_timing *out);
  *   (dense, CTA-hash, team, warp). warp_chunk: warp anchors a warp takes
  *   per grab (1..1024); concurrent: 1 = the class kernels run on separate
  *   streams at once, 0 = one after another; grid_frac: each class kernel's
- *   grid as a fraction (0, 1] of its full-occupancy grid.
+ *   grid as a fraction (0, 1] of its full-occupancy grid; dense_staged: as
+ *   above, for the whole batch. shape[k]: the bucket shape of the members
+ *   in size class k (fewer than 2^14, 2^17, 2^20 edges, and the rest); a
+ *   changed shape re-classifies that class's members (blocking).
  * bb_batch_autotune: times candidate shapes on this batch (each `reps`
- *   times, median) by coordinate descent, keeps the fastest (also written to
+ *   times, median) by coordinate descent over the launch shapes and each
+ *   size class's bucket shape, keeps the fastest (also written to
  *   best_opt) and its time (best_ms_opt). Runs the counts it times. */
+#define BB_NSIZE 4
 typedef struct bb_batch bb_batch;
 typedef struct {
     uint32_t warp_chunk;
     uint32_t concurrent;
     float grid_frac[BB_NKERNELS];
+    uint32_t dense_staged;
+    bb_class_shape shape[BB_NSIZE];
 } bb_batch_tune;
 
 BB_API bb_status bb_batch_create(bb_ctx *ctx, bb_graph *const *graphs, int64_t n, bb_batch **out);

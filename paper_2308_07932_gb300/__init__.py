@@ -53,15 +53,40 @@ class _Timing(ctypes.Structure):
                 ("middles", ctypes.c_int64 * len(KERNELS)),
                 ("anchors", ctypes.c_int64 * len(KERNELS))]
 
+class ClassShape(ctypes.Structure):
+    """Bucket shape of a graph's work classes (``bb_class_shape``)."""
+    _fields_ = [("warp_w_max", ctypes.c_uint32), ("warp_small_w", ctypes.c_uint32),
+                ("team_w_max", ctypes.c_uint32), ("split_wedges", ctypes.c_uint32)]
+    FIELDS = ("warp_w_max", "warp_small_w", "team_w_max", "split_wedges")
+    DEFAULT = {"warp_w_max": 16384, "warp_small_w": 32, "team_w_max": 16384,
+               "split_wedges": 65536}
+
+    def to_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k in self.FIELDS}
+
+    @classmethod
+    def from_dict(cls, d: dict | None) -> "ClassShape":
+        t = cls()
+        for k in cls.FIELDS:
+            setattr(t, k, int((d or cls.DEFAULT).get(k, cls.DEFAULT[k])))
+        return t
+
+
+NSIZE = 4  # batch size classes: < 2^14, < 2^17, < 2^20 edges, the rest
+
+
 class BatchTune(ctypes.Structure):
-    """Launch shapes of a batch (``bb_batch_tune``); per-class fields in
-    ``KERNELS`` order."""
+    """Launch and bucket shapes of a batch (``bb_batch_tune``); per-class
+    fields in ``KERNELS`` order, bucket shapes per size class."""
     _fields_ = [("warp_chunk", ctypes.c_uint32), ("concurrent", ctypes.c_uint32),
-                ("grid_frac", ctypes.c_float * len(KERNELS))]
+                ("grid_frac", ctypes.c_float * len(KERNELS)), ("dense_staged", ctypes.c_uint32),
+                ("shape", ClassShape * NSIZE)]
 
     def to_dict(self) -> dict:
         return {"warp_chunk": int(self.warp_chunk), "concurrent": int(self.concurrent),
-                "grid_frac": {k: round(float(f), 4) for k, f in zip(KERNELS, self.grid_frac)}}
+                "grid_frac": {k: round(float(f), 4) for k, f in zip(KERNELS, self.grid_frac)},
+                "dense_staged": int(self.dense_staged),
+                "shape": [s.to_dict() for s in self.shape]}
 
     @classmethod
     def from_dict(cls, d: dict) -> "BatchTune":
@@ -70,6 +95,10 @@ class BatchTune(ctypes.Structure):
         t.concurrent = int(d["concurrent"])
         for i, k in enumerate(KERNELS):
             t.grid_frac[i] = float(d["grid_frac"][k])
+        t.dense_staged = int(d.get("dense_staged", 0))
+        shapes = d.get("shape") or [None] * NSIZE
+        for i in range(NSIZE):
+            t.shape[i] = ClassShape.from_dict(shapes[i])
         return t
 
 
@@ -123,6 +152,8 @@ def lib() -> ctypes.CDLL:
             "bb_ctx_set_timing": (S, [_VP, ctypes.c_int]),
             "bb_ctx_last_timing": (S, [_VP, ctypes.POINTER(_Timing)]),
             "bb_launch_count": (ctypes.c_uint64, []),
+            "bb_ctx_set_shape": (S, [_VP, ctypes.POINTER(ClassShape), ctypes.c_int]),
+            "bb_graph_set_shape": (S, [_VP, ctypes.POINTER(ClassShape), ctypes.c_int]),
             "bb_batch_create": (S, [_VP, ctypes.POINTER(_VP), ctypes.c_int64, ctypes.POINTER(_VP)]),
             "bb_batch_count": (S, [_VP, _I64P, _I64P, ctypes.POINTER(ctypes.c_int)]),
             "bb_batch_set_tune": (S, [_VP, ctypes.POINTER(BatchTune)]),
@@ -221,6 +252,14 @@ class Context:
                 "kernels": {k: {"ms": t.kernel_ms[i], "wedges": t.wedges[i],
                                 "middles": t.middles[i], "anchors": t.anchors[i]}
                             for i, k in enumerate(KERNELS)}}
+
+    def set_shape(self, shape: dict | None = None, dense_staged: bool = False):
+        """Bucket shape (``bb_ctx_set_shape``) of later one-shot counts and
+        uploads: a dict of ``ClassShape.FIELDS`` (missing keys take their
+        defaults), None for the defaults."""
+        sh = ClassShape.from_dict(shape) if shape is not None else None
+        _check(lib().bb_ctx_set_shape(self._h, ctypes.byref(sh) if sh is not None else None,
+                                      int(dense_staged)))
 
     def set_stream(self, stream_ptr: int | None):
         """Run on a cudaStream_t given as an integer handle (e.g.
@@ -375,6 +414,12 @@ class Graph:
         _check(lib().bb_count(self._h, ctypes.byref(b), ctypes.byref(t),
                               pv.ctypes.data if pv is not None else None))
         return Counts(b.value, t.value, w, pv)
+
+    def set_shape(self, shape: dict | None = None, dense_staged: bool = False):
+        """Re-classifies the graph with a bucket shape (``bb_graph_set_shape``)."""
+        sh = ClassShape.from_dict(shape) if shape is not None else None
+        _check(lib().bb_graph_set_shape(self._h, ctypes.byref(sh) if sh is not None else None,
+                                        int(dense_staged)))
 
     def count_edges(self) -> tuple[np.ndarray, int, int]:
         """Balanced butterflies containing each edge (input CSR order), and

@@ -69,6 +69,39 @@ bb_status bb::wait_bounded(cudaStream_t s, const char *what) {
     return BB_OK;
 }
 
+bb_status bb::shape_params(const bb_class_shape *shape, ClassifyParams *out) {
+    ClassifyParams p;
+    if (shape) {
+        if (shape->warp_w_max < 1 || shape->warp_w_max > WARP_W_MAX)
+            return fail(BB_ERR_INVALID_ARG, "warp_w_max %u outside [1, %llu]", shape->warp_w_max,
+                        (unsigned long long)WARP_W_MAX);
+        if (shape->warp_small_w > shape->warp_w_max)
+            return fail(BB_ERR_INVALID_ARG, "warp_small_w %u above warp_w_max %u",
+                        shape->warp_small_w, shape->warp_w_max);
+        if (shape->team_w_max < 1 || shape->team_w_max > TEAM_W_MAX)
+            return fail(BB_ERR_INVALID_ARG, "team_w_max %u outside [1, %llu]", shape->team_w_max,
+                        (unsigned long long)TEAM_W_MAX);
+        if (shape->split_wedges < 1024 || shape->split_wedges > (1u << 30))
+            return fail(BB_ERR_INVALID_ARG, "split_wedges %u outside [1024, 2^30]",
+                        shape->split_wedges);
+        p.warp_w_max = shape->warp_w_max;
+        p.warp_small_w = shape->warp_small_w;
+        p.team_w_max = shape->team_w_max;
+        p.split_wedges = shape->split_wedges;
+    }
+    *out = p;
+    return BB_OK;
+}
+
+bb_class_shape bb::shape_public(const ClassifyParams &p) {
+    bb_class_shape s;
+    s.warp_w_max = p.warp_w_max;
+    s.warp_small_w = p.warp_small_w;
+    s.team_w_max = p.team_w_max;
+    s.split_wedges = p.split_wedges;
+    return s;
+}
+
 // The same bound without creating anything (no event): polls the stream
 // until it is idle. For paths that must not create CUDA objects.
 bb_status bb::wait_stream_bounded(cudaStream_t s, const char *what) {
@@ -237,10 +270,11 @@ bb_status finish_count(bb_ctx *ctx, const DevGraph &g, cudaStream_t s, int64_t *
 // caller launches directly then.
 bool replay_step(bb_ctx *ctx, DevGraph &g, const bb_csr *csr, const int8_t *signs) {
     // the degree sort's key width depends on the inputs' largest degree
-    const void *key[10] = {(const void *)(intptr_t)csr->nU, (const void *)(intptr_t)csr->nV,
+    const void *key[11] = {(const void *)(intptr_t)csr->nU, (const void *)(intptr_t)csr->nV,
                            (const void *)(intptr_t)csr->nE, csr->rowptr, csr->col, signs,
                            ctx->ws_temp, ctx->ws_graph, (const void *)(intptr_t)ctx->timing,
-                           (const void *)(intptr_t)g.deg_bits};
+                           (const void *)(intptr_t)g.deg_bits,
+                           (const void *)(intptr_t)ctx->shape_version};
     static_assert(sizeof(key) == sizeof(ctx->step_key), "step key size");
     static_assert(sizeof(key) == sizeof(ctx->step_last), "step key size");
     cudaStream_t s = ctx->stream;
@@ -311,6 +345,8 @@ bb_status count_device(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int6
         ctx->layout_key[0] = nU; ctx->layout_key[1] = nV; ctx->layout_key[2] = nE;
     }
     if (ctx->timing) BB_CUDA(cudaEventRecord(ctx->ev[0], s), "event");
+    g.cls = ctx->shape;
+    g.dense_staged = ctx->dense_staged;
     uint32_t verr = 0;
     {
         Range r("validate");
@@ -434,6 +470,48 @@ bb_status bb_set_wait_timeout(double seconds) {
     if (!(seconds > 0.0 && seconds <= 86400.0))
         return fail(BB_ERR_INVALID_ARG, "timeout %g s outside (0, 86400]", seconds);
     g_timeout_s.store(seconds, std::memory_order_relaxed);
+    return BB_OK;
+}
+
+bb_status bb_ctx_set_shape(bb_ctx *ctx, const bb_class_shape *shape, int dense_staged) {
+    if (!ctx) return fail(BB_ERR_INVALID_ARG, "NULL context");
+    if (dense_staged != 0 && dense_staged != 1)
+        return fail(BB_ERR_INVALID_ARG, "dense_staged must be 0 or 1");
+    ClassifyParams p;
+    bb_status st = shape_params(shape, &p);
+    if (st != BB_OK) return st;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->shape = p;
+    ctx->dense_staged = dense_staged != 0;
+    ctx->shape_version++;
+    return BB_OK;
+}
+
+bb_status bb_graph_set_shape(bb_graph *G, const bb_class_shape *shape, int dense_staged) {
+    if (!G) return fail(BB_ERR_INVALID_ARG, "graph is NULL");
+    if (dense_staged != 0 && dense_staged != 1)
+        return fail(BB_ERR_INVALID_ARG, "dense_staged must be 0 or 1");
+    ClassifyParams p;
+    bb_status st = shape_params(shape, &p);
+    if (st != BB_OK) return st;
+    bb_ctx *ctx = G->ctx;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if ((st = set_device(ctx)) != BB_OK) return st;
+    st = ensure(ctx, &ctx->ws_temp, &ctx->ws_temp_cap, classify_temp_bytes(G->g.nU, G->g.nV),
+                "build workspace");
+    if (st != BB_OK) return st;
+    cudaStream_t s = ctx->stream;
+    G->g.cls = p;
+    G->g.dense_staged = dense_staged != 0;
+    classify_graph(G->g, ctx->ws_temp, s);
+    BB_CUDA(cudaGetLastError(), "classification");
+    BB_CUDA(cudaMemcpyAsync(ctx->h_res->ctr, G->g.ctr, sizeof(ctx->h_res->ctr),
+                            cudaMemcpyDeviceToHost, s), "copy class counters");
+    BB_CUDA(cudaMemcpyAsync(ctx->h_res->cls_stats, G->g.cls_stats, sizeof(ctx->h_res->cls_stats),
+                            cudaMemcpyDeviceToHost, s), "copy class statistics");
+    if ((st = wait_bounded(s, "classification")) != BB_OK) return st;
+    memcpy(G->g.h_ctr, ctx->h_res->ctr, sizeof(G->g.h_ctr));
+    memcpy(G->g.h_cls_stats, ctx->h_res->cls_stats, sizeof(G->g.h_cls_stats));
     return BB_OK;
 }
 
@@ -562,6 +640,8 @@ static bb_status upload_impl(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs
     int8_t *sg = G->g.sign;
     layout_graph(G->g, nU, nV, nE, G->mem);
     G->g.rowptr = rp; G->g.col = cl; G->g.sign = sg;
+    G->g.cls = ctx->shape;
+    G->g.dense_staged = ctx->dense_staged;
     cudaMemsetAsync(G->g.gpart, 0, (size_t)G->g.gpart_cap * 4, s);
     cudaMemsetAsync(G->g.gdone, 0, MAX_SPLIT_JOBS * 4, s);
     uint32_t verr = 0;

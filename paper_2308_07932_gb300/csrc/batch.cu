@@ -27,6 +27,11 @@ struct bb_batch {
     cudaGraphExec_t exec = nullptr;
     cudaStream_t exec_stream = nullptr;  // stream the graph was captured on
     uint64_t exec_launches = 0;          // kernels in one replay
+    std::vector<int> size_cls;           // each member's size class
+    // re-classification: device scratch (classification temp, then the
+    // gathered class counters and statistics), allocated on first use
+    void *cmem = nullptr;
+    size_t cbytes = 0;
 };
 
 namespace {
@@ -36,30 +41,118 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // public tune (kernel order dense, CTA-hash, team, warp) <-> class order
 constexpr int KERNEL_CLS[BB_NKERNELS] = {CLS_DENSE, CLS_CTAH, CLS_TEAM, CLS_WARP};
 
-bb_status check_tune(const bb_batch_tune &t) {
+static_assert(BB_NSIZE == NSIZE, "size classes");
+
+// checks t and converts it (kernel order dense, CTA-hash, team, warp ->
+// class order; public shapes -> classification parameters)
+bb_status to_internal(const bb_batch_tune &t, BatchTune *out) {
     if (t.warp_chunk < 1 || t.warp_chunk > 1024)
         return fail(BB_ERR_INVALID_ARG, "warp_chunk %u outside [1, 1024]", t.warp_chunk);
     if (t.concurrent > 1) return fail(BB_ERR_INVALID_ARG, "concurrent must be 0 or 1");
+    if (t.dense_staged > 1) return fail(BB_ERR_INVALID_ARG, "dense_staged must be 0 or 1");
     for (int k = 0; k < BB_NKERNELS; k++)
         if (!(t.grid_frac[k] > 0.f && t.grid_frac[k] <= 1.f))
             return fail(BB_ERR_INVALID_ARG, "grid_frac[%d] outside (0, 1]", k);
-    return BB_OK;
-}
-
-BatchTune to_internal(const bb_batch_tune &t) {
     BatchTune T;
     T.warp_chunk = t.warp_chunk;
     T.concurrent = t.concurrent;
+    T.dense_staged = t.dense_staged;
     for (int k = 0; k < BB_NKERNELS; k++) T.grid_frac[KERNEL_CLS[k]] = t.grid_frac[k];
-    return T;
+    for (int k = 0; k < NSIZE; k++) {
+        bb_status st = shape_params(&t.shape[k], &T.shape[k]);
+        if (st != BB_OK) return st;
+    }
+    *out = T;
+    return BB_OK;
 }
 
 bb_batch_tune to_public(const BatchTune &T) {
     bb_batch_tune t;
     t.warp_chunk = T.warp_chunk;
     t.concurrent = T.concurrent;
+    t.dense_staged = T.dense_staged;
     for (int k = 0; k < BB_NKERNELS; k++) t.grid_frac[k] = T.grid_frac[KERNEL_CLS[k]];
+    for (int k = 0; k < NSIZE; k++) t.shape[k] = shape_public(T.shape[k]);
     return t;
+}
+
+bool same_params(const ClassifyParams &a, const ClassifyParams &b) {
+    return a.warp_w_max == b.warp_w_max && a.warp_small_w == b.warp_small_w &&
+           a.team_w_max == b.team_w_max && a.split_wedges == b.split_wedges;
+}
+
+// class item prefixes over the members (from their host class counters),
+// uploaded; the per-class item totals and work statistics updated
+bb_status rebuild_prefix(bb_batch *b) {
+    const uint32_t n = b->n;
+    std::vector<uint32_t> prefix((size_t)NCLS * (n + 1));
+    for (int c = 0; c < NCLS; c++) {
+        uint64_t acc = 0;
+        for (uint32_t i = 0; i < n; i++) {
+            prefix[(size_t)c * (n + 1) + i] = (uint32_t)acc;
+            acc += b->graphs[i]->g.h_ctr[c];
+        }
+        if (acc >= UINT32_MAX)
+            return fail(BB_ERR_TOO_LARGE, "batch has %llu items of one class (limit 2^32-1)",
+                        (unsigned long long)acc);
+        prefix[(size_t)c * (n + 1) + n] = (uint32_t)acc;
+        b->L.items[c] = (uint32_t)acc;
+    }
+    for (int k = 0; k < 3 * NCLS; k++) b->cls_stats[k] = 0;
+    for (uint32_t i = 0; i < n; i++)
+        for (int k = 0; k < 3 * NCLS; k++) b->cls_stats[k] += b->graphs[i]->g.h_cls_stats[k];
+    cudaStream_t s = b->ctx->stream;
+    BB_CUDA(cudaMemcpyAsync((void *)b->L.prefix, prefix.data(), prefix.size() * 4,
+                            cudaMemcpyHostToDevice, s), "copy class prefixes");
+    // the host vector must outlive the copy
+    return wait_bounded(s, "class prefixes");
+}
+
+// gives every member its size class's bucket shape (re-classifying those
+// whose shape changes) and rebuilds the class prefixes
+bb_status apply_shapes(bb_batch *b, const BatchTune &T) {
+    bb_ctx *ctx = b->ctx;
+    cudaStream_t s = ctx->stream;
+    std::vector<uint32_t> todo;
+    for (uint32_t i = 0; i < b->n; i++)
+        if (!same_params(b->graphs[i]->g.cls, T.shape[b->size_cls[i]])) todo.push_back(i);
+    if (todo.empty()) return BB_OK;
+    if (!b->cmem) {
+        size_t tmp = 0;
+        for (bb_graph *g : b->graphs) tmp = std::max(tmp, classify_temp_bytes(g->g.nU, g->g.nV));
+        b->cbytes = align256(tmp) + align256((size_t)b->n * NCTR * 4) +
+                    align256((size_t)b->n * 3 * NCLS * 8);
+        bb_status st = dev_alloc(ctx, &b->cmem, b->cbytes, "batch re-classification");
+        if (st != BB_OK) { b->cmem = nullptr; return st; }
+    }
+    size_t tmp = 0;
+    for (bb_graph *g : b->graphs) tmp = std::max(tmp, classify_temp_bytes(g->g.nU, g->g.nV));
+    char *p = (char *)b->cmem;
+    uint32_t *d_ctr = (uint32_t *)(p + align256(tmp));
+    unsigned long long *d_stats =
+        (unsigned long long *)(p + align256(tmp) + align256((size_t)b->n * NCTR * 4));
+    for (uint32_t i : todo) {
+        DevGraph &g = b->graphs[i]->g;
+        g.cls = T.shape[b->size_cls[i]];
+        classify_graph(g, b->cmem, s);  // one after another on s: the scratch is shared
+    }
+    BB_CUDA(cudaGetLastError(), "re-classification");
+    launch_batch_classes(b->L, d_ctr, d_stats, s);
+    BB_CUDA(cudaGetLastError(), "class counter gather");
+    bb_status st = wait_bounded(s, "re-classification");
+    if (st != BB_OK) return st;
+    std::vector<uint32_t> h_ctr((size_t)b->n * NCTR);
+    std::vector<unsigned long long> h_stats((size_t)b->n * 3 * NCLS);
+    BB_CUDA(cudaMemcpy(h_ctr.data(), d_ctr, h_ctr.size() * 4, cudaMemcpyDeviceToHost),
+            "copy class counters");
+    BB_CUDA(cudaMemcpy(h_stats.data(), d_stats, h_stats.size() * 8, cudaMemcpyDeviceToHost),
+            "copy class statistics");
+    for (uint32_t i = 0; i < b->n; i++) {
+        DevGraph &g = b->graphs[i]->g;
+        memcpy(g.h_ctr, &h_ctr[(size_t)i * NCTR], sizeof(g.h_ctr));
+        memcpy(g.h_cls_stats, &h_stats[(size_t)i * 3 * NCLS], sizeof(g.h_cls_stats));
+    }
+    return rebuild_prefix(b);
 }
 
 void drop_exec(bb_batch *b) {
@@ -126,26 +219,10 @@ bb_status bb_batch_create(bb_ctx *ctx, bb_graph *const *graphs, int64_t n, bb_ba
     b->ctx = ctx;
     b->n = (uint32_t)n;
     b->graphs.assign(graphs, graphs + n);
-    for (int64_t i = 0; i < n; i++)
-        for (int k = 0; k < 3 * NCLS; k++) b->cls_stats[k] += graphs[i]->g.h_cls_stats[k];
-    // class item prefixes over the graphs
-    std::vector<uint32_t> prefix((size_t)NCLS * (n + 1));
-    for (int c = 0; c < NCLS; c++) {
-        uint64_t acc = 0;
-        for (int64_t i = 0; i < n; i++) {
-            prefix[(size_t)c * (n + 1) + i] = (uint32_t)acc;
-            acc += graphs[i]->g.h_ctr[c];
-        }
-        if (acc >= UINT32_MAX) {
-            delete b;
-            return fail(BB_ERR_TOO_LARGE, "batch has %llu items of one class (limit 2^32-1)",
-                        (unsigned long long)acc);
-        }
-        prefix[(size_t)c * (n + 1) + n] = (uint32_t)acc;
-        b->L.items[c] = (uint32_t)acc;
-    }
+    b->size_cls.resize((size_t)n);
+    for (int64_t i = 0; i < n; i++) b->size_cls[i] = size_class(graphs[i]->g.nE);
     const size_t b_graphs = align256(sizeof(DevGraph) * (size_t)n);
-    const size_t b_prefix = align256(prefix.size() * 4);
+    const size_t b_prefix = align256((size_t)NCLS * (n + 1) * 4);
     const size_t b_next = 256;
     const size_t b_out = align256((size_t)n * BATCH_OUT * 8);
     b->bytes = b_graphs + b_prefix + b_next + b_out;
@@ -169,12 +246,13 @@ bb_status bb_batch_create(bb_ctx *ctx, bb_graph *const *graphs, int64_t n, bb_ba
     if (e == cudaSuccess)
         e = cudaMemcpyAsync((void *)b->L.graphs, descs.data(), sizeof(DevGraph) * (size_t)n,
                             cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync((void *)b->L.prefix, prefix.data(), prefix.size() * 4,
-                            cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) { bb_batch_free(b); return cuda_fail(e, "batch set-up"); }
     // the host arrays above must stay alive until the copies are done
     st = wait_bounded(s, "batch set-up");
+    // members whose shape differs from their size class's default shape are
+    // re-classified; then the class prefixes
+    if (st == BB_OK) st = apply_shapes(b, b->tune);
+    if (st == BB_OK) st = rebuild_prefix(b);
     if (st != BB_OK) { bb_batch_free(b); return st; }
     *out = b;
     return BB_OK;
@@ -239,11 +317,14 @@ bb_status bb_batch_count(bb_batch *b, int64_t *balanced, int64_t *total, bb_stat
 
 bb_status bb_batch_set_tune(bb_batch *b, const bb_batch_tune *tune) {
     if (!b || !tune) return fail(BB_ERR_INVALID_ARG, "NULL argument");
-    bb_status st = check_tune(*tune);
+    BatchTune T;
+    bb_status st = to_internal(*tune, &T);
     if (st != BB_OK) return st;
     std::lock_guard<std::mutex> lk(b->ctx->mu);
-    b->tune = to_internal(*tune);
+    if ((st = set_device(b->ctx)) != BB_OK) return st;
     drop_exec(b);  // recaptured with the new shapes on the next count
+    if ((st = apply_shapes(b, T)) != BB_OK) return st;
+    b->tune = T;
     return BB_OK;
 }
 
@@ -315,8 +396,55 @@ bb_status bb_batch_autotune(bb_batch *b, int reps, bb_batch_tune *best_opt, doub
             }
         }
     }
+    // the dense walker, then each size class's bucket shape, one knob at a time
+    for (uint32_t staged = 0; staged < 2 && st == BB_OK; staged++) {
+        if (staged == best.dense_staged || b->L.items[CLS_DENSE] == 0) continue;
+        BatchTune T = best;
+        T.dense_staged = staged;
+        double ms;
+        if ((st = time_of(T, &ms)) == BB_OK && ms < best_ms) { best = T; best_ms = ms; }
+    }
+    bool have[NSIZE] = {};
+    for (int c : b->size_cls) have[c] = true;
+    const uint32_t small_w[] = {0, 16, 32, 96};
+    const uint32_t warp_w[] = {2048, 8192, 16384};
+    const uint32_t team_w[] = {4096, 16384};
+    const uint32_t split_w[] = {16384, 65536, 262144};
+    for (int k = 0; k < NSIZE && st == BB_OK; k++) {
+        if (!have[k]) continue;
+        auto tryp = [&](const ClassifyParams &p) {
+            if (st != BB_OK || same_params(p, best.shape[k])) return;
+            BatchTune T = best;
+            T.shape[k] = p;
+            double ms;
+            if ((st = apply_shapes(b, T)) != BB_OK) return;
+            if ((st = time_of(T, &ms)) == BB_OK && ms < best_ms) { best = T; best_ms = ms; }
+        };
+        for (uint32_t v : small_w) {
+            ClassifyParams p = best.shape[k];
+            p.warp_small_w = std::min(v, p.warp_w_max);
+            tryp(p);
+        }
+        for (uint32_t v : warp_w) {
+            ClassifyParams p = best.shape[k];
+            p.warp_w_max = v;
+            p.warp_small_w = std::min(p.warp_small_w, v);
+            tryp(p);
+        }
+        for (uint32_t v : team_w) {
+            ClassifyParams p = best.shape[k];
+            p.team_w_max = v;
+            tryp(p);
+        }
+        for (uint32_t v : split_w) {
+            ClassifyParams p = best.shape[k];
+            p.split_wedges = v;
+            tryp(p);
+        }
+    }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
+    if (st == BB_OK) st = apply_shapes(b, best);
     if (st != BB_OK) return st;
     b->tune = best;
     drop_exec(b);
@@ -345,6 +473,7 @@ void bb_batch_free(bb_batch *b) {
         if (b->ev[k]) cudaEventDestroy(b->ev[k]);
     if (b->h_out) cudaFreeHost(b->h_out);
     dev_free(ctx, b->mem, b->bytes);
+    dev_free(ctx, b->cmem, b->cbytes);
     delete b;
 }
 

@@ -549,17 +549,19 @@ __global__ void k_classify(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
             // hash classes also keep their wedge prefixes below 2^31.
             const bool wide = deg > MAX_DEGREE;
             uint32_t cls;
+            const ClassifyParams &P = G.cls;
             if (wide) cls = CLS_DENSE;
-            else if (deg <= WARP_DEG_MAX && W <= WARP_W_MAX &&
-                (W <= WARP_SMALL_W ? dh * 5 / 4 < WARP_CAP : dnh * 5 / 4 < WARP_CAP))
+            else if (deg <= WARP_DEG_MAX && W <= P.warp_w_max &&
+                (W <= P.warp_small_w ? dh * 5 / 4 < WARP_CAP : dnh * 5 / 4 < WARP_CAP))
                 cls = CLS_WARP;
-            else if (W <= TEAM_W_MAX && dnh * 5 / 4 < TEAM_CAP) cls = CLS_TEAM;
+            else if (W <= P.team_w_max && dnh * 5 / 4 < TEAM_CAP) cls = CLS_TEAM;
             else if (above <= DENSE_CAP) cls = CLS_DENSE;
             else if (dnh * 2 < CTAH_CAP && wnh < (1ull << 31)) cls = CLS_CTAH;
             else cls = CLS_DENSE;  // endpoint range walked in DENSE_CAP windows
             uint32_t parts = 1;
             if (cls == CLS_DENSE && !wide && above <= DENSE_CAP && above > 0) {
-                uint64_t unit = SPLIT_WEDGES > 4 * above ? SPLIT_WEDGES : 4 * above;
+                const uint64_t su = P.split_wedges;
+                uint64_t unit = su > 4 * above ? su : 4 * above;
                 uint64_t k = W / unit;
                 uint32_t deg = (uint32_t)(S.off[r + 1] - S.off[r]);
                 if (k > MAX_PARTS) k = MAX_PARTS;
@@ -657,7 +659,8 @@ __global__ void k_emit(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
                 rec.deg = deg;
                 rec.W = W > 0xffffffffull ? 0xffffffffu : (uint32_t)W;
                 rec.wnh = wnh > 0xffffffffull ? 0xffffffffu : (uint32_t)wnh;
-                rec.pad0 = rec.pad1 = rec.pad2 = 0;
+                rec.flags = cls == CLS_WARP && W <= G.cls.warp_small_w ? REC_HASH_ALL : 0u;
+                rec.pad1 = rec.pad2 = 0;
                 AnchorRec *list = cls == CLS_WARP ? G.warp_list
                                   : cls == CLS_TEAM ? G.team_list : G.ctah_list;
                 list[pos] = rec;
@@ -790,6 +793,27 @@ BuildTemp carve_temp(const DevGraph &g, void *temp_mem) {
     t.bounds = c.take<int64_t>(32);
     t.rinfo[0] = c.take<uint4>(nU + 1); t.rinfo[1] = c.take<uint4>(nV + 1);  // per-row records
     return t;
+}
+
+// classification of both sides: classes and bucket counts, bucket bases,
+// then the class lists and dense jobs
+void launch_classes(DevGraph &g, ClassifyTemp T, uint32_t *const *meta, uint32_t *const *grp,
+                    cudaStream_t s) {
+    const int64_t ns[2] = {g.nU, g.nV};
+    for (int sd = 0; sd < 2; sd++) {
+        if (ns[sd] == 0) continue;
+        T.meta = meta[sd];
+        T.grp = grp[sd];
+        k_classify<<<grid_for(ns[sd], BT, 4096), BT, 0, s>>>(g.side[sd], sd, T, g); note_launch();
+    }
+    k_bucket_base<<<1, 32, 0, s>>>(T, g); note_launch();
+    cudaMemsetAsync(T.bucket_cnt, 0, NCLS * NB * 4, s);
+    for (int sd = 0; sd < 2; sd++) {
+        if (ns[sd] == 0) continue;
+        T.meta = meta[sd];
+        T.grp = grp[sd];
+        k_emit<<<grid_for(ns[sd], BT, 2048), BT, 0, s>>>(g.side[sd], sd, T, g); note_launch();
+    }
 }
 
 }  // namespace
@@ -962,21 +986,31 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
             }
     }
 
-    // 5. classes
-    for (int sd = 0; sd < 2; sd++) {
-        if (ns[sd] == 0) continue;
-        T.meta = meta[sd];
-        T.grp = grp[sd];
-        k_classify<<<grid_for(ns[sd], BT, 4096), BT, 0, s>>>(g.side[sd], sd, T, g); note_launch();
-    }
-    k_bucket_base<<<1, 32, 0, s>>>(T, g); note_launch();
+    // 5. classes (bucket counts, class counters and statistics were zeroed
+    // by the validation)
+    launch_classes(g, T, meta, grp, s);
+}
+
+size_t classify_temp_bytes(int64_t nU, int64_t nV) {
+    const int64_t nmax = std::max<int64_t>(std::max(nU, nV), 1);
+    return 4 * align256((size_t)(nmax + 1) * 4) + 2 * align256(NCLS * NB * 4);
+}
+
+void classify_graph(DevGraph &g, void *ctemp, cudaStream_t s) {
+    const int64_t nmax = std::max<int64_t>(std::max(g.nU, g.nV), 1);
+    Carver c{(char *)ctemp};
+    uint32_t *meta[2], *grp[2];
+    meta[0] = c.take<uint32_t>(nmax + 1); meta[1] = c.take<uint32_t>(nmax + 1);
+    grp[0] = c.take<uint32_t>(nmax + 1); grp[1] = c.take<uint32_t>(nmax + 1);
+    ClassifyTemp T;
+    T.bucket_cnt = c.take<uint32_t>(NCLS * NB);
+    T.bucket_base = c.take<uint32_t>(NCLS * NB);
+    // class counters, split-group allocators and statistics start afresh;
+    // the split-merge counters (gpart, gdone) are zero between counts
+    cudaMemsetAsync(g.ctr, 0, CTR_MAXDEG * 4, s);
+    cudaMemsetAsync(g.cls_stats, 0, 3 * NCLS * 8, s);
     cudaMemsetAsync(T.bucket_cnt, 0, NCLS * NB * 4, s);
-    for (int sd = 0; sd < 2; sd++) {
-        if (ns[sd] == 0) continue;
-        T.meta = meta[sd];
-        T.grp = grp[sd];
-        k_emit<<<grid_for(ns[sd], BT, 2048), BT, 0, s>>>(g.side[sd], sd, T, g); note_launch();
-    }
+    launch_classes(g, T, meta, grp, s);
 }
 
 cudaError_t aux_create(BuildAux &a) {

@@ -860,7 +860,7 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
     uint32_t own = 0, other = 0;
     auto none = [](const uint4 &, long long &st, uint32_t &len) { st = 0; len = 0; };
     auto no_quad = [](const uint4 &, uint32_t, uint32_t) {};
-    if (W <= WARP_SMALL_W) {  // hash every endpoint
+    if (rec.flags & REC_HASH_ALL) {  // hash every endpoint
         table_geometry(W < above ? W : above, 32, WARP_CAP, cap, shift);
         const uint32_t mask = cap - 1;
         warp_rounds(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, sm.walk2, lane, none, no_quad,
@@ -1049,24 +1049,27 @@ __global__ void __launch_bounds__(CTAH_THREADS) k_ctah(DevGraph G) {
 }
 
 // ------------------------------------------------------------ dense class
-// Dense CTAs stage the middles' rows in shared memory by bulk copies
-// (DENSE_STAGES rounds per warp in flight) when DENSE_STAGED is set;
-// otherwise each lane loads its quads itself, one round ahead.
-constexpr bool DENSE_STAGED = false;
+// Two dense walkers (a launch choice): STAGED CTAs stage the middles' rows
+// in shared memory by bulk copies (DENSE_STAGES rounds per warp in flight;
+// the rings cost a CTA per SM); otherwise each lane loads its quads itself,
+// one round ahead. On the 2M x 500k graph the direct loads measured faster
+// (1.63 against 2.58 ms) and are the default.
 constexpr int DENSE_STAGES = 4;
 
+template <bool STAGED>
 struct alignas(16) DenseSmem {
     uint32_t cnt[DENSE_CAP];
     WalkSmem<DENSE_THREADS> walk;
-    StageRing<DENSE_STAGES> ring[DENSE_STAGED ? DENSE_THREADS / 32 : 1];
+    StageRing<DENSE_STAGES> ring[STAGED ? DENSE_THREADS / 32 : 1];
     uint32_t job, last;
 };
 
 // one dense job (an anchor, or one middle slice of a split anchor), walked
 // by the whole CTA; adds each thread's part of its sums to bal and tot
-__device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, const DenseJob &J,
-                                          StageState &ss, unsigned long long &bal,
-                                          unsigned long long &tot) {
+template <bool STAGED>
+__device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem<STAGED> &sm,
+                                          const DenseJob &J, StageState &ss,
+                                          unsigned long long &bal, unsigned long long &tot) {
     const int t = threadIdx.x;
     const bool sv = J.anchor & 1u;
     const SideCSR &S = sv ? G.side[1] : G.side[0];
@@ -1104,7 +1107,7 @@ __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, cons
             st = s0;
             l = (uint32_t)(lower_bound_u32(A.oadj, s0, d.z, e1 << 1) - s0);
         };
-        if constexpr (DENSE_STAGED) {
+        if constexpr (STAGED) {
             StageRing<DENSE_STAGES> &ring = sm.ring[t >> 5];
             if (windows)
                 team_rounds_bulk<DENSE_THREADS, DENSE_STAGES>(A.smd, A.oadj, A.rb, J.m0, J.m1,
@@ -1163,8 +1166,10 @@ __device__ __forceinline__ void dense_job(const DevGraph &G, DenseSmem &sm, cons
 // endpoints in the same shared memory. Each wedge adds the previous values
 // of its own tally (balanced) and of both tallies (total) to 64-bit sums,
 // which go to the grid accumulator before they could reach 2^53.
-__device__ __noinline__ void dense_job_wide(const DevGraph &G, DenseSmem &sm, const DenseJob &J,
-                                            unsigned long long &bal, unsigned long long &tot) {
+template <bool STAGED>
+__device__ __forceinline__ void dense_job_wide(const DevGraph &G, DenseSmem<STAGED> &sm,
+                                               const DenseJob &J, unsigned long long &bal,
+                                               unsigned long long &tot) {
     constexpr uint32_t CAP = DENSE_CAP / 2;
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(sm.cnt);
     const int t = threadIdx.x;
@@ -1209,12 +1214,13 @@ __device__ __noinline__ void dense_job_wide(const DevGraph &G, DenseSmem &sm, co
     }
 }
 
-__global__ void __launch_bounds__(DENSE_THREADS, DENSE_STAGED ? 2 : 3) k_dense(DevGraph G) {
+template <bool STAGED>
+__global__ void __launch_bounds__(DENSE_THREADS, STAGED ? 2 : 3) k_dense(DevGraph G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    DenseSmem &sm = *reinterpret_cast<DenseSmem *>(smem_raw);
+    DenseSmem<STAGED> &sm = *reinterpret_cast<DenseSmem<STAGED> *>(smem_raw);
     const uint32_t njobs = G.ctr[CTR_DENSE];
     StageState ss;
-    if constexpr (DENSE_STAGED) stage_ring_init(sm.ring[threadIdx.x >> 5], lane_id());
+    if constexpr (STAGED) stage_ring_init(sm.ring[threadIdx.x >> 5], lane_id());
     unsigned long long bal = 0, tot = 0;  // summed over all jobs of this CTA
     for (;;) {
         if (threadIdx.x == 0) sm.job = atomicAdd(&G.scratch->job_next[CLS_DENSE], 1u);
@@ -1223,8 +1229,32 @@ __global__ void __launch_bounds__(DENSE_THREADS, DENSE_STAGED ? 2 : 3) k_dense(D
         __syncthreads();
         if (jid >= njobs) break;
         const DenseJob J = G.dense_jobs[jid];
-        if (J.group == WIDE_JOB) dense_job_wide(G, sm, J, bal, tot);
-        else dense_job(G, sm, J, ss, bal, tot);
+        if (J.group != WIDE_JOB) dense_job(G, sm, J, ss, bal, tot);  // wide jobs: k_wide
+        spill_if_large(G.scratch, bal, tot);
+    }
+    flush_warp(G.scratch, bal, tot);
+}
+
+// The wide jobs among the dense jobs (anchors of degree above MAX_DEGREE),
+// one CTA per job; a kernel of their own keeps their 64-bit walk out of
+// k_dense's registers. Exits at once when the graph has none.
+__global__ void __launch_bounds__(DENSE_THREADS) k_wide(DevGraph G) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DenseSmem<false> &sm = *reinterpret_cast<DenseSmem<false> *>(smem_raw);
+    const uint32_t njobs = G.ctr[CTR_DENSE];
+    unsigned long long bal = 0, tot = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            uint32_t j = atomicAdd(&G.scratch->job_next[JOB_WIDE], 1u);
+            while (j < njobs && G.dense_jobs[j].group != WIDE_JOB)
+                j = atomicAdd(&G.scratch->job_next[JOB_WIDE], 1u);
+            sm.job = j;
+        }
+        __syncthreads();
+        const uint32_t jid = sm.job;
+        __syncthreads();
+        if (jid >= njobs) break;
+        dense_job_wide(G, sm, G.dense_jobs[jid], bal, tot);
         spill_if_large(G.scratch, bal, tot);
     }
     flush_warp(G.scratch, bal, tot);
@@ -1312,11 +1342,12 @@ __global__ void __launch_bounds__(CTAH_THREADS) k_ctah_batch(BatchArgs B) {
     hybrid_batch_body<CTAH_THREADS, CTAH_CAP, CLS_CTAH>(B);
 }
 
+template <bool STAGED>
 __global__ void __launch_bounds__(DENSE_THREADS) k_dense_batch(BatchArgs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    DenseSmem &sm = *reinterpret_cast<DenseSmem *>(smem_raw);
+    DenseSmem<STAGED> &sm = *reinterpret_cast<DenseSmem<STAGED> *>(smem_raw);
     StageState ss;
-    if constexpr (DENSE_STAGED) stage_ring_init(sm.ring[threadIdx.x >> 5], lane_id());
+    if constexpr (STAGED) stage_ring_init(sm.ring[threadIdx.x >> 5], lane_id());
     const uint32_t *p = B.prefix + (size_t)CLS_DENSE * (B.n + 1);
     const uint32_t total = p[B.n];
     for (;;) {
@@ -1344,8 +1375,18 @@ __global__ void k_batch_prep(BatchArgs B) {
     for (uint32_t g = i; g < B.n; g += gridDim.x * blockDim.x) {
         CountScratch *sc = B.graphs[g].scratch;
         for (int k = 0; k < 4; k++) sc->acc[k] = 0;
-        for (int k = 0; k < 5; k++) sc->job_next[k] = 0;
+        for (int k = 0; k < 7; k++) sc->job_next[k] = 0;
         sc->err = 0;
+    }
+}
+
+// every member's class counters and class statistics (after a
+// re-classification), NCTR and 3 * NCLS words per graph
+__global__ void k_batch_classes(BatchArgs B, uint32_t *ctr, unsigned long long *stats) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n; i += gridDim.x * blockDim.x) {
+        const DevGraph &G = B.graphs[i];
+        for (int k = 0; k < NCTR; k++) ctr[(size_t)i * NCTR + k] = G.ctr[k];
+        for (int k = 0; k < 3 * NCLS; k++) stats[(size_t)i * 3 * NCLS + k] = G.cls_stats[k];
     }
 }
 
@@ -1387,12 +1428,14 @@ __global__ void k_flip(DevGraph G, const int64_t *edge_idx, int64_t n) {
 constexpr size_t WARP_SMEM = (WARP_THREADS / 32) * sizeof(WarpSmem);
 constexpr size_t TEAM_SMEM = sizeof(HybSmem<TEAM_THREADS, TEAM_CAP>);
 constexpr size_t CTAH_SMEM = sizeof(HybSmem<CTAH_THREADS, CTAH_CAP>);
-constexpr size_t DENSE_SMEM = sizeof(DenseSmem);
+constexpr size_t DENSE_SMEM = sizeof(DenseSmem<false>);
+constexpr size_t DENSE_SMEM_STAGED = sizeof(DenseSmem<true>);
 
 
 struct LaunchCfg {
-    int warp_blocks = 0, team_blocks = 0, ctah_blocks = 0, dense_blocks = 0;
+    int warp_blocks = 0, team_blocks = 0, ctah_blocks = 0, dense_blocks[2] = {};
     int batch_blocks[NCLS] = {};
+    int dense_batch_blocks[2] = {};  // direct-load and staged dense batch kernels
     int sms = 0;
 };
 
@@ -1425,11 +1468,16 @@ const LaunchCfg &init_cfg() {
         c.warp_blocks = blocks_for(k_warp, WARP_THREADS, WARP_SMEM, sms);
         c.team_blocks = blocks_for(k_team, TEAM_THREADS, TEAM_SMEM, sms);
         c.ctah_blocks = blocks_for(k_ctah, CTAH_THREADS, CTAH_SMEM, sms);
-        c.dense_blocks = blocks_for(k_dense, DENSE_THREADS, DENSE_SMEM, sms);
+        c.dense_blocks[0] = blocks_for(k_dense<false>, DENSE_THREADS, DENSE_SMEM, sms);
+        c.dense_blocks[1] = blocks_for(k_dense<true>, DENSE_THREADS, DENSE_SMEM_STAGED, sms);
+        blocks_for(k_wide, DENSE_THREADS, DENSE_SMEM, sms);  // shared-memory opt-in
         c.batch_blocks[CLS_WARP] = blocks_for(k_warp_batch, WARP_THREADS, WARP_SMEM, sms);
         c.batch_blocks[CLS_TEAM] = blocks_for(k_team_batch, TEAM_THREADS, TEAM_SMEM, sms);
         c.batch_blocks[CLS_CTAH] = blocks_for(k_ctah_batch, CTAH_THREADS, CTAH_SMEM, sms);
-        c.batch_blocks[CLS_DENSE] = blocks_for(k_dense_batch, DENSE_THREADS, DENSE_SMEM, sms);
+        c.dense_batch_blocks[0] = blocks_for(k_dense_batch<false>, DENSE_THREADS, DENSE_SMEM, sms);
+        c.dense_batch_blocks[1] =
+            blocks_for(k_dense_batch<true>, DENSE_THREADS, DENSE_SMEM_STAGED, sms);
+        c.batch_blocks[CLS_DENSE] = c.dense_batch_blocks[0];
     });
     return g_cfg[dev];
 }
@@ -1443,7 +1491,13 @@ void launch_count(const DevGraph &g, cudaStream_t s, int64_t *per_vertex_dev, cu
     const LaunchCfg &cfg = init_cfg();
     cudaMemsetAsync(g.scratch, 0, sizeof(CountScratch), s);
     if (ev) record_timing_event(ev[0], s);
-    k_dense<<<cfg.dense_blocks, DENSE_THREADS, DENSE_SMEM, s>>>(g); note_launch();
+    if (g.dense_staged)
+        k_dense<true><<<cfg.dense_blocks[1], DENSE_THREADS, DENSE_SMEM_STAGED, s>>>(g);
+    else
+        k_dense<false><<<cfg.dense_blocks[0], DENSE_THREADS, DENSE_SMEM, s>>>(g);
+    note_launch();
+    // wide jobs exist only when some degree exceeds the 16-bit tally range
+    if (g.h_maxdeg > MAX_DEGREE) { k_wide<<<cfg.sms, DENSE_THREADS, DENSE_SMEM, s>>>(g); note_launch(); }
     if (ev) record_timing_event(ev[1], s);
     k_ctah<<<cfg.ctah_blocks, CTAH_THREADS, CTAH_SMEM, s>>>(g); note_launch();
     if (ev) record_timing_event(ev[2], s);
@@ -1483,8 +1537,10 @@ void launch_count_batch(const BatchLaunch &L, const BatchTune &T, cudaStream_t s
         // with concurrency the first class stays on s, the others go to side streams
         cudaStream_t cs = conc && used > 0 ? side[used - 1] : s;
         used++;
-        int blocks = std::max(1, (int)(cfg.batch_blocks[c] * T.grid_frac[c] + 0.5f));
-        blocks = std::min(blocks, cfg.batch_blocks[c]);
+        const int full = c == CLS_DENSE ? cfg.dense_batch_blocks[T.dense_staged ? 1 : 0]
+                                        : cfg.batch_blocks[c];
+        int blocks = std::max(1, (int)(full * T.grid_frac[c] + 0.5f));
+        blocks = std::min(blocks, full);
         if (c == CLS_WARP) {
             const uint64_t warps = ((uint64_t)L.items[c] + B.warp_chunk - 1) / B.warp_chunk;
             blocks = (int)std::min<uint64_t>(blocks, (warps + WARP_THREADS / 32 - 1) / (WARP_THREADS / 32));
@@ -1493,7 +1549,10 @@ void launch_count_batch(const BatchLaunch &L, const BatchTune &T, cudaStream_t s
             blocks = (int)std::min<uint64_t>(blocks, L.items[c]);
             if (c == CLS_TEAM) k_team_batch<<<blocks, TEAM_THREADS, TEAM_SMEM, cs>>>(B);
             else if (c == CLS_CTAH) k_ctah_batch<<<blocks, CTAH_THREADS, CTAH_SMEM, cs>>>(B);
-            else k_dense_batch<<<blocks, DENSE_THREADS, DENSE_SMEM, cs>>>(B);
+            else if (T.dense_staged)
+                k_dense_batch<true><<<blocks, DENSE_THREADS, DENSE_SMEM_STAGED, cs>>>(B);
+            else
+                k_dense_batch<false><<<blocks, DENSE_THREADS, DENSE_SMEM, cs>>>(B);
         }
         note_launch();
     }
@@ -1505,6 +1564,18 @@ void launch_count_batch(const BatchLaunch &L, const BatchTune &T, cudaStream_t s
     if (tev) cudaEventRecord(tev[NCLS], s);
     const uint32_t res_blocks = std::min<uint32_t>((L.n + 255) / 256, 1024);
     if (L.n) { k_batch_results<<<res_blocks, 256, 0, s>>>(B, L.out); note_launch(); }
+}
+
+void launch_batch_classes(const BatchLaunch &L, uint32_t *ctr_dev, unsigned long long *stats_dev,
+                          cudaStream_t s) {
+    BatchArgs B;
+    B.graphs = L.graphs;
+    B.prefix = L.prefix;
+    B.next = L.next;
+    B.n = L.n;
+    B.warp_chunk = 1;
+    const uint32_t blocks = std::min<uint32_t>((L.n + 255) / 256, 1024);
+    if (L.n) { k_batch_classes<<<blocks, 256, 0, s>>>(B, ctr_dev, stats_dev); note_launch(); }
 }
 
 void launch_flip(DevGraph &g, const int64_t *edge_idx_dev, int64_t n, cudaStream_t s) {

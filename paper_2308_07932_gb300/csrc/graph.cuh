@@ -50,11 +50,25 @@ constexpr uint32_t MAX_GPART = 1u << 24;
 
 enum Cls : uint32_t { CLS_WARP = 0, CLS_TEAM = 1, CLS_CTAH = 2, CLS_DENSE = 3, NCLS = 4 };
 
+// The bucket shape of a graph's classification (runtime values within the
+// compile-time bounds above): warp-class anchors have at most warp_w_max
+// wedges and those with at most warp_small_w hash every endpoint; team
+// anchors have at most team_w_max wedges; dense anchors are split into
+// parts of at least split_wedges wedges.
+struct ClassifyParams {
+    uint32_t warp_w_max = (uint32_t)WARP_W_MAX;
+    uint32_t warp_small_w = (uint32_t)WARP_SMALL_W;
+    uint32_t team_w_max = (uint32_t)TEAM_W_MAX;
+    uint32_t split_wedges = (uint32_t)SPLIT_WEDGES;
+};
+
 // One anchor in a class list: (side rank << 1 | side), start of its row,
-// degree, wedges and below-window wedges (saturated to 32 bits).
+// degree, wedges and below-window wedges (saturated to 32 bits), flags
+// (bit 0: a warp-class anchor that hashes every endpoint).
+constexpr uint32_t REC_HASH_ALL = 1u;
 struct alignas(16) AnchorRec {
     uint32_t anchor, rb, deg, W;
-    uint32_t wnh, pad0, pad1, pad2;
+    uint32_t wnh, flags, pad1, pad2;
 };
 
 // One CTA job over dense counters: anchor (side rank << 1 | side), its
@@ -87,12 +101,14 @@ enum Ctr : uint32_t {
 // per-count scratch (zeroed before each count)
 struct CountScratch {
     unsigned long long acc[4];   // balanced lo/hi, total lo/hi (128-bit sums)
-    uint32_t job_next[6];        // dynamic job cursors: one per class, then the per-vertex walks
+    uint32_t job_next[7];        // dynamic job cursors: one per class, the per-vertex walks,
+                                 // the wide jobs
     uint32_t err;
-    uint32_t pad[2];
+    uint32_t pad[1];
 };
 constexpr int JOB_PER_VERTEX = 4;
 constexpr int JOB_PV_TEAM = 5;
+constexpr int JOB_WIDE = 6;
 
 struct DevGraph {
     int64_t nU = 0, nV = 0, nE = 0;
@@ -119,6 +135,8 @@ struct DevGraph {
     // host copies after the build
     uint32_t h_ctr[NCTR] = {};
     uint64_t h_wedges = 0;
+    ClassifyParams cls;      // bucket shape the classes were (or are to be) built with
+    bool dense_staged = false;  // dense walker: rows staged by bulk copies (launch choice)
     uint32_t h_maxdeg = 0;   // largest vertex degree (read back by build_validate)
     int deg_bits = 16;       // key bits of the degree sort (16, 24 or 32, from h_maxdeg)
     unsigned long long h_cls_stats[3 * NCLS] = {};  // resident graphs: copy of cls_stats
@@ -175,6 +193,14 @@ bb_status build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col,
 void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
                 void *temp_mem, cudaStream_t s, const BuildAux *aux);
 
+// Re-runs the classification of a built graph with g.cls (the class lists,
+// dense jobs and split groups are rewritten; the rows, descriptors and
+// work counts are kept). ctemp: device scratch of classify_temp_bytes.
+// Asynchronous on s; the host copies (h_ctr, h_cls_stats) are stale until
+// the caller reads ctr and cls_stats back.
+size_t classify_temp_bytes(int64_t nU, int64_t nV);
+void classify_graph(DevGraph &g, void *ctemp, cudaStream_t s);
+
 // Count balanced/total butterflies of a built graph on stream s. Writes the
 // 128-bit sums to g.scratch->acc (device); per_vertex may be null. When ev
 // is not null, ev[0..4] are recorded before the dense, CTA-hash, team and
@@ -199,10 +225,18 @@ struct BatchLaunch {
 // Launch shapes: items a warp takes per grab, whether the classes run on
 // separate streams at once, and each class's grid as a fraction of its
 // full-occupancy grid.
+// Bucket shapes per graph-size class of a batch: members with fewer than
+// 2^14, 2^17, 2^20 edges, and the rest.
+constexpr int NSIZE = 4;
+inline int size_class(int64_t nE) {
+    return nE < (1 << 14) ? 0 : nE < (1 << 17) ? 1 : nE < (1 << 20) ? 2 : 3;
+}
 struct BatchTune {
     uint32_t warp_chunk = 8;
     uint32_t concurrent = 1;
     float grid_frac[NCLS] = {1.f, 1.f, 1.f, 1.f};
+    uint32_t dense_staged = 0;
+    ClassifyParams shape[NSIZE];
 };
 // side: NCLS-1 streams and ev: NCLS events, used when T.concurrent is set
 // (both may be null otherwise). Works under stream capture. tev (optional,
@@ -212,6 +246,10 @@ void launch_count_batch(const BatchLaunch &L, const BatchTune &T, cudaStream_t s
                         const cudaStream_t *side, const cudaEvent_t *ev,
                         const cudaEvent_t *tev = nullptr);
 int batch_max_blocks(int cls);
+// gathers every member's class counters (NCTR per graph) and class
+// statistics (3 * NCLS per graph) into device arrays
+void launch_batch_classes(const BatchLaunch &L, uint32_t *ctr_dev, unsigned long long *stats_dev,
+                          cudaStream_t s);
 
 // Balanced butterflies containing each vertex (Algorithm 3's quantity) for
 // a built graph: written to out_dev (device int64[nU+nV], U ids then V ids).

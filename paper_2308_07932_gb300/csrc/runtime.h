@@ -53,8 +53,8 @@ struct bb_ctx {
     // the one-shot path's work after validation, captured as a CUDA graph
     // for one shape and set of buffers (key) and replayed while they repeat
     cudaGraphExec_t step_exec = nullptr;
-    const void *step_key[10] = {};   // key of step_exec
-    const void *step_last[10] = {};  // key of the previous call (capture when it repeats)
+    const void *step_key[11] = {};   // key of step_exec
+    const void *step_last[11] = {};  // key of the previous call (capture when it repeats)
     uint64_t step_launches = 0;     // kernels in the captured graph
     bb::HostResult *h_res = nullptr;  // pinned
     // host inputs: rowptr and edge-chunk copy events (copies run on the
@@ -66,6 +66,11 @@ struct bb_ctx {
     bool have_build_ev = false;
     bb_timing last = {};
     bb::Engine *engine = nullptr;  // started by bb_ctx_serve or the first bb_submit
+    // bucket shape of later builds (bb_ctx_set_shape) and its version (part
+    // of the step graph's key)
+    bb::ClassifyParams shape;
+    bool dense_staged = false;
+    uint64_t shape_version = 0;
 };
 
 struct bb_graph {
@@ -94,6 +99,11 @@ bb_status set_device(bb_ctx *ctx);
 bb_status map_build_error(uint32_t e);
 // argument checks of a CSR given to the library (sizes, NULLs, id limits)
 bb_status check_csr(const bb_csr *csr, const int8_t *signs);
+// a public bucket shape (NULL = defaults) as classification parameters,
+// BB_ERR_INVALID_ARG outside its ranges
+bb_status shape_params(const bb_class_shape *shape, ClassifyParams *out);
+// the public form of classification parameters
+bb_class_shape shape_public(const ClassifyParams &p);
 // stops the context's serving engine (waits for running requests)
 void engine_stop(bb_ctx *ctx);
 // adds launches made by replaying a captured CUDA graph to bb_launch_count;

@@ -56,7 +56,7 @@ def test_batch_matches_oracle_and_single_counts(ctx, mix):
 def test_batch_shapes_do_not_change_counts(ctx, mix, chunk, conc, frac):
     hosts, graphs, want = mix
     b = pkg.Batch(ctx, graphs)
-    t = pkg.BatchTune()
+    t = b.tune()
     t.warp_chunk, t.concurrent = chunk, conc
     for k in range(len(pkg.KERNELS)):
         t.grid_frac[k] = frac
@@ -67,6 +67,87 @@ def test_batch_shapes_do_not_change_counts(ctx, mix, chunk, conc, frac):
         bal, tot = b.count()
         assert [(int(x), int(y)) for x, y in zip(bal, tot)] == want
     b.free()
+
+
+SHAPES = [
+    # most anchors out of the warp class, small dense split parts
+    {"warp_w_max": 64, "warp_small_w": 0, "team_w_max": 256, "split_wedges": 1024},
+    # warp anchors hash every endpoint when they can
+    {"warp_w_max": 16384, "warp_small_w": 16384, "team_w_max": 16384, "split_wedges": 1 << 20},
+    {"warp_w_max": 2048, "warp_small_w": 96, "team_w_max": 4096, "split_wedges": 16384},
+]
+
+
+@pytest.mark.parametrize("staged", [0, 1])
+def test_bucket_shapes_per_size_class_keep_counts(ctx, mix, staged):
+    hosts, graphs, want = mix
+    b = pkg.Batch(ctx, graphs)
+    try:
+        for rot in range(len(SHAPES)):
+            t = b.tune()
+            t.dense_staged = staged
+            for k in range(pkg.NSIZE):   # a different shape per size class
+                t.shape[k] = pkg.ClassShape.from_dict(SHAPES[(k + rot) % len(SHAPES)])
+            b.set_tune(t)
+            got = b.tune().to_dict()
+            assert got["dense_staged"] == staged
+            assert got["shape"] == [SHAPES[(k + rot) % len(SHAPES)] for k in range(pkg.NSIZE)]
+            for _ in range(2):
+                bal, tot = b.count()
+                assert [(int(x), int(y)) for x, y in zip(bal, tot)] == want
+            # a re-classified member counts right on its own too
+            for i in (0, len(graphs) - 2, len(graphs) - 1):
+                c = graphs[i].count()
+                assert (c.balanced, c.total) == want[i]
+    finally:
+        b.set_tune({**b.tune().to_dict(), "dense_staged": 0,
+                    "shape": [pkg.ClassShape.DEFAULT] * pkg.NSIZE})
+        b.free()
+
+
+def test_shape_argument_errors(ctx, mix):
+    hosts, graphs, want = mix
+    b = pkg.Batch(ctx, graphs)
+    for bad in ({"warp_w_max": 0}, {"warp_w_max": 20000}, {"warp_w_max": 100, "warp_small_w": 200},
+                {"team_w_max": 0}, {"split_wedges": 100}):
+        t = b.tune()
+        t.shape[1] = pkg.ClassShape.from_dict({**pkg.ClassShape.DEFAULT, **bad})
+        with pytest.raises(pkg.BBError) as ei:
+            b.set_tune(t)
+        assert ei.value.name == "BB_ERR_INVALID_ARG"
+        with pytest.raises(pkg.BBError):
+            ctx.set_shape({**pkg.ClassShape.DEFAULT, **bad})
+    bal, tot = b.count()   # unchanged after the rejected tunes
+    assert [(int(x), int(y)) for x, y in zip(bal, tot)] == want
+    b.free()
+
+
+def test_single_graph_shapes(ctx):
+    graphs = [synth.chung_lu_scaled(71, 300_000), synth.vote(12, 40, 6_000, 0.5, 2, 0.55, 0.8),
+              synth.uniform_2k_1k()]
+    want = [oracle.count(g, threads=4) for g in graphs]
+    try:
+        for shape in SHAPES:
+            for staged in (False, True):
+                ctx.set_shape(shape, staged)
+                for g, w in zip(graphs, want):
+                    c = ctx.count(g)
+                    assert (c.balanced, c.total) == w, (g.name, shape, staged)
+        ctx.set_shape(None)
+        res = ctx.upload(graphs[0])
+        try:
+            for shape in SHAPES:
+                res.set_shape(shape, True)
+                c = res.count(per_vertex=True)
+                assert (c.balanced, c.total) == want[0]
+                assert int(c.per_vertex.sum()) == 4 * want[0][0]
+                gids = np.arange(0, graphs[0].nU + graphs[0].nV, 997)
+                assert np.array_equal(c.per_vertex[gids],
+                                      oracle.per_vertex(graphs[0], gids=gids, threads=4))
+        finally:
+            res.free()
+    finally:
+        ctx.set_shape(None)
 
 
 def test_traced_batch_count(ctx, mix):

@@ -114,3 +114,21 @@ def test_power_law_with_wide_hubs(ctx, swap):
         assert np.array_equal(pe[eids], oracle.per_edge(g, edges=eids, threads=8))
     finally:
         res.free()
+
+
+def test_wide_members_in_a_batch(ctx):
+    # the batched dense kernel walks wide jobs itself
+    hosts = [k2n(70_000, 40_000), synth.swap_sides(k2n(131_072, 65_536)), hub_graph(62),
+             synth.uniform_2k_1k()]
+    want = [lemma2(70_000, 40_000), lemma2(131_072, 65_536), oracle.count(hosts[2], threads=8),
+            oracle.count(hosts[3])]
+    graphs = [ctx.upload(g) for g in hosts]
+    try:
+        b = pkg.Batch(ctx, graphs)
+        for _ in range(2):
+            bal, tot = b.count()
+            assert [(int(x), int(y)) for x, y in zip(bal, tot)] == want
+        b.free()
+    finally:
+        for g in graphs:
+            g.free()
