@@ -293,7 +293,7 @@ bool replay_step(bb_ctx *ctx, DevGraph &g, const bb_csr *csr, const int8_t *sign
         const uint64_t l0 = launches();
         build_rest(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s, &ctx->aux);
         if (ctx->timing) record_timing_event(ctx->ev[1], s);
-        launch_count(g, s, nullptr, ctx->timing ? ctx->ev + 2 : nullptr);
+        launch_count(g, s, ctx->timing ? ctx->ev + 2 : nullptr);
         const uint64_t n = launches() - l0;
         retract_launches(n);  // captured, not run
         cudaGraph_t graph = nullptr;
@@ -365,10 +365,11 @@ bb_status count_device(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int6
         build_rest(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s, &ctx->aux);
         BB_CUDA(cudaGetLastError(), "build kernels");
         if (ctx->timing) BB_CUDA(cudaEventRecord(ctx->ev[1], s), "event");
-        launch_count(g, s, pv_dev, ctx->timing ? ctx->ev + 2 : nullptr);
+        cudaEvent_t *ev = ctx->timing ? ctx->ev + 2 : nullptr;
+        if (pv_dev) launch_per_vertex(g, pv_dev, s, ev);
+        else launch_count(g, s, ev);
     }
     ctx->have_build_ev = ctx->timing;
-    if (pv_dev) launch_per_vertex(g, pv_dev, s);
     BB_CUDA(cudaGetLastError(), "count launch");
     return finish_count(ctx, g, s, balanced, total, wedges_opt);
 }
@@ -694,8 +695,9 @@ bb_status bb_count(bb_graph *G, int64_t *balanced, int64_t *total, int64_t *per_
         if (st != BB_OK) return st;
         pv_dev = ctx->ws_pv;
     }
-    launch_count(G->g, ctx->stream, nullptr, ctx->timing ? ctx->ev + 2 : nullptr);
-    if (pv_dev) launch_per_vertex(G->g, pv_dev, ctx->stream);
+    cudaEvent_t *ev = ctx->timing ? ctx->ev + 2 : nullptr;
+    if (pv_dev) launch_per_vertex(G->g, pv_dev, ctx->stream, ev);
+    else launch_count(G->g, ctx->stream, ev);
     BB_CUDA(cudaGetLastError(), "count launch");
     st = finish_count(ctx, G->g, ctx->stream, balanced, total, nullptr);
     if (st == BB_OK) {
@@ -726,8 +728,7 @@ bb_status bb_count_edges(bb_graph *G, int64_t *per_edge, int64_t *balanced_opt,
     int64_t *out_dev = (int64_t *)ctx->ws_pe;
     unsigned long long *acc = (unsigned long long *)((char *)ctx->ws_pe + b_out);
     cudaStream_t s = ctx->stream;
-    launch_count(G->g, s, nullptr, ctx->timing ? ctx->ev + 2 : nullptr);
-    launch_per_edge(G->g, out_dev, acc, s);
+    launch_per_edge(G->g, out_dev, acc, s, ctx->timing ? ctx->ev + 2 : nullptr);
     BB_CUDA(cudaGetLastError(), "per-edge launch");
     int64_t b = 0, t = 0;
     st = finish_count(ctx, G->g, s, &b, &t, nullptr);
@@ -820,7 +821,7 @@ bb_status bb_count_flipped(bb_graph *G, const int64_t *edge_idx, int64_t n, int6
         }
     } else {
         int64_t b = 0, t = 0;
-        launch_count(G->g, s, nullptr, ctx->timing ? ctx->ev + 2 : nullptr);
+        launch_count(G->g, s, ctx->timing ? ctx->ev + 2 : nullptr);
         BB_CUDA(cudaGetLastError(), "count launch");
         if ((st = finish_count(ctx, G->g, s, &b, &t, nullptr)) != BB_OK) return st;
         G->have_counts = true;

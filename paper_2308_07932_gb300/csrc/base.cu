@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(BASE_THREADS) k_base(DevGraph G, uint8_t *scra
     const int64_t nA = G.nU + G.nV;
     unsigned long long bal = 0, tot = 0;
     for (;;) {
-        if (t == 0) sm.job = atomicAdd(&G.scratch->job_next[JOB_PER_VERTEX], 1u);
+        if (t == 0) sm.job = atomicAdd(&G.scratch->job_next[JOB_BASE], 1u);
         __syncthreads();
         const int64_t a = sm.job;
         __syncthreads();
@@ -254,7 +254,7 @@ void launch_base(const DevGraph &g, uint8_t *scratch, uint64_t per_cta,
                  unsigned long long *acc_dev, cudaStream_t s) {
     const int blocks = base_blocks();
     cudaMemsetAsync(acc_dev, 0, 16, s);
-    cudaMemsetAsync(&g.scratch->job_next[JOB_PER_VERTEX], 0, 4, s);
+    cudaMemsetAsync(&g.scratch->job_next[JOB_BASE], 0, 4, s);
     cudaMemsetAsync(&g.scratch->err, 0, 4, s);
     k_base<<<blocks, BASE_THREADS, sizeof(BaseSmem), s>>>(g, scratch, per_cta, acc_dev); note_launch();
 }

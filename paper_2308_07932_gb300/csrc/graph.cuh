@@ -101,13 +101,13 @@ enum Ctr : uint32_t {
 // per-count scratch (zeroed before each count)
 struct CountScratch {
     unsigned long long acc[4];   // balanced lo/hi, total lo/hi (128-bit sums)
-    uint32_t job_next[7];        // dynamic job cursors: one per class, the per-vertex walks,
-                                 // the wide jobs
+    uint32_t job_next[7];        // dynamic job cursors: one per class, the split parts'
+                                 // second walks, the per-vertex baseline, the wide jobs
     uint32_t err;
     uint32_t pad[1];
 };
-constexpr int JOB_PER_VERTEX = 4;
-constexpr int JOB_PV_TEAM = 5;
+constexpr int JOB_PV_SPLIT = 4;
+constexpr int JOB_BASE = 5;
 constexpr int JOB_WIDE = 6;
 
 struct DevGraph {
@@ -202,11 +202,10 @@ size_t classify_temp_bytes(int64_t nU, int64_t nV);
 void classify_graph(DevGraph &g, void *ctemp, cudaStream_t s);
 
 // Count balanced/total butterflies of a built graph on stream s. Writes the
-// 128-bit sums to g.scratch->acc (device); per_vertex may be null. When ev
-// is not null, ev[0..4] are recorded before the dense, CTA-hash, team and
-// warp kernels and after the last one.
-void launch_count(const DevGraph &g, cudaStream_t s, int64_t *per_vertex_dev,
-                  cudaEvent_t *ev = nullptr);
+// 128-bit sums to g.scratch->acc (device). When ev is not null, ev[0..4]
+// are recorded before the dense, CTA-hash, team and warp kernels and after
+// the last one.
+void launch_count(const DevGraph &g, cudaStream_t s, cudaEvent_t *ev = nullptr);
 
 // Many resident graphs counted in one launch per work class. Items of class
 // c of graph i are numbered prefix[c*(n+1)+i] .. prefix[c*(n+1)+i+1]-1 in
@@ -251,15 +250,18 @@ int batch_max_blocks(int cls);
 void launch_batch_classes(const BatchLaunch &L, uint32_t *ctr_dev, unsigned long long *stats_dev,
                           cudaStream_t s);
 
-// Balanced butterflies containing each vertex (Algorithm 3's quantity) for
+// The count of launch_count (same sums, same events) together with the
+// balanced butterflies containing each vertex (Algorithm 3's quantity) of
 // a built graph: written to out_dev (device int64[nU+nV], U ids then V ids).
-void launch_per_vertex(const DevGraph &g, int64_t *out_dev, cudaStream_t s);
+void launch_per_vertex(const DevGraph &g, int64_t *out_dev, cudaStream_t s,
+                       cudaEvent_t *ev = nullptr);
 
-// Balanced butterflies containing each input edge for a built graph that
-// keeps its raw input (rowptr/col): written to out_dev (device int64[nE],
-// input CSR order); pe_ws is device scratch of 2 * nE u64.
+// The count together with the balanced butterflies containing each input
+// edge of a built graph that keeps its raw input (rowptr/col): written to
+// out_dev (device int64[nE], input CSR order); pe_ws is device scratch of
+// 2 * nE u64.
 void launch_per_edge(const DevGraph &g, int64_t *out_dev, unsigned long long *pe_ws,
-                     cudaStream_t s);
+                     cudaStream_t s, cudaEvent_t *ev = nullptr);
 
 // Incremental re-count under sign flips (flips.cu). The workspace of
 // flip_ws_bytes(nE, n) holds the located edges and two flag bitmaps.

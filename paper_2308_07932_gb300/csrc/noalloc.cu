@@ -97,7 +97,7 @@ extern "C" bb_status bb_count_csr_device_noalloc(const bb_csr *csr_dev, const in
     if (st != BB_OK) return st;
     if ((e = cudaGetLastError()) != cudaSuccess) return report_error(BB_ERR_CUDA, cudaGetErrorString(e));
     if (verr) return map_error(verr);
-    launch_count(g, s, nullptr, nullptr);
+    launch_count(g, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return report_error(BB_ERR_CUDA, cudaGetErrorString(e));
     // the bounded wait comes first (the library's wait limit); the small
     // copies to pageable host memory then complete at once on the idle stream

@@ -273,7 +273,7 @@ bb_ticket_s *pick(Engine *E, Plan &plan) {
 
 // copies the count results back and waits; fills the ticket
 bb_status count_and_wait(Slot &S, const DevGraph &g, bb_ticket_s *t) {
-    launch_count(g, S.s, nullptr, nullptr);
+    launch_count(g, S.s);
     BB_CUDA(cudaGetLastError(), "count launch");
     HostResult *h = S.h;
     BB_CUDA(cudaMemcpyAsync(h->acc, g.scratch->acc, sizeof(h->acc), cudaMemcpyDeviceToHost, S.s),

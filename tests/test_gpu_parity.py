@@ -352,6 +352,41 @@ def test_per_vertex_full_size_sampled(ctx, name, make):
     assert c.per_vertex[g.nU:].sum() == 2 * c.balanced
 
 
+# Bucket shapes that move anchors between the classes: most anchors out of
+# the warp class with small split dense parts, warp anchors hashing every
+# endpoint, and a mix. The per-vertex and per-edge walks of every class
+# (including split parts and their second launch) must give the oracle's
+# values under each.
+PV_SHAPES = [
+    {"warp_w_max": 64, "warp_small_w": 0, "team_w_max": 256, "split_wedges": 1024},
+    {"warp_w_max": 16384, "warp_small_w": 16384, "team_w_max": 16384, "split_wedges": 1 << 20},
+    {"warp_w_max": 2048, "warp_small_w": 96, "team_w_max": 4096, "split_wedges": 16384},
+]
+
+
+@pytest.mark.parametrize("shape", range(len(PV_SHAPES)))
+@pytest.mark.parametrize("make", [
+    lambda: synth.chung_lu_scaled(65, 60_000),
+    lambda: synth.vote(66, 60, 5_000, 0.4, 2, 0.55, 0.8),
+])
+def test_per_vertex_and_edge_under_bucket_shapes(ctx, make, shape):
+    g = make()
+    want_v = oracle.per_vertex(g, threads=4)
+    want_e = oracle.per_edge(g, threads=8)
+    r = ctx.upload(g)
+    try:
+        r.set_shape(PV_SHAPES[shape])
+        for _ in range(2):  # the split parts' merged counters are released for the next call
+            c = r.count(per_vertex=True)
+            assert np.array_equal(c.per_vertex, want_v), g.name
+            pe, b, t = r.count_edges()
+            assert np.array_equal(pe, want_e), g.name
+            assert (b, t) == (c.balanced, c.total)
+        assert (r.count().balanced, r.count().total) == (c.balanced, c.total)
+    finally:
+        r.free()
+
+
 # ------------------------------------------------------------- per edge
 @pytest.mark.parametrize("make", [
     lambda: synth.uniform_2k_1k(),
