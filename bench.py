@@ -200,7 +200,7 @@ def whole_job_rate(units_per_rank: int, world: int, slowest_ms: float) -> float:
 # ---------------------------------------------------------------- our path
 def count_sha() -> str:
     h = hashlib.sha256()
-    for f in ["count.cu", "graph.cuh", "common.cuh"]:
+    for f in ["count.cu", "walk.cuh", "graph.cuh", "common.cuh"]:
         with open(os.path.join(ROOT, "paper_2308_07932_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -368,12 +368,16 @@ __global__ void __launch_bounds__(CTAH_THREADS) k_pv_ctah(DevGraph G, PvOut out)
 // Dense counters (S | A << 16) over the anchor's endpoint range, walked in
 // windows of DENSE_CAP endpoints when longer; u64 counters (S | A << 32)
 // over half the range for wide anchors.
+// acc: the second walk's per-middle sums. A middle's sum over one window
+// (or one split anchor) is below DENSE_CAP wedges times the degree, which
+// fits 32 bits; the u32 sums keep three CTAs per SM.
 struct alignas(16) PvDenseSmem {
     uint32_t cnt[DENSE_CAP];
     WalkSmem<DENSE_THREADS> walk;
-    unsigned long long acc[DENSE_THREADS];
+    uint32_t acc[DENSE_THREADS];
     uint32_t job, last;
 };
+static_assert((unsigned long long)DENSE_CAP * MAX_DEGREE < (1ull << 32), "u32 middle sums");
 
 // the anchor of a dense job (its row start from the side's offsets)
 __device__ __forceinline__ Anchor dense_anchor(const DevGraph &G, uint32_t anchor) {
@@ -505,10 +509,10 @@ __device__ __forceinline__ void pv_split_tally(const DevGraph &G, PvDenseSmem &s
     __syncthreads();  // the next job rewrites the counters
 }
 
-__global__ void __launch_bounds__(DENSE_THREADS) k_pv_dense(DevGraph G, PvOut out) {
+__global__ void __launch_bounds__(DENSE_THREADS, 3) k_pv_dense(DevGraph G, PvOut out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PvDenseSmem &sm = *reinterpret_cast<PvDenseSmem *>(smem_raw);
-    sm.acc[threadIdx.x] = 0ull;
+    sm.acc[threadIdx.x] = 0u;
     const uint32_t njobs = G.ctr[CTR_DENSE];
     unsigned long long bal = 0, tot = 0;
     for (;;) {
@@ -546,11 +550,11 @@ __device__ __forceinline__ uint32_t next_dense_job(const DevGraph &G, PvDenseSme
 // them (the last part to copy resets them for the next count), walk this
 // part's middles; the first part (m0 = 0) adds the endpoints' and the
 // anchor's sums.
-__global__ void __launch_bounds__(DENSE_THREADS) k_pv_split(DevGraph G, PvOut out) {
+__global__ void __launch_bounds__(DENSE_THREADS, 3) k_pv_split(DevGraph G, PvOut out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PvDenseSmem &sm = *reinterpret_cast<PvDenseSmem *>(smem_raw);
     const int t = threadIdx.x;
-    sm.acc[t] = 0ull;
+    sm.acc[t] = 0u;
     const uint32_t njobs = G.ctr[CTR_DENSE];
     for (;;) {
         const uint32_t jid = next_dense_job(G, sm, JOB_PV_SPLIT, njobs, [](uint32_t g) {
@@ -600,7 +604,6 @@ __global__ void __launch_bounds__(DENSE_THREADS) k_pv_wide(DevGraph G, PvOut out
     const int t = threadIdx.x;
     const uint32_t lane = (uint32_t)t & 31u, warp = (uint32_t)t >> 5;
     const uint32_t njobs = G.ctr[CTR_DENSE];
-    sm.acc[t] = 0ull;
     unsigned long long bal = 0, tot = 0;
     for (;;) {
         const uint32_t jid = next_dense_job(G, sm, JOB_WIDE, njobs,
@@ -612,6 +615,7 @@ __global__ void __launch_bounds__(DENSE_THREADS) k_pv_wide(DevGraph G, PvOut out
         const uint32_t e_lo = A.r + 1, e_hi = (uint32_t)A.ns;
         const bool windows = (e_hi - e_lo) > CAP;
         unsigned long long ab = 0, at = 0;
+        unsigned long long anc = 0;  // this thread's part of the anchor's balanced count
         for (uint32_t e0 = e_lo; e0 < e_hi; e0 += CAP) {
             const uint32_t e1 = e_hi - e0 > CAP ? e0 + CAP : e_hi;
             const uint32_t len = e1 - e0;
@@ -643,7 +647,7 @@ __global__ void __launch_bounds__(DENSE_THREADS) k_pv_wide(DevGraph G, PvOut out
                 [&]() {
                     bal += ab;
                     tot += at;
-                    if (P.spv) sm.acc[t] += ab;  // this thread's part of the anchor's count
+                    anc += ab;
                     ab = at = 0;
                     spill_if_large(G.scratch, bal, tot);
                 });
@@ -674,10 +678,9 @@ __global__ void __launch_bounds__(DENSE_THREADS) k_pv_wide(DevGraph G, PvOut out
             __syncthreads();  // the next window rewrites the counters
         }
         if (P.spv) {
-            unsigned long long a = sm.acc[t], unused = 0;
-            sm.acc[t] = 0ull;
-            block_sum2<DENSE_THREADS>(a, unused);
-            if (t == 0 && a) atomicAdd(&P.spv[A.r], a);
+            unsigned long long unused = 0;
+            block_sum2<DENSE_THREADS>(anc, unused);
+            if (t == 0 && anc) atomicAdd(&P.spv[A.r], anc);
         }
     }
     flush_warp(G.scratch, bal, tot);

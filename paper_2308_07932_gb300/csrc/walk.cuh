@@ -357,15 +357,15 @@ struct RoundPos {
 // flush() follows every `span` rounds of a warp and the end of its part.
 // SUMS (BF only): add(entry, vb, sign, position) returns the entry's value;
 // a round's values are summed per segment across its lanes (one warp
-// reduction) and added into acc (TS entries), handed to mid per chunk.
+// reduction) and added into acc (TS entries, u32 or u64 as the caller's
+// sums need), handed to mid per chunk.
 template <int TS, bool BF, bool SUMS = false, typename Seg, typename Add, typename Flush,
-          typename Mid = NoMid>
+          typename Mid = NoMid, typename Acc = unsigned long long>
 __device__ __forceinline__ void team_rounds(const uint4 *__restrict__ smd,
                                             const uint32_t *__restrict__ oadj, int64_t rb,
                                             uint32_t m0, uint32_t m1, WalkSmem<TS> &sm, int t,
                                             uint32_t span, Seg &&seg, Add &&add, Flush &&flush,
-                                            unsigned long long *acc = nullptr,
-                                            Mid &&mid = Mid{}) {
+                                            Acc *acc = nullptr, Mid &&mid = Mid{}) {
     static_assert(BF || !SUMS, "segment sums take the branch-free form");
     constexpr uint32_t NW = TS / 32;
     const uint4 *oadj4 = reinterpret_cast<const uint4 *>(oadj);
@@ -423,7 +423,7 @@ __device__ __forceinline__ void team_rounds(const uint4 *__restrict__ smd,
                                              add(v.z, (vm >> 2) & 1u, swq, pos.p + 2) +
                                              add(v.w, vm >> 3, swq, pos.p + 3);
                         const uint32_t tot = __reduce_add_sync(pos.peers, val);
-                        if (pos.head && tot) atomicAdd(&acc[pos.k], (unsigned long long)tot);
+                        if (pos.head && tot) atomicAdd(&acc[pos.k], (Acc)tot);
                     }
                 } else if constexpr (BF) {
                     add(v.x, vm & 1u, swq);
