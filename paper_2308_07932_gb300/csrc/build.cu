@@ -114,84 +114,167 @@ __global__ void k_global_rank(SideCSR S, const uint32_t *other_deg, int64_t n_ot
 }
 
 // --------------------------------------------------------------- 3. rows
-// One thread per input edge e: the U-side entry keeps the input position
-// within its row u; the V-side entry takes the next free slot of v's row.
-// Each entry is written as one key (packed entry << 32 | input edge id) for
-// the row sorts. A block takes FILL_EDGES consecutive edges per step and
-// stages the slice of rowptr that covers them in shared memory (when it
-// spans at most FILL_ROWS rows), so that a thread finds its row u with a
-// search in shared memory rather than in global memory.
+// Each input edge e is written into the rows of both endpoints: the U-side
+// entry keeps the input position within its row u; the V-side entry takes
+// a free slot of v's row. Each entry is written as one key (packed entry <<
+// 32 | input edge id) for the row sorts. A block takes FILL_EDGES
+// consecutive edges per step. Two warps find the step's first and last row
+// (32 probes per round); every row of the step marks its first edge of the
+// step in shared memory and a block-wide running maximum gives each edge
+// its row (no search per edge, however many empty rows the step spans).
+// The V rows of the step's edges are gathered in a shared hash, so that
+// each distinct V row takes its slots with one global atomic per step (hub
+// rows take edges from most steps).
 constexpr int FILL_THREADS = 256;
 constexpr int FILL_EDGES = 2048;
-constexpr int FILL_ROWS = 2048;
+constexpr int FILL_PER = FILL_EDGES / FILL_THREADS;
+constexpr uint32_t FILL_SLOTS = 4096;
+constexpr uint32_t FILL_EMPTY = 0xffffffffu;
+constexpr uint32_t FILL_HASH_BITS = 12;
+static_assert(FILL_SLOTS == 1u << FILL_HASH_BITS && FILL_SLOTS >= 2 * FILL_EDGES, "fill hash");
 
-// last u in [lo, hi) with rp[u] <= e (rp[lo] <= e)
-template <typename P>
-__device__ __forceinline__ int64_t row_of(const P *rp, int64_t lo, int64_t hi, int64_t e) {
+// last u in [lo, hi) with rp[u] <= e (rp[lo] <= e), by a whole warp (all
+// lanes call it with the same arguments): each round probes 31 evenly
+// spaced rows of (lo, hi) and keeps the gap between the last one at or
+// below e and the next
+__device__ __forceinline__ int64_t row_of_warp(const int64_t *rp, int64_t lo, int64_t hi,
+                                               int64_t e, unsigned lane) {
     while (hi - lo > 1) {
-        const int64_t m = (lo + hi) >> 1;
-        if (rp[m] <= e) lo = m; else hi = m;
+        const int64_t p = lo + ((hi - lo) * (int64_t)(lane + 1)) / 32;
+        const bool le = lane < 31 && rp[p] <= e;
+        const int c = __popc(__ballot_sync(FULL, le));  // the true probes form a prefix
+        const int64_t nlo = c > 0 ? __shfl_sync(FULL, p, c - 1) : lo;
+        const int64_t nhi = c < 31 ? __shfl_sync(FULL, p, c) : hi;
+        lo = nlo;
+        hi = nhi;
     }
     return lo;
+}
+
+// block-wide inclusive running maximum of a[0..FILL_EDGES), FILL_PER
+// consecutive values per thread
+__device__ __forceinline__ void fill_running_max(uint32_t *a, uint32_t *wmax) {
+    const int t = threadIdx.x;
+    const unsigned lane = lane_id();
+    uint32_t v[FILL_PER], m = 0;
+#pragma unroll
+    for (int k = 0; k < FILL_PER; k++) {
+        m = max(m, a[t * FILL_PER + k]);
+        v[k] = m;
+    }
+    uint32_t x = m;  // inclusive warp scan (max) of the threads' maxima
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, d);
+        if (lane >= (unsigned)d) x = max(x, y);
+    }
+    if (lane == 31) wmax[t >> 5] = x;
+    __syncthreads();
+    uint32_t before = __shfl_up_sync(FULL, x, 1);
+    if (lane == 0) before = 0;
+    for (int w = 0; w < (t >> 5); w++) before = max(before, wmax[w]);
+#pragma unroll
+    for (int k = 0; k < FILL_PER; k++) a[t * FILL_PER + k] = max(before, v[k]);
 }
 
 __global__ void __launch_bounds__(FILL_THREADS) k_fill(
     const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
     const int8_t *__restrict__ sign, int64_t nU, int64_t nE, SideCSR U, SideCSR V,
-    uint32_t *cursorV, uint64_t *keyU, uint64_t *keyV) {
-    __shared__ int64_t rp[FILL_ROWS + 1];
-    __shared__ int64_t row0, nrows;
-    // warp-uniform trip counts: lanes that share a V row take their slots
-    // in it with one atomic (hub rows would otherwise serialise on it)
+    uint32_t *cursorV, uint64_t *keyU, uint64_t *keyV, uint32_t *err) {
+    __shared__ int64_t row_lim[2];
+    __shared__ uint32_t srow[FILL_EDGES];  // per edge of the step: its row - u0 + 1
+    __shared__ uint32_t wmax[FILL_THREADS / 32];
+    __shared__ uint32_t hkey[FILL_SLOTS], hcnt[FILL_SLOTS];
+    const int t = threadIdx.x;
+    const unsigned lane = lane_id();
+    for (uint32_t i = t; i < FILL_SLOTS; i += FILL_THREADS) {
+        hkey[i] = FILL_EMPTY;
+        hcnt[i] = 0u;
+    }
     for (int64_t e0 = blockIdx.x * (int64_t)FILL_EDGES; e0 < nE;
          e0 += (int64_t)gridDim.x * FILL_EDGES) {
         const int64_t e1 = nE - e0 > FILL_EDGES ? e0 + FILL_EDGES : nE;
-        if (threadIdx.x == 0) {
-            const int64_t u0 = row_of(rowptr, 0, nU, e0);
-            const int64_t u1 = row_of(rowptr, u0, nU, e1 - 1);
-            row0 = u0;
-            nrows = u1 - u0 + 1;
+        if (t < 64) {
+            const int64_t u = row_of_warp(rowptr, 0, nU, t < 32 ? e0 : e1 - 1, lane);
+            if (lane == 0) row_lim[t >> 5] = u;
+        }
+        for (int i = t; i < FILL_EDGES; i += FILL_THREADS) srow[i] = 0u;
+        __syncthreads();
+        const int64_t u0 = row_lim[0], u1 = row_lim[1];
+        // each row marks its first edge in the step (rows with edges have
+        // distinct starts; u0's is clamped to e0)
+        for (int64_t u = u0 + t; u <= u1; u += FILL_THREADS) {
+            const int64_t a = rowptr[u], b = rowptr[u + 1];
+            const int64_t st = a > e0 ? a : e0;
+            if (b > st && st < e1) srow[st - e0] = (uint32_t)(u - u0 + 1);
         }
         __syncthreads();
-        const int64_t u0 = row0, nr = nrows;
-        const bool staged = nr <= FILL_ROWS;
-        if (staged)
-            for (int64_t i = threadIdx.x; i <= nr && u0 + i <= nU; i += FILL_THREADS)
-                rp[i] = rowptr[u0 + i];
+        fill_running_max(srow, wmax);
         __syncthreads();
-        for (int64_t eb = e0; eb < e1; eb += FILL_THREADS) {
-            const int64_t e = eb + threadIdx.x;
-            const bool in = e < e1;
-            uint32_t rv = 0xffffffffu, r = 0, neg = 0;
-            if (in) {
-                int64_t u, ru;
-                if (staged) {
-                    const int64_t k = row_of(rp, 0, nr, e);
-                    u = u0 + k;
-                    ru = rp[k];
-                } else {
-                    u = row_of(rowptr, u0, u0 + nr, e);
-                    ru = rowptr[u];
+        // 1. U entries; V rows into the shared hash, with each edge's rank
+        // among the step's edges of its row (the loads of all the thread's
+        // edges are issued before the hash inserts)
+        uint32_t slot[FILL_PER], loc[FILL_PER], rvk[FILL_PER], kv[FILL_PER];
+#pragma unroll
+        for (int k = 0; k < FILL_PER; k++) {
+            const int64_t e = e0 + k * FILL_THREADS + t;
+            slot[k] = FILL_SLOTS;
+            loc[k] = rvk[k] = kv[k] = 0u;
+            if (e >= e1) continue;
+            const int64_t u = u0 + srow[e - e0] - 1;
+            const int64_t ru = rowptr[u];
+            const uint32_t r = U.sr_of_id[u];
+            const uint32_t neg = sign[e] < 0 ? 1u : 0u;
+            const uint32_t rv = V.sr_of_id[(uint32_t)col[e]];
+            keyU[U.off[r] + (e - ru)] = ((uint64_t)((rv << 1) | neg) << 32) | (uint32_t)e;
+            slot[k] = 0u;
+            rvk[k] = rv;
+            kv[k] = (r << 1) | neg;
+        }
+#pragma unroll
+        for (int k = 0; k < FILL_PER; k++) {
+            if (slot[k] == FILL_SLOTS) continue;
+            const uint32_t rv = rvk[k];
+            uint32_t h = hash_slot(rv + 1u, 32 - FILL_HASH_BITS);
+            uint32_t probe = 0;
+            for (; probe < FILL_SLOTS; probe++) {
+                const uint32_t cur = *((volatile uint32_t *)&hkey[h]);
+                if (cur == rv) break;
+                if (cur == FILL_EMPTY) {
+                    const uint32_t old = atomicCAS(&hkey[h], FILL_EMPTY, rv);
+                    if (old == FILL_EMPTY || old == rv) break;
                 }
-                r = U.sr_of_id[u];
-                const int64_t pu = U.off[r] + (e - ru);
-                const uint32_t v = (uint32_t)col[e];
-                neg = sign[e] < 0 ? 1u : 0u;
-                rv = V.sr_of_id[v];
-                keyU[pu] = ((uint64_t)((rv << 1) | neg) << 32) | (uint32_t)e;
+                h = (h + 1) & (FILL_SLOTS - 1);
             }
-            const unsigned peers = __match_any_sync(FULL, rv);
-            const unsigned lane = lane_id();
-            const int leader = __ffs(peers) - 1;
-            uint32_t b = 0;
-            if (in && (int)lane == leader) b = atomicAdd(&cursorV[rv], (uint32_t)__popc(peers));
-            b = __shfl_sync(peers, b, leader);
-            if (in) {
-                const int64_t pv = V.off[rv] + b + __popc(peers & ((1u << lane) - 1u));
-                keyV[pv] = ((uint64_t)((r << 1) | neg) << 32) | (uint32_t)e;
+            if (probe == FILL_SLOTS) {  // cannot happen at load <= 1/2
+                set_error(err, E_INTERNAL);
+                slot[k] = FILL_SLOTS;
+                continue;
             }
+            slot[k] = h;
+            loc[k] = atomicAdd(&hcnt[h], 1u);
         }
-        __syncthreads();  // rp is rewritten by the next step
+        __syncthreads();
+        // 2. one global atomic per distinct V row of the step: the base of
+        // its slots replaces its count
+        for (uint32_t i = t; i < FILL_SLOTS; i += FILL_THREADS) {
+            const uint32_t c = hcnt[i];
+            if (!c) continue;
+            hcnt[i] = atomicAdd(&cursorV[hkey[i]], c);
+            hkey[i] = FILL_EMPTY;
+        }
+        __syncthreads();
+        // 3. V entries
+#pragma unroll
+        for (int k = 0; k < FILL_PER; k++) {
+            if (slot[k] == FILL_SLOTS) continue;
+            const int64_t e = e0 + k * FILL_THREADS + t;
+            const int64_t pv = V.off[rvk[k]] + hcnt[slot[k]] + loc[k];
+            keyV[pv] = ((uint64_t)kv[k] << 32) | (uint32_t)e;
+        }
+        __syncthreads();
+        for (uint32_t i = t; i < FILL_SLOTS; i += FILL_THREADS) hcnt[i] = 0u;
+        // (the next step's first barrier orders these stores before its use)
     }
 }
 
@@ -897,7 +980,8 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
         scan_exclusive_u32_to_i64(g.side[sd].deg, g.side[sd].off, ns[sd], ptemp, s);
     if (nU > 0 && nE > 0)
         k_fill<<<grid_for(nE, FILL_EDGES, 4096), FILL_THREADS, 0, s>>>(
-            rowptr, col, sign, nU, nE, g.side[0], g.side[1], cursorV, keys[0], keys[1]); note_launch();
+            rowptr, col, sign, nU, nE, g.side[0], g.side[1], cursorV, keys[0], keys[1],
+            g.err); note_launch();
     // bd[k]: first rank with degree > ROW_LIMS[k]; bd[NLIMS] = n
     for (int sd = 0; sd < 2; sd++)
         if (ns[sd] > 0 && nE > 0) {
