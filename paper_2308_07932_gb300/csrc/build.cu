@@ -601,6 +601,7 @@ struct ClassifyTemp {
     uint32_t *bucket_base;  // [NCLS][NB]
 };
 
+constexpr uint64_t MIDDLE_COST = 8;
 __device__ __forceinline__ uint32_t bucket_of(uint64_t w) { return 63u - (uint32_t)__clzll((long long)w); }
 
 // decides each anchor's class (and split) and counts entries per bucket
@@ -637,7 +638,8 @@ __global__ void k_classify(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
             else if (deg <= WARP_DEG_MAX && W <= P.warp_w_max &&
                 (W <= P.warp_small_w ? dh * 5 / 4 < WARP_CAP : dnh * 5 / 4 < WARP_CAP))
                 cls = CLS_WARP;
-            else if (W <= P.team_w_max && dnh * 5 / 4 < TEAM_CAP) cls = CLS_TEAM;
+            else if (W <= P.team_w_max && deg <= TEAM_DEG_MAX && dnh * 5 / 4 < TEAM_CAP)
+                cls = CLS_TEAM;
             else if (above <= DENSE_CAP) cls = CLS_DENSE;
             else if (dnh * 2 < CTAH_CAP && wnh < (1ull << 31)) cls = CLS_CTAH;
             else cls = CLS_DENSE;  // endpoint range walked in DENSE_CAP windows
@@ -660,7 +662,11 @@ __global__ void k_classify(SideCSR S, int side, ClassifyTemp T, DevGraph G) {
                     }
                 }
             }
-            uint32_t b = bucket_of(parts > 1 ? W / parts : W);
+            // order of work within a class: wedges plus a middle's fixed cost
+            // (its descriptor and chunk-scan slot, about MIDDLE_COST wedges),
+            // so that anchors of many middles and few wedges start early
+            const uint64_t est = W + MIDDLE_COST * (uint64_t)deg;
+            uint32_t b = bucket_of(parts > 1 ? est / parts : est);
             meta = 1u | cls << 1 | b << 3 | parts << 9 | (wide ? 1u << 31 : 0u);
             key = cls * NB + b;
             nparts = parts;

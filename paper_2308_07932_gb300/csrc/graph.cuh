@@ -34,10 +34,14 @@ constexpr uint32_t WARP_DEG_MAX = 255;
 constexpr uint64_t WARP_W_MAX = 16384;
 constexpr uint64_t WARP_SMALL_W = 32;
 constexpr uint32_t WARP_CAP = 256;
-// team class (4 warps): wedges <= TEAM_W_MAX and below-window wedges that fit
-// a TEAM_CAP-slot hash
+// team class (4 warps): wedges <= TEAM_W_MAX, below-window wedges that fit
+// a TEAM_CAP-slot hash, and at most TEAM_DEG_MAX middles (a team scans its
+// middles 128 at a time; an anchor of many middles with few wedges, such as
+// a high-degree vertex whose neighbours rank above it, goes to a 512-thread
+// class instead: one such anchor of 20,261 middles took 0.26 ms as a team)
 constexpr uint64_t TEAM_W_MAX = 16384;
 constexpr uint32_t TEAM_CAP = 1024;
+constexpr uint32_t TEAM_DEG_MAX = 2048;
 // CTA hash class: below-window wedges that fit a CTAH_CAP-slot hash (64 KiB:
 // two or three CTAs per SM; 16Ki slots held one and was 75 % slower)
 constexpr uint32_t CTAH_CAP = 8192;
