@@ -12,6 +12,7 @@
 //      above both v and w, and the wedges anchored at each vertex;
 //   5. split anchors into work classes ordered by decreasing work.
 #include <algorithm>
+#include <mutex>
 #include "graph.cuh"
 #include "prims.cuh"
 
@@ -497,6 +498,113 @@ __global__ void __launch_bounds__(RR_THREADS) k_sort_rows_radix(SideCSR S, uint6
         }
         __syncthreads();
     }
+}
+
+// Rows of more than 2048 entries, when the other side is at most
+// BM_MAX_SLICES * BM_RANKS vertices: one CTA per row. The neighbour ranks of
+// a row are distinct (a repeated one is a duplicate edge), so a bitmap over
+// the rank range sorts them: each entry sets its rank's bit, a block-wide
+// exclusive scan of the words' popcounts gives each word's first position,
+// and an entry's position is that plus the set bits below its own. The
+// rank range is covered in slices of BM_RANKS ranks (the bitmap and the
+// prefixes of one slice fill 128 KiB of shared memory), one pass over the
+// row per slice. Work per row: its entries times the slices, plus the
+// other side's vertices / 32 words per slice.
+constexpr int BM_THREADS = 1024;
+constexpr uint32_t BM_WORDS = 16384;
+constexpr uint32_t BM_RANKS = BM_WORDS * 32;
+constexpr uint32_t BM_MAX_SLICES = 8;
+constexpr uint32_t BM_PER = BM_WORDS / BM_THREADS;  // words per thread in the scan
+constexpr size_t BM_SMEM = 2 * BM_WORDS * 4;
+
+__global__ void __launch_bounds__(BM_THREADS) k_sort_rows_bitmap(SideCSR S, const uint64_t *keys,
+                                                                 uint32_t *eid, uint32_t *rowid,
+                                                                 const int64_t *bounds, int lo_k,
+                                                                 int hi_k, uint32_t n_other,
+                                                                 uint32_t *err) {
+    extern __shared__ uint32_t bm_raw[];
+    uint32_t *bm = bm_raw, *pre = bm_raw + BM_WORDS;
+    __shared__ uint32_t wtot[BM_THREADS / 32];
+    const int t = threadIdx.x;
+    const unsigned lane = lane_id();
+    const int64_t r0 = bounds[lo_k], r1 = bounds[hi_k];
+    const uint32_t slices = (n_other + BM_RANKS - 1) / BM_RANKS;
+    for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
+        const int64_t b = S.off[r];
+        const uint32_t d = (uint32_t)(S.off[r + 1] - b);
+        uint32_t placed = 0;  // entries of the earlier slices
+        for (uint32_t sl = 0; sl < slices; sl++) {
+            const uint32_t lo = sl * BM_RANKS;
+            const uint32_t span = n_other - lo < BM_RANKS ? n_other - lo : BM_RANKS;
+            for (uint32_t i = t; i < BM_WORDS; i += BM_THREADS) bm[i] = 0u;
+            __syncthreads();
+            for (uint32_t i = t; i < d; i += BM_THREADS) {
+                const uint32_t rr = (uint32_t)(keys[b + i] >> 33) - lo;
+                if (rr < span) {
+                    const uint32_t bit = 1u << (rr & 31u);
+                    if (atomicOr(&bm[rr >> 5], bit) & bit) set_error(err, E_DUP);
+                }
+            }
+            __syncthreads();
+            // exclusive prefix of the words' popcounts: BM_PER words a thread
+            uint32_t c[BM_PER], sum = 0;
+#pragma unroll
+            for (uint32_t k = 0; k < BM_PER; k++) {
+                c[k] = __popc(bm[t * BM_PER + k]);
+                sum += c[k];
+            }
+            const uint32_t incl = warp_incl_scan(sum);
+            if (lane == 31) wtot[t >> 5] = incl;
+            __syncthreads();
+            uint32_t ex = incl - sum, total = 0;
+            for (int w = 0; w < BM_THREADS / 32; w++) {
+                const uint32_t v = wtot[w];
+                if (w < (t >> 5)) ex += v;
+                total += v;
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < BM_PER; k++) {
+                pre[t * BM_PER + k] = ex;
+                ex += c[k];
+            }
+            __syncthreads();
+            for (uint32_t i = t; i < d; i += BM_THREADS) {
+                const uint64_t x = keys[b + i];
+                const uint32_t rr = (uint32_t)(x >> 33) - lo;
+                if (rr < span) {
+                    const uint32_t w = rr >> 5;
+                    const uint32_t pos =
+                        placed + pre[w] + __popc(bm[w] & ((1u << (rr & 31u)) - 1u));
+                    if (pos < d) put_entry(S, eid, rowid, b + pos, x, (uint32_t)r);
+                }
+            }
+            placed += total;
+            __syncthreads();  // the next slice rewrites the bitmap
+        }
+        if (placed != d && t == 0) set_error(err, E_DUP);  // only repeated ranks leave gaps
+    }
+}
+
+// per device, once (any thread may build on any device): SM count and the
+// shared-memory opt-in of the bitmap row sort
+constexpr int BUILD_MAX_DEVICES = 64;
+int g_build_sms[BUILD_MAX_DEVICES];
+std::once_flag g_build_once[BUILD_MAX_DEVICES];
+
+int build_sms() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= BUILD_MAX_DEVICES) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    std::call_once(g_build_once[dev], [dev]() {
+        cudaDeviceProp prop;
+        cudaGetDeviceProperties(&prop, dev);
+        g_build_sms[dev] = prop.multiProcessorCount;
+        cudaFuncSetAttribute(k_sort_rows_bitmap, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BM_SMEM);
+    });
+    return g_build_sms[dev] > 0 ? g_build_sms[dev] : 1;
 }
 
 // Per row of a side, as absolute positions in its adjacency: the row's
@@ -1005,6 +1113,12 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
     for (int sd = 0; sd < 2; sd++) {
         if (ns[sd] == 0 || nE == 0) continue;
         const int64_t n_other = ns[1 - sd];
+        if (n_other <= (int64_t)BM_MAX_SLICES * BM_RANKS) {
+            k_sort_rows_bitmap<<<2 * build_sms(), BM_THREADS, BM_SMEM, rs>>>(
+                g.side[sd], keys[sd], eid[sd], rowid[sd], bounds + sd * 16, 7, NLIMS,
+                (uint32_t)n_other, g.err); note_launch();
+            continue;
+        }
         int key_bits = 1;
         while (key_bits < 32 && ((uint64_t)1 << key_bits) < (uint64_t)(2 * n_other + 2)) key_bits++;
         k_sort_rows_radix<<<1024, RR_THREADS, 0, rs>>>(g.side[sd], keys[sd], bufC, eid[sd], rowid[sd],

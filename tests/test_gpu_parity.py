@@ -305,6 +305,24 @@ def test_per_vertex_matches_oracle(ctx, make):
     assert c.per_vertex[g.nU:].sum() == 2 * c.balanced
 
 
+@pytest.mark.parametrize("n_other", [60_000, 4_400_000])
+def test_long_rows_both_row_sorts(ctx, n_other):
+    # rows above 2,048 entries: sorted through a bitmap over the other
+    # side's ranks when that side has at most 8 * 2^19 vertices, by the
+    # per-row radix sort beyond; most of the 4.4M vertices are isolated
+    rng = np.random.default_rng(n_other)
+    us, vs = [], []
+    for v, d in enumerate((3_000, 2_500, 40)):
+        us.append(rng.choice(min(n_other, 20_000), d, replace=False) * (n_other // 20_000))
+        vs.append(np.full(d, v))
+    u, v = np.concatenate(us), np.concatenate(vs)
+    g = synth.from_edges(n_other, 3, u, v, rng.choice([-1, 1], size=u.size), f"long rows {n_other}")
+    want = oracle.count(g, threads=4)
+    for h in (g, synth.swap_sides(g)):
+        c = ctx.count(h)
+        assert (c.balanced, c.total) == want, h.name
+
+
 def test_per_vertex_tiny_and_windowed(ctx):
     for seed in range(40):
         rng = np.random.default_rng(700 + seed)
