@@ -316,18 +316,13 @@ __device__ __forceinline__ void pv_hybrid_anchor(const DevGraph &G, PvHybSmem<TS
                                 noflush, ps.acc, mid);
     }
     __syncthreads();
-    if (tb.hub) {  // four counters per 16-byte read; most blocks are zero
+    if (tb.hub) {
         const uint32_t wb = window_base(A.ns);
-        uint4 *w4 = reinterpret_cast<uint4 *>(sm.win);
-        for (uint32_t q = t; q < HUB_WINDOW / 4; q += TS) {
-            const uint4 c4 = w4[q];
-            if ((c4.x | c4.y | c4.z | c4.w) == 0u) continue;
-            w4[q] = make_uint4(0u, 0u, 0u, 0u);
-            if (!P.spv) continue;
-            const uint32_t cw[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-            for (uint32_t i = 0; i < 4; i++)
-                if (cw[i]) pv_pair(P, window_rank(4 * q + i, wb), pair_b16(cw[i]));
+        for (uint32_t i = t; i < HUB_WINDOW; i += TS) {
+            const uint32_t c = sm.win[i];
+            if (!c) continue;
+            sm.win[i] = 0u;
+            pv_pair(P, window_rank(i, wb), pair_b16(c));
         }
     }
     pv_table_pairs<TS>(P, sm.tab, tb.cap, t);
