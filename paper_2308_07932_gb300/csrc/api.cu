@@ -52,7 +52,6 @@ bb_status bb::wait_bounded(cudaStream_t s, const char *what) {
     cudaError_t e = cudaEventRecord(ev, s);
     if (e != cudaSuccess) { cudaEventDestroy(ev); return cuda_fail(e, what); }
     auto t0 = std::chrono::steady_clock::now();
-    int spins = 0;
     for (;;) {
         e = cudaEventQuery(ev);
         if (e == cudaSuccess) break;
@@ -63,7 +62,11 @@ bb_status bb::wait_bounded(cudaStream_t s, const char *what) {
             cudaEventDestroy(ev);
             return fail(BB_ERR_TIMEOUT, "%s: device work did not finish within %g s", what, limit);
         }
-        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        // poll without sleeping for the first millisecond (short device
+        // work, such as the input validation, then ends within a few
+        // microseconds of its completion), then every 20 us
+        if (dt > 1e-3) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        else std::this_thread::yield();
     }
     cudaEventDestroy(ev);
     return BB_OK;
@@ -106,7 +109,6 @@ bb_class_shape bb::shape_public(const ClassifyParams &p) {
 // until it is idle. For paths that must not create CUDA objects.
 bb_status bb::wait_stream_bounded(cudaStream_t s, const char *what) {
     auto t0 = std::chrono::steady_clock::now();
-    int spins = 0;
     for (;;) {
         const cudaError_t e = cudaStreamQuery(s);
         if (e == cudaSuccess) return BB_OK;
@@ -115,7 +117,8 @@ bb_status bb::wait_stream_bounded(cudaStream_t s, const char *what) {
         const double limit = g_timeout_s.load(std::memory_order_relaxed);
         if (dt > limit)
             return fail(BB_ERR_TIMEOUT, "%s: device work did not finish within %g s", what, limit);
-        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        if (dt > 1e-3) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        else std::this_thread::yield();
     }
 }
 
@@ -350,7 +353,8 @@ bb_status count_device(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int6
     uint32_t verr = 0;
     {
         Range r("validate");
-        st = build_validate(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s, in, &verr);
+        st = build_validate(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s, in, &verr,
+                            &ctx->h_res->build_err, &ctx->h_res->ctr[CTR_MAXDEG]);
     }
     if (st != BB_OK) {
         ctx->layout_key[0] = -1;

@@ -21,6 +21,7 @@ namespace bb {
 namespace {
 
 constexpr int BT = 256;  // default threads per block for simple kernels
+constexpr uint32_t DEG_COPIES = 8;  // V degree counter replicas during validation
 
 inline unsigned grid_for(int64_t n, int threads, int64_t cap = 1 << 20) {
     int64_t b = (n + threads - 1) / threads;
@@ -32,10 +33,12 @@ inline unsigned grid_for(int64_t n, int threads, int64_t cap = 1 << 20) {
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // ------------------------------------------------------------ 1. validate
-// largest of the warp's values into *maxdeg (all lanes of the warp call it)
+// largest of the warp's values into *maxdeg (all lanes of the warp call it);
+// the atomic only when the value exceeds the maximum seen so far (every
+// warp's atomic on one address serialised: 45 us for 2M U vertices)
 __device__ __forceinline__ void warp_max_to(uint32_t v, uint32_t *maxdeg) {
     v = __reduce_max_sync(FULL, v);
-    if (lane_id() == 0 && v) atomicMax(maxdeg, v);
+    if (lane_id() == 0 && v > *(volatile uint32_t *)maxdeg) atomicMax(maxdeg, v);
 }
 
 // rows: rowptr monotone within [0, nE]; U degrees (a degree fits 32 bits
@@ -57,24 +60,34 @@ __global__ void k_validate_rows(const int64_t *rowptr, int64_t nU, int64_t nE, u
     warp_max_to(mx, maxdeg);
 }
 
+// edges: column in range, sign +1/-1, and the V degrees. A hub's degree
+// counter takes one atomic per edge; the counts go to one of `copies`
+// replicas (by block, replica c at degc + c * stride) so that a hub's edges
+// spread over several addresses, summed by k_max_degree.
 __global__ void k_validate_edges(const int32_t *col, const int8_t *sign, int64_t nE, int64_t nV,
-                                 uint32_t *degV, uint32_t *err) {
+                                 uint32_t *degc, int64_t stride, uint32_t copies, uint32_t *err) {
+    uint32_t *deg = degc + (int64_t)(blockIdx.x & (copies - 1u)) * stride;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nE;
          e += (int64_t)gridDim.x * blockDim.x) {
         int32_t c = col[e];
         int8_t sg = sign[e];
         if (c < 0 || (int64_t)c >= nV) set_error(err, E_COL);
-        else atomicAdd(&degV[c], 1u);
+        else atomicAdd(&deg[c], 1u);
         if (sg != 1 && sg != -1) set_error(err, E_SIGN);
     }
 }
 
-// largest V degree
-__global__ void k_max_degree(const uint32_t *deg, int64_t n, uint32_t *maxdeg) {
+// V degrees as the sum of the replicas (written to deg) and their largest
+__global__ void k_max_degree(const uint32_t *degc, int64_t stride, uint32_t copies, uint32_t *deg,
+                             int64_t n, uint32_t *maxdeg) {
     uint32_t mx = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        mx = deg[i] > mx ? deg[i] : mx;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t d = 0;
+        for (uint32_t c = 0; c < copies; c++) d += degc[c * stride + i];
+        if (copies > 1) deg[i] = d;
+        mx = d > mx ? d : mx;
+    }
     warp_max_to(mx, maxdeg);
 }
 
@@ -1016,7 +1029,8 @@ void launch_classes(DevGraph &g, ClassifyTemp T, uint32_t *const *meta, uint32_t
 }  // namespace
 
 bb_status build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
-                         void *temp_mem, cudaStream_t s, const StagedInput *in, uint32_t *verr) {
+                         void *temp_mem, cudaStream_t s, const StagedInput *in, uint32_t *verr,
+                         uint32_t *pin_err, uint32_t *pin_max) {
     const int64_t nU = g.nU, nV = g.nV, nE = g.nE;
     BuildTemp bt = carve_temp(g, temp_mem);
     uint32_t **deg_in = bt.deg_in, *cursorV = bt.cursorV;
@@ -1025,9 +1039,16 @@ bb_status build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col,
     cudaMemsetAsync(g.ctr, 0, NCTR * 4, s);
     cudaMemsetAsync(g.wedges, 0, 8, s);
     cudaMemsetAsync(g.cls_stats, 0, 3 * NCLS * 8, s);
-    cudaMemsetAsync(deg_in[1], 0, (size_t)nV * 4, s);
     cudaMemsetAsync(cursorV, 0, (size_t)nV * 4, s);
     cudaMemsetAsync(T.bucket_cnt, 0, NCLS * NB * 4, s);
+    // V degree replicas in the (not yet used) sort buffer when it has room:
+    // up to DEG_COPIES, a power of two
+    const int64_t stride = (nV + 64) & ~(int64_t)63;
+    uint32_t copies = 1;
+    while (copies < DEG_COPIES &&
+           (int64_t)(2 * copies) * stride * 4 <= (int64_t)(nE + 1) * 8) copies *= 2;
+    uint32_t *degc = copies > 1 ? reinterpret_cast<uint32_t *>(bt.bufC) : deg_in[1];
+    cudaMemsetAsync(degc, 0, (size_t)(copies > 1 ? copies * stride : nV) * 4, s);
 
     // 1. validate + degrees
     if (in) cudaStreamWaitEvent(s, in->rowptr_ready, 0);
@@ -1038,23 +1059,39 @@ bb_status build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col,
             cudaStreamWaitEvent(s, in->ready[c], 0);
             if (n > 0) {
                 k_validate_edges<<<grid_for(n, BT, 16384), BT, 0, s>>>(col + lo, sign + lo, n, nV,
-                                                                      deg_in[1], g.err); note_launch();
+                                                                      degc, stride, copies,
+                                                                      g.err); note_launch();
             }
         }
     } else if (nE > 0) {
-        k_validate_edges<<<grid_for(nE, BT, 16384), BT, 0, s>>>(col, sign, nE, nV, deg_in[1], g.err); note_launch();
+        k_validate_edges<<<grid_for(nE, BT, 16384), BT, 0, s>>>(col, sign, nE, nV, degc, stride,
+                                                                copies, g.err); note_launch();
     }
-    if (nV > 0) k_max_degree<<<grid_for(nV, BT, 8192), BT, 0, s>>>(deg_in[1], nV, g.ctr + CTR_MAXDEG); note_launch();
+    if (nV > 0) k_max_degree<<<grid_for(nV, BT, 8192), BT, 0, s>>>(degc, stride, copies, deg_in[1], nV,
+                                                                   g.ctr + CTR_MAXDEG); note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return report_error(BB_ERR_CUDA, cudaGetErrorString(e));
-    // the one host wait of a build: bounded, creating nothing; the two words
-    // are then copied from the idle stream (to pageable memory)
+    // the one host wait of a build: bounded, creating nothing. With pinned
+    // words the two results are copied behind the checks and read after the
+    // wait; otherwise they are copied from the idle stream to pageable memory
+    uint32_t herr = 0, hmax = 0;
+    if (pin_err && pin_max) {
+        e = cudaMemcpyAsync(pin_err, g.err, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(pin_max, g.ctr + CTR_MAXDEG, 4, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return report_error(BB_ERR_CUDA, cudaGetErrorString(e));
+    }
     bb_status st = wait_stream_bounded(s, "input validation");
     if (st != BB_OK) return st;
-    uint32_t herr = 0, hmax = 0;
-    e = cudaMemcpyAsync(&herr, g.err, 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hmax, g.ctr + CTR_MAXDEG, 4, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return report_error(BB_ERR_CUDA, cudaGetErrorString(e));
+    if (pin_err && pin_max) {
+        herr = *(volatile uint32_t *)pin_err;
+        hmax = *(volatile uint32_t *)pin_max;
+    } else {
+        e = cudaMemcpyAsync(&herr, g.err, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&hmax, g.ctr + CTR_MAXDEG, 4, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return report_error(BB_ERR_CUDA, cudaGetErrorString(e));
+    }
     *verr = herr;
     g.h_maxdeg = hmax;
     g.deg_bits = hmax < (1u << 16) ? 16 : hmax < (1u << 24) ? 24 : 32;
@@ -1147,47 +1184,38 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
         cudaStreamWaitEvent(s, aux->join, 0);
         cudaStreamWaitEvent(s, aux->join2, 0);
     }
+    // 3b-4. per-row records, twin positions, suffix starts and work per
+    // anchor. Side sd's descriptor pass reads the other side's records and
+    // twin positions, so each stream computes those of the other side and
+    // then its own side's descriptors: U descriptors on s, V on the second
+    // auxiliary stream when there is one (the two chains are independent).
+    uint32_t *epos[2] = {(uint32_t *)bufA, (uint32_t *)bufA + (nE + 1)};
+    if (aux) {
+        cudaEventRecord(aux->fork, s);
+        cudaStreamWaitEvent(aux->stream2, aux->fork, 0);
+    }
     for (int sd = 0; sd < 2; sd++) {
         if (ns[sd] == 0) continue;
-        int64_t n_other = ns[1 - sd];
-        uint32_t wb = n_other > (int64_t)HUB_WINDOW ? (uint32_t)(n_other - HUB_WINDOW) : 0u;
-        k_row_info<<<grid_for(ns[sd], BT, 8192), BT, 0, s>>>(g.side[sd], g.side[1 - sd], wb,
-                                                            rinfo[sd]); note_launch();
-    }
-
-    // 4. twin positions, suffix starts, work per anchor
-    uint32_t *epos[2] = {(uint32_t *)bufA, (uint32_t *)bufA + (nE + 1)};
-    if (nE > 0) {
-        for (int sd = 0; sd < 2; sd++)
-            k_epos<<<grid_for(nE, BT, 16384), BT, 0, s>>>(eid[sd], nE, epos[sd]); note_launch();
-        for (int sd = 0; sd < 2; sd++) {
-            if (ns[sd] == 0) continue;
-            cudaMemsetAsync(g.side[sd].work, 0, (size_t)ns[sd] * 8, s);
-            cudaMemsetAsync(g.side[sd].work_nh, 0, (size_t)ns[sd] * 8, s);
+        const cudaStream_t ss = (aux && sd == 1) ? aux->stream2 : s;
+        const int od = 1 - sd;  // the side whose records this side's descriptors read
+        if (ns[od] > 0) {
+            const int64_t n_other = ns[sd];
+            const uint32_t wb = n_other > (int64_t)HUB_WINDOW ? (uint32_t)(n_other - HUB_WINDOW) : 0u;
+            k_row_info<<<grid_for(ns[od], BT, 8192), BT, 0, ss>>>(g.side[od], g.side[sd], wb,
+                                                                 rinfo[od]); note_launch();
         }
-        // the two sides' descriptor passes side by side (V on the second
-        // auxiliary stream when there is one)
-        if (aux) {
-            cudaEventRecord(aux->fork, s);
-            cudaStreamWaitEvent(aux->stream2, aux->fork, 0);
-        }
-        for (int sd = 0; sd < 2; sd++) {
-            if (ns[sd] == 0) continue;
-            const cudaStream_t ss = (aux && sd == 1) ? aux->stream2 : s;
-            k_md_work<<<grid_for(nE, BT, 8192), BT, 0, ss>>>(g.side[sd], rinfo[1 - sd], eid[sd],
-                                                            epos[1 - sd], rowid[sd], nE,
+        if (nE > 0) { k_epos<<<grid_for(nE, BT, 16384), BT, 0, ss>>>(eid[od], nE, epos[od]); note_launch(); }
+        cudaMemsetAsync(g.side[sd].work, 0, (size_t)ns[sd] * 8, ss);
+        cudaMemsetAsync(g.side[sd].work_nh, 0, (size_t)ns[sd] * 8, ss);
+        if (nE > 0) {
+            k_md_work<<<grid_for(nE, BT, 8192), BT, 0, ss>>>(g.side[sd], rinfo[od], eid[sd],
+                                                            epos[od], rowid[sd], nE,
                                                             g.wedges); note_launch();
         }
-        if (aux) {
-            cudaEventRecord(aux->join2, aux->stream2);
-            cudaStreamWaitEvent(s, aux->join2, 0);
-        }
-    } else {
-        for (int sd = 0; sd < 2; sd++)
-            if (ns[sd] > 0) {
-                cudaMemsetAsync(g.side[sd].work, 0, (size_t)ns[sd] * 8, s);
-                cudaMemsetAsync(g.side[sd].work_nh, 0, (size_t)ns[sd] * 8, s);
-            }
+    }
+    if (aux) {
+        cudaEventRecord(aux->join2, aux->stream2);
+        cudaStreamWaitEvent(s, aux->join2, 0);
     }
 
     // 5. classes (bucket counts, class counters and statistics were zeroed

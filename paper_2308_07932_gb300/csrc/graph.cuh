@@ -192,8 +192,12 @@ struct StagedInput {
     cudaEvent_t rowptr_ready = nullptr;
     cudaEvent_t ready[MAX_CHUNKS] = {};
 };
+// pin_err / pin_max: optional pinned host words that receive the error
+// word and the largest degree behind the checks (saves two pageable copies
+// after the wait).
 bb_status build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
-                         void *temp_mem, cudaStream_t s, const StagedInput *in, uint32_t *verr);
+                         void *temp_mem, cudaStream_t s, const StagedInput *in, uint32_t *verr,
+                         uint32_t *pin_err = nullptr, uint32_t *pin_max = nullptr);
 void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
                 void *temp_mem, cudaStream_t s, const BuildAux *aux);
 
