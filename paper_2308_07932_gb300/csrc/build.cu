@@ -295,9 +295,10 @@ __global__ void __launch_bounds__(FILL_THREADS) k_fill(
 // Row length classes of a side (rows are in ascending degree, so each class
 // is a contiguous range of side ranks): bounds[k] = first side rank whose
 // degree exceeds ROW_LIMS[k]; bounds[NLIMS] = n.
-constexpr int NLIMS = 11;
-__constant__ uint32_t ROW_LIMS[NLIMS] = {1u, 2u, 4u, 8u, 16u, 32u, 64u, 128u, 256u, 2048u, 16384u};
-constexpr int LIM_LONG = 9;  // class of the rows above 2,048 entries
+constexpr int NLIMS = 12;
+__constant__ uint32_t ROW_LIMS[NLIMS] = {1u,  2u,   4u,   8u,    16u,   32u,
+                                         64u, 128u, 256u, 512u, 2048u, 16384u};
+constexpr int LIM_LONG = 10;  // class of the rows above 2,048 entries
 
 __global__ void k_row_bounds(const uint32_t *deg, int64_t n, int64_t *bounds) {
     int k = threadIdx.x;
@@ -366,7 +367,7 @@ __global__ void k_sort_rows_sub(SideCSR S, const uint64_t *keys, uint32_t *eid, 
     }
 }
 
-// rows of (16 K, 32 K] entries (K = 2, 4, 8: 33 to 256 entries): one warp
+// rows of (16 K, 32 K] entries (K = 2 to 16: 33 to 512 entries): one warp
 // per row, bitonic sort in registers with K entries per lane (entry i in
 // lane i / K, slot i % K): the partner at distance j < K is in the lane's
 // own registers, a farther one a shuffle away. (A shared-memory bitonic sort
@@ -428,7 +429,7 @@ __global__ void __launch_bounds__(256) k_sort_rows_warpreg(SideCSR S, const uint
     }
 }
 
-// rows of (256, CAP] entries: one CTA per row, bitonic sort in shared memory
+// rows of (512, CAP] entries: one CTA per row, bitonic sort in shared memory
 template <int CAP, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_sort_rows_smem(SideCSR S, const uint64_t *keys,
                                                             uint32_t *eid, uint32_t *rowid,
@@ -1203,7 +1204,8 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
         k_sort_rows_warpreg<2><<<2048, 256, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 5, g.err); note_launch();
         k_sort_rows_warpreg<4><<<2048, 256, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 6, g.err); note_launch();
         k_sort_rows_warpreg<8><<<2048, 256, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 7, g.err); note_launch();
-        k_sort_rows_smem<2048, 256><<<2048, 256, 2048 * 8, ss>>>(S, ky, eid[sd], rowid[sd], bd, 8, g.err); note_launch();
+        k_sort_rows_warpreg<16><<<2048, 256, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 8, g.err); note_launch();
+        k_sort_rows_smem<2048, 256><<<2048, 256, 2048 * 8, ss>>>(S, ky, eid[sd], rowid[sd], bd, 9, g.err); note_launch();
     }
     if (aux) {
         cudaEventRecord(aux->join2, aux->stream2);
