@@ -13,6 +13,7 @@
 //   5. split anchors into work classes ordered by decreasing work.
 #include <algorithm>
 #include <mutex>
+#include "edgerows.cuh"
 #include "graph.cuh"
 #include "prims.cuh"
 
@@ -131,76 +132,27 @@ __global__ void k_global_rank(SideCSR S, const uint32_t *other_deg, int64_t n_ot
 // Each input edge e is written into the rows of both endpoints: the U-side
 // entry keeps the input position within its row u; the V-side entry takes
 // a free slot of v's row. Each entry is written as one key (packed entry <<
-// 32 | input edge id) for the row sorts. A block takes FILL_EDGES
-// consecutive edges per step. Two warps find the step's first and last row
-// (32 probes per round); every row of the step marks its first edge of the
-// step in shared memory and a block-wide running maximum gives each edge
-// its row (no search per edge, however many empty rows the step spans).
-// The V rows of the step's edges are gathered in a shared hash, so that
-// each distinct V row takes its slots with one global atomic per step (hub
-// rows take edges from most steps).
-constexpr int FILL_THREADS = 256;
-constexpr int FILL_EDGES = 2048;
-constexpr int FILL_PER = FILL_EDGES / FILL_THREADS;
+// 32 | input edge id) for the row sorts. A block takes edgerows::EDGES
+// consecutive edges per step and finds their rows without a search per
+// edge (edgerows.cuh). The V rows of the step's edges are gathered in a
+// shared hash, so that each distinct V row takes its slots with one global
+// atomic per step (hub rows take edges from most steps).
+constexpr int FILL_THREADS = edgerows::THREADS;
+constexpr int FILL_EDGES = edgerows::EDGES;
+constexpr int FILL_PER = edgerows::PER;
 constexpr uint32_t FILL_SLOTS = 4096;
 constexpr uint32_t FILL_EMPTY = 0xffffffffu;
 constexpr uint32_t FILL_HASH_BITS = 12;
 static_assert(FILL_SLOTS == 1u << FILL_HASH_BITS && FILL_SLOTS >= 2 * FILL_EDGES, "fill hash");
 
-// last u in [lo, hi) with rp[u] <= e (rp[lo] <= e), by a whole warp (all
-// lanes call it with the same arguments): each round probes 31 evenly
-// spaced rows of (lo, hi) and keeps the gap between the last one at or
-// below e and the next
-__device__ __forceinline__ int64_t row_of_warp(const int64_t *rp, int64_t lo, int64_t hi,
-                                               int64_t e, unsigned lane) {
-    while (hi - lo > 1) {
-        const int64_t p = lo + ((hi - lo) * (int64_t)(lane + 1)) / 32;
-        const bool le = lane < 31 && rp[p] <= e;
-        const int c = __popc(__ballot_sync(FULL, le));  // the true probes form a prefix
-        const int64_t nlo = c > 0 ? __shfl_sync(FULL, p, c - 1) : lo;
-        const int64_t nhi = c < 31 ? __shfl_sync(FULL, p, c) : hi;
-        lo = nlo;
-        hi = nhi;
-    }
-    return lo;
-}
-
-// block-wide inclusive running maximum of a[0..FILL_EDGES), FILL_PER
-// consecutive values per thread
-__device__ __forceinline__ void fill_running_max(uint32_t *a, uint32_t *wmax) {
-    const int t = threadIdx.x;
-    const unsigned lane = lane_id();
-    uint32_t v[FILL_PER], m = 0;
-#pragma unroll
-    for (int k = 0; k < FILL_PER; k++) {
-        m = max(m, a[t * FILL_PER + k]);
-        v[k] = m;
-    }
-    uint32_t x = m;  // inclusive warp scan (max) of the threads' maxima
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULL, x, d);
-        if (lane >= (unsigned)d) x = max(x, y);
-    }
-    if (lane == 31) wmax[t >> 5] = x;
-    __syncthreads();
-    uint32_t before = __shfl_up_sync(FULL, x, 1);
-    if (lane == 0) before = 0;
-    for (int w = 0; w < (t >> 5); w++) before = max(before, wmax[w]);
-#pragma unroll
-    for (int k = 0; k < FILL_PER; k++) a[t * FILL_PER + k] = max(before, v[k]);
-}
-
 __global__ void __launch_bounds__(FILL_THREADS) k_fill(
     const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
     const int8_t *__restrict__ sign, int64_t nU, int64_t nE, SideCSR U, SideCSR V,
     uint32_t *cursorV, uint64_t *keyU, uint64_t *keyV, uint32_t *err) {
-    __shared__ int64_t row_lim[2];
-    __shared__ uint32_t srow[FILL_EDGES];  // per edge of the step: its row - u0 + 1
-    __shared__ uint32_t wmax[FILL_THREADS / 32];
+    __shared__ edgerows::Smem er;
     __shared__ uint32_t hkey[FILL_SLOTS], hcnt[FILL_SLOTS];
     const int t = threadIdx.x;
-    const unsigned lane = lane_id();
+    const uint32_t *srow = er.srow;
     for (uint32_t i = t; i < FILL_SLOTS; i += FILL_THREADS) {
         hkey[i] = FILL_EMPTY;
         hcnt[i] = 0u;
@@ -208,23 +160,7 @@ __global__ void __launch_bounds__(FILL_THREADS) k_fill(
     for (int64_t e0 = blockIdx.x * (int64_t)FILL_EDGES; e0 < nE;
          e0 += (int64_t)gridDim.x * FILL_EDGES) {
         const int64_t e1 = nE - e0 > FILL_EDGES ? e0 + FILL_EDGES : nE;
-        if (t < 64) {
-            const int64_t u = row_of_warp(rowptr, 0, nU, t < 32 ? e0 : e1 - 1, lane);
-            if (lane == 0) row_lim[t >> 5] = u;
-        }
-        for (int i = t; i < FILL_EDGES; i += FILL_THREADS) srow[i] = 0u;
-        __syncthreads();
-        const int64_t u0 = row_lim[0], u1 = row_lim[1];
-        // each row marks its first edge in the step (rows with edges have
-        // distinct starts; u0's is clamped to e0)
-        for (int64_t u = u0 + t; u <= u1; u += FILL_THREADS) {
-            const int64_t a = rowptr[u], b = rowptr[u + 1];
-            const int64_t st = a > e0 ? a : e0;
-            if (b > st && st < e1) srow[st - e0] = (uint32_t)(u - u0 + 1);
-        }
-        __syncthreads();
-        fill_running_max(srow, wmax);
-        __syncthreads();
+        const int64_t u0 = edgerows::step_rows(rowptr, nU, e0, e1, er);
         // 1. U entries; V rows into the shared hash, with each edge's rank
         // among the step's edges of its row (the loads of all the thread's
         // edges are issued before the hash inserts)

@@ -29,6 +29,7 @@
 // MAX_DEGREE, 32-bit tally fields) go to k_pv_wide.
 #include <algorithm>
 #include <mutex>
+#include "edgerows.cuh"
 #include "walk.cuh"
 
 namespace bb {
@@ -688,23 +689,29 @@ __global__ void __launch_bounds__(DENSE_THREADS) k_pv_wide(DevGraph G, PvOut out
 
 // per-edge counts in the caller's edge order: an input edge (u, v) is the
 // entry of v in u's U-side row and the entry of u in v's V-side row; its
-// count is the sum of the two entries' counts
-__global__ void k_pe_out(DevGraph G, const unsigned long long *peU,
-                         const unsigned long long *peV, int64_t *out) {
-    const SideCSR &U = G.side[0];
-    const SideCSR &V = G.side[1];
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < G.nE;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t lo = 0, hi = G.nU;  // last u with rowptr[u] <= e
-        while (hi - lo > 1) {
-            const int64_t m = (lo + hi) >> 1;
-            if (G.rowptr[m] <= e) lo = m; else hi = m;
+// count is the sum of the two entries' counts. A block takes consecutive
+// input edges per step and finds their rows without a search per edge.
+__global__ void __launch_bounds__(edgerows::THREADS) k_pe_out(DevGraph G,
+                                                              const unsigned long long *peU,
+                                                              const unsigned long long *peV,
+                                                              int64_t *out) {
+    __shared__ edgerows::Smem er;
+    const int t = threadIdx.x;
+    const int64_t nE = G.nE;
+    for (int64_t e0 = blockIdx.x * (int64_t)edgerows::EDGES; e0 < nE;
+         e0 += (int64_t)gridDim.x * edgerows::EDGES) {
+        const int64_t e1 = nE - e0 > edgerows::EDGES ? e0 + edgerows::EDGES : nE;
+        const int64_t u0 = edgerows::step_rows(G.rowptr, G.nU, e0, e1, er);
+        for (int64_t e = e0 + t; e < e1; e += edgerows::THREADS) {
+            const uint32_t ru = G.side[0].sr_of_id[u0 + er.srow[e - e0] - 1];
+            const uint32_t rv = G.side[1].sr_of_id[G.col[e]];
+            const int64_t p = lower_bound_u32(G.side[0].adj, G.side[0].off[ru], G.side[0].off[ru + 1],
+                                              rv << 1);
+            const int64_t q = lower_bound_u32(G.side[1].adj, G.side[1].off[rv], G.side[1].off[rv + 1],
+                                              ru << 1);
+            out[e] = (int64_t)(peU[p] + peV[q]);
         }
-        const uint32_t ru = U.sr_of_id[lo];
-        const uint32_t rv = V.sr_of_id[G.col[e]];
-        const int64_t p = lower_bound_u32(U.adj, U.off[ru], U.off[ru + 1], rv << 1);
-        const int64_t q = lower_bound_u32(V.adj, V.off[rv], V.off[rv + 1], ru << 1);
-        out[e] = (int64_t)(peU[p] + peV[q]);
+        __syncthreads();  // the next step rewrites the shared rows
     }
 }
 
@@ -785,8 +792,8 @@ void launch_per_edge(const DevGraph &g, int64_t *out_dev, unsigned long long *pe
     PvOut o{0, {peU, peV}};
     launch_pv_kernels(g, o, s, ev);
     if (g.nE == 0) return;
-    const int64_t blocks = std::min<int64_t>((g.nE + 255) / 256, 16384);
-    k_pe_out<<<(unsigned)blocks, 256, 0, s>>>(g, peU, peV, out_dev); note_launch();
+    const int64_t blocks = std::min<int64_t>((g.nE + edgerows::EDGES - 1) / edgerows::EDGES, 4096);
+    k_pe_out<<<(unsigned)blocks, edgerows::THREADS, 0, s>>>(g, peU, peV, out_dev); note_launch();
 }
 
 void launch_per_vertex(const DevGraph &g, int64_t *out_dev, cudaStream_t s, cudaEvent_t *ev) {
