@@ -884,6 +884,8 @@ BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE) {
     t += 3 * align256((size_t)nE * 8 + 8);                                   // row keys, sort buffer, epos
     t += 2 * align256((size_t)nmax * 4 + 4);                                 // rank sort alt
     t += align256(std::max(radix_temp_bytes(nmax), scan_temp_bytes(nmax + 1)));
+    t += 2 * align256((size_t)nV * 4 + 4);                                   // V rank chain
+    t += align256(std::max(radix_temp_bytes(nV), scan_temp_bytes(nV + 1)));
     t += 2 * align256((size_t)nmax * 4 + 4) * 2;                             // classify meta/grp
     t += 2 * align256(NCLS * NB * 4) + align256(64 * 8);                     // buckets, bounds
     t += align256((size_t)(nU + 1) * 16) + align256((size_t)(nV + 1) * 16);  // row records
@@ -933,8 +935,8 @@ namespace {
 struct BuildTemp {
     uint32_t *deg_in[2], *eid[2], *rowid[2], *cursorV;
     uint64_t *bufA, *bufB, *bufC, *keys[2];
-    uint32_t *ralt_k, *ralt_v;
-    void *ptemp;
+    uint32_t *ralt_k, *ralt_v, *ralt2_k, *ralt2_v;
+    void *ptemp, *ptemp2;
     uint32_t *meta[2], *grp[2];
     ClassifyTemp T;
     int64_t *bounds;
@@ -957,6 +959,9 @@ BuildTemp carve_temp(const DevGraph &g, void *temp_mem) {
     t.ralt_k = c.take<uint32_t>(nmax + 1);
     t.ralt_v = c.take<uint32_t>(nmax + 1);
     t.ptemp = c.take<char>(std::max(radix_temp_bytes(nmax), scan_temp_bytes(nmax + 1)));
+    t.ralt2_k = c.take<uint32_t>(nV + 1);  // the V side's rank chain, beside the U side's
+    t.ralt2_v = c.take<uint32_t>(nV + 1);
+    t.ptemp2 = c.take<char>(std::max(radix_temp_bytes(nV), scan_temp_bytes(nV + 1)));
     t.meta[0] = c.take<uint32_t>(nmax + 1); t.meta[1] = c.take<uint32_t>(nmax + 1);
     t.grp[0] = c.take<uint32_t>(nmax + 1); t.grp[1] = c.take<uint32_t>(nmax + 1);
     t.T.bucket_cnt = c.take<uint32_t>(NCLS * NB);
@@ -1071,25 +1076,40 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
     ClassifyTemp &T = bt.T;
     int64_t *bounds = bt.bounds;
     uint4 **rinfo = bt.rinfo;
-    // 2. side ranks by (degree, id), then the global priority rank
+    // 2. side ranks by (degree, id) and the row offsets in rank order: the
+    // U side on s, the V side on the second auxiliary stream when there is
+    // one (each with its own sort scratch); then the global priority rank
     int64_t ns[2] = {nU, nV};
+    if (aux) {
+        cudaEventRecord(aux->fork, s);
+        cudaStreamWaitEvent(aux->stream2, aux->fork, 0);
+    }
     for (int sd = 0; sd < 2; sd++) {
         int64_t n = ns[sd];
-        if (n == 0) continue;
+        if (n == 0) {  // an empty side's single offset
+            cudaMemsetAsync(g.side[sd].off, 0, 8, s);
+            continue;
+        }
         SideCSR &S = g.side[sd];
+        const cudaStream_t ss = (aux && sd == 1) ? aux->stream2 : s;
+        uint32_t *rk = sd ? bt.ralt2_k : ralt_k, *rv = sd ? bt.ralt2_v : ralt_v;
+        void *pt = sd ? bt.ptemp2 : ptemp;
         // sort ids by degree (stable => ties by id): reuse id_of_sr / deg as buffers
-        k_iota<<<grid_for(n, BT, 8192), BT, 0, s>>>(S.sr_of_id, n); note_launch();
-        cudaMemcpyAsync(S.lo, deg_in[sd], (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
-        radix_sort_pairs_u32(S.lo, S.sr_of_id, ralt_k, ralt_v, n, g.deg_bits, ptemp, s);
-        cudaMemcpyAsync(ralt_v, S.sr_of_id, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
-        k_side_rank<<<grid_for(n, BT, 8192), BT, 0, s>>>(ralt_v, S.lo, n, S); note_launch();
+        k_iota<<<grid_for(n, BT, 8192), BT, 0, ss>>>(S.sr_of_id, n); note_launch();
+        cudaMemcpyAsync(S.lo, deg_in[sd], (size_t)n * 4, cudaMemcpyDeviceToDevice, ss);
+        radix_sort_pairs_u32(S.lo, S.sr_of_id, rk, rv, n, g.deg_bits, pt, ss);
+        cudaMemcpyAsync(rv, S.sr_of_id, (size_t)n * 4, cudaMemcpyDeviceToDevice, ss);
+        k_side_rank<<<grid_for(n, BT, 8192), BT, 0, ss>>>(rv, S.lo, n, S); note_launch();
+        scan_exclusive_u32_to_i64(S.deg, S.off, n, pt, ss);
+    }
+    if (aux) {
+        cudaEventRecord(aux->join2, aux->stream2);
+        cudaStreamWaitEvent(s, aux->join2, 0);
     }
     if (nU > 0) k_global_rank<<<grid_for(nU, BT, 8192), BT, 0, s>>>(g.side[0], g.side[1].deg, nV, 1); note_launch();
     if (nV > 0) k_global_rank<<<grid_for(nV, BT, 8192), BT, 0, s>>>(g.side[1], g.side[0].deg, nU, 0); note_launch();
 
-    // 3. offsets, row fill, row sorts, lo
-    for (int sd = 0; sd < 2; sd++)
-        scan_exclusive_u32_to_i64(g.side[sd].deg, g.side[sd].off, ns[sd], ptemp, s);
+    // 3. row fill, row sorts, lo
     if (nU > 0 && nE > 0)
         k_fill<<<grid_for(nE, FILL_EDGES, 4096), FILL_THREADS, 0, s>>>(
             rowptr, col, sign, nU, nE, g.side[0], g.side[1], cursorV, keys[0], keys[1],
