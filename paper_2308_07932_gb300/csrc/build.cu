@@ -148,7 +148,7 @@ static_assert(FILL_SLOTS == 1u << FILL_HASH_BITS && FILL_SLOTS >= 2 * FILL_EDGES
 __global__ void __launch_bounds__(FILL_THREADS) k_fill(
     const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
     const int8_t *__restrict__ sign, int64_t nU, int64_t nE, SideCSR U, SideCSR V,
-    uint32_t *cursorV, uint64_t *keyU, uint64_t *keyV, uint32_t *err) {
+    uint32_t *cursorV, uint32_t *keyU, uint32_t *keyV, uint32_t *err) {
     __shared__ edgerows::Smem er;
     __shared__ uint32_t hkey[FILL_SLOTS], hcnt[FILL_SLOTS];
     const int t = threadIdx.x;
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(FILL_THREADS) k_fill(
             const uint32_t r = U.sr_of_id[u];
             const uint32_t neg = sign[e] < 0 ? 1u : 0u;
             const uint32_t rv = V.sr_of_id[(uint32_t)col[e]];
-            keyU[U.off[r] + (e - ru)] = ((uint64_t)((rv << 1) | neg) << 32) | (uint32_t)e;
+            keyU[U.off[r] + (e - ru)] = (rv << 1) | neg;
             slot[k] = 0u;
             rvk[k] = rv;
             kv[k] = (r << 1) | neg;
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(FILL_THREADS) k_fill(
             if (slot[k] == FILL_SLOTS) continue;
             const int64_t e = e0 + k * FILL_THREADS + t;
             const int64_t pv = V.off[rvk[k]] + hcnt[slot[k]] + loc[k];
-            keyV[pv] = ((uint64_t)kv[k] << 32) | (uint32_t)e;
+            keyV[pv] = kv[k];
         }
         __syncthreads();
         for (uint32_t i = t; i < FILL_SLOTS; i += FILL_THREADS) hcnt[i] = 0u;
@@ -247,30 +247,26 @@ __global__ void k_row_bounds(const uint32_t *deg, int64_t n, int64_t *bounds) {
 }
 
 
-// writes one sorted key back as the entry, its edge id and its row
-__device__ __forceinline__ void put_entry(SideCSR &S, uint32_t *eid, uint32_t *rowid, int64_t p,
-                                          uint64_t x, uint32_t r) {
-    S.adj[p] = (uint32_t)(x >> 32);
-    eid[p] = (uint32_t)x;
-    rowid[p] = r;
-}
+// A row key is the entry itself (neighbour side rank << 1 | negative); a
+// row's ranks are distinct, so equal ranks next to each other after a sort
+// are a duplicate edge.
+__device__ __forceinline__ bool same_rank(uint32_t a, uint32_t b) { return (a >> 1) == (b >> 1); }
 
 // rows of degree 0 or 1: nothing to sort, unpack the key
-__global__ void k_rows_single(SideCSR S, const uint64_t *keys, uint32_t *eid, uint32_t *rowid,
-                              const int64_t *bounds) {
+__global__ void k_rows_single(SideCSR S, const uint32_t *keys, const int64_t *bounds) {
     const int64_t r1 = bounds[0];
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < r1;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = S.off[r];
-        if (S.off[r + 1] > b) put_entry(S, eid, rowid, b, keys[b], (uint32_t)r);
+        if (S.off[r + 1] > b) S.adj[b] = keys[b];
     }
 }
 
 // rows of (WIDTH/2, WIDTH] entries, WIDTH <= 32: 32/WIDTH rows per warp,
 // bitonic sort in registers across WIDTH lanes
 template <int WIDTH>
-__global__ void k_sort_rows_sub(SideCSR S, const uint64_t *keys, uint32_t *eid, uint32_t *rowid,
-                                const int64_t *bounds, int lo_k, uint32_t *err) {
+__global__ void k_sort_rows_sub(SideCSR S, const uint32_t *keys, const int64_t *bounds, int lo_k,
+                                uint32_t *err) {
     constexpr int PER = 32 / WIDTH;
     const int64_t r0 = bounds[lo_k], r1 = bounds[lo_k + 1];
     const unsigned lane = lane_id();
@@ -285,20 +281,20 @@ __global__ void k_sort_rows_sub(SideCSR S, const uint64_t *keys, uint32_t *eid, 
             b = S.off[r];
             d = (uint32_t)(S.off[r + 1] - b);
         }
-        uint64_t x = el < d ? keys[b + el] : ~0ull;
+        uint32_t x = el < d ? keys[b + el] : ~0u;
 #pragma unroll
         for (int k = 2; k <= WIDTH; k <<= 1) {
 #pragma unroll
             for (int j = k >> 1; j > 0; j >>= 1) {
-                const uint64_t y = __shfl_xor_sync(FULL, x, j);
+                const uint32_t y = __shfl_xor_sync(FULL, x, j);
                 const bool keep_min = ((el & j) == 0) == ((el & k) == 0);
-                x = keep_min ? (x < y ? x : y) : (x < y ? y : x);
+                x = keep_min ? min(x, y) : max(x, y);
             }
         }
-        const uint64_t prev = __shfl_up_sync(FULL, x, 1);
+        const uint32_t prev = __shfl_up_sync(FULL, x, 1);
         if (el < d) {
-            put_entry(S, eid, rowid, b + el, x, (uint32_t)r);
-            if (el > 0 && (prev >> 33) == (x >> 33)) set_error(err, E_DUP);
+            S.adj[b + el] = x;
+            if (el > 0 && same_rank(prev, x)) set_error(err, E_DUP);
         }
     }
 }
@@ -309,8 +305,7 @@ __global__ void k_sort_rows_sub(SideCSR S, const uint64_t *keys, uint32_t *eid, 
 // own registers, a farther one a shuffle away. (A shared-memory bitonic sort
 // of these rows took about 2.5 times the instructions.)
 template <int K>
-__global__ void __launch_bounds__(256) k_sort_rows_warpreg(SideCSR S, const uint64_t *keys,
-                                                           uint32_t *eid, uint32_t *rowid,
+__global__ void __launch_bounds__(256) k_sort_rows_warpreg(SideCSR S, const uint32_t *keys,
                                                            const int64_t *bounds, int lo_k,
                                                            uint32_t *err) {
     constexpr uint32_t P = 32 * K;
@@ -321,20 +316,20 @@ __global__ void __launch_bounds__(256) k_sort_rows_warpreg(SideCSR S, const uint
          r += warps) {
         const int64_t b = S.off[r];
         const uint32_t d = (uint32_t)(S.off[r + 1] - b);
-        uint64_t x[K];
+        uint32_t x[K];
 #pragma unroll
         for (int q = 0; q < K; q++) {
             const uint32_t i = lane * K + q;
-            x[q] = i < d ? keys[b + i] : ~0ull;
+            x[q] = i < d ? keys[b + i] : ~0u;
         }
         for (uint32_t k = 2; k <= P; k <<= 1) {
             for (uint32_t j = k >> 1; j >= (uint32_t)K; j >>= 1) {  // partners in other lanes
 #pragma unroll
                 for (int q = 0; q < K; q++) {
                     const uint32_t i = lane * K + q;
-                    const uint64_t y = __shfl_xor_sync(FULL, x[q], j / K);
+                    const uint32_t y = __shfl_xor_sync(FULL, x[q], j / K);
                     const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
-                    x[q] = keep_min ? (x[q] < y ? x[q] : y) : (x[q] < y ? y : x[q]);
+                    x[q] = keep_min ? min(x[q], y) : max(x[q], y);
                 }
             }
 #pragma unroll
@@ -344,7 +339,7 @@ __global__ void __launch_bounds__(256) k_sort_rows_warpreg(SideCSR S, const uint
                 for (int q = 0; q < K; q++) {
                     if (q & j) continue;  // q is the lower entry of the pair (q, q | j)
                     const bool asc = ((lane * K + q) & k) == 0;
-                    const uint64_t a = x[q], c = x[q | j];
+                    const uint32_t a = x[q], c = x[q | j];
                     const bool swap = asc ? a > c : a < c;
                     x[q] = swap ? c : a;
                     x[q | j] = swap ? a : c;
@@ -352,14 +347,14 @@ __global__ void __launch_bounds__(256) k_sort_rows_warpreg(SideCSR S, const uint
             }
         }
         // write back; a repeated rank is a duplicate edge
-        const uint64_t prev_last = __shfl_up_sync(FULL, x[K - 1], 1);
+        const uint32_t prev_last = __shfl_up_sync(FULL, x[K - 1], 1);
 #pragma unroll
         for (int q = 0; q < K; q++) {
             const uint32_t i = lane * K + q;
             if (i < d) {
-                put_entry(S, eid, rowid, b + i, x[q], (uint32_t)r);
-                const uint64_t pv = q ? x[q - 1] : prev_last;
-                if (i > 0 && (pv >> 33) == (x[q] >> 33)) set_error(err, E_DUP);
+                S.adj[b + i] = x[q];
+                const uint32_t pv = q ? x[q - 1] : prev_last;
+                if (i > 0 && same_rank(pv, x[q])) set_error(err, E_DUP);
             }
         }
     }
@@ -367,11 +362,10 @@ __global__ void __launch_bounds__(256) k_sort_rows_warpreg(SideCSR S, const uint
 
 // rows of (512, CAP] entries: one CTA per row, bitonic sort in shared memory
 template <int CAP, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_sort_rows_smem(SideCSR S, const uint64_t *keys,
-                                                            uint32_t *eid, uint32_t *rowid,
+__global__ void __launch_bounds__(THREADS) k_sort_rows_smem(SideCSR S, const uint32_t *keys,
                                                             const int64_t *bounds, int lo_k,
                                                             uint32_t *err) {
-    extern __shared__ uint64_t sbuf[];
+    extern __shared__ uint32_t sbuf[];
     const int64_t r0 = bounds[lo_k], r1 = bounds[lo_k + 1];
     for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
         int64_t b = S.off[r];
@@ -379,23 +373,23 @@ __global__ void __launch_bounds__(THREADS) k_sort_rows_smem(SideCSR S, const uin
         uint32_t P = 1;
         while (P < d) P <<= 1;
         for (uint32_t i = threadIdx.x; i < P; i += THREADS)
-            sbuf[i] = i < d ? keys[b + i] : ~0ull;
+            sbuf[i] = i < d ? keys[b + i] : ~0u;
         __syncthreads();
         for (uint32_t k = 2; k <= P; k <<= 1) {
             for (uint32_t j = k >> 1; j > 0; j >>= 1) {
                 // compare-exchange pairs (i, i + j), i with bit j clear: P/2 of them
                 for (uint32_t q = threadIdx.x; q < P / 2; q += THREADS) {
                     const uint32_t i = ((q & ~(j - 1)) << 1) | (q & (j - 1));
-                    const uint64_t a = sbuf[i], c = sbuf[i | j];
+                    const uint32_t a = sbuf[i], c = sbuf[i | j];
                     if ((a > c) == ((i & k) == 0)) { sbuf[i] = c; sbuf[i | j] = a; }
                 }
                 __syncthreads();
             }
         }
         for (uint32_t i = threadIdx.x; i < d; i += THREADS) {
-            uint64_t x = sbuf[i];
-            put_entry(S, eid, rowid, b + i, x, (uint32_t)r);
-            if (i > 0 && (sbuf[i - 1] >> 33) == (x >> 33)) set_error(err, E_DUP);
+            const uint32_t x = sbuf[i];
+            S.adj[b + i] = x;
+            if (i > 0 && same_rank(sbuf[i - 1], x)) set_error(err, E_DUP);
         }
         __syncthreads();
     }
@@ -406,9 +400,8 @@ __global__ void __launch_bounds__(THREADS) k_sort_rows_smem(SideCSR S, const uin
 constexpr int RR_THREADS = 1024;
 constexpr int RR_WARPS = RR_THREADS / 32;
 
-__global__ void __launch_bounds__(RR_THREADS) k_sort_rows_radix(SideCSR S, uint64_t *keys,
-                                                                uint64_t *alt, uint32_t *eid,
-                                                                uint32_t *rowid,
+__global__ void __launch_bounds__(RR_THREADS) k_sort_rows_radix(SideCSR S, uint32_t *keys,
+                                                                uint32_t *alt,
                                                                 const int64_t *bounds, int lo_k,
                                                                 int hi_k, int key_bits,
                                                                 uint32_t *err) {
@@ -422,12 +415,12 @@ __global__ void __launch_bounds__(RR_THREADS) k_sort_rows_radix(SideCSR S, uint6
     for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
         int64_t b = S.off[r];
         int64_t d = S.off[r + 1] - b;
-        uint64_t *A = keys + b, *B = alt + b;
+        uint32_t *A = keys + b, *B = alt + b;
         for (int k = t; k < RR_WARPS * 256; k += RR_THREADS) (&wcnt[0][0])[k] = 0;
         __syncthreads();
-        uint64_t *src = A, *dst = B;
+        uint32_t *src = A, *dst = B;
         for (int p = 0; p < passes; p++) {
-            const int shift = 32 + 8 * p;
+            const int shift = 8 * p;
             if (t < 256) run[t] = 0;
             __syncthreads();
             for (int64_t i = t; i < d; i += RR_THREADS) atomicAdd(&run[(src[i] >> shift) & 255u], 1u);
@@ -445,7 +438,7 @@ __global__ void __launch_bounds__(RR_THREADS) k_sort_rows_radix(SideCSR S, uint6
             for (int64_t base = 0; base < d; base += RR_THREADS) {
                 int64_t i = base + t;
                 bool valid = i < d;
-                uint64_t x = valid ? src[i] : 0;
+                uint32_t x = valid ? src[i] : 0u;
                 uint32_t dg = valid ? (uint32_t)((x >> shift) & 255u) : 256u + lane;
                 unsigned peers = __match_any_sync(FULL, dg);
                 uint32_t rank = __popc(peers & lt_mask);
@@ -463,12 +456,12 @@ __global__ void __launch_bounds__(RR_THREADS) k_sort_rows_radix(SideCSR S, uint6
                     for (int w = 0; w < RR_WARPS; w++) wcnt[w][t] = 0;
                 __syncthreads();
             }
-            uint64_t *tmp = src; src = dst; dst = tmp;
+            uint32_t *tmp = src; src = dst; dst = tmp;
         }
         for (int64_t i = t; i < d; i += RR_THREADS) {
-            uint64_t x = src[i];
-            put_entry(S, eid, rowid, b + i, x, (uint32_t)r);
-            if (i > 0 && (src[i - 1] >> 33) == (x >> 33)) set_error(err, E_DUP);
+            const uint32_t x = src[i];
+            S.adj[b + i] = x;
+            if (i > 0 && same_rank(src[i - 1], x)) set_error(err, E_DUP);
         }
         __syncthreads();
     }
@@ -491,8 +484,7 @@ constexpr uint32_t BM_MAX_SLICES = 8;
 constexpr uint32_t BM_PER = BM_WORDS / BM_THREADS;  // words per thread in the scan
 constexpr size_t BM_SMEM = 2 * BM_WORDS * 4;
 
-__global__ void __launch_bounds__(BM_THREADS) k_sort_rows_bitmap(SideCSR S, const uint64_t *keys,
-                                                                 uint32_t *eid, uint32_t *rowid,
+__global__ void __launch_bounds__(BM_THREADS) k_sort_rows_bitmap(SideCSR S, const uint32_t *keys,
                                                                  const int64_t *bounds, int lo_k,
                                                                  int hi_k, uint32_t n_other,
                                                                  uint32_t *err) {
@@ -513,7 +505,7 @@ __global__ void __launch_bounds__(BM_THREADS) k_sort_rows_bitmap(SideCSR S, cons
             for (uint32_t i = t; i < BM_WORDS; i += BM_THREADS) bm[i] = 0u;
             __syncthreads();
             for (uint32_t i = t; i < d; i += BM_THREADS) {
-                const uint32_t rr = (uint32_t)(keys[b + i] >> 33) - lo;
+                const uint32_t rr = (keys[b + i] >> 1) - lo;
                 if (rr < span) {
                     const uint32_t bit = 1u << (rr & 31u);
                     if (atomicOr(&bm[rr >> 5], bit) & bit) set_error(err, E_DUP);
@@ -543,13 +535,13 @@ __global__ void __launch_bounds__(BM_THREADS) k_sort_rows_bitmap(SideCSR S, cons
             }
             __syncthreads();
             for (uint32_t i = t; i < d; i += BM_THREADS) {
-                const uint64_t x = keys[b + i];
-                const uint32_t rr = (uint32_t)(x >> 33) - lo;
+                const uint32_t x = keys[b + i];
+                const uint32_t rr = (x >> 1) - lo;
                 if (rr < span) {
                     const uint32_t w = rr >> 5;
                     const uint32_t pos =
                         placed + pre[w] + __popc(bm[w] & ((1u << (rr & 31u)) - 1u));
-                    if (pos < d) put_entry(S, eid, rowid, b + pos, x, (uint32_t)r);
+                    if (pos < d) S.adj[b + pos] = x;
                 }
             }
             placed += total;
@@ -601,75 +593,81 @@ __global__ void k_row_info(SideCSR S, SideCSR O, uint32_t window_base, uint4 *in
     }
 }
 
-__global__ void k_epos(const uint32_t *eid, int64_t nE, uint32_t *epos) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nE;
-         p += (int64_t)gridDim.x * blockDim.x)
-        epos[eid[p]] = (uint32_t)p;
-}
-
 // ------------------------------------------------- 4. suffixes and work
 // For the entry w -> v at position p of anchor w's row: the wedge suffix of
 // v's row holds the neighbours ranked above max(v, w). If v outranks w that
-// is v's own upper part, from lo(v); otherwise it starts right after w's
-// position in v's row (w and the suffix are on the same side). w lies below
-// lo(v) exactly when v outranks w, so the start is max(lo(v), pos_v(w) + 1).
-// One thread per entry; the per-row sums of suffix lengths (wedges) and of
-// their parts below the hub window are reduced per warp segment, then added
-// per row.
-__global__ void k_md_work(SideCSR S, const uint4 *__restrict__ info_o,
-                          const uint32_t *__restrict__ eid_s, const uint32_t *__restrict__ epos_o,
-                          const uint32_t *__restrict__ row_s, int64_t nE,
-                          unsigned long long *wedges) {
+// is v's own upper part, from lo(v); otherwise w lies in that upper part
+// and the suffix starts right after w's position there (w and the suffix
+// are on the same side), found by binary search. A block takes
+// edgerows::EDGES consecutive entries per step and finds their rows from
+// the side's offsets (edgerows.cuh). The per-row sums of suffix lengths
+// (wedges) and of their parts below the hub window are reduced per warp
+// segment, then added per row.
+__global__ void __launch_bounds__(edgerows::THREADS) k_md_work(SideCSR S, SideCSR O,
+                                                               const uint4 *__restrict__ info_o,
+                                                               int64_t nE,
+                                                               unsigned long long *wedges,
+                                                               uint32_t *err) {
+    __shared__ edgerows::Smem er;
     __shared__ unsigned long long block_sum;
-    if (threadIdx.x == 0) block_sum = 0;
-    __syncthreads();
+    const int t = threadIdx.x;
     const unsigned lane = lane_id();
+    if (t == 0) block_sum = 0;
     unsigned long long mine = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // all lanes of a warp run the same number of iterations (shuffles below)
-    const int64_t start = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t iters = (nE + stride - 1) / stride;
-    for (int64_t it = 0; it < iters; it++) {
-        const int64_t p = start + it * stride;
-        const bool valid = p < nE;
-        uint32_t r = 0xffffffffu, len = 0, nh = 0;
-        if (valid) {
-            r = row_s[p];
-            const uint32_t ent = S.adj[p];
-            const uint4 vi = info_o[ent >> 1];  // v's row: start, end, lo, hub start
-            const uint32_t pw = epos_o[eid_s[p]];
-            const uint32_t st = vi.z > pw + 1u ? vi.z : pw + 1u;
-            const uint32_t hs = vi.w > st ? vi.w : st;
-            S.md[p] = make_uint4(st, hs, vi.y, ent & 1u);
-            len = vi.y - st;
-            nh = hs - st;
-        }
-        // segmented sums over runs of equal r within the warp
-        const uint32_t rprev = __shfl_up_sync(FULL, r, 1);
-        const bool head = lane == 0 || rprev != r;
-        const unsigned heads = __ballot_sync(FULL, head);
-        uint32_t a = len, b = nh;
+    for (int64_t p0 = blockIdx.x * (int64_t)edgerows::EDGES; p0 < nE;
+         p0 += (int64_t)gridDim.x * edgerows::EDGES) {
+        const int64_t p1 = nE - p0 > edgerows::EDGES ? p0 + edgerows::EDGES : nE;
+        const int64_t r0 = edgerows::step_rows(S.off, S.n, p0, p1, er);
+        // all lanes of a warp run every iteration (shuffles below)
+#pragma unroll 1
+        for (int k = 0; k < edgerows::PER; k++) {
+            const int64_t p = p0 + k * edgerows::THREADS + t;
+            const bool valid = p < p1;
+            uint32_t r = 0xffffffffu, len = 0, nh = 0;
+            if (valid) {
+                r = (uint32_t)(r0 + er.srow[p - p0] - 1);
+                const uint32_t ent = S.adj[p];
+                const uint32_t v = ent >> 1;
+                const uint4 vi = info_o[v];  // v's row: start, end, lo, hub start
+                uint32_t st = vi.z;
+                if (S.grank[r] > O.grank[v]) {  // w outranks v: w is in v's upper part
+                    const int64_t pw = lower_bound_u32(O.adj, vi.z, vi.y, r << 1);
+                    if (pw >= vi.y || (O.adj[pw] >> 1) != r) set_error(err, E_INTERNAL);
+                    st = (uint32_t)pw + 1u;
+                }
+                const uint32_t hs = vi.w > st ? vi.w : st;
+                S.md[p] = make_uint4(st, hs, vi.y, ent & 1u);
+                len = vi.y - st;
+                nh = hs - st;
+            }
+            // segmented sums over runs of equal r within the warp
+            const uint32_t rprev = __shfl_up_sync(FULL, r, 1);
+            const bool head = lane == 0 || rprev != r;
+            const unsigned heads = __ballot_sync(FULL, head);
+            uint32_t a = len, b = nh;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t ya = __shfl_up_sync(FULL, a, d), yb = __shfl_up_sync(FULL, b, d);
-            if (lane >= (unsigned)d) { a += ya; b += yb; }
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t ya = __shfl_up_sync(FULL, a, d), yb = __shfl_up_sync(FULL, b, d);
+                if (lane >= (unsigned)d) { a += ya; b += yb; }
+            }
+            const unsigned below = heads & ((2u << lane) - 1u);  // heads at or before me
+            const int sstart = 31 - __clz(below);                 // my segment's head
+            const uint32_t pa = __shfl_sync(FULL, a, sstart > 0 ? sstart - 1 : 0);
+            const uint32_t pb = __shfl_sync(FULL, b, sstart > 0 ? sstart - 1 : 0);
+            const uint32_t seg_a = a - (sstart > 0 ? pa : 0u), seg_b = b - (sstart > 0 ? pb : 0u);
+            const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+            if (valid && tail) {
+                if (seg_a) atomicAdd((unsigned long long *)&S.work[r], (unsigned long long)seg_a);
+                if (seg_b) atomicAdd((unsigned long long *)&S.work_nh[r], (unsigned long long)seg_b);
+            }
+            mine += len;
         }
-        const unsigned below = heads & ((2u << lane) - 1u);     // heads at or before me
-        const int sstart = 31 - __clz(below);                    // my segment's head
-        const uint32_t pa = __shfl_sync(FULL, a, sstart > 0 ? sstart - 1 : 0);
-        const uint32_t pb = __shfl_sync(FULL, b, sstart > 0 ? sstart - 1 : 0);
-        const uint32_t seg_a = a - (sstart > 0 ? pa : 0u), seg_b = b - (sstart > 0 ? pb : 0u);
-        const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
-        if (valid && tail) {
-            if (seg_a) atomicAdd((unsigned long long *)&S.work[r], (unsigned long long)seg_a);
-            if (seg_b) atomicAdd((unsigned long long *)&S.work_nh[r], (unsigned long long)seg_b);
-        }
-        mine += len;
+        __syncthreads();  // the next step rewrites the shared rows
     }
     mine = warp_sum_u64(mine);
     if (lane == 0 && mine) atomicAdd(&block_sum, mine);
     __syncthreads();
-    if (threadIdx.x == 0 && block_sum) atomicAdd(wedges, block_sum);
+    if (t == 0 && block_sum) atomicAdd(wedges, block_sum);
 }
 
 // ------------------------------------------------------ 5. classification
@@ -879,9 +877,8 @@ BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE) {
     g += align256(NCTR * 4) + 256 + 256 + 256 + align256(sizeof(CountScratch));
     size_t t = 0;
     t += align256((size_t)nU * 4 + 4) + align256((size_t)nV * 4 + 4);      // deg by id
-    t += 4 * align256((size_t)nE * 4 + 4);                                   // eid, row ids
     t += align256((size_t)nV * 4 + 4);                                       // cursor
-    t += 3 * align256((size_t)nE * 8 + 8);                                   // row keys, sort buffer, epos
+    t += 3 * align256((size_t)nE * 4 + 4);                                   // row keys, sort buffer
     t += 2 * align256((size_t)nmax * 4 + 4);                                 // rank sort alt
     t += align256(std::max(radix_temp_bytes(nmax), scan_temp_bytes(nmax + 1)));
     t += 2 * align256((size_t)nV * 4 + 4);                                   // V rank chain
@@ -933,8 +930,8 @@ namespace {
 // The build's temporaries, carved from the caller's block in one fixed
 // order (so the two build stages below see the same layout).
 struct BuildTemp {
-    uint32_t *deg_in[2], *eid[2], *rowid[2], *cursorV;
-    uint64_t *bufA, *bufB, *bufC, *keys[2];
+    uint32_t *deg_in[2], *cursorV;
+    uint32_t *bufA, *bufB, *bufC, *keys[2];
     uint32_t *ralt_k, *ralt_v, *ralt2_k, *ralt2_v;
     void *ptemp, *ptemp2;
     uint32_t *meta[2], *grp[2];
@@ -949,12 +946,10 @@ BuildTemp carve_temp(const DevGraph &g, void *temp_mem) {
     Carver c{(char *)temp_mem};
     BuildTemp t;
     t.deg_in[0] = c.take<uint32_t>(nU + 1); t.deg_in[1] = c.take<uint32_t>(nV + 1);
-    t.eid[0] = c.take<uint32_t>(nE + 1); t.eid[1] = c.take<uint32_t>(nE + 1);
-    t.rowid[0] = c.take<uint32_t>(nE + 1); t.rowid[1] = c.take<uint32_t>(nE + 1);
     t.cursorV = c.take<uint32_t>(nV + 1);
-    t.bufA = c.take<uint64_t>(nE + 1);   // U-side row keys, later twin positions
-    t.bufB = c.take<uint64_t>(nE + 1);   // V-side row keys
-    t.bufC = c.take<uint64_t>(nE + 1);   // radix sort alternate buffer
+    t.bufA = c.take<uint32_t>(nE + 1);   // U-side row keys
+    t.bufB = c.take<uint32_t>(nE + 1);   // V-side row keys
+    t.bufC = c.take<uint32_t>(nE + 1);   // radix sort alternate buffer (validation: degree replicas)
     t.keys[0] = t.bufA; t.keys[1] = t.bufB;
     t.ralt_k = c.take<uint32_t>(nmax + 1);
     t.ralt_v = c.take<uint32_t>(nmax + 1);
@@ -1012,7 +1007,7 @@ bb_status build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col,
     const int64_t stride = (nV + 64) & ~(int64_t)63;
     uint32_t copies = 1;
     while (copies < DEG_COPIES &&
-           (int64_t)(2 * copies) * stride * 4 <= (int64_t)(nE + 1) * 8) copies *= 2;
+           (int64_t)(2 * copies) * stride * 4 <= (int64_t)(nE + 1) * 4) copies *= 2;
     uint32_t *degc = copies > 1 ? reinterpret_cast<uint32_t *>(bt.bufC) : deg_in[1];
     cudaMemsetAsync(degc, 0, (size_t)(copies > 1 ? copies * stride : nV) * 4, s);
 
@@ -1068,8 +1063,8 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
                 void *temp_mem, cudaStream_t s, const BuildAux *aux) {
     const int64_t nU = g.nU, nV = g.nV, nE = g.nE;
     BuildTemp bt = carve_temp(g, temp_mem);
-    uint32_t **deg_in = bt.deg_in, **eid = bt.eid, **rowid = bt.rowid, *cursorV = bt.cursorV;
-    uint64_t *bufA = bt.bufA, *bufC = bt.bufC, **keys = bt.keys;
+    uint32_t **deg_in = bt.deg_in, *cursorV = bt.cursorV;
+    uint32_t *bufC = bt.bufC, **keys = bt.keys;
     uint32_t *ralt_k = bt.ralt_k, *ralt_v = bt.ralt_v;
     void *ptemp = bt.ptemp;
     uint32_t **meta = bt.meta, **grp = bt.grp;
@@ -1133,13 +1128,13 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
         const int64_t n_other = ns[1 - sd];
         if (n_other <= (int64_t)BM_MAX_SLICES * BM_RANKS) {
             k_sort_rows_bitmap<<<2 * build_sms(), BM_THREADS, BM_SMEM, rs>>>(
-                g.side[sd], keys[sd], eid[sd], rowid[sd], bounds + sd * 16, LIM_LONG, NLIMS,
+                g.side[sd], keys[sd], bounds + sd * 16, LIM_LONG, NLIMS,
                 (uint32_t)n_other, g.err); note_launch();
             continue;
         }
         int key_bits = 1;
         while (key_bits < 32 && ((uint64_t)1 << key_bits) < (uint64_t)(2 * n_other + 2)) key_bits++;
-        k_sort_rows_radix<<<1024, RR_THREADS, 0, rs>>>(g.side[sd], keys[sd], bufC, eid[sd], rowid[sd],
+        k_sort_rows_radix<<<1024, RR_THREADS, 0, rs>>>(g.side[sd], keys[sd], bufC,
                                                         bounds + sd * 16, LIM_LONG, NLIMS, key_bits, g.err); note_launch();
     }
     if (aux) cudaEventRecord(aux->join, rs);
@@ -1149,35 +1144,36 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
         if (n == 0 || nE == 0) continue;
         SideCSR &S = g.side[sd];
         int64_t *bd = bounds + sd * 16;
-        uint64_t *ky = keys[sd];
+        const uint32_t *ky = keys[sd];
         const cudaStream_t ss = (aux && sd == 1) ? aux->stream2 : s;
-        k_rows_single<<<grid_for(n, BT, 4096), BT, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd); note_launch();
-        k_sort_rows_sub<2><<<grid_for(n * 2, BT, 8192), BT, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 0, g.err); note_launch();
-        k_sort_rows_sub<4><<<grid_for(n * 4, BT, 8192), BT, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 1, g.err); note_launch();
-        k_sort_rows_sub<8><<<grid_for(n * 8, BT, 8192), BT, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 2, g.err); note_launch();
-        k_sort_rows_sub<16><<<grid_for(n * 16, BT, 8192), BT, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 3, g.err); note_launch();
-        k_sort_rows_sub<32><<<grid_for(n * 32, BT, 8192), BT, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 4, g.err); note_launch();
-        k_sort_rows_warpreg<2><<<2048, 256, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 5, g.err); note_launch();
-        k_sort_rows_warpreg<4><<<2048, 256, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 6, g.err); note_launch();
-        k_sort_rows_warpreg<8><<<2048, 256, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 7, g.err); note_launch();
-        k_sort_rows_warpreg<16><<<2048, 256, 0, ss>>>(S, ky, eid[sd], rowid[sd], bd, 8, g.err); note_launch();
-        k_sort_rows_smem<2048, 256><<<2048, 256, 2048 * 8, ss>>>(S, ky, eid[sd], rowid[sd], bd, 9, g.err); note_launch();
+        k_rows_single<<<grid_for(n, BT, 4096), BT, 0, ss>>>(S, ky, bd); note_launch();
+        k_sort_rows_sub<2><<<grid_for(n * 2, BT, 8192), BT, 0, ss>>>(S, ky, bd, 0, g.err); note_launch();
+        k_sort_rows_sub<4><<<grid_for(n * 4, BT, 8192), BT, 0, ss>>>(S, ky, bd, 1, g.err); note_launch();
+        k_sort_rows_sub<8><<<grid_for(n * 8, BT, 8192), BT, 0, ss>>>(S, ky, bd, 2, g.err); note_launch();
+        k_sort_rows_sub<16><<<grid_for(n * 16, BT, 8192), BT, 0, ss>>>(S, ky, bd, 3, g.err); note_launch();
+        k_sort_rows_sub<32><<<grid_for(n * 32, BT, 8192), BT, 0, ss>>>(S, ky, bd, 4, g.err); note_launch();
+        k_sort_rows_warpreg<2><<<2048, 256, 0, ss>>>(S, ky, bd, 5, g.err); note_launch();
+        k_sort_rows_warpreg<4><<<2048, 256, 0, ss>>>(S, ky, bd, 6, g.err); note_launch();
+        k_sort_rows_warpreg<8><<<2048, 256, 0, ss>>>(S, ky, bd, 7, g.err); note_launch();
+        k_sort_rows_warpreg<16><<<2048, 256, 0, ss>>>(S, ky, bd, 8, g.err); note_launch();
+        k_sort_rows_smem<2048, 256><<<2048, 256, 2048 * 4, ss>>>(S, ky, bd, 9, g.err); note_launch();
     }
     if (aux) {
         cudaEventRecord(aux->join2, aux->stream2);
         cudaStreamWaitEvent(s, aux->join, 0);
         cudaStreamWaitEvent(s, aux->join2, 0);
     }
-    // 3b-4. per-row records, twin positions, suffix starts and work per
-    // anchor. Side sd's descriptor pass reads the other side's records and
-    // twin positions, so each stream computes those of the other side and
-    // then its own side's descriptors: U descriptors on s, V on the second
-    // auxiliary stream when there is one (the two chains are independent).
-    uint32_t *epos[2] = {(uint32_t *)bufA, (uint32_t *)bufA + (nE + 1)};
+    // 3b-4. per-row records, suffix starts and work per anchor. Side sd's
+    // descriptor pass reads the other side's records, so each stream
+    // computes those of the other side and then its own side's
+    // descriptors: U on s, V on the second auxiliary stream when there is
+    // one (the two chains are independent).
     if (aux) {
         cudaEventRecord(aux->fork, s);
         cudaStreamWaitEvent(aux->stream2, aux->fork, 0);
     }
+    const unsigned md_blocks =
+        (unsigned)std::min<int64_t>((nE + edgerows::EDGES - 1) / edgerows::EDGES, 8192);
     for (int sd = 0; sd < 2; sd++) {
         if (ns[sd] == 0) continue;
         const cudaStream_t ss = (aux && sd == 1) ? aux->stream2 : s;
@@ -1188,13 +1184,11 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
             k_row_info<<<grid_for(ns[od], BT, 8192), BT, 0, ss>>>(g.side[od], g.side[sd], wb,
                                                                  rinfo[od]); note_launch();
         }
-        if (nE > 0) { k_epos<<<grid_for(nE, BT, 16384), BT, 0, ss>>>(eid[od], nE, epos[od]); note_launch(); }
         cudaMemsetAsync(g.side[sd].work, 0, (size_t)ns[sd] * 8, ss);
         cudaMemsetAsync(g.side[sd].work_nh, 0, (size_t)ns[sd] * 8, ss);
         if (nE > 0) {
-            k_md_work<<<grid_for(nE, BT, 8192), BT, 0, ss>>>(g.side[sd], rinfo[od], eid[sd],
-                                                            epos[od], rowid[sd], nE,
-                                                            g.wedges); note_launch();
+            k_md_work<<<md_blocks, edgerows::THREADS, 0, ss>>>(g.side[sd], g.side[od], rinfo[od], nE,
+                                                              g.wedges, g.err); note_launch();
         }
     }
     if (aux) {
