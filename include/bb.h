@@ -193,8 +193,8 @@ BB_API void bb_graph_free(bb_graph *g);
  * carved out of one device array of BB_NOALLOC_SCRATCH_BYTES that the
  * library reserves on every GPU it is loaded on until the process exits.
  * A graph whose workspace does not fit is rejected with BB_ERR_TOO_LARGE
- * (roughly 1M edges fit). Every call looks the array's device address up
- * on the current device; the first call on a device may load the
+ * (roughly 1.3M edges of a power-law graph fit). Every call looks the
+ * array's device address up on the current device; the first call on a device may load the
  * library's device code, so make it before any stream capture. Work is
  * queued on `stream` (NULL = the legacy default stream) and the call
  * returns when it is done; its waits honour bb_set_wait_timeout
