@@ -204,6 +204,29 @@ def test_high_degree_star_and_invalid_inputs(ctx):
     same(ctx, synth.uniform(3, 50, 50, 600, 0.5))
 
 
+@pytest.mark.parametrize("length", [2, 3, 5, 17, 33, 100, 300, 600, 3000])
+def test_duplicate_edge_found_in_every_row_sort(ctx, length):
+    # one edge listed twice in a row of `length` entries, on the U side
+    # (one U vertex's row) and on the V side (one V vertex's row): each row
+    # length class is sorted by a different kernel, and each must report it
+    rng = np.random.default_rng(length)
+    nbrs = rng.choice(4 * length, length, replace=False)
+    u_side = synth.SignedBipartite(
+        1, 4 * length, np.array([0, length + 1], np.int64),
+        np.concatenate([nbrs, nbrs[:1]]).astype(np.int32), np.ones(length + 1, np.int8),
+        f"dup in a U row of {length}")
+    rows = np.concatenate([np.arange(length), [length // 2]])
+    order = np.argsort(rows, kind="stable")
+    v_side = synth.SignedBipartite(
+        length, 1, np.searchsorted(rows[order], np.arange(length + 1)).astype(np.int64),
+        np.zeros(length + 1, np.int32), np.ones(length + 1, np.int8), f"dup in a V row of {length}")
+    for g in (u_side, v_side):
+        with pytest.raises(pkg.BBError) as ei:
+            ctx.count(g)
+        assert ei.value.name == "BB_ERR_INVALID_ARG", g.name
+    same(ctx, synth.uniform(5, 40, 40, 500, 0.5))
+
+
 def test_budget_is_enforced():
     with pkg.Context(0, budget_bytes=1 << 20) as small:
         with pytest.raises(pkg.BBError) as ei:
