@@ -194,10 +194,10 @@ BB_API void bb_graph_free(bb_graph *g);
  * library reserves on every GPU it is loaded on until the process exits.
  * A graph whose workspace does not fit is rejected with BB_ERR_TOO_LARGE
  * (roughly 1.3M edges of a power-law graph fit). Every call looks the
- * array's device address up on the current device; the first call on a device may load the
- * library's device code, so make it before any stream capture. Work is
- * queued on `stream` (NULL = the legacy default stream) and the call
- * returns when it is done; its waits honour bb_set_wait_timeout
+ * array's device address up on the current device; the first call on a
+ * device may load the library's device code. Work is queued on `stream`
+ * (NULL = the legacy default stream) and the call blocks until it is done
+ * (it synchronizes with the stream); its waits honour bb_set_wait_timeout
  * (BB_ERR_TIMEOUT). All calls share the array and it keeps the last call's
  * contents: the call clears what must start at zero itself, and two calls
  * whose work overlaps on the GPU (another thread, another stream) race and
