@@ -573,11 +573,12 @@ int build_sms() {
     return g_build_sms[dev] > 0 ? g_build_sms[dev] : 1;
 }
 
-// Per row of a side, as absolute positions in its adjacency: the row's
-// start and end, lo (the first neighbour of higher global priority than the
-// row's vertex; the neighbours below it form a prefix) and the first
-// neighbour inside the other side's hub window (side ranks >= window_base).
-// One 16-byte record per row, read once per entry by k_md_work.
+// Per row of a side: the row vertex's global rank, and as absolute
+// positions in the side's adjacency the row's end, lo (the first neighbour
+// of higher global priority than the row's vertex; the neighbours below it
+// form a prefix) and the first neighbour inside the other side's hub window
+// (side ranks >= window_base). One 16-byte record per row, read once per
+// entry by k_md_work.
 __global__ void k_row_info(SideCSR S, SideCSR O, uint32_t window_base, uint4 *info) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < S.n;
          r += (int64_t)gridDim.x * blockDim.x) {
@@ -589,7 +590,7 @@ __global__ void k_row_info(SideCSR S, SideCSR O, uint32_t window_base, uint4 *in
             if (O.grank[S.adj[m] >> 1] < g) lo = m + 1; else hi = m;
         }
         const int64_t h = lower_bound_u32(S.adj, b, e, window_base << 1);
-        info[r] = make_uint4((uint32_t)b, (uint32_t)e, (uint32_t)lo, (uint32_t)h);
+        info[r] = make_uint4(g, (uint32_t)e, (uint32_t)lo, (uint32_t)h);
     }
 }
 
@@ -628,9 +629,9 @@ __global__ void __launch_bounds__(edgerows::THREADS) k_md_work(SideCSR S, SideCS
                 r = (uint32_t)(r0 + er.srow[p - p0] - 1);
                 const uint32_t ent = S.adj[p];
                 const uint32_t v = ent >> 1;
-                const uint4 vi = info_o[v];  // v's row: start, end, lo, hub start
+                const uint4 vi = info_o[v];  // v's row: global rank, end, lo, hub start
                 uint32_t st = vi.z;
-                if (S.grank[r] > O.grank[v]) {  // w outranks v: w is in v's upper part
+                if (S.grank[r] > vi.x) {  // w outranks v: w is in v's upper part
                     const int64_t pw = lower_bound_u32(O.adj, vi.z, vi.y, r << 1);
                     if (pw >= vi.y || (O.adj[pw] >> 1) != r) set_error(err, E_INTERNAL);
                     st = (uint32_t)pw + 1u;

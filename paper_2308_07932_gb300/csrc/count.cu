@@ -229,7 +229,7 @@ __device__ __forceinline__ void warp_anchor(const DevGraph &G, WarpSmem &sm, con
                                             unsigned long long &tot) {
     const Anchor A = load_anchor(G, rec);
     uint32_t own = 0, other = 0;
-    const WarpTab tb = warp_tally(G, sm, rec, A, lane, own, other);
+    const WarpTab tb = warp_tally<true>(G, sm, rec, A, lane, own, other);
     if (!(rec.flags & REC_HASH_ALL)) {
         uint4 *w4 = reinterpret_cast<uint4 *>(sm.win);
         for (uint32_t q = lane; q < HUB_WINDOW / 8; q += 32) w4[q] = make_uint4(0u, 0u, 0u, 0u);

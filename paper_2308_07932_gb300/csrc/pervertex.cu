@@ -290,7 +290,7 @@ __device__ __forceinline__ void pv_hybrid_anchor(const DevGraph &G, PvHybSmem<TS
     const Anchor A = load_anchor(G, rec);
     const PvSides P = pv_sides(G, out, rec.anchor, nullptr);
     unsigned long long ab = 0, at = 0;  // this anchor's part of the counts
-    const HybTab tb = hybrid_tally<TS, HCAP>(G, sm, A, ab, at);
+    const HybTab tb = hybrid_tally<TS, HCAP, false>(G, sm, A, ab, at);
     bal += ab;
     tot += at;
     __syncthreads();

@@ -541,8 +541,11 @@ __device__ __forceinline__ void wedge_walk(const uint4 *__restrict__ smd,
 // OR-reduction): it is the last segment starting at or before its
 // position. quada(v, vm, sw) takes a loaded quad (vm: its entries inside
 // the segment, bit j for entry j; the quad is only read when vm != 0) and
-// oneb(x, sw) one wedge of the second family; sw is the sign bit of the
-// anchor's edge to the middle.
+// oneb(x, sw, valid) one wedge of the second family; sw is the sign bit of
+// the anchor's edge to the middle. The second family's first round calls
+// oneb on every lane of the warp (valid = false: no wedge on this lane), so
+// that oneb may use warp-wide operations when that round is the only one
+// (at most 32 wedges in the chunk); later rounds call it on valid lanes.
 //
 // SUMS: quada(v, vm, sw, p) and oneb(x, sw, p) also get the position p of
 // the quad's first entry or of the wedge and return a value; the values of
@@ -660,7 +663,7 @@ __device__ __forceinline__ void warp_rounds(const uint4 *__restrict__ smd,
         if constexpr (SUMS) {
             if (hb0) round_sum(oneb(xb0, swb0, posb0.p), posb0, 32u);
         } else {
-            if (hb0) oneb(xb0, swb0);
+            if (TB > 0) oneb(xb0, swb0, hb0);
         }
         for (uint32_t r = 32; r < TB; r += 32) {
             const uint32_t s = eb - r;
@@ -677,7 +680,7 @@ __device__ __forceinline__ void warp_rounds(const uint4 *__restrict__ smd,
                     pb.peers = round_peers(M, lane, TB - r, pb.head);
                     round_sum(oneb(oadj[e], d.excl_sw >> 31, e), pb, 32u);
                 } else {
-                    oneb(oadj[e], d.excl_sw >> 31);
+                    oneb(oadj[e], d.excl_sw >> 31, true);
                 }
             }
         }
@@ -697,20 +700,31 @@ __device__ __forceinline__ void warp_rounds(const uint4 *__restrict__ smd,
 // (S | A << 16) in the low half. hash_add inserts or finds the key and adds
 // inc to its tallies (an insert sets key and first tally in one
 // compare-and-swap); it returns the tallies the key held before.
+// CAS_FIRST tries the insert before any read of the slot (most keys of the
+// hashed endpoints are new; a slot that holds the key then takes the add);
+// otherwise the slot is read first. Both give the same result.
+template <bool CAS_FIRST = true>
 __device__ __forceinline__ uint32_t hash_add(unsigned long long *tab, uint32_t shift,
                                              uint32_t mask, uint32_t key, uint32_t inc,
                                              uint32_t *err) {
     uint32_t h = hash_slot(key, shift);
+    const unsigned long long want = ((unsigned long long)key << 32) | inc;
     for (uint32_t probe = 0; probe <= mask; probe++) {
-        const unsigned long long cur = *((volatile unsigned long long *)&tab[h]);
-        const uint32_t k = (uint32_t)(cur >> 32);
-        if (k == key) return (uint32_t)atomicAdd(&tab[h], (unsigned long long)inc);
-        if (k == 0) {
-            const unsigned long long want = ((unsigned long long)key << 32) | inc;
+        if constexpr (CAS_FIRST) {
             const unsigned long long old = atomicCAS(&tab[h], 0ull, want);
             if (old == 0ull) return 0u;
             if ((uint32_t)(old >> 32) == key)
                 return (uint32_t)atomicAdd(&tab[h], (unsigned long long)inc);
+        } else {
+            const unsigned long long cur = *((volatile unsigned long long *)&tab[h]);
+            const uint32_t k = (uint32_t)(cur >> 32);
+            if (k == key) return (uint32_t)atomicAdd(&tab[h], (unsigned long long)inc);
+            if (k == 0) {
+                const unsigned long long old = atomicCAS(&tab[h], 0ull, want);
+                if (old == 0ull) return 0u;
+                if ((uint32_t)(old >> 32) == key)
+                    return (uint32_t)atomicAdd(&tab[h], (unsigned long long)inc);
+            }
         }
         h = (h + 1) & mask;
     }
@@ -738,14 +752,36 @@ __device__ __forceinline__ uint32_t hash_find(const unsigned long long *tab, uin
 // Over all wedges own is the balanced count (C(S,2) + C(A,2) per pair) and
 // own + other the total (C(S+A,2)). dp2a picks a 16-bit half of the packed
 // tallies by a byte mask: 1 for S, 0x100 for A.
+template <bool CAS_FIRST = true>
 __device__ __forceinline__ void hash_wedge32(unsigned long long *tab, uint32_t shift,
                                              uint32_t mask, uint32_t x, uint32_t sw,
                                              uint32_t *err, uint32_t &own, uint32_t &other) {
     const uint32_t asym = (x ^ sw) & 1u;
-    const uint32_t old = hash_add(tab, shift, mask, (x >> 1) + 1, asym ? INC_ASYM : INC_SYM, err);
+    const uint32_t old =
+        hash_add<CAS_FIRST>(tab, shift, mask, (x >> 1) + 1, asym ? INC_ASYM : INC_SYM, err);
     const uint32_t pick = 1u << (asym << 3);
     own = __dp2a_lo(old, pick, own);
     other = __dp2a_lo(old, pick ^ 0x0101u, other);
+}
+
+// One round of at most 32 wedges of an anchor (all lanes of the warp call
+// it; valid = false: no wedge on this lane), counted without a table: the
+// lanes holding the same endpoint are found by one warp match, and a
+// wedge's previous tallies are the matching wedges on lower lanes of its
+// own and of the other type (the same sums as hash_wedge32, for wedges
+// taken in lane order).
+__device__ __forceinline__ void match_wedges(uint32_t x, uint32_t sw, bool valid, uint32_t lane,
+                                             uint32_t &own, uint32_t &other) {
+    const unsigned vmask = __ballot_sync(FULL, valid);
+    const unsigned m = __match_any_sync(FULL, valid ? (x >> 1) : 0xffffffffu) & vmask;
+    const uint32_t asym = (x ^ sw) & 1u;
+    const unsigned B = __ballot_sync(FULL, asym);
+    const unsigned same = m & (asym ? B : ~B);
+    const unsigned lower = (1u << lane) - 1u;
+    if (valid) {
+        own += __popc(same & lower);
+        other += __popc(m & ~same & lower);
+    }
 }
 
 // zero the first `cap` slots of a table (cap a multiple of 2) as a team
@@ -855,6 +891,10 @@ struct WarpTab {
 // The tally pass of one warp-class anchor, walked by one warp: every wedge
 // adds 1 to its pair's tally, own += the previous value of that tally and
 // other += the previous value of the pair's other tally (per lane).
+// MATCH: an anchor of at most 32 middles whose hashed wedges number at most
+// 32 (one round) counts them by warp matching and keeps no table (its
+// WarpTab has cap = 0); without MATCH every hashed wedge is in the table.
+template <bool MATCH = false>
 __device__ __forceinline__ WarpTab warp_tally(const DevGraph &G, WarpSmem &sm,
                                               const AnchorRec &rec, const Anchor &A,
                                               unsigned lane, uint32_t &own, uint32_t &other) {
@@ -867,18 +907,22 @@ __device__ __forceinline__ WarpTab warp_tally(const DevGraph &G, WarpSmem &sm,
     auto none = [](const uint4 &, long long &st, uint32_t &len) { st = 0; len = 0; };
     auto no_quad = [](const uint4 &, uint32_t, uint32_t) {};
     if (rec.flags & REC_HASH_ALL) {  // hash every endpoint
-        table_geometry(W < above ? W : above, 32, WARP_CAP, tb.cap, tb.shift);
+        const bool small = MATCH && A.deg <= 32u && W <= 32u;
+        if (!small) table_geometry(W < above ? W : above, 32, WARP_CAP, tb.cap, tb.shift);
         const uint32_t mask = tb.cap - 1, shift = tb.shift;
         warp_rounds(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, sm.walk2, lane, none, no_quad,
-                    FullSeg{}, [&](uint32_t x, uint32_t sw) {
-                        hash_wedge32(sm.tab, shift, mask, x, sw, err, own, other);
+                    FullSeg{}, [&](uint32_t x, uint32_t sw, bool valid) {
+                        if (small) match_wedges(x, sw, valid, lane, own, other);
+                        else if (valid) hash_wedge32(sm.tab, shift, mask, x, sw, err, own, other);
                     });
     } else {
         tb.hub = true;
         const uint32_t wb = window_base(A.ns);
         const uint64_t wnh = A.wnh;
         const uint64_t above_nh = wb > A.r + 1 ? (uint64_t)wb - A.r - 1 : 0;
-        if (wnh > 0) table_geometry(wnh < above_nh ? wnh : above_nh, 32, WARP_CAP, tb.cap, tb.shift);
+        const bool small = MATCH && A.deg <= 32u && wnh <= 32u;
+        if (wnh > 0 && !small)
+            table_geometry(wnh < above_nh ? wnh : above_nh, 32, WARP_CAP, tb.cap, tb.shift);
         const uint32_t mask = tb.cap - 1, shift = tb.shift;
         char *win = reinterpret_cast<char *>(sm.win);
         // one hub-window wedge (vb = 1) or an entry of the quad outside the
@@ -901,8 +945,9 @@ __device__ __forceinline__ WarpTab warp_tally(const DevGraph &G, WarpSmem &sm,
                         hub_one(v.z, (vm >> 2) & 1u, sw);
                         hub_one(v.w, vm >> 3, sw);
                     },
-                    LowSeg{}, [&](uint32_t x, uint32_t sw) {
-                        hash_wedge32(sm.tab, shift, mask, x, sw, err, own, other);
+                    LowSeg{}, [&](uint32_t x, uint32_t sw, bool valid) {
+                        if (small) match_wedges(x, sw, valid, lane, own, other);
+                        else if (valid) hash_wedge32(sm.tab, shift, mask, x, sw, err, own, other);
                     });
     }
     return tb;
@@ -958,7 +1003,9 @@ struct HybTab {
 
 // The tally pass of one team/CTA-hash anchor, walked by the whole CTA; adds
 // each thread's part of the anchor's balanced and total counts to bal, tot.
-template <int TS, uint32_t HCAP>
+// CAS_FIRST: as in hash_add (the per-vertex kernels keep the read-first
+// insert, which compiles to fewer registers in their larger bodies).
+template <int TS, uint32_t HCAP, bool CAS_FIRST = true>
 __device__ __forceinline__ HybTab hybrid_tally(const DevGraph &G, HybSmem<TS, HCAP> &sm,
                                                const Anchor &A, unsigned long long &bal,
                                                unsigned long long &tot) {
@@ -998,7 +1045,8 @@ __device__ __forceinline__ HybTab hybrid_tally(const DevGraph &G, HybSmem<TS, HC
         const uint32_t mask = tb.cap - 1, shift = tb.shift;
         wedge_walk<TS, 2>(A.smd, A.oadj, A.rb, 0, A.deg, sm.walk, t, 4 * SUM_SPAN, LowSeg{},
                           [&](uint32_t x, uint32_t sw) {
-                              hash_wedge32(sm.tab, shift, mask, x, sw, err, own, other);
+                              hash_wedge32<CAS_FIRST>(sm.tab, shift, mask, x, sw, err, own,
+                                                      other);
                           },
                           flush);
     }
