@@ -214,7 +214,9 @@ BB_API bb_status bb_count_csr_device_noalloc(const bb_csr *csr_dev, const int8_t
  * team and warp wedge kernel, in launch order; wedges/middles/anchors are
  * the work each kernel was given (middle = one neighbour v of an anchor w,
  * whose wedge suffix the kernel walks). build_ms covers validation through
- * classification (0 for resident-graph counts). */
+ * classification (0 for resident-graph counts). product_ms is the time of
+ * the matrix-product path (bb_set_matrix_product) when it counted instead
+ * of the wedge kernels, whose entries are then 0; 0 otherwise. */
 #define BB_NKERNELS 4
 typedef struct {
     double build_ms;
@@ -223,6 +225,7 @@ typedef struct {
     int64_t wedges[BB_NKERNELS];
     int64_t middles[BB_NKERNELS];
     int64_t anchors[BB_NKERNELS];
+    double product_ms;
 } bb_timing;
 
 BB_API bb_status bb_ctx_set_timing(bb_ctx *ctx, int enable);
@@ -412,6 +415,32 @@ BB_API bb_status bb_probe_shared_atomics(int device, uint32_t window, double *at
 
 /* Kernel launches the library has issued in this process. */
 BB_API uint64_t bb_launch_count(void);
+
+/* ------------------------------------------------- matrix-product path
+ * Lemma 2 per pair of vertices on one side, with the pair's symmetric and
+ * asymmetric tallies (Defs. 5-6) taken over all middles at once: for the
+ * a x b signed adjacency X of the smaller side (rows) against the other
+ * (columns), X X^T holds S - A and |X| |X|^T holds S + A per pair, and the
+ * counts are the sums of C(S,2) + C(A,2) and C(S+A,2) over the pairs. The
+ * paper enumerates wedges instead; on a graph whose smaller side is small
+ * and dense the two products (tensor-core GEMMs in bf16 with fp32 sums,
+ * exact for these integer operands) take less time than the wedges.
+ * Counts through bb_count_csr, bb_count_csr_device, resident graphs and
+ * the serving engine take this path when the graph qualifies: the smaller
+ * side has 2..8192 vertices, the other fewer than 2^21, there are at least
+ * 65,536 edges and at least one edge per 16 vertex pairs across the sides
+ * (and the two bf16 matrices fit 512 MiB each); the graph's device
+ * workspace then includes the matrices (bb_graph_bytes). Per-vertex and
+ * per-edge counts, flips, batches, BB-Base and the allocation-free call
+ * always use the wedge path. Results are identical on both paths.
+ * bb_set_matrix_product: process-wide, 0 = take the path when the graph
+ * qualifies (default), 1 = always the wedge kernels; returns the previous
+ * mode (-1 for another value). A count whose step was captured for replay
+ * under the other mode is captured again.
+ * bb_matrix_product_plan: 1 if a graph of these sizes would be counted on
+ * this path under the current mode, 0 if not, -1 for a negative size. */
+BB_API int bb_set_matrix_product(int mode);
+BB_API int bb_matrix_product_plan(int64_t nU, int64_t nV, int64_t nE);
 
 #ifdef __cplusplus
 }

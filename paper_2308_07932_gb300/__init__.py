@@ -51,7 +51,8 @@ class _Timing(ctypes.Structure):
                 ("kernel_ms", ctypes.c_double * len(KERNELS)),
                 ("wedges", ctypes.c_int64 * len(KERNELS)),
                 ("middles", ctypes.c_int64 * len(KERNELS)),
-                ("anchors", ctypes.c_int64 * len(KERNELS))]
+                ("anchors", ctypes.c_int64 * len(KERNELS)),
+                ("product_ms", ctypes.c_double)]
 
 class ClassShape(ctypes.Structure):
     """Bucket shape of a graph's work classes (``bb_class_shape``)."""
@@ -175,6 +176,9 @@ def lib() -> ctypes.CDLL:
                                             ctypes.POINTER(ctypes.c_double)]),
             "bb_graph_bytes": (S, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                    ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+            "bb_set_matrix_product": (ctypes.c_int, [ctypes.c_int]),
+            "bb_matrix_product_plan": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64,
+                                                      ctypes.c_int64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -248,7 +252,7 @@ class Context:
         """Phase timings (ms) and per-kernel work of the last count."""
         t = _Timing()
         _check(lib().bb_ctx_last_timing(self._h, ctypes.byref(t)))
-        return {"build_ms": t.build_ms, "count_ms": t.count_ms,
+        return {"build_ms": t.build_ms, "count_ms": t.count_ms, "product_ms": t.product_ms,
                 "kernels": {k: {"ms": t.kernel_ms[i], "wedges": t.wedges[i],
                                 "middles": t.middles[i], "anchors": t.anchors[i]}
                             for i, k in enumerate(KERNELS)}}
@@ -561,3 +565,19 @@ def version() -> str:
 def launch_count() -> int:
     """Kernel launches the library has issued in this process."""
     return int(lib().bb_launch_count())
+
+
+def set_matrix_product(enabled: bool) -> bool:
+    """Whether counts of graphs with a small dense side may take the
+    matrix-product path (``bb_set_matrix_product``; process-wide, on by
+    default). Returns the previous setting."""
+    return lib().bb_set_matrix_product(0 if enabled else 1) == 0
+
+
+def matrix_product_plan(nU: int, nV: int, nE: int) -> bool:
+    """True if a graph of these sizes is counted on the matrix-product path
+    under the current setting."""
+    r = lib().bb_matrix_product_plan(nU, nV, nE)
+    if r < 0:
+        raise BBError(1, "negative size")
+    return r == 1

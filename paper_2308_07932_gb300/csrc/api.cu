@@ -251,6 +251,13 @@ bb_status finish_count(bb_ctx *ctx, const DevGraph &g, cudaStream_t s, int64_t *
             T.middles[k] = (int64_t)h->cls_stats[NCLS + order[k]];
             T.anchors[k] = (int64_t)h->cls_stats[2 * NCLS + order[k]];
         }
+        if (ctx->last_product) {  // ev[0] .. ev[1] spans the product path
+            T.product_ms = T.kernel_ms[0];
+            for (int k = 0; k < BB_NKERNELS; k++) {
+                T.kernel_ms[k] = 0;
+                T.wedges[k] = T.middles[k] = T.anchors[k] = 0;
+            }
+        }
         cudaGetLastError();
     }
     if (h->build_err) return map_build_error(h->build_err);
@@ -275,7 +282,8 @@ bool replay_step(bb_ctx *ctx, DevGraph &g, const bb_csr *csr, const int8_t *sign
     // the degree sort's key width depends on the inputs' largest degree
     const void *key[11] = {(const void *)(intptr_t)csr->nU, (const void *)(intptr_t)csr->nV,
                            (const void *)(intptr_t)csr->nE, csr->rowptr, csr->col, signs,
-                           ctx->ws_temp, ctx->ws_graph, (const void *)(intptr_t)ctx->timing,
+                           ctx->ws_temp, ctx->ws_graph,
+                           (const void *)(intptr_t)(ctx->timing | (product_enabled() ? 2 : 0)),
                            (const void *)(intptr_t)g.deg_bits,
                            (const void *)(intptr_t)ctx->shape_version};
     static_assert(sizeof(key) == sizeof(ctx->step_key), "step key size");
@@ -296,7 +304,7 @@ bool replay_step(bb_ctx *ctx, DevGraph &g, const bb_csr *csr, const int8_t *sign
         const uint64_t l0 = launches();
         build_rest(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s, &ctx->aux);
         if (ctx->timing) record_timing_event(ctx->ev[1], s);
-        launch_count(g, s, ctx->timing ? ctx->ev + 2 : nullptr);
+        ctx->step_product = launch_count(g, s, ctx->timing ? ctx->ev + 2 : nullptr);
         const uint64_t n = launches() - l0;
         retract_launches(n);  // captured, not run
         cudaGraph_t graph = nullptr;
@@ -321,6 +329,7 @@ bool replay_step(bb_ctx *ctx, DevGraph &g, const bb_csr *csr, const int8_t *sign
         cudaGetLastError();
         return false;
     }
+    ctx->last_product = ctx->step_product;
     note_launches(ctx->step_launches);
     return true;
 }
@@ -370,8 +379,12 @@ bb_status count_device(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int6
         BB_CUDA(cudaGetLastError(), "build kernels");
         if (ctx->timing) BB_CUDA(cudaEventRecord(ctx->ev[1], s), "event");
         cudaEvent_t *ev = ctx->timing ? ctx->ev + 2 : nullptr;
-        if (pv_dev) launch_per_vertex(g, pv_dev, s, ev);
-        else launch_count(g, s, ev);
+        if (pv_dev) {
+            launch_per_vertex(g, pv_dev, s, ev);
+            ctx->last_product = false;
+        } else {
+            ctx->last_product = launch_count(g, s, ev);
+        }
     }
     ctx->have_build_ev = ctx->timing;
     BB_CUDA(cudaGetLastError(), "count launch");
@@ -700,8 +713,12 @@ bb_status bb_count(bb_graph *G, int64_t *balanced, int64_t *total, int64_t *per_
         pv_dev = ctx->ws_pv;
     }
     cudaEvent_t *ev = ctx->timing ? ctx->ev + 2 : nullptr;
-    if (pv_dev) launch_per_vertex(G->g, pv_dev, ctx->stream, ev);
-    else launch_count(G->g, ctx->stream, ev);
+    if (pv_dev) {
+        launch_per_vertex(G->g, pv_dev, ctx->stream, ev);
+        ctx->last_product = false;
+    } else {
+        ctx->last_product = launch_count(G->g, ctx->stream, ev);
+    }
     BB_CUDA(cudaGetLastError(), "count launch");
     st = finish_count(ctx, G->g, ctx->stream, balanced, total, nullptr);
     if (st == BB_OK) {
@@ -733,6 +750,7 @@ bb_status bb_count_edges(bb_graph *G, int64_t *per_edge, int64_t *balanced_opt,
     unsigned long long *acc = (unsigned long long *)((char *)ctx->ws_pe + b_out);
     cudaStream_t s = ctx->stream;
     launch_per_edge(G->g, out_dev, acc, s, ctx->timing ? ctx->ev + 2 : nullptr);
+    ctx->last_product = false;
     BB_CUDA(cudaGetLastError(), "per-edge launch");
     int64_t b = 0, t = 0;
     st = finish_count(ctx, G->g, s, &b, &t, nullptr);
@@ -825,7 +843,7 @@ bb_status bb_count_flipped(bb_graph *G, const int64_t *edge_idx, int64_t n, int6
         }
     } else {
         int64_t b = 0, t = 0;
-        launch_count(G->g, s, ctx->timing ? ctx->ev + 2 : nullptr);
+        ctx->last_product = launch_count(G->g, s, ctx->timing ? ctx->ev + 2 : nullptr);
         BB_CUDA(cudaGetLastError(), "count launch");
         if ((st = finish_count(ctx, G->g, s, &b, &t, nullptr)) != BB_OK) return st;
         G->have_counts = true;

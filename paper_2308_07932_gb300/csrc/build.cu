@@ -866,7 +866,34 @@ size_t side_bytes(int64_t n, int64_t nE) {
 
 }  // namespace
 
-BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE) {
+ProductPlan product_plan(int64_t nU, int64_t nV, int64_t nE) {
+    ProductPlan p;
+    const int side = nV < nU ? 1 : 0;
+    const int64_t a = side ? nV : nU, b = side ? nU : nV;
+    if (a < 2 || a > (int64_t)PROD_A_MAX || b >= (int64_t)PROD_B_MAX || nE < PROD_MIN_EDGES ||
+        nE * PROD_DENSITY < a * b)
+        return p;
+    const uint64_t tiles = (uint64_t)((a + 127) / 128) * (uint64_t)((a + 127) / 128);
+    uint64_t split = 1;
+    while (split * 2 * tiles <= PROD_TARGET_TILES && (uint64_t)b >= split * 2 * PROD_MIN_SLICE)
+        split *= 2;
+    const uint64_t kc = (((uint64_t)b + split - 1) / split + 7) & ~7ull;
+    const uint64_t ld = split * kc;
+    if ((uint64_t)a * ld > PROD_MAX_CELLS) return p;
+    p.side = side;
+    p.a = (uint32_t)a;
+    p.b = (uint32_t)b;
+    p.split = (uint32_t)split;
+    p.kc = (uint32_t)kc;
+    p.ld = (uint32_t)ld;
+    p.x_bytes = align256(2 * (size_t)a * ld * 2);
+    p.c_bytes = align256(2 * split * (size_t)a * (size_t)a * 4);
+    p.ws_bytes = (size_t)32 << 20;
+    p.total = p.x_bytes + p.c_bytes + p.ws_bytes;
+    return p;
+}
+
+BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE, bool product) {
     int64_t n = nU + nV;
     int64_t nmax = std::max<int64_t>(std::max(nU, nV), 1);
     size_t g = side_bytes(nU, nE) + side_bytes(nV, nE);
@@ -887,10 +914,12 @@ BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE) {
     t += 2 * align256((size_t)nmax * 4 + 4) * 2;                             // classify meta/grp
     t += 2 * align256(NCLS * NB * 4) + align256(64 * 8);                     // buckets, bounds
     t += align256((size_t)(nU + 1) * 16) + align256((size_t)(nV + 1) * 16);  // row records
+    if (product) g += product_plan(nU, nV, nE).total;
     return {g, t};
 }
 
-void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_mem) {
+void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_mem,
+                  bool product) {
     Carver c{(char *)graph_mem};
     g.nU = nU; g.nV = nV; g.nE = nE;
     int64_t ns[2] = {nU, nV};
@@ -924,6 +953,17 @@ void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_m
     g.cls_stats = c.take<unsigned long long>(3 * NCLS);
     g.err = c.take<uint32_t>(1);
     g.scratch = c.take<CountScratch>(1);
+    g.prod = product ? product_plan(nU, nV, nE) : ProductPlan{};
+    if (g.prod.side >= 0) {
+        g.prod_x = (uint16_t *)c.p;
+        g.prod_c = (float *)(c.p + g.prod.x_bytes);
+        g.prod_ws = c.p + g.prod.x_bytes + g.prod.c_bytes;
+        c.p += g.prod.total;
+    } else {
+        g.prod_x = nullptr;
+        g.prod_c = nullptr;
+        g.prod_ws = nullptr;
+    }
 }
 
 namespace {

@@ -743,10 +743,15 @@ const LaunchCfg &init_cfg() {
 
 void count_init() { init_cfg(); }
 
-void launch_count(const DevGraph &g, cudaStream_t s, cudaEvent_t *ev) {
+bool launch_count(const DevGraph &g, cudaStream_t s, cudaEvent_t *ev) {
     const LaunchCfg &cfg = init_cfg();
     cudaMemsetAsync(g.scratch, 0, sizeof(CountScratch), s);
     if (ev) record_timing_event(ev[0], s);
+    if (g.prod.side >= 0 && product_enabled() && launch_product(g, s)) {
+        if (ev)
+            for (int k = 1; k <= 4; k++) record_timing_event(ev[k], s);
+        return true;
+    }
     if (g.dense_staged)
         k_dense<true><<<cfg.dense_blocks[1], DENSE_THREADS, DENSE_SMEM_STAGED, s>>>(g);
     else
@@ -761,6 +766,7 @@ void launch_count(const DevGraph &g, cudaStream_t s, cudaEvent_t *ev) {
     if (ev) record_timing_event(ev[3], s);
     k_warp<<<cfg.warp_blocks, WARP_THREADS, WARP_SMEM, s>>>(g); note_launch();
     if (ev) record_timing_event(ev[4], s);
+    return false;
 }
 
 int batch_max_blocks(int cls) { return init_cfg().batch_blocks[cls]; }

@@ -114,6 +114,53 @@ constexpr int JOB_PV_SPLIT = 4;
 constexpr int JOB_BASE = 5;
 constexpr int JOB_WIDE = 6;
 
+// ------------------------------------------------------ matrix-product path
+// On a graph with a small, dense side the tallies of every pair on that
+// side over all middles come from two dense products of its a x b signed
+// adjacency X (entries +1, -1, 0; rows the pair side P, columns the other
+// side): X X^T holds S - A and |X| |X|^T holds S + A for each pair (Defs.
+// 5-6), so the count is the sum over pairs of C(S,2) + C(A,2) and
+// C(S+A,2) (Lemma 2) without enumerating wedges. Each butterfly has exactly
+// one pair of P vertices, so no priority order is needed on this path.
+// The products run on the tensor cores in bf16 with fp32 sums: every
+// product is exactly -1, 0 or 1 and every partial sum an integer of
+// magnitude at most b < 2^21, so the sums are exact.
+//
+// product_plan picks the path from the sizes alone (the same answer for a
+// graph's workspace sizing, layout and launch): the smaller side as P, at
+// most PROD_A_MAX pair vertices, fewer than PROD_B_MAX middles, at least
+// PROD_MIN_EDGES edges, and an edge density of at least 1/PROD_DENSITY
+// (where the products' a^2 b work is below the wedges' b (nE/b)^2 / 2 at
+// the measured rates of both). side = -1: the wedge classes count.
+constexpr uint32_t PROD_A_MAX = 8192;
+constexpr uint32_t PROD_B_MAX = 1u << 21;
+constexpr int64_t PROD_MIN_EDGES = 1 << 16;
+constexpr int64_t PROD_DENSITY = 16;
+constexpr uint64_t PROD_MAX_CELLS = 1ull << 28;  // a * ld: 512 MiB per bf16 matrix
+// The middles are split into `split` equal slices of kc columns and each
+// product is a batch of one GEMM per slice (partial a x a sums, added by
+// the pair kernel in integers), so that a small pair side still gives the
+// GPU about PROD_TARGET_TILES output tiles of 128 x 128 to work on.
+constexpr uint32_t PROD_TARGET_TILES = 1024;
+constexpr uint32_t PROD_MIN_SLICE = 1024;
+struct ProductPlan {
+    int side = -1;          // pair side (0 = U, 1 = V), -1 = wedge classes
+    uint32_t a = 0, b = 0;  // pair-side and middle-side vertex counts
+    uint32_t split = 1;     // middle slices (GEMMs per product)
+    uint32_t kc = 0;        // columns per slice (a multiple of 8)
+    uint32_t ld = 0;        // row pitch of X in elements: split * kc >= b
+    size_t x_bytes = 0;     // X then |X| (bf16)
+    size_t c_bytes = 0;     // per product and slice an a x a fp32 partial
+    size_t ws_bytes = 0;    // GEMM workspace
+    size_t total = 0;       // device bytes of the three, 256-byte aligned
+};
+ProductPlan product_plan(int64_t nU, int64_t nV, int64_t nE);
+
+// Process-wide choice between the paths for graphs the plan admits (0 =
+// product when planned, 1 = always the wedge classes); see
+// bb_set_matrix_product.
+bool product_enabled();
+
 struct DevGraph {
     int64_t nU = 0, nV = 0, nE = 0;
     SideCSR side[2];
@@ -144,6 +191,11 @@ struct DevGraph {
     uint32_t h_maxdeg = 0;   // largest vertex degree (read back by build_validate)
     int deg_bits = 16;       // key bits of the degree sort (16, 24 or 32, from h_maxdeg)
     unsigned long long h_cls_stats[3 * NCLS] = {};  // resident graphs: copy of cls_stats
+    // matrix-product path (prod.side >= 0 when the layout reserved it)
+    ProductPlan prod;
+    uint16_t *prod_x = nullptr;  // [2][a][ld] bf16 bit patterns: X, |X|
+    float *prod_c = nullptr;     // [2][a][a]: X X^T, |X| |X|^T
+    void *prod_ws = nullptr;     // GEMM workspace (prod.ws_bytes)
 };
 
 // Bytes of device memory a graph of this size needs (graph + build temps).
@@ -151,10 +203,13 @@ struct BuildSizes {
     size_t graph_bytes;   // kept while the graph lives
     size_t temp_bytes;    // needed only during the build
 };
-BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE);
+// product = false: no matrix-product buffers (the graph always takes the
+// wedge classes); layout_graph must be given the same choice.
+BuildSizes build_sizes(int64_t nU, int64_t nV, int64_t nE, bool product = true);
 
 // Carve the graph's arrays out of `graph_mem` (graph_bytes long).
-void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_mem);
+void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_mem,
+                  bool product = true);
 
 // Two auxiliary streams and their events the build may fork work onto (both
 // are joined back to s before the build's later stages): the long-row radix
@@ -212,8 +267,15 @@ void classify_graph(DevGraph &g, void *ctemp, cudaStream_t s);
 // Count balanced/total butterflies of a built graph on stream s. Writes the
 // 128-bit sums to g.scratch->acc (device). When ev is not null, ev[0..4]
 // are recorded before the dense, CTA-hash, team and warp kernels and after
-// the last one.
-void launch_count(const DevGraph &g, cudaStream_t s, cudaEvent_t *ev = nullptr);
+// the last one. Returns true when the matrix-product path counted instead
+// (then ev[0] precedes it and ev[1..4] follow it).
+bool launch_count(const DevGraph &g, cudaStream_t s, cudaEvent_t *ev = nullptr);
+
+// The matrix-product path on stream s (g.prod.side >= 0): adds the sums to
+// g.scratch->acc. Returns false, with nothing counted, when the GEMM library
+// could not be set up or refused the call (the caller counts with the
+// wedge classes then).
+bool launch_product(const DevGraph &g, cudaStream_t s);
 
 // Many resident graphs counted in one launch per work class. Items of class
 // c of graph i are numbered prefix[c*(n+1)+i] .. prefix[c*(n+1)+i+1]-1 in

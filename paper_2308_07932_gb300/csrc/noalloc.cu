@@ -69,7 +69,7 @@ extern "C" bb_status bb_count_csr_device_noalloc(const bb_csr *csr_dev, const in
         return report_error(BB_ERR_INVALID_ARG, "rowptr, col or signs is NULL");
     if (nU + nV >= ((int64_t)1 << 31) || nE >= ((int64_t)1 << 32) - 1)
         return report_error(BB_ERR_TOO_LARGE, "graph beyond the id limits");
-    const BuildSizes bs = build_sizes(nU, nV, nE);
+    const BuildSizes bs = build_sizes(nU, nV, nE, false);  // always the wedge classes
     const size_t need = align256(bs.graph_bytes) + bs.temp_bytes;
     if (need > SCRATCH_BYTES)
         return err(BB_ERR_TOO_LARGE,
@@ -87,7 +87,7 @@ extern "C" bb_status bb_count_csr_device_noalloc(const bb_csr *csr_dev, const in
     count_init();
     cudaStream_t s = (cudaStream_t)stream;
     DevGraph g;
-    layout_graph(g, nU, nV, nE, base);
+    layout_graph(g, nU, nV, nE, base, false);
     void *temp = (char *)base + align256(bs.graph_bytes);
     // the split-merge counters must start at zero; the array keeps the last call's bytes
     cudaMemsetAsync(g.gpart, 0, (size_t)g.gpart_cap * 4, s);

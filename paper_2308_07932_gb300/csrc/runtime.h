@@ -64,6 +64,8 @@ struct bb_ctx {
     bool timing = false;
     cudaEvent_t ev[bb::NEV] = {};
     bool have_build_ev = false;
+    // the last count (and the captured step) took the matrix-product path
+    bool last_product = false, step_product = false;
     bb_timing last = {};
     bb::Engine *engine = nullptr;  // started by bb_ctx_serve or the first bb_submit
     // bucket shape of later builds (bb_ctx_set_shape) and its version (part

@@ -87,3 +87,32 @@ def test_wait_timeout_argument_checks(built):
     with pytest.raises(pkg.BBError):
         pkg.set_wait_timeout(-1.0)
     pkg.set_wait_timeout(600.0)
+
+
+def test_matrix_product_plan(built):
+    """The size rule of the matrix-product path (host only)."""
+    plan = pkg.matrix_product_plan
+    assert plan(500, 50_000, 10_000_000)          # vote-like: small dense side
+    assert plan(50_000, 500, 10_000_000)          # the same with the sides swapped
+    assert not plan(2_000_000, 500_000, 20_000_000)  # power-law: both sides large
+    assert not plan(2_000, 1_000, 20_000)         # too few edges
+    assert plan(2, 40_000, 65_536)                # K_{2,n}-like: dense
+    assert not plan(1, 100_000, 100_000)          # no pairs on the smaller side
+    assert not plan(8_193, 8_193, 20_000_000)     # pair side above 8192
+    assert not plan(100, (1 << 21), 50_000_000)   # middles at the exactness bound
+    assert not plan(200, 1_000_000, 12_000_000)   # density 1/16.7, below 1/16
+    assert plan(200, 1_000_000, 13_000_000)       # density 1/15.4
+    assert not plan(300, 1_000_000, 30_000_000)   # 3e8 matrix cells, above 2^28
+    with pytest.raises(pkg.BBError):
+        plan(-1, 2, 3)
+    prev = pkg.set_matrix_product(False)
+    try:
+        assert not plan(500, 50_000, 10_000_000)
+    finally:
+        pkg.set_matrix_product(prev)
+    assert plan(500, 50_000, 10_000_000)
+    # the product buffers are part of a qualifying graph's resident bytes
+    r_prod, _ = pkg.graph_bytes(500, 50_000, 2_000_000)
+    r_wedge, _ = pkg.graph_bytes(5_000, 50_000, 2_000_000)
+    assert r_prod > 500 * 50_000 * 4  # X and |X| in bf16
+    assert r_wedge < r_prod
