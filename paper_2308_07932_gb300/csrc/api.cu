@@ -278,7 +278,8 @@ bb_status finish_count(bb_ctx *ctx, const DevGraph &g, cudaStream_t s, int64_t *
 // launches directly and pays no capture). Returns false (nothing launched)
 // when the call is not a repeat or the stream cannot be captured; the
 // caller launches directly then.
-bool replay_step(bb_ctx *ctx, DevGraph &g, const bb_csr *csr, const int8_t *signs) {
+bool replay_step(bb_ctx *ctx, DevGraph &g, const bb_csr *csr, const int8_t *signs,
+                 bool product_only) {
     // the degree sort's key width depends on the inputs' largest degree
     const void *key[11] = {(const void *)(intptr_t)csr->nU, (const void *)(intptr_t)csr->nV,
                            (const void *)(intptr_t)csr->nE, csr->rowptr, csr->col, signs,
@@ -302,7 +303,7 @@ bool replay_step(bb_ctx *ctx, DevGraph &g, const bb_csr *csr, const int8_t *sign
             return false;
         }
         const uint64_t l0 = launches();
-        build_rest(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s, &ctx->aux);
+        build_rest(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s, &ctx->aux, product_only);
         if (ctx->timing) record_timing_event(ctx->ev[1], s);
         ctx->step_product = launch_count(g, s, ctx->timing ? ctx->ev + 2 : nullptr);
         const uint64_t n = launches() - l0;
@@ -374,8 +375,14 @@ bb_status count_device(bb_ctx *ctx, const bb_csr *csr, const int8_t *signs, int6
         return map_build_error(verr);
     }
     Range r_rest("build and count");
-    if (pv_dev || !replay_step(ctx, g, csr, signs)) {
-        build_rest(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s, &ctx->aux);
+    // a plain count of a graph the matrix-product path takes needs only the
+    // ranks and the wedge count from the build; that path reads the inputs
+    const bool product_only = !pv_dev && g.prod.side >= 0 && product_enabled() && product_ready();
+    g.rowptr = const_cast<int64_t *>(csr->rowptr);
+    g.col = const_cast<int32_t *>(csr->col);
+    g.sign = const_cast<int8_t *>(signs);
+    if (pv_dev || !replay_step(ctx, g, csr, signs, product_only)) {
+        build_rest(g, csr->rowptr, csr->col, signs, ctx->ws_temp, s, &ctx->aux, product_only);
         BB_CUDA(cudaGetLastError(), "build kernels");
         if (ctx->timing) BB_CUDA(cudaEventRecord(ctx->ev[1], s), "event");
         cudaEvent_t *ev = ctx->timing ? ctx->ev + 2 : nullptr;

@@ -873,23 +873,26 @@ ProductPlan product_plan(int64_t nU, int64_t nV, int64_t nE) {
     if (a < 2 || a > (int64_t)PROD_A_MAX || b >= (int64_t)PROD_B_MAX || nE < PROD_MIN_EDGES ||
         nE * PROD_DENSITY < a * b)
         return p;
-    const uint64_t tiles = (uint64_t)((a + 127) / 128) * (uint64_t)((a + 127) / 128);
+    const uint64_t ap = ((uint64_t)a + 15) & ~15ull;
+    const uint64_t tiles = ((ap + 127) / 128) * ((ap + 127) / 128);
     uint64_t split = 1;
     while (split * 2 * tiles <= PROD_TARGET_TILES && (uint64_t)b >= split * 2 * PROD_MIN_SLICE)
         split *= 2;
-    const uint64_t kc = (((uint64_t)b + split - 1) / split + 7) & ~7ull;
+    const uint64_t kc = (((uint64_t)b + split - 1) / split + 63) & ~63ull;
     const uint64_t ld = split * kc;
-    if ((uint64_t)a * ld > PROD_MAX_CELLS) return p;
+    if (ap * ld > PROD_MAX_CELLS) return p;
     p.side = side;
     p.a = (uint32_t)a;
     p.b = (uint32_t)b;
+    p.ap = (uint32_t)ap;
     p.split = (uint32_t)split;
     p.kc = (uint32_t)kc;
     p.ld = (uint32_t)ld;
-    p.x_bytes = align256(2 * (size_t)a * ld * 2);
-    p.c_bytes = align256(2 * split * (size_t)a * (size_t)a * 4);
+    p.x_bytes = align256(2 * (size_t)ap * ld * 2);
+    p.c_bytes = align256(2 * split * (size_t)ap * (size_t)ap * 4);
+    p.cnt_bytes = align256(((size_t)a + (size_t)b + 2 * (size_t)ap + 2 * (size_t)ld) * 4);
     p.ws_bytes = (size_t)32 << 20;
-    p.total = p.x_bytes + p.c_bytes + p.ws_bytes;
+    p.total = p.x_bytes + p.c_bytes + p.cnt_bytes + p.ws_bytes;
     return p;
 }
 
@@ -957,11 +960,13 @@ void layout_graph(DevGraph &g, int64_t nU, int64_t nV, int64_t nE, void *graph_m
     if (g.prod.side >= 0) {
         g.prod_x = (uint16_t *)c.p;
         g.prod_c = (float *)(c.p + g.prod.x_bytes);
-        g.prod_ws = c.p + g.prod.x_bytes + g.prod.c_bytes;
+        g.prod_cnt = (uint32_t *)(c.p + g.prod.x_bytes + g.prod.c_bytes);
+        g.prod_ws = c.p + g.prod.x_bytes + g.prod.c_bytes + g.prod.cnt_bytes;
         c.p += g.prod.total;
     } else {
         g.prod_x = nullptr;
         g.prod_c = nullptr;
+        g.prod_cnt = nullptr;
         g.prod_ws = nullptr;
     }
 }
@@ -1101,7 +1106,7 @@ bb_status build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col,
 }
 
 void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
-                void *temp_mem, cudaStream_t s, const BuildAux *aux) {
+                void *temp_mem, cudaStream_t s, const BuildAux *aux, bool product_only) {
     const int64_t nU = g.nU, nV = g.nV, nE = g.nE;
     BuildTemp bt = carve_temp(g, temp_mem);
     uint32_t **deg_in = bt.deg_in, *cursorV = bt.cursorV;
@@ -1144,6 +1149,8 @@ void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const in
     }
     if (nU > 0) k_global_rank<<<grid_for(nU, BT, 8192), BT, 0, s>>>(g.side[0], g.side[1].deg, nV, 1); note_launch();
     if (nV > 0) k_global_rank<<<grid_for(nV, BT, 8192), BT, 0, s>>>(g.side[1], g.side[0].deg, nU, 0); note_launch();
+    g.product_only = product_only;
+    if (product_only) return;  // the product path fills its matrices and counts the wedges
 
     // 3. row fill, row sorts, lo
     if (nU > 0 && nE > 0)

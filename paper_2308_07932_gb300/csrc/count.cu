@@ -747,10 +747,15 @@ bool launch_count(const DevGraph &g, cudaStream_t s, cudaEvent_t *ev) {
     const LaunchCfg &cfg = init_cfg();
     cudaMemsetAsync(g.scratch, 0, sizeof(CountScratch), s);
     if (ev) record_timing_event(ev[0], s);
-    if (g.prod.side >= 0 && product_enabled() && launch_product(g, s)) {
-        if (ev)
-            for (int k = 1; k <= 4; k++) record_timing_event(ev[k], s);
-        return true;
+    if (g.product_only || (g.prod.side >= 0 && product_enabled())) {
+        const bool ok = launch_product(g, s);
+        // a graph built for the product path alone has no classes to fall
+        // back on (a failed launch has marked its error word instead)
+        if (ok || g.product_only) {
+            if (ev)
+                for (int k = 1; k <= 4; k++) record_timing_event(ev[k], s);
+            return ok;
+        }
     }
     if (g.dense_staged)
         k_dense<true><<<cfg.dense_blocks[1], DENSE_THREADS, DENSE_SMEM_STAGED, s>>>(g);

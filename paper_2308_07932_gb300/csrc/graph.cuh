@@ -105,6 +105,7 @@ enum Ctr : uint32_t {
 // per-count scratch (zeroed before each count)
 struct CountScratch {
     unsigned long long acc[4];   // balanced lo/hi, total lo/hi (128-bit sums)
+    unsigned long long cells;    // matrix-product path: distinct nonzero cells of X
     uint32_t job_next[7];        // dynamic job cursors: one per class, the split parts'
                                  // second walks, the per-vertex baseline, the wide jobs
     uint32_t err;
@@ -146,13 +147,16 @@ constexpr uint32_t PROD_MIN_SLICE = 1024;
 struct ProductPlan {
     int side = -1;          // pair side (0 = U, 1 = V), -1 = wedge classes
     uint32_t a = 0, b = 0;  // pair-side and middle-side vertex counts
+    uint32_t ap = 0;        // rows of X: a rounded up to 16 (the rest zero)
     uint32_t split = 1;     // middle slices (GEMMs per product)
-    uint32_t kc = 0;        // columns per slice (a multiple of 8)
+    uint32_t kc = 0;        // columns per slice (a multiple of 64: 128-byte slices)
     uint32_t ld = 0;        // row pitch of X in elements: split * kc >= b
-    size_t x_bytes = 0;     // X then |X| (bf16)
-    size_t c_bytes = 0;     // per product and slice an a x a fp32 partial
+    size_t x_bytes = 0;     // X then |X| (bf16, ap x ld each)
+    size_t c_bytes = 0;     // per product and slice an ap x ap fp32 partial
+    size_t cnt_bytes = 0;   // wedge count: global ranks by id (a + b), and
+                            // per row and column its cells and cells ranked above
     size_t ws_bytes = 0;    // GEMM workspace
-    size_t total = 0;       // device bytes of the three, 256-byte aligned
+    size_t total = 0;       // device bytes of all, 256-byte aligned
 };
 ProductPlan product_plan(int64_t nU, int64_t nV, int64_t nE);
 
@@ -191,10 +195,14 @@ struct DevGraph {
     uint32_t h_maxdeg = 0;   // largest vertex degree (read back by build_validate)
     int deg_bits = 16;       // key bits of the degree sort (16, 24 or 32, from h_maxdeg)
     unsigned long long h_cls_stats[3 * NCLS] = {};  // resident graphs: copy of cls_stats
-    // matrix-product path (prod.side >= 0 when the layout reserved it)
+    // matrix-product path (prod.side >= 0 when the layout reserved it);
+    // product_only: built for that path alone (ranks and the wedge count;
+    // no rows, descriptors or classes), so only it may count the graph
     ProductPlan prod;
-    uint16_t *prod_x = nullptr;  // [2][a][ld] bf16 bit patterns: X, |X|
-    float *prod_c = nullptr;     // [2][a][a]: X X^T, |X| |X|^T
+    bool product_only = false;
+    uint16_t *prod_x = nullptr;  // [2][ap][ld] bf16 bit patterns: X, |X|
+    float *prod_c = nullptr;     // [2][split][ap][ap]: partials of X X^T, |X| |X|^T
+    uint32_t *prod_cnt = nullptr;  // [a + b] ranks, [2][ap] row and [2][ld] column counts
     void *prod_ws = nullptr;     // GEMM workspace (prod.ws_bytes)
 };
 
@@ -253,8 +261,11 @@ struct StagedInput {
 bb_status build_validate(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
                          void *temp_mem, cudaStream_t s, const StagedInput *in, uint32_t *verr,
                          uint32_t *pin_err = nullptr, uint32_t *pin_max = nullptr);
+// product_only: stop after the ranks (a graph that the matrix-product
+// path counts next, on the same inputs, and whose wedges that path counts;
+// sets g.product_only).
 void build_rest(DevGraph &g, const int64_t *rowptr, const int32_t *col, const int8_t *sign,
-                void *temp_mem, cudaStream_t s, const BuildAux *aux);
+                void *temp_mem, cudaStream_t s, const BuildAux *aux, bool product_only = false);
 
 // Re-runs the classification of a built graph with g.cls (the class lists,
 // dense jobs and split groups are rewritten; the rows, descriptors and
@@ -276,6 +287,10 @@ bool launch_count(const DevGraph &g, cudaStream_t s, cudaEvent_t *ev = nullptr);
 // could not be set up or refused the call (the caller counts with the
 // wedge classes then).
 bool launch_product(const DevGraph &g, cudaStream_t s);
+
+// Sets up the GEMM library on the current device (once); false if it
+// cannot be used (then no graph is built for the product path alone).
+bool product_ready();
 
 // Many resident graphs counted in one launch per work class. Items of class
 // c of graph i are numbered prefix[c*(n+1)+i] .. prefix[c*(n+1)+i+1]-1 in

@@ -164,3 +164,18 @@ def test_allocation_free_call_keeps_the_wedge_kernels():
                                                ctypes.byref(w))
     assert st == 0
     assert (b.value, t.value) == want
+
+
+def test_duplicate_edge_is_reported_on_the_product_path(ctx):
+    g = synth.vote(61, 48, 5_000, 0.4, 2, 0.55, 0.8)
+    u, v, s = g.edges()
+    for k in (0, len(u) // 2, len(u) - 1):  # first, middle and last edge listed twice
+        d = synth.from_edges(g.nU, g.nV, np.append(u, u[k]), np.append(v, v[k]),
+                             np.append(s, -s[k]), "dup")
+        assert pkg.matrix_product_plan(d.nU, d.nV, d.nE)
+        with pytest.raises(pkg.BBError) as ei:
+            ctx.count(d)
+        assert ei.value.name == "BB_ERR_INVALID_ARG"
+        assert "twice" in str(ei.value)
+    c = ctx.count(g)  # the context is usable afterwards
+    assert (c.balanced, c.total) == oracle.count(g, threads=4)
