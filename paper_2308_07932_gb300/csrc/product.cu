@@ -49,44 +49,56 @@ constexpr uint16_t BF16_PLUS_ONE = 0x3F80u;
 constexpr uint16_t BF16_MINUS_ONE = 0xBF80u;
 constexpr uint32_t BF16_ABS_MASK2 = 0x7FFF7FFFu;  // clears the sign bits of two bf16
 constexpr int PROD_THREADS = 256;
-// columns of a row staged in shared memory at a time (64 KiB of bf16); rows
-// needing more than FILL_MAX_WINDOWS windows are scattered instead
+// Row fill through shared memory: the matrix rows are cut into windows of
+// at most FILL_WIN columns (64 KiB of bf16), one CTA per (row, window), as
+// many windows per row as keep the GPU busy; a row whose entries would be
+// scanned more than FILL_MAX_WINDOWS times is scattered instead.
 constexpr uint32_t FILL_WIN = 32768;
-constexpr uint32_t FILL_MAX_WINDOWS = 4;
+constexpr uint32_t FILL_MAX_WINDOWS = 8;
 constexpr size_t FILL_SMEM = FILL_WIN * sizeof(uint16_t);
 
-// One CTA per matrix row r < ap (grid-stride; rows past nU are zero): the
-// row's entries of each FILL_WIN-column window are written into a zeroed
-// shared copy, which then goes out in 16-byte stores to X and, with the
-// sign bits cleared, to |X|. Pair side U: row r of X is input row r.
+// CTA (blockIdx.x, blockIdx.y) = (window, row r < ap; rows past nU are
+// zero): the row's entries inside the window's width columns go into a
+// zeroed shared copy, which then goes out in 16-byte stores to X and, with
+// the sign bits cleared, to |X|. Pair side U: row r of X is input row r.
 __global__ void __launch_bounds__(PROD_THREADS) k_prod_fill_rows(
     const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-    const int8_t *__restrict__ sign, int64_t nU, uint32_t ap, uint32_t ld, size_t plane,
+    const int8_t *__restrict__ sign, int64_t nU, uint32_t ld, uint32_t width, size_t plane,
     uint16_t *x) {
     extern __shared__ uint4 win4[];
     uint16_t *win = reinterpret_cast<uint16_t *>(win4);
-    for (int64_t r = blockIdx.x; r < (int64_t)ap; r += gridDim.x) {
-        const int64_t b = r < nU ? rowptr[r] : 0, e = r < nU ? rowptr[r + 1] : 0;
-        for (uint32_t c0 = 0; c0 < ld; c0 += FILL_WIN) {
-            const uint32_t w = ld - c0 < FILL_WIN ? ld - c0 : FILL_WIN;  // a multiple of 64
-            for (uint32_t i = threadIdx.x; i < w / 8; i += PROD_THREADS)
-                win4[i] = make_uint4(0u, 0u, 0u, 0u);
-            __syncthreads();
-            for (int64_t p = b + threadIdx.x; p < e; p += PROD_THREADS) {
-                const uint32_t c = (uint32_t)col[p] - c0;  // wraps for columns before c0
-                if (c < w) win[c] = sign[p] < 0 ? BF16_MINUS_ONE : BF16_PLUS_ONE;
-            }
-            __syncthreads();
-            uint4 *xr = reinterpret_cast<uint4 *>(x + (size_t)r * ld + c0);
-            uint4 *ar = reinterpret_cast<uint4 *>(x + plane + (size_t)r * ld + c0);
-            for (uint32_t i = threadIdx.x; i < w / 8; i += PROD_THREADS) {
-                const uint4 q = win4[i];
-                xr[i] = q;
-                ar[i] = make_uint4(q.x & BF16_ABS_MASK2, q.y & BF16_ABS_MASK2,
-                                   q.z & BF16_ABS_MASK2, q.w & BF16_ABS_MASK2);
-            }
-            __syncthreads();  // the window is rewritten next
+    const int64_t r = blockIdx.y;
+    const uint32_t c0 = blockIdx.x * width;
+    if (c0 >= ld) return;  // (uniform over the CTA)
+    const uint32_t w = ld - c0 < width ? ld - c0 : width;  // a multiple of 64
+    for (uint32_t i = threadIdx.x; i < w / 8; i += PROD_THREADS) win4[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    const int64_t b = r < nU ? rowptr[r] : 0, e = r < nU ? rowptr[r + 1] : 0;
+    int64_t p = b + threadIdx.x;
+    for (; p + 3 * PROD_THREADS < e; p += 4 * PROD_THREADS) {  // four entries in flight
+        uint32_t c[4];
+        int8_t sg[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            c[k] = (uint32_t)col[p + k * PROD_THREADS] - c0;  // wraps for columns before c0
+            sg[k] = sign[p + k * PROD_THREADS];
         }
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (c[k] < w) win[c[k]] = sg[k] < 0 ? BF16_MINUS_ONE : BF16_PLUS_ONE;
+    }
+    for (; p < e; p += PROD_THREADS) {
+        const uint32_t c = (uint32_t)col[p] - c0;
+        if (c < w) win[c] = sign[p] < 0 ? BF16_MINUS_ONE : BF16_PLUS_ONE;
+    }
+    __syncthreads();
+    uint4 *xr = reinterpret_cast<uint4 *>(x + (size_t)r * ld + c0);
+    uint4 *ar = reinterpret_cast<uint4 *>(x + plane + (size_t)r * ld + c0);
+    for (uint32_t i = threadIdx.x; i < w / 8; i += PROD_THREADS) {
+        const uint4 q = win4[i];
+        xr[i] = q;
+        ar[i] = make_uint4(q.x & BF16_ABS_MASK2, q.y & BF16_ABS_MASK2, q.z & BF16_ABS_MASK2,
+                           q.w & BF16_ABS_MASK2);
     }
 }
 
@@ -268,10 +280,15 @@ bool launch_product(const DevGraph &g, cudaStream_t s) {
     ProdHandle &H = *Hp;
     const size_t plane = (size_t)p.ap * p.ld;
     const int ctas = H.sms * 8;
-    // 1. X and |X|
-    if (p.side == 0 && p.ld <= FILL_WIN * FILL_MAX_WINDOWS) {
-        k_prod_fill_rows<<<std::min<int>((int)p.ap, ctas), PROD_THREADS, FILL_SMEM, s>>>(
-            g.rowptr, g.col, g.sign, g.nU, p.ap, p.ld, plane, g.prod_x);
+    // 1. X and |X|: windows per row for about six CTAs per SM (at least
+    // enough to stay within FILL_WIN columns), 64-column aligned
+    uint32_t nwin = (p.ld + FILL_WIN - 1) / FILL_WIN;
+    nwin = std::max<uint32_t>(nwin, (6u * H.sms + p.ap - 1) / p.ap);
+    uint32_t width = ((p.ld + nwin - 1) / nwin + 63) & ~63u;
+    nwin = (p.ld + width - 1) / width;
+    if (p.side == 0 && nwin <= FILL_MAX_WINDOWS) {
+        k_prod_fill_rows<<<dim3(nwin, p.ap), PROD_THREADS, (size_t)width * sizeof(uint16_t), s>>>(
+            g.rowptr, g.col, g.sign, g.nU, p.ld, width, plane, g.prod_x);
         note_launch();
     } else {
         cudaMemsetAsync(g.prod_x, 0, 2 * plane * sizeof(uint16_t), s);
