@@ -151,7 +151,9 @@ BB_API bb_status bb_count_edges(bb_graph *g, int64_t *per_edge, int64_t *balance
  * wedges, only those are walked: a butterfly with an odd number of flipped
  * edges changes balance, the others do not (incremental re-count; the paper
  * has no counterpart beyond its edge-level extension). Otherwise the graph
- * is recounted. *incremental_opt tells which was done. Blocking. */
+ * is recounted, and always when its counts take the matrix-product path
+ * (bb_set_matrix_product: such a recount costs less than any walk on a
+ * graph that dense). *incremental_opt tells which was done. Blocking. */
 BB_API bb_status bb_count_flipped(bb_graph *g, const int64_t *edge_idx, int64_t n,
                                   int64_t *balanced, int64_t *total, int *incremental_opt);
 

@@ -820,9 +820,12 @@ bb_status bb_count_flipped(bb_graph *G, const int64_t *edge_idx, int64_t n, int6
         BB_CUDA(cudaMemcpyAsync(d_list, flips_host, (size_t)m * 8, cudaMemcpyHostToDevice, s),
                 "copy flip list");
     // Enumeration steps (a binary search each, at random places) cost about
-    // 16 to 20 times a wedge of the full count on the 2M x 500k graph.
+    // 16 to 20 times a wedge of the full count on the 2M x 500k graph. A
+    // graph the matrix-product path counts is recounted (on the 500 x 50k
+    // vote graph 10 flipped edges took 23 ms to walk, a recount 0.16 ms).
+    const bool by_product = G->g.prod.side >= 0 && product_enabled();
     bool incremental = false;
-    if (G->have_counts && m > 0 && small) {
+    if (G->have_counts && m > 0 && small && !by_product) {
         launch_flip_estimate(G->g, d_list, m, ws, d_acc, s);
         BB_CUDA(cudaGetLastError(), "flip estimate");
         BB_CUDA(cudaMemcpyAsync(ctx->h_res->acc, d_acc, 8, cudaMemcpyDeviceToHost, s), "copy estimate");

@@ -179,3 +179,24 @@ def test_duplicate_edge_is_reported_on_the_product_path(ctx):
         assert "twice" in str(ei.value)
     c = ctx.count(g)  # the context is usable afterwards
     assert (c.balanced, c.total) == oracle.count(g, threads=4)
+
+
+def test_flips_on_a_product_graph_recount_exactly(ctx):
+    # a resident graph counted by the products: flips recount (no walk) and
+    # the counts follow the oracle on the flipped graph
+    g = synth.vote(71, 64, 6_000, 0.4, 2, 0.55, 0.8)
+    G = ctx.upload(g)
+    try:
+        c = G.count()
+        assert (c.balanced, c.total) == oracle.count(g, threads=4) and counted_by_product(ctx)
+        sign = g.sign.copy()
+        rng = np.random.default_rng(72)
+        for k in (10, 1000):
+            idx = rng.choice(g.nE, size=k, replace=False)
+            b, t, inc = G.count_flipped(idx)
+            sign[idx] = -sign[idx]
+            fl = synth.SignedBipartite(g.nU, g.nV, g.rowptr, g.col, sign, g.name + "/f")
+            assert (b, t) == oracle.count(fl, threads=4)
+            assert not inc
+    finally:
+        G.free()
