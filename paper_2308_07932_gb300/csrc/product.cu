@@ -8,12 +8,15 @@
 // With X the signed adjacency (X[w][v] = sign(w,v), 0 for no edge),
 // (X X^T)[w][u] = S - A and (|X| |X|^T)[w][u] = S + A. On the caller's
 // stream:
-//   fill          X and |X| (bf16, rows = P's vertex ids, columns = O's
-//                 ids; the sums do not depend on the order of rows or
-//                 columns) from the input rows: k_prod_fill_rows stages each
-//                 row in shared memory and writes it whole (P = U), and
-//                 k_prod_fill scatters the entries after a clear (P = V, or
-//                 rows too long to stage);
+//   fill          X and |X| (bf16; the sums do not depend on the order of
+//                 rows or columns). A fully built graph fills from its
+//                 sign-packed rows of P (rows and columns in side-rank
+//                 order; these rows carry later sign flips); a graph built
+//                 for this path alone fills from the input rows (ids).
+//                 k_prod_fill_rows stages a window of a row in shared
+//                 memory and writes it whole; k_prod_fill scatters the
+//                 entries after a clear (input rows with P = V, or rows too
+//                 long to stage);
 //   wedge count   (a graph built for this path alone) the priority wedges
 //                 the library reports, from one pass over |X|: for a vertex
 //                 of degree d with k neighbours ranked above it (Def. 4)
@@ -57,14 +60,33 @@ constexpr uint32_t FILL_WIN = 32768;
 constexpr uint32_t FILL_MAX_WINDOWS = 8;
 constexpr size_t FILL_SMEM = FILL_WIN * sizeof(uint16_t);
 
-// CTA (blockIdx.x, blockIdx.y) = (window, row r < ap; rows past nU are
+// The rows a fill reads: the input rows (rowptr, col, sign; pair side U)
+// or a side's built rows (off, adj: entry = column << 1 | negative).
+struct FillRows {
+    const int64_t *rowptr;
+    const int32_t *col;
+    const int8_t *sign;
+    const uint32_t *adj;  // non-null: built rows (rowptr = the side's offsets)
+    int64_t n;            // rows
+    __device__ __forceinline__ void entry(int64_t p, uint32_t &c, bool &neg) const {
+        if (adj) {
+            const uint32_t x = adj[p];
+            c = x >> 1;
+            neg = x & 1u;
+        } else {
+            c = (uint32_t)col[p];
+            neg = sign[p] < 0;
+        }
+    }
+};
+
+// CTA (blockIdx.x, blockIdx.y) = (window, row r < ap; rows past n are
 // zero): the row's entries inside the window's width columns go into a
 // zeroed shared copy, which then goes out in 16-byte stores to X and, with
-// the sign bits cleared, to |X|. Pair side U: row r of X is input row r.
-__global__ void __launch_bounds__(PROD_THREADS) k_prod_fill_rows(
-    const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-    const int8_t *__restrict__ sign, int64_t nU, uint32_t ld, uint32_t width, size_t plane,
-    uint16_t *x) {
+// the sign bits cleared, to |X|.
+__global__ void __launch_bounds__(PROD_THREADS) k_prod_fill_rows(FillRows R, uint32_t ld,
+                                                                  uint32_t width, size_t plane,
+                                                                  uint16_t *x) {
     extern __shared__ uint4 win4[];
     uint16_t *win = reinterpret_cast<uint16_t *>(win4);
     const int64_t r = blockIdx.y;
@@ -73,23 +95,26 @@ __global__ void __launch_bounds__(PROD_THREADS) k_prod_fill_rows(
     const uint32_t w = ld - c0 < width ? ld - c0 : width;  // a multiple of 64
     for (uint32_t i = threadIdx.x; i < w / 8; i += PROD_THREADS) win4[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
-    const int64_t b = r < nU ? rowptr[r] : 0, e = r < nU ? rowptr[r + 1] : 0;
+    const int64_t b = r < R.n ? R.rowptr[r] : 0, e = r < R.n ? R.rowptr[r + 1] : 0;
     int64_t p = b + threadIdx.x;
     for (; p + 3 * PROD_THREADS < e; p += 4 * PROD_THREADS) {  // four entries in flight
         uint32_t c[4];
-        int8_t sg[4];
+        bool neg[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            c[k] = (uint32_t)col[p + k * PROD_THREADS] - c0;  // wraps for columns before c0
-            sg[k] = sign[p + k * PROD_THREADS];
+            R.entry(p + k * PROD_THREADS, c[k], neg[k]);
+            c[k] -= c0;  // wraps for columns before c0
         }
 #pragma unroll
         for (int k = 0; k < 4; k++)
-            if (c[k] < w) win[c[k]] = sg[k] < 0 ? BF16_MINUS_ONE : BF16_PLUS_ONE;
+            if (c[k] < w) win[c[k]] = neg[k] ? BF16_MINUS_ONE : BF16_PLUS_ONE;
     }
     for (; p < e; p += PROD_THREADS) {
-        const uint32_t c = (uint32_t)col[p] - c0;
-        if (c < w) win[c] = sign[p] < 0 ? BF16_MINUS_ONE : BF16_PLUS_ONE;
+        uint32_t c;
+        bool neg;
+        R.entry(p, c, neg);
+        c -= c0;
+        if (c < w) win[c] = neg ? BF16_MINUS_ONE : BF16_PLUS_ONE;
     }
     __syncthreads();
     uint4 *xr = reinterpret_cast<uint4 *>(x + (size_t)r * ld + c0);
@@ -102,19 +127,20 @@ __global__ void __launch_bounds__(PROD_THREADS) k_prod_fill_rows(
     }
 }
 
-// one CTA per input row u (grid-stride) into a cleared X and |X|: X[u][v]
-// (pair side U) or X[v][u] (pair side V) for each edge u - v
-__global__ void __launch_bounds__(PROD_THREADS) k_prod_fill(const int64_t *__restrict__ rowptr,
-                                                             const int32_t *__restrict__ col,
-                                                             const int8_t *__restrict__ sign,
-                                                             int64_t nU, int side, uint32_t ld,
-                                                             size_t plane, uint16_t *x) {
-    for (int64_t u = blockIdx.x; u < nU; u += gridDim.x) {
-        const int64_t b = rowptr[u], e = rowptr[u + 1];
+// one CTA per row u of R (grid-stride) into a cleared X and |X|: X[u][c]
+// for each entry (u, c), or X[c][u] when `transpose` (input rows, pair
+// side V)
+__global__ void __launch_bounds__(PROD_THREADS) k_prod_fill(FillRows R, bool transpose,
+                                                             uint32_t ld, size_t plane,
+                                                             uint16_t *x) {
+    for (int64_t u = blockIdx.x; u < R.n; u += gridDim.x) {
+        const int64_t b = R.rowptr[u], e = R.rowptr[u + 1];
         for (int64_t p = b + threadIdx.x; p < e; p += PROD_THREADS) {
-            const size_t v = (size_t)(uint32_t)col[p];
-            const size_t cell = side == 0 ? (size_t)u * ld + v : v * ld + (size_t)u;
-            x[cell] = sign[p] < 0 ? BF16_MINUS_ONE : BF16_PLUS_ONE;
+            uint32_t c;
+            bool neg;
+            R.entry(p, c, neg);
+            const size_t cell = transpose ? (size_t)c * ld + (size_t)u : (size_t)u * ld + c;
+            x[cell] = neg ? BF16_MINUS_ONE : BF16_PLUS_ONE;
             x[plane + cell] = BF16_PLUS_ONE;
         }
     }
@@ -269,7 +295,7 @@ bool product_ready() { return prod_handle() != nullptr; }
 
 bool launch_product(const DevGraph &g, cudaStream_t s) {
     const ProductPlan &p = g.prod;
-    ProdHandle *Hp = p.side >= 0 && g.prod_x && g.rowptr ? prod_handle() : nullptr;
+    ProdHandle *Hp = p.side >= 0 && g.prod_x && (g.rowptr || !g.product_only) ? prod_handle() : nullptr;
     if (!Hp) {
         if (g.product_only) {  // nothing else can count it
             k_prod_error<<<1, 1, 0, s>>>(g.err, E_INTERNAL);
@@ -280,21 +306,31 @@ bool launch_product(const DevGraph &g, cudaStream_t s) {
     ProdHandle &H = *Hp;
     const size_t plane = (size_t)p.ap * p.ld;
     const int ctas = H.sms * 8;
-    // 1. X and |X|: windows per row for about six CTAs per SM (at least
-    // enough to stay within FILL_WIN columns), 64-column aligned
+    // 1. X and |X| from the built rows of P (they carry sign flips), or
+    // from the input rows when the build stopped at the ranks; windows per
+    // row for about six CTAs per SM (at least enough to stay within
+    // FILL_WIN columns), 64-column aligned
+    FillRows R;
+    if (g.product_only) {
+        R = FillRows{g.rowptr, g.col, g.sign, nullptr, g.nU};
+    } else {
+        const SideCSR &P = g.side[p.side];
+        R = FillRows{P.off, nullptr, nullptr, P.adj, P.n};
+    }
+    const bool transpose = g.product_only && p.side == 1;
     uint32_t nwin = (p.ld + FILL_WIN - 1) / FILL_WIN;
     nwin = std::max<uint32_t>(nwin, (6u * H.sms + p.ap - 1) / p.ap);
     uint32_t width = ((p.ld + nwin - 1) / nwin + 63) & ~63u;
     nwin = (p.ld + width - 1) / width;
-    if (p.side == 0 && nwin <= FILL_MAX_WINDOWS) {
+    if (!transpose && nwin <= FILL_MAX_WINDOWS) {
         k_prod_fill_rows<<<dim3(nwin, p.ap), PROD_THREADS, (size_t)width * sizeof(uint16_t), s>>>(
-            g.rowptr, g.col, g.sign, g.nU, p.ld, width, plane, g.prod_x);
+            R, p.ld, width, plane, g.prod_x);
         note_launch();
     } else {
         cudaMemsetAsync(g.prod_x, 0, 2 * plane * sizeof(uint16_t), s);
-        if (g.nU > 0 && g.nE > 0) {
-            k_prod_fill<<<(int)std::min<int64_t>(g.nU, ctas), PROD_THREADS, 0, s>>>(
-                g.rowptr, g.col, g.sign, g.nU, p.side, p.ld, plane, g.prod_x);
+        if (R.n > 0 && g.nE > 0) {
+            k_prod_fill<<<(int)std::min<int64_t>(R.n, ctas), PROD_THREADS, 0, s>>>(
+                R, transpose, p.ld, plane, g.prod_x);
             note_launch();
         }
     }
