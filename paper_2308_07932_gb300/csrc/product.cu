@@ -154,8 +154,10 @@ __global__ void k_prod_gid(SideCSR P, SideCSR O, uint32_t a, uint32_t b, uint32_
 
 // Per row p and column o of |X|: its cells (the degree) and the cells whose
 // other vertex is ranked above it. A thread takes 8 consecutive columns of
-// the rows [blockIdx.y * rows, ...): row figures are reduced per warp,
-// column figures per thread, then added to the counters.
+// the rows [blockIdx.y * rows, ...) (rows <= DEG_ROWS): row figures are
+// reduced per warp, then across the block's warps in shared memory, column
+// figures per thread; each is then added to its counter once per block.
+constexpr uint32_t DEG_ROWS = 128;
 __global__ void __launch_bounds__(PROD_THREADS) k_prod_degrees(
     const uint16_t *__restrict__ ax, uint32_t a, uint32_t b, uint32_t ld, uint32_t rows,
     const uint32_t *__restrict__ gid, uint32_t *row_d, uint32_t *row_k, uint32_t *col_d,
@@ -170,27 +172,51 @@ __global__ void __launch_bounds__(PROD_THREADS) k_prod_degrees(
         gcol[j] = live && c < b ? go[c] : 0u;
         dc[j] = kc[j] = 0u;
     }
+    __shared__ uint32_t s_d[DEG_ROWS][PROD_THREADS / 32], s_k[DEG_ROWS][PROD_THREADS / 32];
+    const uint32_t warp = threadIdx.x >> 5;
     const uint32_t p0 = blockIdx.y * rows, p1 = p0 + rows < a ? p0 + rows : a;
-    for (uint32_t p = p0; p < p1; p++) {
-        const uint32_t gp = gid[p];
-        uint4 q = make_uint4(0u, 0u, 0u, 0u);
-        if (live) q = reinterpret_cast<const uint4 *>(ax + (size_t)p * ld)[c8];
-        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-        uint32_t dr = 0, kr = 0;
+    constexpr uint32_t RU = 4;  // rows whose loads are in flight together
+    for (uint32_t pb = p0; pb < p1; pb += RU) {
+        uint4 q[RU];
+        uint32_t gp[RU];
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            const uint32_t nz = ((w[j >> 1] >> ((j & 1) * 16)) & 0x7FFFu) != 0u;
-            dc[j] += nz;
-            kc[j] += nz & (gp > gcol[j]);
-            dr += nz;
-            kr += nz & (gcol[j] > gp);
+        for (uint32_t i = 0; i < RU; i++) {
+            const uint32_t p = pb + i;
+            q[i] = make_uint4(0u, 0u, 0u, 0u);
+            gp[i] = p < p1 ? gid[p] : 0u;
+            if (live && p < p1) q[i] = reinterpret_cast<const uint4 *>(ax + (size_t)p * ld)[c8];
         }
-        dr = warp_sum_u32(dr);
-        kr = warp_sum_u32(kr);
-        if (lane_id() == 0 && dr) {
-            atomicAdd(&row_d[p], dr);
-            if (kr) atomicAdd(&row_k[p], kr);
+#pragma unroll
+        for (uint32_t i = 0; i < RU; i++) {
+            if (pb + i >= p1) break;  // (uniform over the block)
+            const uint32_t w[4] = {q[i].x, q[i].y, q[i].z, q[i].w};
+            uint32_t dr = 0, kr = 0;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const uint32_t nz = ((w[j >> 1] >> ((j & 1) * 16)) & 0x7FFFu) != 0u;
+                dc[j] += nz;
+                kc[j] += nz & (gp[i] > gcol[j]);
+                dr += nz;
+                kr += nz & (gcol[j] > gp[i]);
+            }
+            dr = warp_sum_u32(dr);
+            kr = warp_sum_u32(kr);
+            if (lane_id() == 0) {
+                s_d[pb + i - p0][warp] = dr;
+                s_k[pb + i - p0][warp] = kr;
+            }
         }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < p1 - p0; i += PROD_THREADS) {
+        uint32_t d = 0, k = 0;
+#pragma unroll
+        for (int w = 0; w < PROD_THREADS / 32; w++) {
+            d += s_d[i][w];
+            k += s_k[i][w];
+        }
+        if (d) atomicAdd(&row_d[p0 + i], d);
+        if (k) atomicAdd(&row_k[p0 + i], k);
     }
     if (live)
 #pragma unroll
@@ -344,8 +370,9 @@ bool launch_product(const DevGraph &g, cudaStream_t s) {
                      PROD_THREADS, 0, s>>>(P, O, p.a, p.b, gid);
         note_launch();
         const uint32_t gx = (p.ld / 8 + PROD_THREADS - 1) / PROD_THREADS;
-        const uint32_t gy = std::max<uint32_t>(1, std::min<uint32_t>(p.a, (4u * H.sms + gx - 1) / gx));
-        const uint32_t rows = (p.a + gy - 1) / gy;
+        uint32_t gy = std::max<uint32_t>(1, std::min<uint32_t>(p.a, (4u * H.sms + gx - 1) / gx));
+        gy = std::max<uint32_t>(gy, (p.a + DEG_ROWS - 1) / DEG_ROWS);
+        const uint32_t rows = (p.a + gy - 1) / gy;  // <= DEG_ROWS
         k_prod_degrees<<<dim3(gx, (p.a + rows - 1) / rows), PROD_THREADS, 0, s>>>(
             g.prod_x + plane, p.a, p.b, p.ld, rows, gid, row_d, row_k, col_d, col_k);
         note_launch();
